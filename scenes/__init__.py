@@ -1,0 +1,313 @@
+"""Seeded synthetic bundle-adjustment scenes.
+
+This module only makes input data: camera poses, 3-D points, which camera sees
+which point, and noisy image observations.  It holds none of the solver's
+arithmetic (no residual Jacobians, no normal equations, no Schur complement, no
+PCG); both the FP64 oracle and the CUDA library consume what it returns.
+
+Conventions shared with every consumer (the problem statement, Sec. 3.1):
+
+* a camera is 6 numbers ``[omega(3), t(3)]``: an angle-axis rotation ``omega``
+  and a translation ``t`` with ``X_cam = R(omega) X + t``;
+* a pinhole with focal length ``f`` (px) and principal point ``(cx, cy)`` (px),
+  +z in front of the camera, no distortion;
+* observations are ``(cam, point, u, v)`` in pixels.
+
+The observations are synthesised from ground truth with rotation matrices built
+by a look-at construction and converted to angle-axis with scipy, then Gaussian
+pixel noise is added; the initial values handed to the solver are perturbed
+ground truth.  Scene shapes follow the paper's workloads (aerial grids, tracks
+of a few cameras per point, N(0, sigma^2) px noise, Sec. 7.1).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+from scipy.spatial import cKDTree
+from scipy.spatial.transform import Rotation
+
+F_PX = 1000.0
+C_PX = 500.0
+IMG_PX = 1000.0
+
+
+@dataclasses.dataclass
+class Scene:
+    """A synthetic scene.  Arrays are host numpy arrays.
+
+    cams_gt, cams0: (n, 6) float64  [omega, t], ground truth and initial value
+    pts_gt, pts0:   (P, 3) float64
+    obs_cam: (m,) int32, obs_pt: (m,) int64, obs_uv: (m, 2) float64 (noisy px)
+    """
+    name: str
+    cams_gt: np.ndarray
+    pts_gt: np.ndarray
+    cams0: np.ndarray
+    pts0: np.ndarray
+    obs_cam: np.ndarray
+    obs_pt: np.ndarray
+    obs_uv: np.ndarray
+    f: float = F_PX
+    cx: float = C_PX
+    cy: float = C_PX
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_cams(self) -> int:
+        return self.cams_gt.shape[0]
+
+    @property
+    def n_pts(self) -> int:
+        return self.pts_gt.shape[0]
+
+    @property
+    def n_obs(self) -> int:
+        return self.obs_cam.shape[0]
+
+
+# --------------------------------------------------------------------------
+# geometry helpers for synthesis only (look-at frames, ground-truth pixels)
+# --------------------------------------------------------------------------
+
+def _look_at(centers: np.ndarray, targets: np.ndarray, up: np.ndarray) -> np.ndarray:
+    """World->camera rotation matrices whose third row looks from center to target."""
+    fwd = targets - centers
+    fwd /= np.linalg.norm(fwd, axis=1, keepdims=True)
+    down = -up[None, :] + (fwd @ up)[:, None] * fwd
+    down /= np.linalg.norm(down, axis=1, keepdims=True)
+    right = np.cross(down, fwd)
+    return np.stack([right, down, fwd], axis=1)  # rows: x, y, z axes
+
+
+def _nadir(centers: np.ndarray, yaw: np.ndarray) -> np.ndarray:
+    c, s = np.cos(yaw), np.sin(yaw)
+    z = np.zeros_like(c)
+    r1 = np.stack([c, s, z], axis=1)
+    r2 = np.stack([s, -c, z], axis=1)
+    r3 = np.tile(np.array([0.0, 0.0, -1.0]), (len(c), 1))
+    return np.stack([r1, r2, r3], axis=1)
+
+
+def _pack_cams(Rw2c: np.ndarray, centers: np.ndarray) -> np.ndarray:
+    omega = Rotation.from_matrix(Rw2c).as_rotvec()
+    t = -np.einsum("nij,nj->ni", Rw2c, centers)
+    return np.concatenate([omega, t], axis=1)
+
+
+def _pixels(Rw2c, centers, cam_idx, X, f, cx, cy):
+    """Ground-truth pixel positions of points X seen by cameras cam_idx."""
+    Xc = np.einsum("mij,mj->mi", Rw2c[cam_idx], X - centers[cam_idx])
+    return np.stack([f * Xc[:, 0] / Xc[:, 2] + cx, f * Xc[:, 1] / Xc[:, 2] + cy], 1), Xc[:, 2]
+
+
+def _finish(name, Rw2c, centers, pts, obs_cam, obs_pt, rng, sigma_px, rot_sd, t_sd, pt_sd,
+            outlier_frac=0.0, meta=None):
+    uv, _ = _pixels(Rw2c, centers, obs_cam, pts[obs_pt], F_PX, C_PX, C_PX)
+    if sigma_px > 0:
+        uv = uv + rng.normal(0.0, sigma_px, uv.shape)
+    meta = dict(meta or {})
+    if outlier_frac > 0:
+        k = int(round(outlier_frac * len(obs_cam)))
+        idx = rng.choice(len(obs_cam), size=k, replace=False)
+        uv[idx] = rng.uniform(0.0, IMG_PX, (k, 2))
+        meta["n_outliers"] = k
+    cams_gt = _pack_cams(Rw2c, centers)
+    cams0 = cams_gt.copy()
+    cams0[:, :3] += rng.normal(0.0, rot_sd, (len(cams0), 3))
+    cams0[:, 3:] += rng.normal(0.0, t_sd, (len(cams0), 3))
+    pts0 = pts + rng.normal(0.0, pt_sd, pts.shape)
+    meta.setdefault("sigma_px", sigma_px)
+    meta["mean_track"] = len(obs_cam) / len(pts)
+    return Scene(name, cams_gt, pts.copy(), cams0, pts0, obs_cam.astype(np.int32),
+                 obs_pt.astype(np.int64), uv, meta=meta)
+
+
+def _choose_visible(rng, vis_lists, lo, hi):
+    cams, ptid = [], []
+    for k, vis in enumerate(vis_lists):
+        L = int(rng.integers(lo, hi + 1))
+        L = min(L, len(vis))
+        pick = np.sort(rng.choice(vis, size=L, replace=False))
+        cams.append(pick)
+        ptid.append(np.full(L, k))
+    return np.concatenate(cams), np.concatenate(ptid)
+
+
+# --------------------------------------------------------------------------
+# ring scene (the tiny FP64 workload and its scaled-down variants)
+# --------------------------------------------------------------------------
+
+def ring_scene(n_cams=50, n_pts=2000, track=(3, 8), seed=1001, sigma_px=0.5,
+               rot_sd=0.01, t_sd=0.05, pt_sd=0.1, radius=30.0, half=5.0,
+               name="ring") -> Scene:
+    """Cameras on a horizontal ring looking at the centre of a cube of points.
+
+    n_cams cameras evenly spaced on a circle of ``radius`` m at mid-height,
+    n_pts points uniform in [-half, half]^3, each seen by L ~ U{track} cameras
+    chosen uniformly among those that image it inside the frame with z > 0.
+    """
+    rng = np.random.default_rng(seed)
+    phi = 2 * np.pi * np.arange(n_cams) / n_cams
+    centers = np.stack([radius * np.cos(phi), radius * np.sin(phi), np.zeros(n_cams)], 1)
+    Rw2c = _look_at(centers, np.zeros_like(centers), np.array([0.0, 0.0, 1.0]))
+    pts = rng.uniform(-half, half, (n_pts, 3))
+    # visibility: inside the image with positive depth
+    vis = []
+    for k in range(n_pts):
+        uv, z = _pixels(Rw2c, centers, np.arange(n_cams), np.repeat(pts[k:k + 1], n_cams, 0),
+                        F_PX, C_PX, C_PX)
+        ok = (z > 0) & (uv[:, 0] >= 0) & (uv[:, 0] < IMG_PX) & (uv[:, 1] >= 0) & (uv[:, 1] < IMG_PX)
+        vis.append(np.nonzero(ok)[0])
+    lo, hi = track
+    lo = min(lo, n_cams)
+    hi = min(hi, n_cams)
+    obs_cam, obs_pt = _choose_visible(rng, vis, lo, hi)
+    return _finish(name, Rw2c, centers, pts, obs_cam, obs_pt, rng, sigma_px, rot_sd, t_sd, pt_sd,
+                   meta={"seed": seed, "layout": "ring"})
+
+
+def tiny_scene(n_cams=5, n_pts=30, seed=7, sigma_px=0.5, track=(2, 4), **kw) -> Scene:
+    """A few cameras and points, small enough for dense brute force."""
+    return ring_scene(n_cams=n_cams, n_pts=n_pts, track=track, seed=seed, sigma_px=sigma_px,
+                      radius=30.0, name="tiny", **kw)
+
+
+# --------------------------------------------------------------------------
+# aerial grids (the FP32 workloads)
+# --------------------------------------------------------------------------
+
+def _terrain(x, y):
+    return 10.0 * np.sin(2 * np.pi * x / 500.0) * np.sin(2 * np.pi * y / 500.0)
+
+
+def _geom_track(rng, size, mean, lo, hi):
+    """L = lo + G with G geometric on {0,1,...} of mean (mean - lo); redrawn above hi."""
+    p = 1.0 / (mean - lo + 1.0)
+    L = lo + rng.geometric(p, size) - 1
+    bad = L > hi
+    while bad.any():
+        L[bad] = lo + rng.geometric(p, bad.sum()) - 1
+        bad = L > hi
+    return L
+
+
+def _nearest_tracks(rng, cam_xy, pts_xy, L, chunk=1 << 20):
+    """For each point, the L[k] camera centres nearest in xy (sorted by camera id)."""
+    tree = cKDTree(cam_xy)
+    kmax = int(L.max())
+    cams, ptid = [], []
+    for s in range(0, len(pts_xy), chunk):
+        e = min(s + chunk, len(pts_xy))
+        _, nn = tree.query(pts_xy[s:e], k=kmax)
+        nn = nn.reshape(e - s, kmax)
+        Lc = L[s:e]
+        mask = np.arange(kmax)[None, :] < Lc[:, None]
+        nn_sorted = np.where(mask, nn, np.iinfo(np.int64).max)
+        nn_sorted.sort(axis=1)
+        cams.append(nn_sorted[np.arange(kmax)[None, :] < Lc[:, None]])
+        ptid.append(np.repeat(np.arange(s, e), Lc))
+    return np.concatenate(cams), np.concatenate(ptid)
+
+
+def aerial_scene(n_along=100, n_across=50, n_pts=1_000_000, along_m=40.0, across_m=70.0,
+                 height=100.0, track_mean=5.0, track_max=20, seed=2001, sigma_px=1.0,
+                 rot_sd=0.01, t_sd=0.05, pt_sd=0.1, yaw_sd=0.02, outlier_frac=0.0,
+                 origin=(0.0, 0.0), name="aerial") -> Scene:
+    """Nadir cameras on an n_along x n_across flight grid over sinusoidal terrain.
+
+    Default: 50 x 100 = 5,000 cameras at 100 m (100 m footprint at f = 1000 px),
+    40 m along track (60% forward overlap), 70 m across (30% side overlap),
+    1M points uniform in xy, track length L = 2 + Geometric (mean 5, max 20),
+    the L cameras being the nearest camera centres in xy (image bounds are not
+    enforced: tracks of 20 do not fit a 60/30 overlap).
+    """
+    rng = np.random.default_rng(seed)
+    ix, iy = np.meshgrid(np.arange(n_along), np.arange(n_across), indexing="ij")
+    cx = origin[0] + ix.ravel() * along_m
+    cy = origin[1] + iy.ravel() * across_m
+    centers = np.stack([cx, cy, np.full(cx.shape, height)], 1)
+    yaw = rng.normal(0.0, yaw_sd, len(cx))
+    Rw2c = _nadir(centers, yaw)
+    x = rng.uniform(cx.min(), cx.max(), n_pts)
+    y = rng.uniform(cy.min(), cy.max(), n_pts)
+    pts = np.stack([x, y, _terrain(x, y)], 1)
+    L = _geom_track(rng, n_pts, track_mean, 2, track_max)
+    obs_cam, obs_pt = _nearest_tracks(rng, centers[:, :2], pts[:, :2], L)
+    return _finish(name, Rw2c, centers, pts, obs_cam, obs_pt, rng, sigma_px, rot_sd, t_sd, pt_sd,
+                   outlier_frac=outlier_frac,
+                   meta={"seed": seed, "layout": f"aerial {n_along}x{n_across}",
+                         "track_mean_target": track_mean, "track_max": track_max})
+
+
+def blocks_scene(n_blocks_x=5, n_blocks_y=4, block_side=50, n_pts=10_000_000, overlap=0.2,
+                 track_mean=6.0, track_max=40, seed=3001, sigma_px=1.0, outlier_frac=0.01,
+                 along_m=40.0, across_m=70.0, height=100.0, name="blocks") -> Scene:
+    """Several overlapping aerial blocks (20 blocks of 50 x 50 cameras by default).
+
+    Block origins sit on an n_blocks_x x n_blocks_y layout so that neighbouring
+    blocks overlap by ``overlap`` of their extent; points are spread uniformly
+    over the union, tracks are L = 2 + Geometric (mean 6, max 40) nearest
+    cameras, 1% of observations are replaced by uniform draws in the image.
+    """
+    rng = np.random.default_rng(seed)
+    ext_x = (block_side - 1) * along_m
+    ext_y = (block_side - 1) * across_m
+    step_x = ext_x * (1 - overlap)
+    step_y = ext_y * (1 - overlap)
+    ix, iy = np.meshgrid(np.arange(block_side), np.arange(block_side), indexing="ij")
+    cs = []
+    for bx in range(n_blocks_x):
+        for by in range(n_blocks_y):
+            cs.append(np.stack([bx * step_x + ix.ravel() * along_m,
+                                by * step_y + iy.ravel() * across_m], 1))
+    cxy = np.concatenate(cs)
+    centers = np.concatenate([cxy, np.full((len(cxy), 1), height)], 1)
+    yaw = rng.normal(0.0, 0.02, len(cxy))
+    Rw2c = _nadir(centers, yaw)
+    x = rng.uniform(cxy[:, 0].min(), cxy[:, 0].max(), n_pts)
+    y = rng.uniform(cxy[:, 1].min(), cxy[:, 1].max(), n_pts)
+    pts = np.stack([x, y, _terrain(x, y)], 1)
+    L = _geom_track(rng, n_pts, track_mean, 2, track_max)
+    obs_cam, obs_pt = _nearest_tracks(rng, centers[:, :2], pts[:, :2], L)
+    return _finish(name, Rw2c, centers, pts, obs_cam, obs_pt, rng, sigma_px, 0.01, 0.05, 0.1,
+                   outlier_frac=outlier_frac,
+                   meta={"seed": seed, "layout": f"{n_blocks_x*n_blocks_y} blocks of "
+                                                 f"{block_side}x{block_side}",
+                         "track_mean_target": track_mean, "track_max": track_max})
+
+
+def aerial_small(n_along=20, n_across=10, pts_per_cam=200, seed=2101, **kw) -> Scene:
+    """The aerial layout scaled down (same density of points per camera)."""
+    return aerial_scene(n_along=n_along, n_across=n_across, n_pts=pts_per_cam * n_along * n_across,
+                        seed=seed, name="aerial_small", **kw)
+
+
+def preconditioner_scene(seed: int, n_cams=None, pts_per_cam=200) -> Scene:
+    """A training / held-out instance for the learned preconditioner.
+
+    Aerial-shaped, n ~ U[2000, 8000] cameras on a grid of aspect 1:2 and 200
+    points per camera; seeds 0-199 train, 200-219 are held out.
+    """
+    rng = np.random.default_rng(10_000 + seed)
+    if n_cams is None:
+        n_cams = int(rng.integers(2000, 8001))
+    n_across = max(2, int(round(np.sqrt(n_cams / 2))))
+    n_along = max(2, int(round(n_cams / n_across)))
+    return aerial_scene(n_along=n_along, n_across=n_across, n_pts=pts_per_cam * n_along * n_across,
+                        seed=40_000 + seed, name=f"precond{seed}")
+
+
+CONFIGS = {
+    "ring50": lambda: ring_scene(seed=1001),
+    "aerial5k": lambda: aerial_scene(seed=2001),
+    "blocks50k": lambda: blocks_scene(seed=3001),
+}
+
+
+def shuffled(scene: Scene, seed: int = 0) -> Scene:
+    """The same scene with its observation list in random order."""
+    rng = np.random.default_rng(seed)
+    p = rng.permutation(scene.n_obs)
+    return dataclasses.replace(scene, obs_cam=scene.obs_cam[p], obs_pt=scene.obs_pt[p],
+                               obs_uv=scene.obs_uv[p])
