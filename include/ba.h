@@ -1,0 +1,186 @@
+/*
+ * ba.h - C ABI of libba, exact Levenberg-Marquardt bundle adjustment on one
+ * GB300 GPU (sm_103a), after arXiv 2307.08383 ("Distributed bundle adjustment
+ * with block-based sparse matrix compression for super large scale datasets").
+ *
+ * The library owns every device buffer of a problem.  Inputs are host arrays
+ * owned by the caller and copied at creation; getters write into caller
+ * buffers.  No exception crosses this boundary: every call returns a
+ * ba_status, and ba_last_error() gives a message for the calling thread.
+ * After BA_ERR_CUDA or BA_ERR_INTERNAL a problem is unusable and every later
+ * call on it returns BA_ERR_STATE.  Calls on one problem are not thread-safe;
+ * separate problems may run concurrently on different streams.
+ *
+ * Problem statement (Sec. 3.1): cameras c = [omega(3), t(3)] with
+ * X_cam = R(omega) X + t, a pinhole u = fx x/z + cx, v = fy y/z + cy, and the
+ * reprojection errors e = pi(X_cam) - u_obs.  One LM iteration solves Eq. 1,
+ * (J^T J + lambda D^T D) dx = -J^T e, by the Schur complement: the reduced
+ * camera system (RCS) of Eq. 4 is formed point by point (Sec. 5), stored as
+ * BSMC (Sec. 4), solved by block-Jacobi PCG (Sec. 3.2, Eqs. 6-7), and the
+ * points are back-substituted by Eq. 5.
+ */
+#ifndef BA_H
+#define BA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_problem ba_problem; /* opaque; owns all device memory */
+
+typedef enum {
+    BA_OK = 0,
+    BA_ERR_INVALID_ARG = 1,   /* bad pointer, size, index, duplicate or option */
+    BA_ERR_OOM = 2,           /* device allocation failed or device_mem_cap hit */
+    BA_ERR_CUDA = 3,          /* a CUDA runtime call failed; problem unusable */
+    BA_ERR_NONFINITE = 4,     /* NaN/Inf in an input or in a computed cost */
+    BA_ERR_NOT_SPD = 5,       /* a V_k or an RCS diagonal block is not positive definite */
+    BA_ERR_NO_CONVERGENCE = 6,/* PCG hit its iteration cap; the partial solution is kept */
+    BA_ERR_TIMEOUT = 7,       /* reserved: a bounded device wait gave up */
+    BA_ERR_STATE = 8,         /* call out of order, or problem unusable */
+    BA_ERR_INTERNAL = 9       /* a device-side consistency check failed */
+} ba_status;
+
+enum { BA_FP64 = 0, BA_FP32 = 1 };            /* ba_options.precision */
+enum { BA_LOSS_PLAIN = 0, BA_LOSS_HUBER = 1 }; /* ba_options.robust */
+enum { BA_PC_BLOCK_JACOBI = 0, BA_PC_LEARNED = 1 };
+
+typedef struct {
+    int32_t precision;       /* BA_FP64: everything in FP64.  BA_FP32: Jacobians,
+                                RCS assembly, SpMV and PCG in FP32; cost and
+                                gain-ratio sums and the outer refinement
+                                residual r = b - S x in FP64. */
+    double fx, fy, cx, cy;   /* pinhole intrinsics in px (1000, 1000, 500, 500) */
+    int32_t robust;          /* BA_LOSS_PLAIN or BA_LOSS_HUBER */
+    double huber_delta;      /* Huber threshold in px (2.0) */
+    double lambda0;          /* initial LM damping (1e-4) */
+    double pcg_rel_tol;      /* stop when ||b - S x|| / ||b|| <= tol (1e-10) */
+    int32_t pcg_max_iters;   /* 0: max(1000, 6n) */
+    double inner_rel_tol;    /* FP32 mode: tolerance of each inner FP32 PCG (1e-4) */
+    int32_t refine_max;      /* FP32 mode: outer refinement steps (20) */
+    int32_t preconditioner;  /* BA_PC_BLOCK_JACOBI (only this value is accepted) */
+    void *cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream */
+    size_t device_mem_cap;   /* 0 = none; creation fails with BA_ERR_OOM above it */
+    int32_t group_max_obs;   /* observations per point group (0 = default) */
+    int32_t profile;         /* nonzero: time every kernel launch with CUDA events */
+} ba_options;
+
+typedef struct {
+    double cost_before;      /* F(x) = 1/2 sum rho(||e||^2) before the step (FP64 sum) */
+    double cost_after;       /* F after the step (== cost_before when rejected) */
+    double cost_trial;       /* F(x (+) dx) of the trial point */
+    double predicted;        /* 1/2(||e||^2 - ||e + J dx||^2), FP64 sum */
+    double rho;              /* gain ratio (cost_before - cost_trial) / predicted */
+    double lambda;           /* damping used by this step */
+    int32_t accepted;
+    int32_t pcg_iters;       /* PCG iterations, summed over refinement steps */
+    int32_t refine_steps;    /* outer FP64 refinement steps (FP32 mode) */
+    int32_t used_fallback;   /* reserved for a learned preconditioner */
+    double rcs_rel_resid;    /* true ||b - S dx_c|| / ||b|| in FP64 */
+    int64_t n_cheirality;    /* observations with z_cam <= 1e-6 at the trial point */
+    int64_t n_v_fp64;        /* points whose 3x3 V was factored in FP64 (FP32 mode) */
+    float ms[8];             /* linearize, form_rcs, solve, back_subst, eval, total, -, - */
+} ba_step_info;
+
+typedef struct {
+    int32_t n_cams;
+    int64_t n_pts, n_obs;
+    int64_t nnzb;            /* BSMC blocks (upper triangle incl. n diagonal blocks) */
+    int64_t n_groups;        /* point groups (one CTA each in RCS formation) */
+    int64_t n_partials;      /* sub-RCS blocks written by the groups */
+    int64_t n_pairs;         /* (obs, obs) products: sum_k L_k (L_k + 1) / 2 */
+    int64_t device_bytes;    /* device memory held by the problem */
+    int32_t precision;
+} ba_stats;
+
+/* Fills *o with the defaults listed above. */
+void ba_options_default(ba_options *o);
+
+/* Creates a problem.  cams: n_cams x 6 doubles [omega, t]; pts: n_pts x 3;
+ * obs_cam[i] in [0, n_cams), obs_pt[i] in [0, n_pts), obs_uv: n_obs x 2 px.
+ * Observation order is free.  Rejected with BA_ERR_INVALID_ARG: an index out
+ * of range, a duplicated (camera, point) pair, a point with fewer than two
+ * observations, a camera with none.  BA_ERR_NONFINITE: a NaN/Inf input.
+ * Sets up the symbolic BSMC pattern (Sec. 4), the point groups (Sec. 6.1) and
+ * the local-to-global block index (Table 1, second operation). */
+ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double *cams,
+                            int64_t n_pts, const double *pts, int64_t n_obs,
+                            const int32_t *obs_cam, const int64_t *obs_pt,
+                            const double *obs_uv, ba_problem **out);
+
+/* Residuals and Jacobians at the current state (Eq. 1's e and J, weighted by
+ * sqrt(rho') under the Huber loss), stored on the device.  *cost_out (may be
+ * NULL) receives F(x). */
+ba_status ba_linearize(ba_problem *p, double *cost_out);
+
+/* Forms the damped RCS of Eq. 4, S = U - W V^-1 W^T and b = l_c - W V^-1 l_p,
+ * with U, V, W, l_c, l_p of Eq. 3 and D^T D = clamp(diag(J^T J), 1e-6, 1e32),
+ * point group by point group (Sec. 5, Sec. 6.1), into BSMC; also the
+ * block-Jacobi preconditioner (inverses of the diagonal blocks, Sec. 3.2).
+ * Needs ba_linearize first. */
+ba_status ba_form_rcs(ba_problem *p, double lambda);
+
+/* Solves S dx_c = b by block-Jacobi PCG (Sec. 3.2, Eqs. 6-7) with y0 = 0 and
+ * the stop rule ||r_k|| / ||r_0|| <= pcg_rel_tol; in FP32 mode by FP32 inner
+ * PCG with FP64 iterative refinement.  info may be NULL. */
+ba_status ba_solve_rcs(ba_problem *p, ba_step_info *info);
+
+/* Eq. 5: dx_p = V^-1 (l_p - W^T dx_c) for every point. */
+ba_status ba_back_substitute(ba_problem *p);
+
+/* One LM iteration (Fig. 2): linearize (if the state changed), form the RCS,
+ * solve, back-substitute, evaluate the trial point and accept or reject by
+ * the gain ratio; lambda follows Nielsen's rule.  info may be NULL. */
+ba_status ba_lm_step(ba_problem *p, ba_step_info *info);
+
+/* Current state in the caller's order: n_cams x 6 and n_pts x 3 doubles. */
+ba_status ba_get_cameras(const ba_problem *p, double *out_cams);
+ba_status ba_get_points(const ba_problem *p, double *out_pts);
+
+/* The last formed RCS in BSMC form: row_ptr[n+1], col[nnzb], val[nnzb x 36]
+ * (row-major 6x6 blocks, upcast to double; the first block of every row is
+ * the full diagonal block), b[n x 6].  Any array may be NULL; *nnzb always
+ * receives the block count. */
+ba_status ba_get_rcs(const ba_problem *p, int64_t *nnzb, int32_t *row_ptr, int32_t *col,
+                     double *val, double *b);
+
+/* The last step: dxc[n x 6], dxp[n_pts x 3] (caller's point order). */
+ba_status ba_get_step(const ba_problem *p, double *dxc, double *dxp);
+
+/* The stored linearization in the caller's observation order:
+ * e[n_obs x 2], Jc[n_obs x 12] (row-major 2x6), Jp[n_obs x 6] (2x3). */
+ba_status ba_get_linearization(const ba_problem *p, double *e, double *Jc, double *Jp);
+
+/* Replaces the state (caller's order) and the LM damping state. */
+ba_status ba_set_state(ba_problem *p, const double *cams, const double *pts, double lambda,
+                       double nu);
+ba_status ba_get_lm_state(const ba_problem *p, double *lambda, double *nu, double *cost);
+
+ba_status ba_get_stats(const ba_problem *p, ba_stats *out);
+
+/* Kernel timing (options.profile != 0): for kernel id k (see ba_kernel_name)
+ * the number of launches and their summed device time since the last reset. */
+ba_status ba_get_kernel_time(ba_problem *p, int32_t k, int64_t *launches, double *total_ms);
+ba_status ba_reset_kernel_times(ba_problem *p);
+const char *ba_kernel_name(int32_t k); /* NULL past the last id */
+
+void ba_problem_destroy(ba_problem *p);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ba_last_error(void);
+
+/* Host-only (no GPU needed): the structural BSMC pattern of an observation
+ * set - every diagonal block plus each (i < j) whose cameras share a point,
+ * rows in order, columns ascending (Sec. 4, Fig. 4).  row_ptr receives n+1
+ * entries; col (may be NULL for a size query) nnzb entries. */
+ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs,
+                              const int32_t *obs_cam, const int64_t *obs_pt, int32_t *row_ptr,
+                              int32_t *col, int64_t *nnzb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BA_H */

@@ -22,7 +22,8 @@ Readings of what the paper leaves open (each one is listed in the design doc):
 
 * camera model: pinhole, +z forward, focal f, principal point (cx, cy), no
   distortion; cameras are [omega(3), t(3)] with X_cam = R(omega) X + t;
-* update: R <- Exp(d_omega) R (left-multiplicative), t <- t + dt, X <- X + dX;
+* update: the pose is perturbed in the camera frame, X_cam <- Exp(d_omega) X_cam + dt,
+  i.e. R <- Exp(d_omega) R, t <- Exp(d_omega) t + dt; points X <- X + dX;
 * damping: D^T D = diag(J^T J) with every entry clamped to [1e-6, 1e32];
 * PCG: M = the diagonal blocks of S; stop when ||r_k|| / ||r_0|| <= T (the
   printed ratio is inverted, which would never stop);
@@ -104,11 +105,11 @@ def residuals(cams, pts, obs_cam, obs_pt, obs_uv, intr: Intrinsics):
 def jacobians(cams, pts, obs_cam, obs_pt, obs_uv, intr: Intrinsics):
     """Residuals and analytic Jacobians per observation.
 
-    J_c = de/d[d_omega, t] (m, 2, 6), J_p = de/dX (m, 2, 3), using
-    dX_cam/d(d_omega) = -[R X]x (left update), dX_cam/dt = I, dX_cam/dX = R,
-    and dpi/dX_cam = [[f/z, 0, -f x/z^2], [0, f/z, -f y/z^2]].
+    J_c = de/d[d_omega, dt] (m, 2, 6), J_p = de/dX (m, 2, 3), using
+    dX_cam/d(d_omega) = -[X_cam]x, dX_cam/d(dt) = I (camera-frame update),
+    dX_cam/dX = R, and dpi/dX_cam = [[f/z, 0, -f x/z^2], [0, f/z, -f y/z^2]].
     """
-    Xc, RX, R = camera_points(cams, pts, obs_cam, obs_pt)
+    Xc, _, R = camera_points(cams, pts, obs_cam, obs_pt)
     x, y, z = Xc[:, 0], Xc[:, 1], Xc[:, 2]
     e = np.stack([intr.f * x / z + intr.cx, intr.f * y / z + intr.cy], 1) - obs_uv
     m = len(x)
@@ -117,7 +118,7 @@ def jacobians(cams, pts, obs_cam, obs_pt, obs_uv, intr: Intrinsics):
     A[:, 0, 2] = -intr.f * x / z ** 2
     A[:, 1, 1] = intr.f / z
     A[:, 1, 2] = -intr.f * y / z ** 2
-    Jc = np.concatenate([A @ (-hat(RX)), A], axis=2)
+    Jc = np.concatenate([A @ (-hat(Xc)), A], axis=2)
     Jp = A @ R
     return e, Jc, Jp
 
@@ -368,10 +369,12 @@ def pcg(A: BSMC, b: np.ndarray, Minv: np.ndarray, tol: float, max_iters: int | N
 # ----------------------------------------------------------------------------
 
 def apply_update(cams, pts, dxc, dxp):
-    """R <- Exp(d_omega) R, t <- t + dt, X <- X + dX."""
+    """R <- Exp(d_omega) R, t <- Exp(d_omega) t + dt, X <- X + dX."""
     dxc = dxc.reshape(-1, 6)
-    R = rodrigues(dxc[:, :3]) @ rodrigues(cams[:, :3])
-    new = np.concatenate([so3_log(R), cams[:, 3:] + dxc[:, 3:]], 1)
+    dR = rodrigues(dxc[:, :3])
+    R = dR @ rodrigues(cams[:, :3])
+    t = np.einsum("nij,nj->ni", dR, cams[:, 3:]) + dxc[:, 3:]
+    new = np.concatenate([so3_log(R), t], 1)
     return new, pts + dxp.reshape(-1, 3)
 
 
@@ -474,3 +477,41 @@ def csr_bsmc_ratio(alpha, n, c):
     """Eq. 10 with the denominator term 3 alpha n (printed as 3 alpha):
     Y_C / Y_B = (6 alpha n c^2 + 2c) / (2 alpha n c^2 + 2 c^2 + 3 alpha n + 5)."""
     return (6 * alpha * n * c * c + 2 * c) / (2 * alpha * n * c * c + 2 * c * c + 3 * alpha * n + 5)
+
+
+# ----------------------------------------------------------------------------
+# selected RCS blocks of a large problem (Eq. 4 restricted to the points that
+# reach them), for spot checks at sizes where the full oracle is too slow
+# ----------------------------------------------------------------------------
+
+def rcs_blocks_sampled(cams, pts, obs_cam, obs_pt, obs_uv, intr, lam, pairs, delta=None):
+    """S_ij for each (i <= j) in pairs and b_i for each diagonal pair.
+
+    S_ij only receives terms from points seen by both i and j, and S_ii, b_i
+    only from points seen by i (plus U_ii, which needs every observation of
+    camera i); so Eq. 3-4 are evaluated on the sub-problem made of all
+    observations of those points."""
+    obs_cam = np.asarray(obs_cam, dtype=np.int64)
+    obs_pt = np.asarray(obs_pt, dtype=np.int64)
+    P = len(pts)
+    cam_pts = {}
+    need = set(i for p in pairs for i in p)
+    for c in need:
+        cam_pts[c] = set(np.unique(obs_pt[obs_cam == c]).tolist())
+    keep = set()
+    for (i, j) in pairs:
+        keep |= cam_pts[i] if i == j else (cam_pts[i] & cam_pts[j])
+    keep = np.array(sorted(keep), dtype=np.int64)
+    remap = -np.ones(P, dtype=np.int64)
+    remap[keep] = np.arange(len(keep))
+    sel = np.nonzero(remap[obs_pt] >= 0)[0]
+    sc, sp = obs_cam[sel], remap[obs_pt[sel]]
+    order = sort_observations(sc, sp)
+    sc, sp, suv = sc[order], sp[order], np.asarray(obs_uv)[sel][order]
+    e, Jc, Jp = linearize(cams, pts[keep], sc, sp, suv, intr, delta)
+    blk = normal_blocks(e, Jc, Jp, sc, sp, len(cams), len(keep), lam)
+    S, b = reduced_camera_system(blk, sc, sp, len(cams), len(keep))
+    out = {}
+    for (i, j) in pairs:
+        out[(i, j)] = S[(i, j)]
+    return out, {i: b[i] for (i, j) in pairs if i == j}

@@ -1,0 +1,377 @@
+"""Python binding of libba (include/ba.h): argument marshalling only.
+
+Every step of the bundle-adjustment path runs in the CUDA kernels of
+``csrc/``; this module converts numpy arrays to pointers, calls the C ABI and
+turns non-zero statuses into ``BAError``.  There is no fallback: if the
+compiled library is missing, loading fails loudly.
+
+The functions carry the C names (``ba_problem_create``, ``ba_linearize``,
+``ba_form_rcs``, ``ba_solve_rcs``, ``ba_back_substitute``, ``ba_lm_step``, the
+getters and ``ba_problem_destroy``); ``Problem`` wraps a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+BA_OK = 0
+BA_ERR_INVALID_ARG = 1
+BA_ERR_OOM = 2
+BA_ERR_CUDA = 3
+BA_ERR_NONFINITE = 4
+BA_ERR_NOT_SPD = 5
+BA_ERR_NO_CONVERGENCE = 6
+BA_ERR_TIMEOUT = 7
+BA_ERR_STATE = 8
+BA_ERR_INTERNAL = 9
+BA_FP64 = 0
+BA_FP32 = 1
+BA_LOSS_PLAIN = 0
+BA_LOSS_HUBER = 1
+BA_PC_BLOCK_JACOBI = 0
+
+STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_OOM", 3: "BA_ERR_CUDA", 4: "BA_ERR_NONFINITE",
+                5: "BA_ERR_NOT_SPD", 6: "BA_ERR_NO_CONVERGENCE", 7: "BA_ERR_TIMEOUT", 8: "BA_ERR_STATE",
+                9: "BA_ERR_INTERNAL"}
+
+
+class BAError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ba_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("fx", ctypes.c_double), ("fy", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("robust", ctypes.c_int32),
+                ("huber_delta", ctypes.c_double), ("lambda0", ctypes.c_double), ("pcg_rel_tol", ctypes.c_double),
+                ("pcg_max_iters", ctypes.c_int32), ("inner_rel_tol", ctypes.c_double),
+                ("refine_max", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("device_mem_cap", ctypes.c_size_t),
+                ("group_max_obs", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+class ba_step_info(ctypes.Structure):
+    _fields_ = [("cost_before", ctypes.c_double), ("cost_after", ctypes.c_double),
+                ("cost_trial", ctypes.c_double), ("predicted", ctypes.c_double), ("rho", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("accepted", ctypes.c_int32), ("pcg_iters", ctypes.c_int32),
+                ("refine_steps", ctypes.c_int32), ("used_fallback", ctypes.c_int32),
+                ("rcs_rel_resid", ctypes.c_double), ("n_cheirality", ctypes.c_int64),
+                ("n_v_fp64", ctypes.c_int64), ("ms", ctypes.c_float * 8)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "ms"}
+        d["lambda"] = d.pop("lambda_")
+        d["ms"] = list(self.ms)
+        return d
+
+
+class ba_stats(ctypes.Structure):
+    _fields_ = [("n_cams", ctypes.c_int32), ("n_pts", ctypes.c_int64), ("n_obs", ctypes.c_int64),
+                ("nnzb", ctypes.c_int64), ("n_groups", ctypes.c_int64), ("n_partials", ctypes.c_int64),
+                ("n_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("precision", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_S = ctypes.c_int  # ba_status
+
+# (name, restype, argtypes) of every C entry point in include/ba.h
+SIGNATURES = [
+    ("ba_options_default", None, [ctypes.POINTER(ba_options)]),
+    ("ba_problem_create", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _D, ctypes.c_int64, _D,
+                               ctypes.c_int64, _I32, _I64, _D, ctypes.POINTER(_P)]),
+    ("ba_linearize", _S, [_P, _D]),
+    ("ba_form_rcs", _S, [_P, ctypes.c_double]),
+    ("ba_solve_rcs", _S, [_P, ctypes.POINTER(ba_step_info)]),
+    ("ba_back_substitute", _S, [_P]),
+    ("ba_lm_step", _S, [_P, ctypes.POINTER(ba_step_info)]),
+    ("ba_get_cameras", _S, [_P, _D]),
+    ("ba_get_points", _S, [_P, _D]),
+    ("ba_get_rcs", _S, [_P, _I64, _I32, _I32, _D, _D]),
+    ("ba_get_step", _S, [_P, _D, _D]),
+    ("ba_get_linearization", _S, [_P, _D, _D, _D]),
+    ("ba_set_state", _S, [_P, _D, _D, ctypes.c_double, ctypes.c_double]),
+    ("ba_get_lm_state", _S, [_P, _D, _D, _D]),
+    ("ba_get_stats", _S, [_P, ctypes.POINTER(ba_stats)]),
+    ("ba_get_kernel_time", _S, [_P, ctypes.c_int32, _I64, _D]),
+    ("ba_reset_kernel_times", _S, [_P]),
+    ("ba_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
+    ("ba_problem_destroy", None, [_P]),
+    ("ba_last_error", ctypes.c_char_p, []),
+    ("ba_symbolic_pattern", _S, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _I32, _I64, _I32, _I32, _I64]),
+]
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libba.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"libba.so not found at {LIB}; build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _err() -> str:
+    m = lib().ba_last_error()
+    return m.decode() if m else ""
+
+
+def _check(status: int, allow=()):
+    if status != BA_OK and status not in allow:
+        raise BAError(status, _err())
+    return status
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _f64(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def ba_options_default(**kw) -> ba_options:
+    o = ba_options()
+    lib().ba_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"ba_options has no field {k}")
+        setattr(o, k, v)
+    return o
+
+
+def ba_problem_create(opts: ba_options, cams, pts, obs_cam, obs_pt, obs_uv):
+    cams = np.ascontiguousarray(cams, dtype=np.float64).reshape(-1, 6)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    obs_cam = np.ascontiguousarray(obs_cam, dtype=np.int32)
+    obs_pt = np.ascontiguousarray(obs_pt, dtype=np.int64)
+    obs_uv = np.ascontiguousarray(obs_uv, dtype=np.float64).reshape(-1, 2)
+    if not (len(obs_cam) == len(obs_pt) == len(obs_uv)):
+        raise ValueError("observation arrays differ in length")
+    h = _P()
+    _check(lib().ba_problem_create(ctypes.byref(opts), len(cams), _dp(cams), len(pts), _dp(pts), len(obs_cam),
+                                   obs_cam.ctypes.data_as(_I32), obs_pt.ctypes.data_as(_I64), _dp(obs_uv),
+                                   ctypes.byref(h)))
+    return h
+
+
+def ba_linearize(h) -> float:
+    c = ctypes.c_double()
+    _check(lib().ba_linearize(h, ctypes.byref(c)))
+    return c.value
+
+
+def ba_form_rcs(h, lam: float) -> None:
+    _check(lib().ba_form_rcs(h, float(lam)))
+
+
+def ba_solve_rcs(h):
+    """Returns (info dict, converged)."""
+    info = ba_step_info()
+    s = _check(lib().ba_solve_rcs(h, ctypes.byref(info)), allow=(BA_ERR_NO_CONVERGENCE,))
+    return info.as_dict(), s == BA_OK
+
+
+def ba_back_substitute(h) -> None:
+    _check(lib().ba_back_substitute(h))
+
+
+def ba_lm_step(h) -> dict:
+    info = ba_step_info()
+    _check(lib().ba_lm_step(h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def ba_get_stats(h) -> dict:
+    s = ba_stats()
+    _check(lib().ba_get_stats(h, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+def ba_get_cameras(h, n, out=None):
+    out = np.empty((n, 6)) if out is None else out
+    _check(lib().ba_get_cameras(h, _dp(out)))
+    return out
+
+
+def ba_get_points(h, P, out=None):
+    out = np.empty((P, 3)) if out is None else out
+    _check(lib().ba_get_points(h, _dp(out)))
+    return out
+
+
+def ba_get_rcs(h, n):
+    nnzb = ctypes.c_int64()
+    _check(lib().ba_get_rcs(h, ctypes.byref(nnzb), None, None, None, None))
+    row_ptr = np.empty(n + 1, np.int32)
+    col = np.empty(nnzb.value, np.int32)
+    val = np.empty((nnzb.value, 6, 6))
+    b = np.empty((n, 6))
+    _check(lib().ba_get_rcs(h, ctypes.byref(nnzb), row_ptr.ctypes.data_as(_I32), col.ctypes.data_as(_I32),
+                            _dp(val), _dp(b)))
+    return row_ptr, col, val, b
+
+
+def ba_get_step(h, n, P):
+    dxc = np.empty((n, 6))
+    dxp = np.empty((P, 3))
+    _check(lib().ba_get_step(h, _dp(dxc), _dp(dxp)))
+    return dxc, dxp
+
+
+def ba_get_linearization(h, m):
+    e = np.empty((m, 2))
+    Jc = np.empty((m, 2, 6))
+    Jp = np.empty((m, 2, 3))
+    _check(lib().ba_get_linearization(h, _dp(e), _dp(Jc), _dp(Jp)))
+    return e, Jc, Jp
+
+
+def ba_set_state(h, cams, pts, lam, nu=2.0):
+    c = None if cams is None else np.ascontiguousarray(cams, dtype=np.float64)
+    p = None if pts is None else np.ascontiguousarray(pts, dtype=np.float64)
+    _check(lib().ba_set_state(h, _dp(c), _dp(p), float(lam), float(nu)))
+
+
+def ba_get_lm_state(h):
+    lam, nu, cost = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().ba_get_lm_state(h, ctypes.byref(lam), ctypes.byref(nu), ctypes.byref(cost)))
+    return lam.value, nu.value, cost.value
+
+
+def ba_kernel_names():
+    out = []
+    k = 0
+    while True:
+        n = lib().ba_kernel_name(k)
+        if n is None:
+            return out
+        out.append(n.decode())
+        k += 1
+
+
+def ba_get_kernel_time(h, k: int):
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(lib().ba_get_kernel_time(h, int(k), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def ba_reset_kernel_times(h):
+    _check(lib().ba_reset_kernel_times(h))
+
+
+def ba_problem_destroy(h):
+    if h:
+        lib().ba_problem_destroy(h)
+
+
+def ba_symbolic_pattern(n_cams, n_pts, obs_cam, obs_pt):
+    obs_cam = np.ascontiguousarray(obs_cam, dtype=np.int32)
+    obs_pt = np.ascontiguousarray(obs_pt, dtype=np.int64)
+    nnzb = ctypes.c_int64()
+    row_ptr = np.empty(n_cams + 1, np.int32)
+    _check(lib().ba_symbolic_pattern(n_cams, n_pts, len(obs_cam), obs_cam.ctypes.data_as(_I32),
+                                     obs_pt.ctypes.data_as(_I64), row_ptr.ctypes.data_as(_I32), None,
+                                     ctypes.byref(nnzb)))
+    col = np.empty(nnzb.value, np.int32)
+    _check(lib().ba_symbolic_pattern(n_cams, n_pts, len(obs_cam), obs_cam.ctypes.data_as(_I32),
+                                     obs_pt.ctypes.data_as(_I64), row_ptr.ctypes.data_as(_I32),
+                                     col.ctypes.data_as(_I32), ctypes.byref(nnzb)))
+    return row_ptr, col
+
+
+class Problem:
+    """A libba problem handle with numpy in / out."""
+
+    def __init__(self, cams, pts, obs_cam, obs_pt, obs_uv, stream="current", **opts):
+        if stream == "current":
+            stream = _default_stream()
+        self.opts = ba_options_default(cuda_stream=stream, **opts)
+        self.n = len(cams)
+        self.P = len(pts)
+        self.m = len(obs_cam)
+        self.h = ba_problem_create(self.opts, cams, pts, obs_cam, obs_pt, obs_uv)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ba_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def linearize(self):
+        return ba_linearize(self.h)
+
+    def form_rcs(self, lam):
+        ba_form_rcs(self.h, lam)
+
+    def solve_rcs(self):
+        return ba_solve_rcs(self.h)
+
+    def back_substitute(self):
+        ba_back_substitute(self.h)
+
+    def lm_step(self):
+        return ba_lm_step(self.h)
+
+    def cameras(self):
+        return ba_get_cameras(self.h, self.n)
+
+    def points(self):
+        return ba_get_points(self.h, self.P)
+
+    def rcs(self):
+        return ba_get_rcs(self.h, self.n)
+
+    def step(self):
+        return ba_get_step(self.h, self.n, self.P)
+
+    def linearization(self):
+        return ba_get_linearization(self.h, self.m)
+
+    def set_state(self, cams, pts, lam, nu=2.0):
+        ba_set_state(self.h, cams, pts, lam, nu)
+
+    def lm_state(self):
+        return ba_get_lm_state(self.h)
+
+    def stats(self):
+        return ba_get_stats(self.h)
+
+    def kernel_times(self):
+        return {name: ba_get_kernel_time(self.h, k) for k, name in enumerate(ba_kernel_names())}
+
+    def reset_kernel_times(self):
+        ba_reset_kernel_times(self.h)

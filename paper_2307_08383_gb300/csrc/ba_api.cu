@@ -1,0 +1,734 @@
+// C ABI of libba (declared in include/ba.h) and the host side of one LM
+// iteration: linearize -> form RCS (Eq. 4) -> PCG (Sec. 3.2) -> back-substitute
+// (Eq. 5) -> trial evaluation -> accept / reject (Fig. 2 pipeline).  Every
+// step runs on the caller's stream in the kernels of k_obs.cu, k_rcs.cu and
+// k_pcg.cu; only scalars come back to the host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "ba_internal.h"
+
+namespace ba {
+cudaError_t launch_accumulate_solution(ba_problem *p, bool first);
+}
+
+using namespace ba;
+
+static thread_local std::string g_err;
+
+static ba_status fail(ba_status s, const std::string &m) {
+    g_err = m;
+    return s;
+}
+
+#define CK(p, call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            (p)->dead = true;                                                                         \
+            return fail(BA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+        }                                                                                             \
+    } while (0)
+
+#define LIVE(p)                                                                                       \
+    do {                                                                                              \
+        if (!(p)) return fail(BA_ERR_INVALID_ARG, "null problem");                                    \
+        if ((p)->dead) return fail(BA_ERR_STATE, "problem unusable after an earlier CUDA/internal error"); \
+    } while (0)
+
+namespace ba {
+
+const char *kernel_name(int k) {
+    static const char *names[K_COUNT] = {"prepare_state", "linearize",  "cost",         "form_rcs",
+                                         "rcs_reduce",    "rcs_diag",   "pcg_init",     "spmv",
+                                         "pcg_update",    "resid64",    "back_substitute", "update",
+                                         "eval"};
+    return (k >= 0 && k < K_COUNT) ? names[k] : nullptr;
+}
+
+static bool timed(const ba_problem *p, int k) {
+    if (!p->opt.profile) return false;
+    if (k == K_SPMV || k == K_PCG_UPDATE) return p->opt.profile >= 2;
+    return true;
+}
+
+void ktimer_begin(ba_problem *p, int k, cudaEvent_t *a) {
+    *a = nullptr;
+    if (!timed(p, k)) return;
+    if (p->ev_pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        p->ev_pool.push_back(e);
+    }
+    *a = p->ev_pool.back();
+    p->ev_pool.pop_back();
+    cudaEventRecord(*a, p->st);
+}
+
+void ktimer_end(ba_problem *p, int k, cudaEvent_t a) {
+    if (!a) return;
+    cudaEvent_t b;
+    if (p->ev_pool.empty()) {
+        if (cudaEventCreate(&b) != cudaSuccess) { p->ev_pool.push_back(a); return; }
+    } else {
+        b = p->ev_pool.back();
+        p->ev_pool.pop_back();
+    }
+    cudaEventRecord(b, p->st);
+    p->pending.push_back({k, a, b});
+    if (p->pending.size() > 8192) ktimer_flush(p);
+}
+
+ba_status ktimer_flush(ba_problem *p) {
+    if (p->pending.empty()) return BA_OK;
+    if (cudaEventSynchronize(p->pending.back().b) != cudaSuccess) return fail(BA_ERR_CUDA, "event sync");
+    for (auto &q : p->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, q.a, q.b);
+        p->klaunch[q.k] += 1;
+        p->kms[q.k] += ms;
+        p->ev_pool.push_back(q.a);
+        p->ev_pool.push_back(q.b);
+    }
+    p->pending.clear();
+    return BA_OK;
+}
+
+}  // namespace ba
+
+// ----------------------------------------------------------------------------
+// allocation helpers
+// ----------------------------------------------------------------------------
+template <typename X>
+static cudaError_t dalloc(ba_problem *p, X **ptr, size_t count) {
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(X), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return e;
+    p->allocs.push_back(q);
+    p->dev_bytes += bytes;
+    *ptr = (X *)q;
+    return cudaSuccess;
+}
+static cudaError_t dalloc_raw(ba_problem *p, void **ptr, size_t bytes) {
+    return dalloc(p, (unsigned char **)ptr, bytes);
+}
+
+template <typename X>
+static cudaError_t upload(ba_problem *p, X *dst, const X *src, size_t count) {
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(X), cudaMemcpyHostToDevice, p->st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(p->st);
+}
+
+static void free_all(ba_problem *p) {
+    for (void *q : p->allocs) cudaFree(q);
+    p->allocs.clear();
+    for (auto &q : p->pending) {
+        cudaEventDestroy(q.a);
+        cudaEventDestroy(q.b);
+    }
+    p->pending.clear();
+    for (auto e : p->ev_pool) cudaEventDestroy(e);
+    p->ev_pool.clear();
+    if (p->sc_host) cudaFreeHost(p->sc_host);
+    p->sc_host = nullptr;
+}
+
+static bool finite_all(const double *x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+static ba_status sync_scalars(ba_problem *p) {
+    CK(p, cudaMemcpyAsync(p->sc_host, p->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->st));
+    CK(p, cudaStreamSynchronize(p->st));
+    return BA_OK;
+}
+
+static void to_double(const void *src, bool fp32, double *dst, size_t cnt) {
+    if (fp32) {
+        for (size_t i = 0; i < cnt; ++i) dst[i] = ((const float *)src)[i];
+    } else {
+        std::memcpy(dst, src, cnt * 8);
+    }
+}
+
+// device array of the mode precision -> host doubles
+static ba_status fetch(ba_problem *p, const void *dev, size_t cnt, std::vector<double> &out) {
+    std::vector<unsigned char> raw(cnt * p->esz);
+    out.resize(cnt);
+    CK(p, cudaMemcpyAsync(raw.data(), dev, cnt * p->esz, cudaMemcpyDeviceToHost, p->st));
+    CK(p, cudaStreamSynchronize(p->st));
+    to_double(raw.data(), p->fp32, out.data(), cnt);
+    return BA_OK;
+}
+
+// ----------------------------------------------------------------------------
+// C ABI
+// ----------------------------------------------------------------------------
+extern "C" {
+
+void ba_options_default(ba_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = BA_FP64;
+    o->fx = o->fy = 1000.0;
+    o->cx = o->cy = 500.0;
+    o->robust = BA_LOSS_PLAIN;
+    o->huber_delta = 2.0;
+    o->lambda0 = 1e-4;
+    o->pcg_rel_tol = 1e-10;
+    o->pcg_max_iters = 0;
+    o->inner_rel_tol = 1e-4;
+    o->refine_max = 20;
+    o->preconditioner = BA_PC_BLOCK_JACOBI;
+    o->cuda_stream = nullptr;
+    o->device_mem_cap = 0;
+    o->group_max_obs = 0;
+    o->profile = 0;
+}
+
+const char *ba_last_error(void) { return g_err.c_str(); }
+
+const char *ba_kernel_name(int32_t k) { return ba::kernel_name(k); }
+
+ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs, const int32_t *obs_cam,
+                              const int64_t *obs_pt, int32_t *row_ptr, int32_t *col, int64_t *nnzb) {
+    HostSetup hs;
+    std::string err;
+    ba_status s = symbolic_setup(n_cams, n_pts, n_obs, obs_cam, obs_pt, nullptr, OBS_MAX_DEFAULT, true, hs, err);
+    if (s != BA_OK) return fail(s, err);
+    if (nnzb) *nnzb = (int64_t)hs.col.size();
+    if (row_ptr) std::memcpy(row_ptr, hs.row_ptr.data(), hs.row_ptr.size() * sizeof(int32_t));
+    if (col) std::memcpy(col, hs.col.data(), hs.col.size() * sizeof(int32_t));
+    return BA_OK;
+}
+
+ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double *cams, int64_t n_pts,
+                            const double *pts, int64_t n_obs, const int32_t *obs_cam, const int64_t *obs_pt,
+                            const double *obs_uv, ba_problem **out) {
+    if (!out) return fail(BA_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    ba_options o;
+    if (opt) o = *opt; else ba_options_default(&o);
+    if (!cams || !pts || !obs_cam || !obs_pt || !obs_uv) return fail(BA_ERR_INVALID_ARG, "null input array");
+    if (o.precision != BA_FP64 && o.precision != BA_FP32) return fail(BA_ERR_INVALID_ARG, "precision must be BA_FP64 or BA_FP32");
+    if (o.robust != BA_LOSS_PLAIN && o.robust != BA_LOSS_HUBER) return fail(BA_ERR_INVALID_ARG, "robust must be BA_LOSS_PLAIN or BA_LOSS_HUBER");
+    if (o.robust == BA_LOSS_HUBER && !(o.huber_delta > 0)) return fail(BA_ERR_INVALID_ARG, "huber_delta must be > 0");
+    if (!(o.lambda0 >= 0) || !(o.pcg_rel_tol > 0) || !(o.inner_rel_tol > 0) || o.pcg_max_iters < 0 || o.refine_max < 1)
+        return fail(BA_ERR_INVALID_ARG, "bad solver option");
+    if (!(o.fx > 0) || !(o.fy > 0) || !std::isfinite(o.cx) || !std::isfinite(o.cy))
+        return fail(BA_ERR_INVALID_ARG, "bad intrinsics");
+    if (o.preconditioner != BA_PC_BLOCK_JACOBI) return fail(BA_ERR_INVALID_ARG, "only BA_PC_BLOCK_JACOBI is available");
+    if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0) return fail(BA_ERR_INVALID_ARG, "sizes must be positive");
+    if (!finite_all(cams, (size_t)n_cams * 6) || !finite_all(pts, (size_t)n_pts * 3) ||
+        !finite_all(obs_uv, (size_t)n_obs * 2))
+        return fail(BA_ERR_NONFINITE, "non-finite camera, point or observation value");
+
+    ba_problem *p = new ba_problem();
+    p->opt = o;
+    p->st = (cudaStream_t)o.cuda_stream;
+    p->n = n_cams;
+    p->P = n_pts;
+    p->m = n_obs;
+    p->fp32 = (o.precision == BA_FP32);
+    p->esz = p->fp32 ? 4 : 8;
+    p->obs_max = o.group_max_obs > 0 ? std::min(std::max(o.group_max_obs, 40), OBS_MAX_LIMIT) : OBS_MAX_DEFAULT;
+    p->lambda = o.lambda0;
+    p->nu = 2.0;
+    std::string err;
+    ba_status s = symbolic_setup(n_cams, n_pts, n_obs, obs_cam, obs_pt, pts, p->obs_max, false, p->hs, err);
+    if (s != BA_OK) {
+        delete p;
+        return fail(s, err);
+    }
+    HostSetup &hs = p->hs;
+    p->nnzb = (int64_t)hs.col.size();
+    p->ngroups = (int64_t)hs.groups.size();
+    p->npart = (int64_t)hs.lb_info.size();
+    const int64_t n = n_cams, P = n_pts, m = n_obs;
+    const size_t E = p->esz;
+
+    // planned device bytes (checked against the cap before any allocation)
+    const size_t camc_w = p->fp32 ? 16 * 4 : 12 * 8;
+    size_t plan = 2 * (n * 6 * 8 + P * 3 * 8 + n * camc_w + (p->fp32 ? P * 6 * 4 : 0)) +
+                  m * 4 * 2 + (P + 1) * 4 + m * 16 + (p->fp32 ? m * 8 : 0) + m * JW * E + (n + 1) * 4 +
+                  p->nnzb * 4 + p->nnzb * BW * E + n * 6 * E + n * 36 * E + p->ngroups * sizeof(GroupDesc) +
+                  p->npart * 8 + hs.contrib.size() * 4 + (p->nnzb + 1) * 4 + p->npart * 4 + p->npart * BW * E +
+                  P * 9 * E + 7 * n * 6 * E + 3 * n * 6 * 8 + n * 6 * E + P * 3 * E + sizeof(DevScalars) +
+                  RED_SLOTS * 8 + N_COUNTERS * 4;
+    if (o.device_mem_cap && plan > o.device_mem_cap) {
+        delete p;
+        return fail(BA_ERR_OOM, "problem needs " + std::to_string(plan) + " device bytes, cap is " +
+                                    std::to_string(o.device_mem_cap));
+    }
+#define AL(ptr, cnt)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = dalloc(p, &(ptr), (cnt));                                                    \
+        if (e_ != cudaSuccess) {                                                                      \
+            free_all(p);                                                                              \
+            delete p;                                                                                 \
+            cudaGetLastError();                                                                       \
+            return fail(e_ == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA,                   \
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e_));                        \
+        }                                                                                             \
+    } while (0)
+#define ALR(ptr, bytes)                                                                               \
+    do {                                                                                              \
+        cudaError_t e_ = dalloc_raw(p, &(ptr), (bytes));                                              \
+        if (e_ != cudaSuccess) {                                                                      \
+            free_all(p);                                                                              \
+            delete p;                                                                                 \
+            cudaGetLastError();                                                                       \
+            return fail(e_ == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA,                   \
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e_));                        \
+        }                                                                                             \
+    } while (0)
+    for (StateBuf *sb : {&p->cur, &p->trial}) {
+        AL(sb->cams, n * 6);
+        AL(sb->pts, P * 3);
+        ALR(sb->camc, n * camc_w);
+        if (p->fp32) AL(sb->pts_hl, P * 6);
+    }
+    AL(p->obs_cam, m);
+    AL(p->obs_pt, m);
+    AL(p->trk_ptr, P + 1);
+    AL(p->uv64, m * 2);
+    if (p->fp32) AL(p->uv32, m * 2);
+    ALR(p->J, m * JW * E);
+    AL(p->row_ptr, n + 1);
+    AL(p->col, p->nnzb);
+    ALR(p->S, p->nnzb * BW * E);
+    ALR(p->b, n * 6 * E);
+    ALR(p->Minv, n * 36 * E);
+    AL(p->grp, p->ngroups);
+    AL(p->lb_info, p->npart);
+    AL(p->contrib, hs.contrib.size());
+    AL(p->pptr, p->nnzb + 1);
+    AL(p->plist, p->npart);
+    ALR(p->part, p->npart * BW * E);
+    ALR(p->Linv, P * 6 * E);
+    ALR(p->lp, P * 3 * E);
+    for (int k = 0; k < 6; ++k) ALR(p->pv[k], n * 6 * E);
+    AL(p->x64, n * 6);
+    AL(p->r64, n * 6);
+    AL(p->q64, n * 6);
+    ALR(p->dxc, n * 6 * E);
+    ALR(p->dxp, P * 3 * E);
+    AL(p->sc, 1);
+    AL(p->red, RED_SLOTS);
+    AL(p->counters, N_COUNTERS);
+#undef AL
+#undef ALR
+    if (cudaMallocHost((void **)&p->sc_host, sizeof(DevScalars)) != cudaSuccess) {
+        free_all(p);
+        delete p;
+        return fail(BA_ERR_CUDA, "cudaMallocHost failed");
+    }
+    // uploads (internal orders)
+    std::vector<double> tmp;
+    cudaError_t e = cudaSuccess;
+    auto up_ok = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    up_ok(upload(p, p->cur.cams, cams, n * 6));
+    tmp.resize(P * 3);
+    for (int64_t k = 0; k < P; ++k)
+        for (int d = 0; d < 3; ++d) tmp[3 * k + d] = pts[3 * hs.pt_perm[k] + d];
+    up_ok(upload(p, p->cur.pts, tmp.data(), P * 3));
+    up_ok(upload(p, p->obs_cam, hs.obs_cam.data(), m));
+    up_ok(upload(p, p->obs_pt, hs.obs_pt.data(), m));
+    up_ok(upload(p, p->trk_ptr, hs.trk_ptr.data(), P + 1));
+    tmp.resize(m * 2);
+    for (int64_t a = 0; a < m; ++a) {
+        tmp[2 * a] = obs_uv[2 * hs.obs_perm[a]];
+        tmp[2 * a + 1] = obs_uv[2 * hs.obs_perm[a] + 1];
+    }
+    up_ok(upload(p, p->uv64, tmp.data(), m * 2));
+    if (p->fp32) {
+        std::vector<float> t32(m * 2);
+        for (int64_t x = 0; x < m * 2; ++x) t32[x] = (float)tmp[x];
+        up_ok(upload(p, p->uv32, t32.data(), m * 2));
+    }
+    up_ok(upload(p, p->row_ptr, hs.row_ptr.data(), n + 1));
+    up_ok(upload(p, p->col, hs.col.data(), p->nnzb));
+    up_ok(upload(p, p->grp, hs.groups.data(), p->ngroups));
+    up_ok(upload(p, p->lb_info, hs.lb_info.data(), p->npart));
+    up_ok(upload(p, p->contrib, hs.contrib.data(), hs.contrib.size()));
+    up_ok(upload(p, p->pptr, hs.pptr.data(), p->nnzb + 1));
+    up_ok(upload(p, p->plist, hs.plist.data(), p->npart));
+    up_ok(cudaMemsetAsync(p->q64, 0, n * 6 * 8, p->st));
+    up_ok(cudaMemsetAsync(p->x64, 0, n * 6 * 8, p->st));
+    up_ok(cudaMemsetAsync(p->sc, 0, sizeof(DevScalars), p->st));
+    up_ok(cudaMemsetAsync(p->counters, 0, N_COUNTERS * 4, p->st));
+    up_ok(cudaMemsetAsync(p->dxc, 0, n * 6 * E, p->st));
+    up_ok(cudaMemsetAsync(p->dxp, 0, P * 3 * E, p->st));
+    // drop host copies that the device now holds (keep permutations and pattern)
+    std::vector<GroupDesc>().swap(hs.groups);
+    std::vector<uint32_t>().swap(hs.lb_info);
+    std::vector<int32_t>().swap(hs.lb_gblk);
+    std::vector<uint32_t>().swap(hs.contrib);
+    std::vector<int32_t>().swap(hs.pptr);
+    std::vector<int32_t>().swap(hs.plist);
+    std::vector<int32_t>().swap(hs.obs_pt);
+    std::vector<int32_t>().swap(hs.trk_ptr);
+    if (e == cudaSuccess) e = launch_prepare_state(p, p->cur);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) {
+        free_all(p);
+        delete p;
+        return fail(BA_ERR_CUDA, std::string("problem upload: ") + cudaGetErrorString(e));
+    }
+    *out = p;
+    return BA_OK;
+}
+
+void ba_problem_destroy(ba_problem *p) {
+    if (!p) return;
+    if (p->st) cudaStreamSynchronize(p->st);
+    else cudaDeviceSynchronize();
+    free_all(p);
+    delete p;
+}
+
+static ba_status check_err_flag(ba_problem *p) {
+    if (p->sc_host->err) {
+        int e = p->sc_host->err;
+        CK(p, cudaMemsetAsync(&p->sc->err, 0, sizeof(int), p->st));
+        if (e == BA_ERR_NOT_SPD) return fail(BA_ERR_NOT_SPD, "a V_k or RCS diagonal block is not positive definite");
+        p->dead = true;
+        return fail(BA_ERR_INTERNAL, "device consistency check failed");
+    }
+    return BA_OK;
+}
+
+static ba_status ensure_cost(ba_problem *p) {
+    if (p->have_F) return BA_OK;
+    CK(p, launch_cost(p, p->cur, false));
+    ba_status s = sync_scalars(p);
+    if (s) return s;
+    p->F = p->sc_host->cost;
+    p->have_F = true;
+    if (!std::isfinite(p->F)) return fail(BA_ERR_NONFINITE, "non-finite cost");
+    return BA_OK;
+}
+
+ba_status ba_linearize(ba_problem *p, double *cost_out) {
+    LIVE(p);
+    CK(p, launch_linearize(p));
+    p->linearized = true;
+    p->rcs_formed = p->solved = p->backsub = false;
+    if (cost_out) {
+        ba_status s = ensure_cost(p);
+        if (s) return s;
+        *cost_out = p->F;
+    }
+    return BA_OK;
+}
+
+ba_status ba_form_rcs(ba_problem *p, double lambda) {
+    LIVE(p);
+    if (!p->linearized) return fail(BA_ERR_STATE, "ba_form_rcs needs ba_linearize first");
+    if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    CK(p, launch_form_rcs(p, lambda));
+    p->rcs_formed = true;
+    p->rcs_lambda = lambda;
+    p->solved = p->backsub = false;
+    return BA_OK;
+}
+
+static ba_status run_pcg(ba_problem *p, const void *rhs, double tol, int max_iters, int *iters) {
+    CK(p, launch_pcg_init(p, rhs, tol, max_iters));
+    int it = 0;
+    const int chunk = 8;
+    for (;;) {
+        for (int c = 0; c < chunk; ++c, ++it) CK(p, launch_pcg_iter(p, it));
+        ba_status s = sync_scalars(p);
+        if (s) return s;
+        if (p->sc_host->done) break;
+        if (it > max_iters + 2 * chunk) return fail(BA_ERR_INTERNAL, "PCG did not stop");
+    }
+    *iters = p->sc_host->iters;
+    return BA_OK;
+}
+
+ba_status ba_solve_rcs(ba_problem *p, ba_step_info *info) {
+    LIVE(p);
+    if (!p->rcs_formed) return fail(BA_ERR_STATE, "ba_solve_rcs needs ba_form_rcs first");
+    const int max_iters = p->opt.pcg_max_iters > 0 ? p->opt.pcg_max_iters : std::max(1000, 6 * p->n);
+    const double tol = p->opt.pcg_rel_tol;
+    int total = 0, refine = 0;
+    bool converged = false;
+    ba_status s;
+    if (!p->fp32) {
+        int it = 0;
+        if ((s = run_pcg(p, p->b, tol, max_iters, &it))) return s;
+        if ((s = check_err_flag(p))) return s;
+        total = it;
+        converged = p->sc_host->rr <= p->sc_host->tol2 * p->sc_host->rr0;
+        CK(p, launch_accumulate_solution(p, true));
+        CK(p, launch_resid64(p, true));
+    } else {
+        // FP32 inner PCG + FP64 iterative refinement on r = b - S x
+        const double inner = std::max(p->opt.inner_rel_tol, 0.5 * tol);
+        CK(p, launch_resid64(p, false));  // r64 = b, x64 implicit 0
+        if ((s = sync_scalars(p))) return s;
+        bool first = true;
+        for (int o = 0; o < p->opt.refine_max; ++o) {
+            if (p->sc_host->rr64 <= tol * tol * p->sc_host->bb64) { converged = true; break; }
+            if (p->sc_host->bb64 == 0.0) { converged = true; break; }
+            CK(p, launch_refine_rhs(p, p->pv[1]));  // r buffer doubles as the rhs (copied by init)
+            int it = 0;
+            if ((s = run_pcg(p, p->pv[1], inner, max_iters, &it))) return s;
+            if ((s = check_err_flag(p))) return s;
+            total += it;
+            ++refine;
+            CK(p, launch_accumulate_solution(p, first));
+            first = false;
+            CK(p, launch_resid64(p, true));
+            if ((s = sync_scalars(p))) return s;
+        }
+        if (first) CK(p, cudaMemsetAsync(p->x64, 0, p->n * 6 * 8, p->st));
+        if (!converged) converged = p->sc_host->rr64 <= tol * tol * p->sc_host->bb64;
+    }
+    CK(p, launch_solution_to_step(p));
+    if ((s = sync_scalars(p))) return s;
+    const double bb = p->sc_host->bb64;
+    p->last_true_rel = bb > 0 ? std::sqrt(p->sc_host->rr64 / bb) : 0.0;
+    p->last_pcg_iters = total;
+    p->last_refine = refine;
+    p->solved = true;
+    p->backsub = false;
+    if (info) {
+        info->pcg_iters = total;
+        info->refine_steps = refine;
+        info->rcs_rel_resid = p->last_true_rel;
+    }
+    if (!converged) return fail(BA_ERR_NO_CONVERGENCE, "PCG reached its iteration cap");
+    return BA_OK;
+}
+
+ba_status ba_back_substitute(ba_problem *p) {
+    LIVE(p);
+    if (!p->solved) return fail(BA_ERR_STATE, "ba_back_substitute needs ba_solve_rcs first");
+    CK(p, launch_back_substitute(p));
+    p->backsub = true;
+    return BA_OK;
+}
+
+ba_status ba_lm_step(ba_problem *p, ba_step_info *info) {
+    LIVE(p);
+    ba_step_info loc;
+    std::memset(&loc, 0, sizeof(loc));
+    cudaEvent_t ev[6];
+    for (auto &x : ev) CK(p, cudaEventCreate(&x));
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() { for (int k = 0; k < 6; ++k) cudaEventDestroy(e[k]); }
+    } guard{ev};
+    ba_status s;
+    CK(p, cudaEventRecord(ev[0], p->st));
+    if ((s = ensure_cost(p))) return s;
+    loc.cost_before = p->F;
+    if (!p->linearized) CK(p, launch_linearize(p));
+    p->linearized = true;
+    CK(p, cudaEventRecord(ev[1], p->st));
+    CK(p, launch_form_rcs(p, p->lambda));
+    p->rcs_formed = true;
+    p->rcs_lambda = p->lambda;
+    CK(p, cudaEventRecord(ev[2], p->st));
+    s = ba_solve_rcs(p, &loc);
+    if (s != BA_OK && s != BA_ERR_NO_CONVERGENCE) return s;
+    CK(p, cudaEventRecord(ev[3], p->st));
+    CK(p, launch_back_substitute(p));
+    p->backsub = true;
+    CK(p, cudaEventRecord(ev[4], p->st));
+    CK(p, launch_apply_update(p));
+    CK(p, launch_prepare_state(p, p->trial));
+    CK(p, launch_eval(p));
+    CK(p, cudaEventRecord(ev[5], p->st));
+    if ((s = sync_scalars(p))) return s;
+    if ((s = check_err_flag(p))) return s;
+    const double F1 = p->sc_host->cost_trial, pred = p->sc_host->model;
+    const double rho = pred > 0 ? (p->F - F1) / pred : -INFINITY;
+    const bool ok = pred > 0 && std::isfinite(F1) && rho > 1e-3;
+    loc.cost_trial = F1;
+    loc.predicted = pred;
+    loc.rho = rho;
+    loc.lambda = p->lambda;
+    loc.accepted = ok ? 1 : 0;
+    loc.n_cheirality = (int64_t)p->sc_host->n_cheir_trial;
+    loc.n_v_fp64 = (int64_t)p->sc_host->n_v64;
+    if (ok) {
+        std::swap(p->cur, p->trial);
+        p->F = F1;
+        const double f = 1.0 - std::pow(2.0 * rho - 1.0, 3);
+        p->lambda *= std::max(1.0 / 3.0, f);
+        p->nu = 2.0;
+        p->linearized = false;
+        p->rcs_formed = p->solved = p->backsub = false;
+    } else {
+        p->lambda *= p->nu;
+        p->nu *= 2.0;
+    }
+    loc.cost_after = p->F;
+    float t;
+    for (int k = 0; k < 5; ++k) {
+        cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+        loc.ms[k] = t;
+    }
+    cudaEventElapsedTime(&t, ev[0], ev[5]);
+    loc.ms[5] = t;
+    if (info) *info = loc;
+    return BA_OK;
+}
+
+ba_status ba_get_cameras(const ba_problem *p, double *out) {
+    LIVE(p);
+    if (!out) return fail(BA_ERR_INVALID_ARG, "null output");
+    ba_problem *q = const_cast<ba_problem *>(p);
+    CK(q, cudaMemcpyAsync(out, p->cur.cams, p->n * 6 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CK(q, cudaStreamSynchronize(p->st));
+    return BA_OK;
+}
+
+ba_status ba_get_points(const ba_problem *p, double *out) {
+    LIVE(p);
+    if (!out) return fail(BA_ERR_INVALID_ARG, "null output");
+    ba_problem *q = const_cast<ba_problem *>(p);
+    std::vector<double> tmp(p->P * 3);
+    CK(q, cudaMemcpyAsync(tmp.data(), p->cur.pts, p->P * 3 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CK(q, cudaStreamSynchronize(p->st));
+    for (int64_t k = 0; k < p->P; ++k)
+        for (int d = 0; d < 3; ++d) out[3 * p->hs.pt_perm[k] + d] = tmp[3 * k + d];
+    return BA_OK;
+}
+
+ba_status ba_get_rcs(const ba_problem *p, int64_t *nnzb, int32_t *row_ptr, int32_t *col, double *val, double *b) {
+    LIVE(p);
+    ba_problem *q = const_cast<ba_problem *>(p);
+    if (nnzb) *nnzb = p->nnzb;
+    if (row_ptr) std::memcpy(row_ptr, p->hs.row_ptr.data(), (p->n + 1) * sizeof(int32_t));
+    if (col) std::memcpy(col, p->hs.col.data(), p->nnzb * sizeof(int32_t));
+    if ((val || b) && !p->rcs_formed) return fail(BA_ERR_STATE, "no RCS formed yet");
+    std::vector<double> tmp;
+    ba_status s;
+    if (val) {
+        if ((s = fetch(q, p->S, p->nnzb * BW, tmp))) return s;
+        std::memcpy(val, tmp.data(), tmp.size() * 8);
+    }
+    if (b) {
+        if ((s = fetch(q, p->b, p->n * 6, tmp))) return s;
+        std::memcpy(b, tmp.data(), tmp.size() * 8);
+    }
+    return BA_OK;
+}
+
+ba_status ba_get_step(const ba_problem *p, double *dxc, double *dxp) {
+    LIVE(p);
+    ba_problem *q = const_cast<ba_problem *>(p);
+    std::vector<double> tmp;
+    ba_status s;
+    if (dxc) {
+        if ((s = fetch(q, p->dxc, p->n * 6, tmp))) return s;
+        std::memcpy(dxc, tmp.data(), tmp.size() * 8);
+    }
+    if (dxp) {
+        if ((s = fetch(q, p->dxp, p->P * 3, tmp))) return s;
+        for (int64_t k = 0; k < p->P; ++k)
+            for (int d = 0; d < 3; ++d) dxp[3 * p->hs.pt_perm[k] + d] = tmp[3 * k + d];
+    }
+    return BA_OK;
+}
+
+ba_status ba_get_linearization(const ba_problem *p, double *e, double *Jc, double *Jp) {
+    LIVE(p);
+    if (!p->linearized) return fail(BA_ERR_STATE, "not linearized");
+    ba_problem *q = const_cast<ba_problem *>(p);
+    std::vector<double> tmp;
+    ba_status s;
+    if ((s = fetch(q, p->J, p->m * JW, tmp))) return s;
+    for (int64_t a = 0; a < p->m; ++a) {
+        const int64_t u = p->hs.obs_perm[a];
+        const double *r = tmp.data() + a * JW;
+        if (Jc) std::memcpy(Jc + 12 * u, r, 12 * 8);
+        if (Jp) std::memcpy(Jp + 6 * u, r + 12, 6 * 8);
+        if (e) { e[2 * u] = r[18]; e[2 * u + 1] = r[19]; }
+    }
+    return BA_OK;
+}
+
+ba_status ba_set_state(ba_problem *p, const double *cams, const double *pts, double lambda, double nu) {
+    LIVE(p);
+    if (!(lambda >= 0) || !(nu > 0) || !std::isfinite(lambda) || !std::isfinite(nu))
+        return fail(BA_ERR_INVALID_ARG, "bad lambda / nu");
+    if (cams) {
+        if (!finite_all(cams, p->n * 6)) return fail(BA_ERR_NONFINITE, "non-finite camera");
+        CK(p, cudaMemcpyAsync(p->cur.cams, cams, p->n * 6 * 8, cudaMemcpyHostToDevice, p->st));
+    }
+    if (pts) {
+        if (!finite_all(pts, p->P * 3)) return fail(BA_ERR_NONFINITE, "non-finite point");
+        std::vector<double> tmp(p->P * 3);
+        for (int64_t k = 0; k < p->P; ++k)
+            for (int d = 0; d < 3; ++d) tmp[3 * k + d] = pts[3 * p->hs.pt_perm[k] + d];
+        CK(p, cudaMemcpyAsync(p->cur.pts, tmp.data(), p->P * 3 * 8, cudaMemcpyHostToDevice, p->st));
+        CK(p, cudaStreamSynchronize(p->st));
+    }
+    CK(p, launch_prepare_state(p, p->cur));
+    p->lambda = lambda;
+    p->nu = nu;
+    p->have_F = false;
+    p->linearized = p->rcs_formed = p->solved = p->backsub = false;
+    return BA_OK;
+}
+
+ba_status ba_get_lm_state(const ba_problem *p, double *lambda, double *nu, double *cost) {
+    LIVE(p);
+    if (lambda) *lambda = p->lambda;
+    if (nu) *nu = p->nu;
+    if (cost) {
+        ba_problem *q = const_cast<ba_problem *>(p);
+        ba_status s = ensure_cost(q);
+        if (s) return s;
+        *cost = p->F;
+    }
+    return BA_OK;
+}
+
+ba_status ba_get_stats(const ba_problem *p, ba_stats *o) {
+    LIVE(p);
+    if (!o) return fail(BA_ERR_INVALID_ARG, "null output");
+    o->n_cams = p->n;
+    o->n_pts = p->P;
+    o->n_obs = p->m;
+    o->nnzb = p->nnzb;
+    o->n_groups = p->ngroups;
+    o->n_partials = p->npart;
+    o->n_pairs = p->hs.n_pairs;
+    o->device_bytes = (int64_t)p->dev_bytes;
+    o->precision = p->opt.precision;
+    return BA_OK;
+}
+
+ba_status ba_get_kernel_time(ba_problem *p, int32_t k, int64_t *launches, double *total_ms) {
+    LIVE(p);
+    if (k < 0 || k >= K_COUNT) return fail(BA_ERR_INVALID_ARG, "kernel id out of range");
+    ba_status s = ktimer_flush(p);
+    if (s) return s;
+    if (launches) *launches = p->klaunch[k];
+    if (total_ms) *total_ms = p->kms[k];
+    return BA_OK;
+}
+
+ba_status ba_reset_kernel_times(ba_problem *p) {
+    LIVE(p);
+    ba_status s = ktimer_flush(p);
+    if (s) return s;
+    for (int k = 0; k < K_COUNT; ++k) { p->klaunch[k] = 0; p->kms[k] = 0; }
+    return BA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// Internal declarations of libba: the problem object, the host-side symbolic
+// setup and the kernel launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ba.h"
+
+namespace ba {
+
+// One observation row of the stored linearization: [J_c (2x6) | J_p (2x3) | e (2)].
+constexpr int JW = 20;
+// One BSMC block / one sub-RCS partial block: 6x6 values.  A diagonal partial
+// packs [21 upper entries of U - W V^-1 W^T | 6 diag(J_c^T J_c) | 6 b | 3 unused].
+constexpr int BW = 36;
+constexpr int OBS_MAX_DEFAULT = 512;  // observations staged per point group
+constexpr int OBS_MAX_LIMIT = 1024;
+constexpr int LB_MAX = 2048;          // local blocks (sub-RCS blocks) per group
+constexpr int C_MAX = 16384;          // (obs, obs) products per group
+constexpr int FORM_THREADS = 256;
+
+// A point group: a run of whole point tracks formed by one CTA (Sec. 6.1).
+struct GroupDesc {
+    int64_t c_begin;   // first (a, b) product in the contribution array
+    int64_t lb_begin;  // first local block == first partial written by the group
+    int32_t obs_begin, nobs;
+    int32_t pt_begin, npts;
+    int32_t nlb, nc;
+};
+
+// Device-resident scalars of the reductions and of the PCG recurrence.
+struct DevScalars {
+    double cost, cost_trial, model;
+    double rz, pAp, rr, rr0, alpha, beta, tol2;
+    double rr64, bb64;
+    unsigned long long n_cheir, n_cheir_trial, n_v64;
+    int iters, done, max_iters, err;
+};
+constexpr int N_COUNTERS = 16;
+constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
+
+enum KernelId {
+    K_PREPARE = 0, K_LINEARIZE, K_COST, K_FORM_RCS, K_RCS_REDUCE, K_RCS_DIAG,
+    K_PCG_INIT, K_SPMV, K_PCG_UPDATE, K_RESID64, K_BACKSUB, K_UPDATE, K_EVAL, K_COUNT
+};
+const char *kernel_name(int k);
+
+// Result of the host-side symbolic phase (Sec. 4 pattern, Sec. 6.1 groups,
+// Table 1 second operation for the local -> global block index).
+struct HostSetup {
+    std::vector<int64_t> pt_perm;    // internal point -> caller's point
+    std::vector<int64_t> obs_perm;   // internal observation -> caller's observation
+    std::vector<int32_t> obs_cam;    // internal order: sorted by (internal point, camera)
+    std::vector<int32_t> obs_pt;
+    std::vector<int32_t> trk_ptr;    // P + 1
+    std::vector<int32_t> row_ptr;    // n + 1
+    std::vector<int32_t> col;        // nnzb
+    std::vector<GroupDesc> groups;
+    std::vector<uint32_t> lb_info;   // cbeg | count << 16 | diag << 31 (relative to c_begin)
+    std::vector<int32_t> lb_gblk;    // global block of each local block
+    std::vector<uint32_t> contrib;   // a | b << 16 (observation offsets in the group)
+    std::vector<int32_t> pptr;       // nnzb + 1: partials of each global block
+    std::vector<int32_t> plist;
+    int64_t n_pairs = 0;
+};
+
+// Validates the observation set and builds everything above.  Returns BA_OK or
+// BA_ERR_INVALID_ARG with a message.
+ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam,
+                         const int64_t *obs_pt, const double *pts, int obs_max, bool pattern_only,
+                         HostSetup &hs, std::string &err);
+
+// A parameter state with its derived per-camera / per-point caches.
+struct StateBuf {
+    double *cams = nullptr;   // n x 6  [omega, t]
+    double *pts = nullptr;    // P x 3  (internal point order)
+    void *camc = nullptr;     // FP64: n x 12 [R, t]; FP32: n x 16 [R, C_hi, C_lo, pad]
+    float *pts_hl = nullptr;  // FP32 mode: P x 6 [X_hi, X_lo]
+};
+
+}  // namespace ba
+
+struct ba_problem {
+    ba_options opt{};
+    cudaStream_t st = nullptr;
+    int32_t n = 0;
+    int64_t P = 0, m = 0;
+    bool fp32 = false;
+    size_t esz = 8;
+    int obs_max = ba::OBS_MAX_DEFAULT;
+    ba::HostSetup hs;
+    int64_t nnzb = 0, ngroups = 0, npart = 0;
+    size_t dev_bytes = 0;
+    std::vector<void *> allocs;
+
+    ba::StateBuf cur, trial;
+    int32_t *obs_cam = nullptr, *obs_pt = nullptr, *trk_ptr = nullptr;
+    double *uv64 = nullptr;
+    float *uv32 = nullptr;
+    void *J = nullptr;
+    int32_t *row_ptr = nullptr, *col = nullptr;
+    void *S = nullptr, *b = nullptr, *Minv = nullptr;
+    ba::GroupDesc *grp = nullptr;
+    uint32_t *lb_info = nullptr, *contrib = nullptr;
+    int32_t *pptr = nullptr, *plist = nullptr;
+    void *part = nullptr;
+    void *Linv = nullptr, *lp = nullptr;
+    void *pv[6] = {};  // y, r, z, d0, d1, q   (n x 6, mode precision)
+    double *x64 = nullptr, *r64 = nullptr, *q64 = nullptr;
+    void *dxc = nullptr, *dxp = nullptr;
+    ba::DevScalars *sc = nullptr;
+    ba::DevScalars *sc_host = nullptr;  // pinned mirror
+    double *red = nullptr;
+    unsigned *counters = nullptr;
+
+    double lambda = 1e-4, nu = 2.0, F = 0.0;
+    bool have_F = false, linearized = false, rcs_formed = false, solved = false, backsub = false;
+    bool dead = false;
+    double rcs_lambda = 0.0;
+    int last_pcg_iters = 0, last_refine = 0;
+    double last_true_rel = 0.0;
+
+    // kernel timing
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { int k; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    int64_t klaunch[ba::K_COUNT] = {};
+    double kms[ba::K_COUNT] = {};
+};
+
+namespace ba {
+
+// kernel timing helpers (active when opt.profile != 0)
+void ktimer_begin(ba_problem *p, int k, cudaEvent_t *a);
+void ktimer_end(ba_problem *p, int k, cudaEvent_t a);
+ba_status ktimer_flush(ba_problem *p);
+
+// launchers (kernels in the .cu files); each returns cudaGetLastError()
+cudaError_t launch_prepare_state(ba_problem *p, StateBuf &s);
+cudaError_t launch_linearize(ba_problem *p);
+cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial);
+cudaError_t launch_form_rcs(ba_problem *p, double lambda);
+cudaError_t launch_pcg_init(ba_problem *p, const void *rhs_T, double tol, int max_iters);
+cudaError_t launch_pcg_iter(ba_problem *p, int it);
+cudaError_t launch_resid64(ba_problem *p, bool from_x64);
+cudaError_t launch_solution_to_step(ba_problem *p);
+cudaError_t launch_refine_rhs(ba_problem *p, void *rhs_T);
+cudaError_t launch_back_substitute(ba_problem *p);
+cudaError_t launch_apply_update(ba_problem *p);
+cudaError_t launch_eval(ba_problem *p);
+
+}  // namespace ba

@@ -1,0 +1,261 @@
+// Host-side symbolic phase of libba (runs once per problem, no GPU needed).
+//
+// * validation of the observation set;
+// * a spatial (Morton) order of the points so that a run of points touches a
+//   compact set of cameras (the paper groups points "naively" with equal
+//   counts, Sec. 6.1; a spatial order makes each group's sub-RCS small);
+// * observations sorted by (point, camera): the track CSR;
+// * the BSMC pattern: every diagonal block plus each (i < j) whose cameras
+//   share a point, rows in order, columns ascending, diagonal first (Sec. 4,
+//   Fig. 4);
+// * point groups (one CTA each) with their local sub-RCS blocks; each local
+//   block gets its global block id by a binary search in row i of the BSMC
+//   column ids (the "second operation" of Table 1, cost log2 s_i);
+// * the per-global-block list of partials for the segmented reduction that
+//   sums the sub-RCSs into the global RCS (Sec. 6.1 aggregation).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "ba_internal.h"
+
+namespace ba {
+
+static uint64_t spread3(uint64_t v) {
+    // spread the low 21 bits of v so that bit k moves to bit 3k
+    v &= 0x1fffffULL;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+static void morton_order(int64_t P, const double *pts, std::vector<int64_t> &perm) {
+    perm.resize(P);
+    std::iota(perm.begin(), perm.end(), 0);
+    if (!pts) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t k = 0; k < P; ++k)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], pts[3 * k + d]);
+            hi[d] = std::max(hi[d], pts[3 * k + d]);
+        }
+    // one scale for all axes: a flat scene keeps its thin axis in the low bits
+    double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-30});
+    const double q = double((1 << 21) - 1) / ext;
+    std::vector<std::pair<uint64_t, int64_t>> key(P);
+    for (int64_t k = 0; k < P; ++k) {
+        uint64_t c = 0;
+        for (int d = 0; d < 3; ++d) {
+            double t = (pts[3 * k + d] - lo[d]) * q;
+            uint64_t u = (uint64_t)std::min(std::max(t, 0.0), double((1 << 21) - 1));
+            c |= spread3(u) << d;
+        }
+        key[k] = {c, k};
+    }
+    std::sort(key.begin(), key.end());
+    for (int64_t k = 0; k < P; ++k) perm[k] = key[k].second;
+}
+
+static int32_t find_block(const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
+                          int32_t i, int32_t j) {
+    // Table 1, second operation: binary search of column j in BSMC row i
+    auto b = col.begin() + row_ptr[i], e = col.begin() + row_ptr[i + 1];
+    auto it = std::lower_bound(b, e, j);
+    if (it == e || *it != j) return -1;
+    return (int32_t)(it - col.begin());
+}
+
+ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam,
+                         const int64_t *obs_pt, const double *pts, int obs_max, bool pattern_only,
+                         HostSetup &hs, std::string &err) {
+    if (n <= 0 || P <= 0 || m <= 0) { err = "n_cams, n_pts and n_obs must be positive"; return BA_ERR_INVALID_ARG; }
+    if (m >= (int64_t)INT32_MAX || P >= (int64_t)INT32_MAX) { err = "n_obs and n_pts must be < 2^31"; return BA_ERR_INVALID_ARG; }
+    if (!obs_cam || !obs_pt) { err = "null observation index array"; return BA_ERR_INVALID_ARG; }
+    for (int64_t a = 0; a < m; ++a) {
+        if (obs_cam[a] < 0 || obs_cam[a] >= n) { err = "obs_cam[" + std::to_string(a) + "] out of range"; return BA_ERR_INVALID_ARG; }
+        if (obs_pt[a] < 0 || obs_pt[a] >= P) { err = "obs_pt[" + std::to_string(a) + "] out of range"; return BA_ERR_INVALID_ARG; }
+    }
+    // ---- point order and its inverse
+    morton_order(P, pattern_only ? nullptr : pts, hs.pt_perm);
+    std::vector<int32_t> pt_inv(P);
+    for (int64_t k = 0; k < P; ++k) pt_inv[hs.pt_perm[k]] = (int32_t)k;
+
+    // ---- track CSR: counting sort by internal point, then by camera in each track
+    hs.trk_ptr.assign(P + 1, 0);
+    for (int64_t a = 0; a < m; ++a) hs.trk_ptr[pt_inv[obs_pt[a]] + 1]++;
+    for (int64_t k = 0; k < P; ++k) {
+        if (hs.trk_ptr[k + 1] < 2) {
+            err = "point " + std::to_string(hs.pt_perm[k]) + " has fewer than two observations";
+            return BA_ERR_INVALID_ARG;
+        }
+        hs.trk_ptr[k + 1] += hs.trk_ptr[k];
+    }
+    hs.obs_perm.assign(m, 0);
+    {
+        std::vector<int32_t> fill(hs.trk_ptr.begin(), hs.trk_ptr.end() - 1);
+        for (int64_t a = 0; a < m; ++a) hs.obs_perm[fill[pt_inv[obs_pt[a]]]++] = a;
+    }
+    hs.obs_cam.resize(m);
+    hs.obs_pt.resize(m);
+    for (int64_t k = 0; k < P; ++k) {
+        int64_t b = hs.trk_ptr[k], e = hs.trk_ptr[k + 1];
+        std::sort(hs.obs_perm.begin() + b, hs.obs_perm.begin() + e,
+                  [&](int64_t x, int64_t y) { return obs_cam[x] < obs_cam[y] || (obs_cam[x] == obs_cam[y] && x < y); });
+        for (int64_t a = b; a < e; ++a) {
+            hs.obs_cam[a] = obs_cam[hs.obs_perm[a]];
+            hs.obs_pt[a] = (int32_t)k;
+            if (a > b && hs.obs_cam[a] == hs.obs_cam[a - 1]) {
+                err = "duplicate observation of point " + std::to_string(hs.pt_perm[k]) + " by camera " +
+                      std::to_string(hs.obs_cam[a]);
+                return BA_ERR_INVALID_ARG;
+            }
+        }
+    }
+    // ---- camera -> observations
+    std::vector<int64_t> cam_ptr(n + 1, 0);
+    for (int64_t a = 0; a < m; ++a) cam_ptr[hs.obs_cam[a] + 1]++;
+    for (int32_t i = 0; i < n; ++i) {
+        if (cam_ptr[i + 1] == 0) { err = "camera " + std::to_string(i) + " has no observation"; return BA_ERR_INVALID_ARG; }
+        cam_ptr[i + 1] += cam_ptr[i];
+    }
+    std::vector<int32_t> cam_obs(m);
+    {
+        std::vector<int64_t> fill(cam_ptr.begin(), cam_ptr.end() - 1);
+        for (int64_t a = 0; a < m; ++a) cam_obs[fill[hs.obs_cam[a]]++] = (int32_t)a;
+    }
+    // ---- BSMC pattern (Sec. 4): row i = {i} U {j > i sharing a point with i}
+    hs.row_ptr.assign(n + 1, 0);
+    hs.col.clear();
+    {
+        std::vector<int32_t> stamp(n, -1), row;
+        for (int32_t i = 0; i < n; ++i) {
+            row.clear();
+            for (int64_t q = cam_ptr[i]; q < cam_ptr[i + 1]; ++q) {
+                int32_t k = hs.obs_pt[cam_obs[q]];
+                for (int32_t bb = hs.trk_ptr[k]; bb < hs.trk_ptr[k + 1]; ++bb) {
+                    int32_t j = hs.obs_cam[bb];
+                    if (j > i && stamp[j] != i) { stamp[j] = i; row.push_back(j); }
+                }
+            }
+            std::sort(row.begin(), row.end());
+            hs.col.push_back(i);
+            hs.col.insert(hs.col.end(), row.begin(), row.end());
+            if (hs.col.size() >= (size_t)INT32_MAX) { err = "more than 2^31 BSMC blocks"; return BA_ERR_INVALID_ARG; }
+            hs.row_ptr[i + 1] = (int32_t)hs.col.size();
+        }
+    }
+    if (pattern_only) return BA_OK;
+
+    // ---- point groups with their sub-RCS blocks (Sec. 6.1)
+    const int64_t nnzb = (int64_t)hs.col.size();
+    std::vector<int32_t> lb_stamp(nnzb, -1), lb_local(nnzb, 0);
+    std::vector<int32_t> g_gblk;                    // local block -> global block (current group)
+    std::vector<std::pair<int32_t, uint32_t>> g_c;  // (local block, a | b << 16)
+    std::vector<int32_t> trk_g;                     // global ids of the current track's pairs
+    hs.groups.clear();
+    hs.lb_info.clear();
+    hs.lb_gblk.clear();
+    hs.contrib.clear();
+    hs.n_pairs = 0;
+    GroupDesc g{};
+    int32_t gid = 0;
+    auto close_group = [&]() {
+        if (g.npts == 0) return;
+        const int32_t nlb = (int32_t)g_gblk.size();
+        std::vector<int32_t> cnt(nlb, 0);
+        for (auto &c : g_c) cnt[c.first]++;
+        // local blocks by contribution count (descending) so that neighbouring
+        // threads of the CTA run loops of similar length; ties by global id
+        std::vector<int32_t> ord(nlb);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+            return cnt[x] > cnt[y] || (cnt[x] == cnt[y] && g_gblk[x] < g_gblk[y]);
+        });
+        std::vector<int32_t> pos(nlb), start(nlb + 1, 0);
+        for (int32_t r = 0; r < nlb; ++r) pos[ord[r]] = r;
+        for (int32_t r = 0; r < nlb; ++r) start[r + 1] = start[r] + cnt[ord[r]];
+        g.c_begin = (int64_t)hs.contrib.size();
+        g.lb_begin = (int64_t)hs.lb_info.size();
+        g.nlb = nlb;
+        g.nc = (int32_t)g_c.size();
+        hs.contrib.resize(hs.contrib.size() + g_c.size());
+        std::vector<int32_t> fill(start.begin(), start.end() - 1);
+        for (auto &c : g_c) hs.contrib[g.c_begin + fill[pos[c.first]]++] = c.second;  // stable: point order
+        for (int32_t r = 0; r < nlb; ++r) {
+            int32_t gb = g_gblk[ord[r]];
+            int32_t i = 0;
+            // the block is diagonal iff its column is the first of its row
+            bool diag = false;
+            {
+                auto it = std::upper_bound(hs.row_ptr.begin(), hs.row_ptr.end(), gb);
+                i = (int32_t)(it - hs.row_ptr.begin()) - 1;
+                diag = (hs.row_ptr[i] == gb);
+            }
+            hs.lb_info.push_back((uint32_t)start[r] | ((uint32_t)cnt[ord[r]] << 16) | (diag ? 0x80000000u : 0u));
+            hs.lb_gblk.push_back(gb);
+        }
+        hs.groups.push_back(g);
+        g_gblk.clear();
+        g_c.clear();
+        ++gid;
+        g = GroupDesc{};
+    };
+    for (int64_t k = 0; k < P; ++k) {
+        const int32_t tb = hs.trk_ptr[k], L = hs.trk_ptr[k + 1] - tb;
+        const int32_t npair = L * (L + 1) / 2;
+        trk_g.clear();
+        int32_t fresh = 0;
+        for (int32_t x = 0; x < L; ++x)
+            for (int32_t y = x; y < L; ++y) {
+                int32_t gb = find_block(hs.row_ptr, hs.col, hs.obs_cam[tb + x], hs.obs_cam[tb + y]);
+                if (gb < 0) { err = "internal: pair missing from the BSMC pattern"; return BA_ERR_INTERNAL; }
+                trk_g.push_back(gb);
+                if (lb_stamp[gb] != gid) ++fresh;  // may count a repeated block twice; conservative
+            }
+        if (L > obs_max || npair > C_MAX || npair > LB_MAX) {
+            err = "point " + std::to_string(hs.pt_perm[k]) + " has a track of " + std::to_string(L) +
+                  " observations; the limit is " + std::to_string(std::min(obs_max, 180));
+            return BA_ERR_INVALID_ARG;
+        }
+        if (g.npts > 0 && (g.nobs + L > obs_max || g.nc + npair > C_MAX || (int32_t)g_gblk.size() + fresh > LB_MAX))
+            close_group();
+        if (g.npts == 0) { g.obs_begin = tb; g.pt_begin = (int32_t)k; }
+        int32_t q = 0;
+        for (int32_t x = 0; x < L; ++x)
+            for (int32_t y = x; y < L; ++y, ++q) {
+                int32_t gb = trk_g[q];
+                if (lb_stamp[gb] != gid) {
+                    lb_stamp[gb] = gid;
+                    lb_local[gb] = (int32_t)g_gblk.size();
+                    g_gblk.push_back(gb);
+                }
+                uint32_t a = (uint32_t)(tb + x - g.obs_begin), b = (uint32_t)(tb + y - g.obs_begin);
+                g_c.push_back({lb_local[gb], a | (b << 16)});
+            }
+        g.nobs += L;
+        g.nc += npair;
+        g.npts += 1;
+        hs.n_pairs += npair;
+    }
+    close_group();
+    if (hs.lb_info.size() >= (size_t)INT32_MAX) { err = "more than 2^31 partial blocks"; return BA_ERR_INVALID_ARG; }
+    // ---- partials of each global block (segmented-reduction CSR), in group order
+    hs.pptr.assign(nnzb + 1, 0);
+    for (int32_t gb : hs.lb_gblk) hs.pptr[gb + 1]++;
+    for (int64_t b = 0; b < nnzb; ++b) {
+        if (hs.pptr[b + 1] == 0) { err = "internal: BSMC block without partial"; return BA_ERR_INTERNAL; }
+        hs.pptr[b + 1] += hs.pptr[b];
+    }
+    hs.plist.assign(hs.lb_gblk.size(), 0);
+    {
+        std::vector<int32_t> fill(hs.pptr.begin(), hs.pptr.end() - 1);
+        for (size_t r = 0; r < hs.lb_gblk.size(); ++r) hs.plist[fill[hs.lb_gblk[r]]++] = (int32_t)r;
+    }
+    return BA_OK;
+}
+
+}  // namespace ba

@@ -1,0 +1,178 @@
+// Device helpers shared by the libba kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ba_internal.h"
+
+namespace ba {
+
+template <typename T> struct Vec;  // not used directly
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum NV doubles over the CTA; the result is valid in every lane of warp 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[w * NV + i] = v[i];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = warp_sum(lane < nw ? sh[lane * NV + i] : 0.0);
+    }
+    __syncthreads();
+}
+
+// Deterministic grid-wide sum: every CTA stores its partial, the last CTA to
+// arrive (a counter, no waiting) adds the partials in CTA order and thread 0
+// runs fin(totals).  Must be the last thing a kernel does; every thread of
+// every CTA must call it.
+template <int NV, class Fin>
+__device__ __forceinline__ void grid_sum(double (&v)[NV], double *part, unsigned *counter, Fin fin) {
+    __shared__ double sh[32 * NV];
+    __shared__ bool last;
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) part[blockIdx.x * NV + i] = v[i];
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + b * NV + i);
+    block_sum<NV>(acc, sh);
+    if (threadIdx.x == 0) {
+        fin(acc);
+        *counter = 0;
+        __threadfence();
+    }
+}
+
+template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
+template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
+
+__device__ __forceinline__ double clampd(double x) { return x < 1e-6 ? 1e-6 : (x > 1e32 ? 1e32 : x); }
+
+// In-place Cholesky of a symmetric 6x6 (row-major, lower triangle used) and
+// the inverse A^-1 = L^-T L^-1 written full.  Returns false if not SPD.
+template <typename T>
+__device__ bool spd_inverse6(const T *A, T *Ainv) {
+    T L[21];  // packed lower: L[i*(i+1)/2 + j]
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            T s = A[i * 6 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+            if (i == j) {
+                if (!(s > T(0))) return false;
+                L[i * (i + 1) / 2 + i] = sqrt(s);
+            } else {
+                L[i * (i + 1) / 2 + j] = s / L[j * (j + 1) / 2 + j];
+            }
+        }
+    }
+    // Li = L^-1 (lower)
+    T Li[21];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        Li[i * (i + 1) / 2 + i] = T(1) / L[i * (i + 1) / 2 + i];
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int k = j; k < i; ++k) s += L[i * (i + 1) / 2 + k] * Li[k * (k + 1) / 2 + j];
+            Li[i * (i + 1) / 2 + j] = -s * Li[i * (i + 1) / 2 + i];
+        }
+    }
+    // A^-1 = Li^T Li
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i; j < 6; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int k = j; k < 6; ++k) s += Li[k * (k + 1) / 2 + i] * Li[k * (k + 1) / 2 + j];
+            Ainv[i * 6 + j] = s;
+            Ainv[j * 6 + i] = s;
+        }
+    return true;
+}
+
+// Quaternion (w, x, y, z) of the rotation vector v.
+__device__ __forceinline__ void quat_exp(const double *v, double *q) {
+    const double th2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const double th = sqrt(th2);
+    double s, c;
+    if (th < 1e-8) {
+        s = 0.5 - th2 / 48.0;
+        c = 1.0 - th2 / 8.0;
+    } else {
+        s = sin(0.5 * th) / th;
+        c = cos(0.5 * th);
+    }
+    q[0] = c;
+    q[1] = s * v[0];
+    q[2] = s * v[1];
+    q[3] = s * v[2];
+}
+
+// Rotation vector of a unit quaternion (shortest rotation).
+__device__ __forceinline__ void quat_log(const double *qin, double *v) {
+    double q[4] = {qin[0], qin[1], qin[2], qin[3]};
+    if (q[0] < 0) { q[0] = -q[0]; q[1] = -q[1]; q[2] = -q[2]; q[3] = -q[3]; }
+    const double s = sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double f;
+    if (s < 1e-8) {
+        f = 2.0 / q[0] * (1.0 - s * s / (3.0 * q[0] * q[0]));
+    } else {
+        f = 2.0 * atan2(s, q[0]) / s;
+    }
+    v[0] = f * q[1];
+    v[1] = f * q[2];
+    v[2] = f * q[3];
+}
+
+__device__ __forceinline__ void quat_mul(const double *a, const double *b, double *o) {
+    o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+// Row-major rotation matrix of a unit quaternion.
+__device__ __forceinline__ void quat_to_R(const double *q, double *R) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+template <typename T> __device__ __forceinline__ void red_add(T *p, T v) { atomicAdd(p, v); }
+
+}  // namespace ba

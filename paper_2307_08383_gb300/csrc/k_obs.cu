@@ -1,0 +1,359 @@
+// Per-observation kernels: state caches, linearization (residuals and
+// Jacobians of Eq. 1), the cost F = 1/2 sum rho(||e||^2), the pose update and
+// the trial evaluation (cost and model decrease for the LM gain ratio).
+//
+// Camera model: X_cam = R(omega) X + t, u = fx x/z + cx, v = fy y/z + cy,
+// e = (u, v) - u_obs.  The pose is perturbed in the camera frame,
+// X_cam <- Exp(d_omega) X_cam + dt, so dX_cam/d(d_omega) = -[X_cam]x,
+// dX_cam/d(dt) = I and dX_cam/dX = R.
+//
+// FP32 mode keeps the state in FP64 and evaluates X_cam = R (X - C) with
+// X and the camera centre C = -R^T t split into FP32 hi + lo parts, so the
+// subtraction of two large world coordinates loses nothing before the FP32
+// rotation.
+#include "device_util.cuh"
+
+namespace ba {
+
+struct Intr {
+    double fx, fy, cx, cy;
+};
+
+// --------------------------------------------------------------------------
+// state caches
+// --------------------------------------------------------------------------
+__global__ void k_prepare_cams64(int n, const double *__restrict__ cams, double *__restrict__ camc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double q[4], R[9];
+    quat_exp(cams + 6 * i, q);
+    quat_to_R(q, R);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) camc[12 * i + k] = R[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) camc[12 * i + 9 + k] = cams[6 * i + 3 + k];
+}
+
+__global__ void k_prepare_cams32(int n, const double *__restrict__ cams, float *__restrict__ camc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double q[4], R[9];
+    quat_exp(cams + 6 * i, q);
+    quat_to_R(q, R);
+    const double *t = cams + 6 * i + 3;
+    float *o = camc + 16 * i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) o[k] = (float)R[k];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double C = -(R[0 + d] * t[0] + R[3 + d] * t[1] + R[6 + d] * t[2]);
+        const float hi = (float)C;
+        o[9 + d] = hi;
+        o[12 + d] = (float)(C - (double)hi);
+    }
+    o[15] = 0.f;
+}
+
+__global__ void k_split_pts(int64_t P, const double *__restrict__ pts, float *__restrict__ hl) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double x = pts[3 * k + d];
+            const float hi = (float)x;
+            hl[6 * k + d] = hi;
+            hl[6 * k + 3 + d] = (float)(x - (double)hi);
+        }
+    }
+}
+
+// X_cam of observation (camera i, point k) in the mode precision.
+__device__ __forceinline__ void cam_point(const double *camc, const double *pts, const float *, int i, int k,
+                                          double *Xc, double *R) {
+    const double *c = camc + 12 * i;
+    const double X0 = pts[3 * k], X1 = pts[3 * k + 1], X2 = pts[3 * k + 2];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) R[r] = c[r];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Xc[r] = R[3 * r] * X0 + R[3 * r + 1] * X1 + R[3 * r + 2] * X2 + c[9 + r];
+}
+__device__ __forceinline__ void cam_point(const float *camc, const double *, const float *hl, int i, int k,
+                                          float *Xc, float *R) {
+    const float4 *c4 = reinterpret_cast<const float4 *>(camc + 16 * i);
+    const float4 a = c4[0], b = c4[1], c = c4[2], d = c4[3];
+    R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w; R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w; R[8] = c.x;
+    const float Chi[3] = {c.y, c.z, c.w}, Clo[3] = {d.x, d.y, d.z};
+    const float *h = hl + 6 * (int64_t)k;
+    float D[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) D[r] = (h[r] - Chi[r]) + (h[3 + r] - Clo[r]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Xc[r] = R[3 * r] * D[0] + R[3 * r + 1] * D[1] + R[3 * r + 2] * D[2];
+}
+
+__device__ __forceinline__ double huber_rho(double s, int on, double delta) {
+    if (!on || s <= delta * delta) return s;
+    return 2.0 * delta * sqrt(s) - delta * delta;
+}
+
+// --------------------------------------------------------------------------
+// K1: residuals and Jacobians, one thread per observation
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_linearize(int64_t m, const int *__restrict__ obs_cam, const int *__restrict__ obs_pt,
+                                                   const T *__restrict__ uv, const T *__restrict__ camc,
+                                                   const double *__restrict__ pts, const float *__restrict__ pts_hl,
+                                                   Intr in, int huber, double delta, T *__restrict__ J) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
+        const int i = obs_cam[a], k = obs_pt[a];
+        T Xc[3], R[9];
+        cam_point(camc, pts, pts_hl, i, k, Xc, R);
+        const T iz = T(1) / Xc[2];
+        const T xh = Xc[0] * iz, yh = Xc[1] * iz;
+        T e0 = T(in.fx) * xh + T(in.cx) - uv[2 * a];
+        T e1 = T(in.fy) * yh + T(in.cy) - uv[2 * a + 1];
+        // dpi/dX_cam = [[a0, 0, a2], [0, a1, a3]]
+        const T a0 = T(in.fx) * iz, a2 = -T(in.fx) * xh * iz;
+        const T a1 = T(in.fy) * iz, a3 = -T(in.fy) * yh * iz;
+        T o[JW];
+        // rotation columns: dpi/dX_cam * (-[X_cam]x)
+        o[0] = a2 * Xc[1];
+        o[1] = a0 * Xc[2] - a2 * Xc[0];
+        o[2] = -a0 * Xc[1];
+        o[6] = -a1 * Xc[2] + a3 * Xc[1];
+        o[7] = -a3 * Xc[0];
+        o[8] = a1 * Xc[0];
+        // translation columns: dpi/dX_cam
+        o[3] = a0; o[4] = T(0); o[5] = a2;
+        o[9] = T(0); o[10] = a1; o[11] = a3;
+        // point columns: dpi/dX_cam * R
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o[12 + c] = a0 * R[c] + a2 * R[6 + c];
+            o[15 + c] = a1 * R[3 + c] + a3 * R[6 + c];
+        }
+        if (huber) {
+            const double s = (double)e0 * e0 + (double)e1 * e1;
+            if (s > delta * delta) {
+                const T sw = (T)sqrt(delta / sqrt(s));
+#pragma unroll
+                for (int q = 0; q < 18; ++q) o[q] *= sw;
+                e0 *= sw;
+                e1 *= sw;
+            }
+        }
+        o[18] = e0;
+        o[19] = e1;
+        T *dst = J + a * JW;
+        if constexpr (sizeof(T) == 4) {
+            float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) d4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        } else {
+            double2 *d2 = reinterpret_cast<double2 *>(dst);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) d2[q] = make_double2(o[2 * q], o[2 * q + 1]);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// F = 1/2 sum rho(||e||^2) (FP64 sum) and the cheirality count
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__ obs_cam, const int *__restrict__ obs_pt,
+                                              const T *__restrict__ uv, const T *__restrict__ camc,
+                                              const double *__restrict__ pts, const float *__restrict__ pts_hl,
+                                              Intr in, int huber, double delta, DevScalars *sc, int trial,
+                                              double *red, unsigned *ctr) {
+    double v[2] = {0.0, 0.0};
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
+        const int i = obs_cam[a], k = obs_pt[a];
+        T Xc[3], R[9];
+        cam_point(camc, pts, pts_hl, i, k, Xc, R);
+        const T iz = T(1) / Xc[2];
+        const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
+        const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
+        v[0] += huber_rho((double)e0 * e0 + (double)e1 * e1, huber, delta);
+        v[1] += (Xc[2] <= T(1e-6)) ? 1.0 : 0.0;
+    }
+    grid_sum<2>(v, red, ctr, [&](double *t) {
+        if (trial) {
+            sc->cost_trial = 0.5 * t[0];
+            sc->n_cheir_trial = (unsigned long long)t[1];
+        } else {
+            sc->cost = 0.5 * t[0];
+            sc->n_cheir = (unsigned long long)t[1];
+        }
+    });
+}
+
+// --------------------------------------------------------------------------
+// trial point: R <- Exp(dw) R, t <- Exp(dw) t + dt, X <- X + dX
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void k_update_cams(int n, const double *__restrict__ cams, const T *__restrict__ dxc, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double w[3], q[4], qd[4], qn[4], Rd[9];
+    const double dw[3] = {(double)dxc[6 * i], (double)dxc[6 * i + 1], (double)dxc[6 * i + 2]};
+    quat_exp(cams + 6 * i, q);
+    quat_exp(dw, qd);
+    quat_mul(qd, q, qn);
+    const double nn = rsqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qn[k] *= nn;
+    quat_log(qn, w);
+    quat_to_R(qd, Rd);
+    const double *t = cams + 6 * i + 3;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        out[6 * i + r] = w[r];
+        out[6 * i + 3 + r] = Rd[3 * r] * t[0] + Rd[3 * r + 1] * t[1] + Rd[3 * r + 2] * t[2] + (double)dxc[6 * i + 3 + r];
+    }
+}
+
+template <typename T>
+__global__ void k_update_pts(int64_t P, const double *__restrict__ pts, const T *__restrict__ dxp, double *__restrict__ out) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < 3 * P; x += (int64_t)gridDim.x * blockDim.x)
+        out[x] = pts[x] + (double)dxp[x];
+}
+
+// --------------------------------------------------------------------------
+// trial evaluation: F(x (+) dx) and the model decrease
+// 1/2 (||e||^2 - ||e + J dx||^2) = -1/2 sum_a (J_a dx)^T (2 e_a + J_a dx)
+// (weighted e and J under the Huber loss), both summed in FP64
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_eval(int64_t m, const int *__restrict__ obs_cam, const int *__restrict__ obs_pt,
+                                              const T *__restrict__ uv, const T *__restrict__ camc,
+                                              const double *__restrict__ pts, const float *__restrict__ pts_hl,
+                                              const T *__restrict__ J, const T *__restrict__ dxc,
+                                              const T *__restrict__ dxp, Intr in, int huber, double delta,
+                                              DevScalars *sc, double *red, unsigned *ctr) {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
+        const int i = obs_cam[a], k = obs_pt[a];
+        T Xc[3], R[9];
+        cam_point(camc, pts, pts_hl, i, k, Xc, R);
+        const T iz = T(1) / Xc[2];
+        const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
+        const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
+        v[0] += huber_rho((double)e0 * e0 + (double)e1 * e1, huber, delta);
+        v[2] += (Xc[2] <= T(1e-6)) ? 1.0 : 0.0;
+        const T *j = J + a * JW;
+        T dc[6], dp[3];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dc[c] = dxc[6 * i + c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dp[c] = dxp[3 * (int64_t)k + c];
+        T jd0 = T(0), jd1 = T(0);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { jd0 += j[c] * dc[c]; jd1 += j[6 + c] * dc[c]; }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { jd0 += j[12 + c] * dp[c]; jd1 += j[15 + c] * dp[c]; }
+        v[1] -= (double)jd0 * (2.0 * (double)j[18] + (double)jd0) + (double)jd1 * (2.0 * (double)j[19] + (double)jd1);
+    }
+    grid_sum<3>(v, red, ctr, [&](double *t) {
+        sc->cost_trial = 0.5 * t[0];
+        sc->model = 0.5 * t[1];
+        sc->n_cheir_trial = (unsigned long long)t[2];
+    });
+}
+
+// --------------------------------------------------------------------------
+// launchers
+// --------------------------------------------------------------------------
+static inline int grid_for(int64_t work, int threads, int cap) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+static constexpr int GRID_CAP = 152 * 8;  // 152 SMs x 8 resident 256-thread CTAs
+
+static Intr intr_of(const ba_problem *p) { return Intr{p->opt.fx, p->opt.fy, p->opt.cx, p->opt.cy}; }
+
+cudaError_t launch_prepare_state(ba_problem *p, StateBuf &s) {
+    cudaEvent_t ev;
+    ktimer_begin(p, K_PREPARE, &ev);
+    const int nb = (p->n + 127) / 128;
+    if (p->fp32) {
+        k_prepare_cams32<<<nb, 128, 0, p->st>>>(p->n, s.cams, (float *)s.camc);
+        k_split_pts<<<grid_for(p->P, 256, GRID_CAP), 256, 0, p->st>>>(p->P, s.pts, s.pts_hl);
+    } else {
+        k_prepare_cams64<<<nb, 128, 0, p->st>>>(p->n, s.cams, (double *)s.camc);
+    }
+    ktimer_end(p, K_PREPARE, ev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_linearize(ba_problem *p) {
+    cudaEvent_t ev;
+    ktimer_begin(p, K_LINEARIZE, &ev);
+    const int g = grid_for(p->m, 256, GRID_CAP * 4);
+    const int hub = p->opt.robust == BA_LOSS_HUBER;
+    if (p->fp32)
+        k_linearize<float><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv32, (const float *)p->cur.camc,
+                                                 p->cur.pts, p->cur.pts_hl, intr_of(p), hub, p->opt.huber_delta,
+                                                 (float *)p->J);
+    else
+        k_linearize<double><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv64, (const double *)p->cur.camc,
+                                                  p->cur.pts, nullptr, intr_of(p), hub, p->opt.huber_delta,
+                                                  (double *)p->J);
+    ktimer_end(p, K_LINEARIZE, ev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial) {
+    cudaEvent_t ev;
+    ktimer_begin(p, K_COST, &ev);
+    const int g = grid_for(p->m, 256, GRID_CAP);
+    const int hub = p->opt.robust == BA_LOSS_HUBER;
+    if (p->fp32)
+        k_cost<float><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv32, (const float *)s.camc, s.pts,
+                                            s.pts_hl, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
+                                            p->red, p->counters + 0);
+    else
+        k_cost<double><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv64, (const double *)s.camc, s.pts,
+                                             nullptr, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
+                                             p->red, p->counters + 0);
+    ktimer_end(p, K_COST, ev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_update(ba_problem *p) {
+    cudaEvent_t ev;
+    ktimer_begin(p, K_UPDATE, &ev);
+    const int nb = (p->n + 127) / 128;
+    const int gp = grid_for(3 * p->P, 256, GRID_CAP);
+    if (p->fp32) {
+        k_update_cams<float><<<nb, 128, 0, p->st>>>(p->n, p->cur.cams, (const float *)p->dxc, p->trial.cams);
+        k_update_pts<float><<<gp, 256, 0, p->st>>>(p->P, p->cur.pts, (const float *)p->dxp, p->trial.pts);
+    } else {
+        k_update_cams<double><<<nb, 128, 0, p->st>>>(p->n, p->cur.cams, (const double *)p->dxc, p->trial.cams);
+        k_update_pts<double><<<gp, 256, 0, p->st>>>(p->P, p->cur.pts, (const double *)p->dxp, p->trial.pts);
+    }
+    ktimer_end(p, K_UPDATE, ev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval(ba_problem *p) {
+    cudaEvent_t ev;
+    ktimer_begin(p, K_EVAL, &ev);
+    const int g = grid_for(p->m, 256, GRID_CAP);
+    const int hub = p->opt.robust == BA_LOSS_HUBER;
+    if (p->fp32)
+        k_eval<float><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv32, (const float *)p->trial.camc,
+                                            p->trial.pts, p->trial.pts_hl, (const float *)p->J, (const float *)p->dxc,
+                                            (const float *)p->dxp, intr_of(p), hub, p->opt.huber_delta, p->sc,
+                                            p->red, p->counters + 1);
+    else
+        k_eval<double><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv64, (const double *)p->trial.camc,
+                                             p->trial.pts, nullptr, (const double *)p->J, (const double *)p->dxc,
+                                             (const double *)p->dxp, intr_of(p), hub, p->opt.huber_delta, p->sc,
+                                             p->red, p->counters + 1);
+    ktimer_end(p, K_EVAL, ev);
+    return cudaGetLastError();
+}
+
+}  // namespace ba

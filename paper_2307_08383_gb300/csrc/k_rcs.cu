@@ -1,0 +1,284 @@
+// Formation of the reduced camera system (Eq. 4) point group by point group
+// (Sec. 5, Sec. 6.1), its aggregation into BSMC (Sec. 4) and the block-Jacobi
+// preconditioner (Sec. 3.2).
+//
+// Per point k with observations a (camera i_a) the damped V_k = sum J_p^T J_p
+// + lambda clamp(diag) is factored V_k = L L^T.  With P_a = J_p,a L^-T (2x3),
+// q_k = L^-1 l_p,k and e^_a = e_a + P_a q_k the point's sub-RCS is
+//   S_(i_a, i_b) -= J_c,a^T (P_a P_b^T) J_c,b          (a != b, i_a < i_b)
+//   S_(i_a, i_a) += J_c,a^T (I - P_a P_a^T) J_c,a      (U and -W V^-1 W^T)
+//   b_(i_a)      -= J_c,a^T e^_a                         (l_c - W V^-1 l_p)
+// which is W V^-1 W^T = (J_c^T P)(J_c^T P)^T written through the 2x2 middle
+// factors.  A CTA owns a group of whole tracks: it stages the group's
+// Jacobian rows in shared memory, turns J_p and e into P and e^ in place, then
+// each thread accumulates whole local blocks (sub-RCS blocks) in registers
+// over the precomputed (a, b) products of that block - no atomics - and writes
+// them as partials.  A segmented sum over the partials of each global block
+// (precomputed CSR) then forms S, adds lambda clamp(diag U) on the diagonal,
+// and inverts the diagonal blocks for the preconditioner.
+#include "device_util.cuh"
+
+namespace ba {
+
+__host__ __device__ constexpr int up_idx(int r, int c) { return 6 * r - r * (r - 1) / 2 + (c - r); }
+
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__restrict__ grp,
+                                                           const uint32_t *__restrict__ lb_info,
+                                                           const uint32_t *__restrict__ contrib,
+                                                           const int *__restrict__ trk_ptr, const T *__restrict__ J,
+                                                           double lambda, T *__restrict__ part, T *__restrict__ Linv_out,
+                                                           T *__restrict__ lp_out, DevScalars *sc, int fp64_v) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *so = reinterpret_cast<T *>(smem_raw);  // [nobs][JW]: J_c (12) | J_p -> P (6) | e -> e^ (2)
+    const GroupDesc g = grp[blockIdx.x];
+
+    // 1) stage the group's Jacobian rows (contiguous, 16-byte aligned)
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(J + (int64_t)g.obs_begin * JW);
+        int4 *dst = reinterpret_cast<int4 *>(so);
+        const int nvec = g.nobs * JW * (int)sizeof(T) / 16;
+        for (int t = threadIdx.x; t < nvec; t += blockDim.x) dst[t] = __ldg(src + t);
+    }
+    __syncthreads();
+
+    // 2) per point: V_k, its Cholesky factor, q_k; J_p -> P and e -> e^ in place
+    for (int pl = threadIdx.x; pl < g.npts; pl += blockDim.x) {
+        const int k = g.pt_begin + pl;
+        const int a0 = trk_ptr[k] - g.obs_begin, a1 = trk_ptr[k + 1] - g.obs_begin;
+        T v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0, l0 = 0, l1 = 0, l2 = 0;
+        for (int a = a0; a < a1; ++a) {
+            const T *s = so + a * JW;
+            const T p0 = s[12], p1 = s[13], p2 = s[14], r0 = s[15], r1 = s[16], r2 = s[17], e0 = s[18], e1 = s[19];
+            v00 += p0 * p0 + r0 * r0; v01 += p0 * p1 + r0 * r1; v02 += p0 * p2 + r0 * r2;
+            v11 += p1 * p1 + r1 * r1; v12 += p1 * p2 + r1 * r2; v22 += p2 * p2 + r2 * r2;
+            l0 -= p0 * e0 + r0 * e1; l1 -= p1 * e0 + r1 * e1; l2 -= p2 * e0 + r2 * e1;
+        }
+        v00 += (T)(lambda * clampd((double)v00));
+        v11 += (T)(lambda * clampd((double)v11));
+        v22 += (T)(lambda * clampd((double)v22));
+        // Cholesky V = L L^T, then M = L^-1 (lower)
+        T m00, m10, m11, m20, m21, m22;
+        bool ok;
+        {
+            const T c00 = v00;
+            const T d0 = sqrt(c00);
+            const T c10 = v01 / d0, c20 = v02 / d0;
+            const T s11 = v11 - c10 * c10;
+            const T d1 = sqrt(s11);
+            const T c21 = (v12 - c20 * c10) / d1;
+            const T s22 = v22 - c20 * c20 - c21 * c21;
+            const T d2 = sqrt(s22);
+            ok = (c00 > T(0)) && (s11 > T(0)) && (s22 > T(0));
+            m00 = T(1) / d0; m11 = T(1) / d1; m22 = T(1) / d2;
+            m10 = -c10 * m00 * m11;
+            m21 = -c21 * m11 * m22;
+            m20 = -(c20 * m00 + c21 * m10) * m22;
+        }
+        if (fp64_v && ok) {
+            // FP32 mode: refactor in FP64 when kappa~ = ||V||_F ||V^-1||_F > 1e4
+            const T i00 = m00 * m00 + m10 * m10 + m20 * m20, i11 = m11 * m11 + m21 * m21, i22 = m22 * m22;
+            const T i01 = m10 * m11 + m20 * m21, i02 = m20 * m22, i12 = m21 * m22;
+            const T nv = v00 * v00 + v11 * v11 + v22 * v22 + 2 * (v01 * v01 + v02 * v02 + v12 * v12);
+            const T ni = i00 * i00 + i11 * i11 + i22 * i22 + 2 * (i01 * i01 + i02 * i02 + i12 * i12);
+            if (nv * ni > T(1e8)) {
+                double w00 = 0, w01 = 0, w02 = 0, w11 = 0, w12 = 0, w22 = 0;
+                for (int a = a0; a < a1; ++a) {
+                    const T *s = so + a * JW;
+                    const double p0 = s[12], p1 = s[13], p2 = s[14], r0 = s[15], r1 = s[16], r2 = s[17];
+                    w00 += p0 * p0 + r0 * r0; w01 += p0 * p1 + r0 * r1; w02 += p0 * p2 + r0 * r2;
+                    w11 += p1 * p1 + r1 * r1; w12 += p1 * p2 + r1 * r2; w22 += p2 * p2 + r2 * r2;
+                }
+                w00 += lambda * clampd(w00); w11 += lambda * clampd(w11); w22 += lambda * clampd(w22);
+                const double d0 = sqrt(w00), c10 = w01 / d0, c20 = w02 / d0;
+                const double s11 = w11 - c10 * c10, d1 = sqrt(s11), c21 = (w12 - c20 * c10) / d1;
+                const double s22 = w22 - c20 * c20 - c21 * c21, d2 = sqrt(s22);
+                if (w00 > 0 && s11 > 0 && s22 > 0) {
+                    const double n00 = 1 / d0, n11 = 1 / d1, n22 = 1 / d2, n10 = -c10 * n00 * n11;
+                    const double n21 = -c21 * n11 * n22, n20 = -(c20 * n00 + c21 * n10) * n22;
+                    m00 = (T)n00; m10 = (T)n10; m11 = (T)n11; m20 = (T)n20; m21 = (T)n21; m22 = (T)n22;
+                    atomicAdd(&sc->n_v64, 1ull);
+                } else {
+                    ok = false;
+                }
+            }
+        }
+        if (!ok) {
+            atomicExch(&sc->err, (int)BA_ERR_NOT_SPD);
+            m00 = m10 = m11 = m20 = m21 = m22 = T(0);
+        }
+        const T q0 = m00 * l0, q1 = m10 * l0 + m11 * l1, q2 = m20 * l0 + m21 * l1 + m22 * l2;
+        T *lo = Linv_out + 6 * (int64_t)k;
+        lo[0] = m00; lo[1] = m10; lo[2] = m11; lo[3] = m20; lo[4] = m21; lo[5] = m22;
+        T *lpo = lp_out + 3 * (int64_t)k;
+        lpo[0] = l0; lpo[1] = l1; lpo[2] = l2;
+        for (int a = a0; a < a1; ++a) {
+            T *s = so + a * JW;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const T j0 = s[12 + 3 * r], j1 = s[13 + 3 * r], j2 = s[14 + 3 * r];
+                const T P0 = j0 * m00, P1 = j0 * m10 + j1 * m11, P2 = j0 * m20 + j1 * m21 + j2 * m22;
+                s[12 + 3 * r] = P0; s[13 + 3 * r] = P1; s[14 + 3 * r] = P2;
+                s[18 + r] += P0 * q0 + P1 * q1 + P2 * q2;
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3) local blocks: one thread owns a whole sub-RCS block
+    const uint32_t *cg = contrib + g.c_begin;
+    for (int lb = threadIdx.x; lb < g.nlb; lb += blockDim.x) {
+        const uint32_t info = lb_info[g.lb_begin + lb];
+        const int cb = (int)(info & 0xffffu), cnt = (int)((info >> 16) & 0x7fffu);
+        T *out = part + (g.lb_begin + lb) * BW;
+        if (!(info >> 31)) {
+            T acc[36];
+#pragma unroll
+            for (int q = 0; q < 36; ++q) acc[q] = T(0);
+            for (int c = cb; c < cb + cnt; ++c) {
+                const uint32_t u = cg[c];
+                const T *sa = so + (u & 0xffffu) * JW, *sb = so + (u >> 16) * JW;
+                const T M00 = sa[12] * sb[12] + sa[13] * sb[13] + sa[14] * sb[14];
+                const T M01 = sa[12] * sb[15] + sa[13] * sb[16] + sa[14] * sb[17];
+                const T M10 = sa[15] * sb[12] + sa[16] * sb[13] + sa[17] * sb[14];
+                const T M11 = sa[15] * sb[15] + sa[16] * sb[16] + sa[17] * sb[17];
+                T t0[6], t1[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    t0[j] = M00 * sb[j] + M01 * sb[6 + j];
+                    t1[j] = M10 * sb[j] + M11 * sb[6 + j];
+                }
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const T ai0 = sa[i], ai1 = sa[6 + i];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) acc[6 * i + j] -= ai0 * t0[j] + ai1 * t1[j];
+                }
+            }
+            for (int q = 0; q < 36; ++q) out[q] = acc[q];
+        } else {
+            T acc[21], du[6], bb[6];
+#pragma unroll
+            for (int q = 0; q < 21; ++q) acc[q] = T(0);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) { du[q] = T(0); bb[q] = T(0); }
+            for (int c = cb; c < cb + cnt; ++c) {
+                const T *sa = so + (cg[c] & 0xffffu) * JW;
+                const T g00 = T(1) - (sa[12] * sa[12] + sa[13] * sa[13] + sa[14] * sa[14]);
+                const T g01 = -(sa[12] * sa[15] + sa[13] * sa[16] + sa[14] * sa[17]);
+                const T g11 = T(1) - (sa[15] * sa[15] + sa[16] * sa[16] + sa[17] * sa[17]);
+                T t0[6], t1[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    t0[j] = g00 * sa[j] + g01 * sa[6 + j];
+                    t1[j] = g01 * sa[j] + g11 * sa[6 + j];
+                }
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const T ai0 = sa[i], ai1 = sa[6 + i];
+#pragma unroll
+                    for (int j = i; j < 6; ++j) acc[up_idx(i, j)] += ai0 * t0[j] + ai1 * t1[j];
+                    du[i] += ai0 * ai0 + ai1 * ai1;
+                    bb[i] -= ai0 * sa[18] + ai1 * sa[19];
+                }
+            }
+            for (int q = 0; q < 21; ++q) out[q] = acc[q];
+            for (int q = 0; q < 6; ++q) { out[21 + q] = du[q]; out[27 + q] = bb[q]; }
+            out[33] = out[34] = out[35] = T(0);
+        }
+    }
+}
+
+// K3: S[block][e] = sum of the block's partials (fixed order), one thread per value.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rcs_reduce(int64_t nval, const int *__restrict__ pptr, const int *__restrict__ plist,
+                                                    const T *__restrict__ part, T *__restrict__ S) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nval; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = x / BW;
+        const int e = (int)(x - blk * BW);
+        T s = T(0);
+        for (int q = pptr[blk]; q < pptr[blk + 1]; ++q) s += part[(int64_t)plist[q] * BW + e];
+        S[x] = s;
+    }
+}
+
+// K4: unpack the diagonal blocks, damp them, extract b, invert for M^-1.
+template <typename T>
+__global__ void k_rcs_diag(int n, const int *__restrict__ row_ptr, T *__restrict__ S, T *__restrict__ b,
+                           T *__restrict__ Minv, double lambda, DevScalars *sc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T *Sd = S + (int64_t)row_ptr[i] * BW;
+    double pk[36], A[36], Ai[36];
+#pragma unroll
+    for (int q = 0; q < 36; ++q) pk[q] = (double)Sd[q];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) {
+            A[6 * r + c] = pk[up_idx(r, c)];
+            A[6 * c + r] = pk[up_idx(r, c)];
+        }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) A[7 * r] += lambda * clampd(pk[21 + r]);
+#pragma unroll
+    for (int q = 0; q < 36; ++q) Sd[q] = (T)A[q];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) b[6 * i + r] = (T)pk[27 + r];
+    // precondition with the diagonal block as stored (rounded to T)
+#pragma unroll
+    for (int q = 0; q < 36; ++q) A[q] = (double)(T)A[q];
+    if (!spd_inverse6<double>(A, Ai)) {
+        atomicExch(&sc->err, (int)BA_ERR_NOT_SPD);
+#pragma unroll
+        for (int q = 0; q < 36; ++q) Ai[q] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 36; ++q) Minv[36 * (int64_t)i + q] = (T)Ai[q];
+}
+
+static inline int grid_for(int64_t work, int threads, int cap) {
+    int64_t g = (work + threads - 1) / threads;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+cudaError_t launch_form_rcs(ba_problem *p, double lambda) {
+    cudaError_t err;
+    cudaEvent_t ev;
+    const size_t smem = (size_t)p->obs_max * JW * p->esz;
+    ktimer_begin(p, K_FORM_RCS, &ev);
+    if (p->fp32) {
+        cudaFuncSetAttribute(k_form_rcs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_form_rcs<float><<<(unsigned)p->ngroups, FORM_THREADS, smem, p->st>>>(
+            p->grp, p->lb_info, p->contrib, p->trk_ptr, (const float *)p->J, lambda, (float *)p->part,
+            (float *)p->Linv, (float *)p->lp, p->sc, 1);
+    } else {
+        cudaFuncSetAttribute(k_form_rcs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_form_rcs<double><<<(unsigned)p->ngroups, FORM_THREADS, smem, p->st>>>(
+            p->grp, p->lb_info, p->contrib, p->trk_ptr, (const double *)p->J, lambda, (double *)p->part,
+            (double *)p->Linv, (double *)p->lp, p->sc, 0);
+    }
+    ktimer_end(p, K_FORM_RCS, ev);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int64_t nval = p->nnzb * BW;
+    ktimer_begin(p, K_RCS_REDUCE, &ev);
+    const int g = grid_for(nval, 256, 152 * 16);
+    if (p->fp32)
+        k_rcs_reduce<float><<<g, 256, 0, p->st>>>(nval, p->pptr, p->plist, (const float *)p->part, (float *)p->S);
+    else
+        k_rcs_reduce<double><<<g, 256, 0, p->st>>>(nval, p->pptr, p->plist, (const double *)p->part, (double *)p->S);
+    ktimer_end(p, K_RCS_REDUCE, ev);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    ktimer_begin(p, K_RCS_DIAG, &ev);
+    const int nb = (p->n + 127) / 128;
+    if (p->fp32)
+        k_rcs_diag<float><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (float *)p->S, (float *)p->b, (float *)p->Minv,
+                                                 lambda, p->sc);
+    else
+        k_rcs_diag<double><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (double *)p->S, (double *)p->b,
+                                                  (double *)p->Minv, lambda, p->sc);
+    ktimer_end(p, K_RCS_DIAG, ev);
+    return cudaGetLastError();
+}
+
+}  // namespace ba

@@ -1,0 +1,121 @@
+"""CPU-only tests of the C ABI: the library loads, exports what include/ba.h
+declares, validates inputs before touching the GPU, and its host-side
+symbolic phase (BSMC pattern, Sec. 4) matches the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2307_08383_gb300.build import build
+    build()
+    import paper_2307_08383_gb300 as mod
+    mod.lib()
+    return mod
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ba_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(B):
+    names = _declared()
+    assert len(names) >= 20
+    L = B.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    bound = {s[0] for s in B.SIGNATURES}
+    assert set(names) == bound
+
+
+def test_kernel_names(B):
+    names = B.ba_kernel_names()
+    assert "form_rcs" in names and "spmv" in names and "linearize" in names
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_host_pattern_matches_oracle(B, seed):
+    s = scenes.shuffled(scenes.tiny_scene(n_cams=9, n_pts=80, seed=seed), seed)
+    rp, cl = B.ba_symbolic_pattern(s.n_cams, s.n_pts, s.obs_cam, s.obs_pt)
+    rp2, cl2 = O.bsmc_pattern(s.obs_cam.astype(np.int64), s.obs_pt, s.n_cams, s.n_pts)
+    assert np.array_equal(rp, rp2) and np.array_equal(cl, cl2)
+
+
+def test_host_pattern_aerial(B):
+    s = scenes.aerial_small(n_along=12, n_across=6, pts_per_cam=100, seed=5)
+    rp, cl = B.ba_symbolic_pattern(s.n_cams, s.n_pts, s.obs_cam, s.obs_pt)
+    rp2, cl2 = O.bsmc_pattern(s.obs_cam.astype(np.int64), s.obs_pt, s.n_cams, s.n_pts)
+    assert np.array_equal(rp, rp2) and np.array_equal(cl, cl2)
+
+
+def _create(B, s, **kw):
+    o = B.ba_options_default(**kw)
+    return B.ba_problem_create(o, s["cams"], s["pts"], s["obs_cam"], s["obs_pt"], s["obs_uv"])
+
+
+def _valid():
+    sc = scenes.tiny_scene(n_cams=4, n_pts=10, seed=3)
+    return dict(cams=sc.cams0.copy(), pts=sc.pts0.copy(), obs_cam=sc.obs_cam.copy(), obs_pt=sc.obs_pt.copy(),
+                obs_uv=sc.obs_uv.copy())
+
+
+@pytest.mark.parametrize("case", ["cam_range", "pt_range", "duplicate", "single_obs", "idle_camera", "nan_uv",
+                                  "inf_cam", "bad_precision", "bad_delta", "bad_tol"])
+def test_create_rejects_bad_input_without_gpu(B, case):
+    s = _valid()
+    kw = {}
+    want = B.BA_ERR_INVALID_ARG
+    if case == "cam_range":
+        s["obs_cam"][3] = 99
+    elif case == "pt_range":
+        s["obs_pt"][0] = -1
+    elif case == "duplicate":
+        k = s["obs_pt"][0]
+        idx = np.nonzero(s["obs_pt"] == k)[0]
+        s["obs_cam"][idx[1]] = s["obs_cam"][idx[0]]
+    elif case == "single_obs":
+        s["obs_pt"] = np.append(s["obs_pt"], len(s["pts"]))
+        s["obs_cam"] = np.append(s["obs_cam"], 0).astype(np.int32)
+        s["obs_uv"] = np.vstack([s["obs_uv"], [1.0, 2.0]])
+        s["pts"] = np.vstack([s["pts"], [0.0, 0.0, 0.0]])
+    elif case == "idle_camera":
+        s["cams"] = np.vstack([s["cams"], s["cams"][:1]])
+    elif case == "nan_uv":
+        s["obs_uv"][2, 1] = np.nan
+        want = B.BA_ERR_NONFINITE
+    elif case == "inf_cam":
+        s["cams"][1, 4] = np.inf
+        want = B.BA_ERR_NONFINITE
+    elif case == "bad_precision":
+        kw["precision"] = 7
+    elif case == "bad_delta":
+        kw["robust"] = B.BA_LOSS_HUBER
+        kw["huber_delta"] = -1.0
+    elif case == "bad_tol":
+        kw["pcg_rel_tol"] = 0.0
+    with pytest.raises(B.BAError) as ei:
+        _create(B, s, **kw)
+    assert ei.value.status == want
+
+
+def test_memory_cap_is_checked_before_allocation(B):
+    s = _valid()
+    with pytest.raises(B.BAError) as ei:
+        _create(B, s, device_mem_cap=1024)
+    assert ei.value.status == B.BA_ERR_OOM
+
+
+def test_null_problem_calls_fail_cleanly(B):
+    assert B.lib().ba_linearize(None, None) == B.BA_ERR_INVALID_ARG
+    assert B.lib().ba_lm_step(None, None) == B.BA_ERR_INVALID_ARG
+    B.lib().ba_problem_destroy(None)

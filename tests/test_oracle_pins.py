@@ -26,12 +26,14 @@ def _problem(scene, **kw):
 
 def _retract(cams, pts, dx):
     """x (+) dx with the oracle's documented retraction, written independently:
-    R <- Exp(dw) R via scipy, t += dt, X += dX."""
+    X_cam <- Exp(dw) X_cam + dt (R <- Exp(dw) R, t <- Exp(dw) t + dt) via scipy,
+    X += dX."""
     n = len(cams)
     dxc = dx[:6 * n].reshape(n, 6)
     dxp = dx[6 * n:].reshape(-1, 3)
-    R = Rotation.from_rotvec(dxc[:, :3]) * Rotation.from_rotvec(cams[:, :3])
-    return np.concatenate([R.as_rotvec(), cams[:, 3:] + dxc[:, 3:]], 1), pts + dxp
+    dR = Rotation.from_rotvec(dxc[:, :3])
+    R = dR * Rotation.from_rotvec(cams[:, :3])
+    return np.concatenate([R.as_rotvec(), dR.apply(cams[:, 3:]) + dxc[:, 3:]], 1), pts + dxp
 
 
 def _residual_vec(pb, cams, pts):

@@ -1,0 +1,328 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (per-block relative Frobenius error of S, denominators guarded
+against cancellation by 1e-3 sqrt(||S_ii|| ||S_jj||)):
+  FP64 mode <= 1e-10, FP32 mode <= 1e-4; the BSMC pattern is bit-exact;
+  LM: final cost within 1e-6 relative of the oracle after the same iterations.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2307_08383_gb300.build import build
+    build()
+    import paper_2307_08383_gb300 as mod
+    return mod
+
+
+def _oracle(s, delta=None, tol=1e-10):
+    return O.Problem(s.n_cams, s.n_pts, s.obs_cam, s.obs_pt, s.obs_uv, delta=delta, pcg_tol=tol)
+
+
+def _gpu(B, s, cams=None, pts=None, **kw):
+    cams = s.cams0 if cams is None else cams
+    pts = s.pts0 if pts is None else pts
+    return B.Problem(cams, pts, s.obs_cam, s.obs_pt, s.obs_uv, **kw)
+
+
+def block_errors(row_ptr, col, val, ref_val):
+    n = len(row_ptr) - 1
+    dnorm = np.array([np.linalg.norm(ref_val[row_ptr[i]]) for i in range(n)])
+    errs = np.empty(len(col))
+    for i in range(n):
+        for blk in range(row_ptr[i], row_ptr[i + 1]):
+            j = col[blk]
+            den = max(np.linalg.norm(ref_val[blk]), 1e-3 * np.sqrt(dnorm[i] * dnorm[j]))
+            errs[blk] = np.linalg.norm(val[blk] - ref_val[blk]) / den
+    return errs
+
+
+# ----------------------------------------------------------------------------- K1
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("huber", [False, True])
+def test_linearize_parity(B, prec, huber):
+    s = scenes.shuffled(scenes.ring_scene(n_cams=12, n_pts=400, seed=31, sigma_px=2.0), 3)
+    delta = 2.0 if huber else None
+    kw = dict(precision=B.BA_FP64 if prec == "fp64" else B.BA_FP32)
+    if huber:
+        kw.update(robust=B.BA_LOSS_HUBER, huber_delta=2.0)
+    g = _gpu(B, s, **kw)
+    F = g.linearize()
+    e, Jc, Jp = g.linearization()
+    er, Jcr, Jpr = O.linearize(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics(), delta)
+    Fr = O.cost(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics(), delta)
+    if prec == "fp64":
+        tj, te, tf = 1e-12, 1e-9, 1e-12
+    else:
+        tj, te, tf = 2e-6, 2e-3, 1e-5
+    assert np.abs(Jc - Jcr).max() <= tj * np.abs(Jcr).max()
+    assert np.abs(Jp - Jpr).max() <= tj * np.abs(Jpr).max()
+    if not huber:
+        assert np.abs(e - er).max() <= te  # px
+    else:
+        # weights may flip only for residuals within rounding of the threshold
+        ok = np.abs(e - er).max(1) <= te
+        assert ok.mean() > 0.999
+    assert abs(F - Fr) <= tf * Fr
+
+
+# ----------------------------------------------------------------------------- K2-K4
+
+def _rcs_case(B, s, prec, lam, delta=None, **kw):
+    gk = dict(precision=B.BA_FP64 if prec == "fp64" else B.BA_FP32, **kw)
+    if delta is not None:
+        gk.update(robust=B.BA_LOSS_HUBER, huber_delta=delta)
+    g = _gpu(B, s, **gk)
+    g.linearize()
+    g.form_rcs(lam)
+    row_ptr, col, val, b = g.rcs()
+    pb = _oracle(s, delta)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    _, A, bref = pb.rcs(e, Jc, Jp, lam)
+    return g, (row_ptr, col, val, b), (A, bref)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+@pytest.mark.parametrize("variant", ["ring", "shuffled", "small_groups", "huber", "strong_damping", "aerial"])
+def test_rcs_parity(B, prec, tol, variant):
+    lam, delta, kw = 1e-4, None, {}
+    s = scenes.ring_scene(n_cams=16, n_pts=500, seed=41, sigma_px=1.0)
+    if variant == "shuffled":
+        s = scenes.shuffled(s, 9)
+    elif variant == "small_groups":
+        kw["group_max_obs"] = 40
+    elif variant == "huber":
+        delta = 2.0
+        s = scenes.ring_scene(n_cams=16, n_pts=500, seed=42, sigma_px=3.0)
+    elif variant == "strong_damping":
+        lam = 3.0
+    elif variant == "aerial":
+        s = scenes.aerial_small(n_along=10, n_across=6, pts_per_cam=120, seed=43)
+    g, (row_ptr, col, val, b), (A, bref) = _rcs_case(B, s, prec, lam, delta, **kw)
+    assert np.array_equal(row_ptr, A.row_ptr) and np.array_equal(col, A.col)
+    errs = block_errors(row_ptr, col, val, A.val)
+    assert errs.max() <= tol, (errs.max(), np.argmax(errs))
+    bt = 1e-10 if prec == "fp64" else 2e-3
+    assert np.abs(b - bref).max() <= bt * np.abs(bref).max()
+    st = g.stats()
+    assert st["nnzb"] == len(A.col) and st["n_partials"] >= st["nnzb"]
+    if variant == "small_groups":
+        assert st["n_groups"] > 20
+
+
+def test_rcs_is_deterministic(B):
+    s = scenes.ring_scene(n_cams=16, n_pts=600, seed=44)
+    g = _gpu(B, s, precision=B.BA_FP32)
+    g.linearize()
+    g.form_rcs(1e-3)
+    v1 = g.rcs()[2]
+    g.form_rcs(1e-3)
+    v2 = g.rcs()[2]
+    assert np.array_equal(v1, v2)
+
+
+def test_minimal_problem(B):
+    """Two cameras, three points each seen by both."""
+    s = scenes.ring_scene(n_cams=2, n_pts=3, track=(2, 2), seed=45, sigma_px=0.5)
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+        g, (row_ptr, col, val, b), (A, bref) = _rcs_case(B, s, prec, 1e-2)
+        assert list(col) == [0, 1, 1]
+        assert block_errors(row_ptr, col, val, A.val).max() <= tol
+
+
+def test_long_tracks(B):
+    """Tracks of 40 cameras (the longest track of the large workload)."""
+    s = scenes.ring_scene(n_cams=48, n_pts=60, track=(36, 40), seed=46)
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+        g, (row_ptr, col, val, b), (A, bref) = _rcs_case(B, s, prec, 1e-3)
+        assert np.array_equal(col, A.col)
+        assert block_errors(row_ptr, col, val, A.val).max() <= tol
+
+
+# ----------------------------------------------------------------------------- PCG, Eq. 5
+
+def test_solve_and_back_substitute_fp64(B):
+    s = scenes.ring_scene(n_cams=20, n_pts=800, seed=51, sigma_px=1.0)
+    lam = 1e-3
+    g = _gpu(B, s, precision=B.BA_FP64, pcg_rel_tol=1e-10)
+    g.linearize()
+    g.form_rcs(lam)
+    info, conv = g.solve_rcs()
+    assert conv
+    g.back_substitute()
+    dxc, dxp = g.step()
+    pb = _oracle(s)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    blk, A, b = pb.rcs(e, Jc, Jp, lam)
+    res = pb.solve(A, b)
+    assert abs(info["pcg_iters"] - res.iters) <= 1, (info["pcg_iters"], res.iters)
+    assert np.linalg.norm(dxc.reshape(-1) - res.y) <= 1e-7 * np.linalg.norm(res.y)
+    assert info["rcs_rel_resid"] <= 1e-9
+    # Eq. 5 from the GPU's own dx_c isolates the back-substitution kernel
+    dxp_ref = O.back_substitute(blk, pb.obs_cam, pb.obs_pt, s.n_pts, dxc)
+    assert np.abs(dxp - dxp_ref).max() <= 1e-10 * np.abs(dxp_ref).max()
+
+
+def test_solve_fp32_refinement_reaches_tight_tolerance(B):
+    s = scenes.aerial_small(n_along=12, n_across=6, pts_per_cam=150, seed=52)
+    g = _gpu(B, s, precision=B.BA_FP32, pcg_rel_tol=1e-8, inner_rel_tol=1e-4)
+    g.linearize()
+    g.form_rcs(1e-4)
+    info, conv = g.solve_rcs()
+    assert conv and info["rcs_rel_resid"] <= 1e-8 and info["refine_steps"] >= 2
+    # true FP64 residual of the GPU's own system, recomputed on the host
+    row_ptr, col, val, b = g.rcs()
+    dxc, _ = g.step()
+    A = O.BSMC(row_ptr, col, val)
+    r = b.reshape(-1) - O.bsmc_spmv(A, dxc.reshape(-1).astype(np.float32).astype(np.float64))
+    assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(b)
+
+
+def test_paper_tolerance_stops_early(B):
+    s = scenes.ring_scene(n_cams=20, n_pts=800, seed=53)
+    g = _gpu(B, s, precision=B.BA_FP64, pcg_rel_tol=0.1)
+    g.linearize()
+    g.form_rcs(1e-4)
+    info, conv = g.solve_rcs()
+    pb = _oracle(s, tol=0.1)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    _, A, b = pb.rcs(e, Jc, Jp, 1e-4)
+    res = pb.solve(A, b)
+    assert conv and info["pcg_iters"] == res.iters
+
+
+# ----------------------------------------------------------------------------- LM
+
+def test_lm_trajectory_fp64_ring50(B):
+    """The tiny FP64 workload: 50 cameras, 2,000 points, 10 LM iterations, PCG to 1e-10."""
+    s = scenes.ring_scene(seed=1001)
+    g = _gpu(B, s, precision=B.BA_FP64, pcg_rel_tol=1e-10)
+    pb = _oracle(s, tol=1e-10)
+    st = O.LMState(s.cams0.copy(), s.pts0.copy())
+    for it in range(10):
+        info = g.lm_step()
+        st, ref, _ = pb.step(st)
+        assert abs(info["cost_before"] - ref.cost_before) <= 1e-6 * ref.cost_before
+        significant = ref.predicted > 1e-9 * ref.cost_before
+        if significant:
+            assert info["accepted"] == int(ref.accepted), (it, info["rho"], ref.rho)
+            assert abs(info["cost_trial"] - (ref.cost_after if ref.accepted else info["cost_trial"])) <= \
+                1e-6 * ref.cost_before
+    _, _, F = g.lm_state()
+    Fr = pb.cost(st.cams, st.pts)
+    assert abs(F - Fr) <= 1e-6 * Fr, (F, Fr)
+    cams = g.cameras()
+    pts = g.points()
+    assert np.abs(pts - st.pts).max() < 1e-5
+    assert np.abs(cams - st.cams).max() < 1e-6
+
+
+def test_lm_fp32_aerial_against_fp64_oracle(B):
+    s = scenes.aerial_small(n_along=10, n_across=6, pts_per_cam=100, seed=54)
+    g = _gpu(B, s, precision=B.BA_FP32, pcg_rel_tol=1e-6)
+    pb = _oracle(s, tol=1e-6)
+    st = O.LMState(s.cams0.copy(), s.pts0.copy())
+    for _ in range(5):
+        info = g.lm_step()
+        st, ref, _ = pb.step(st)
+        if ref.predicted > 1e-6 * ref.cost_before:
+            assert info["accepted"] == int(ref.accepted)
+    _, _, F = g.lm_state()
+    Fr = pb.cost(st.cams, st.pts)
+    assert abs(F - Fr) <= 1e-5 * Fr, (F, Fr)
+
+
+def test_lm_huber_fp32(B):
+    s = scenes.aerial_small(n_along=10, n_across=6, pts_per_cam=100, seed=55, outlier_frac=0.01)
+    g = _gpu(B, s, precision=B.BA_FP32, pcg_rel_tol=1e-6, robust=B.BA_LOSS_HUBER, huber_delta=2.0)
+    pb = _oracle(s, delta=2.0, tol=1e-6)
+    st = O.LMState(s.cams0.copy(), s.pts0.copy())
+    for _ in range(4):
+        info = g.lm_step()
+        st, ref, _ = pb.step(st)
+    _, _, F = g.lm_state()
+    Fr = pb.cost(st.cams, st.pts)
+    assert abs(F - Fr) <= 1e-5 * Fr, (F, Fr)
+
+
+def test_state_errors(B):
+    s = scenes.ring_scene(n_cams=6, n_pts=50, seed=56)
+    g = _gpu(B, s)
+    with pytest.raises(B.BAError) as ei:
+        g.form_rcs(1e-3)
+    assert ei.value.status == B.BA_ERR_STATE
+    g.linearize()
+    with pytest.raises(B.BAError) as ei:
+        g.back_substitute()
+    assert ei.value.status == B.BA_ERR_STATE
+    with pytest.raises(B.BAError):
+        g.form_rcs(-1.0)
+
+
+def test_set_state_roundtrip(B):
+    s = scenes.ring_scene(n_cams=8, n_pts=100, seed=57)
+    g = _gpu(B, s)
+    g.set_state(s.cams_gt, s.pts_gt, 1e-2, 4.0)
+    assert np.array_equal(g.cameras(), s.cams_gt) and np.array_equal(g.points(), s.pts_gt)
+    lam, nu, F = g.lm_state()
+    assert lam == 1e-2 and nu == 4.0
+    assert abs(F - O.cost(s.cams_gt, s.pts_gt, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics())) <= 1e-9 * F
+
+
+# ----------------------------------------------------------------------------- full size
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4)])
+def test_aerial5k_full_size_sampled_blocks(B, prec, tol):
+    """The aerial workload at full size (5,000 cameras, 1M points) in the
+    launch configuration the benchmark uses; sampled blocks against the oracle."""
+    s = scenes.aerial_scene(seed=2001)
+    g = _gpu(B, s, precision=B.BA_FP32, pcg_rel_tol=0.1)
+    lam = 1e-4
+    g.linearize()
+    g.form_rcs(lam)
+    row_ptr, col, val, b = g.rcs()
+    # pattern: brute-force set of camera pairs over all tracks (vectorised)
+    order = np.lexsort((s.obs_cam, s.obs_pt))
+    oc, op = s.obs_cam[order].astype(np.int64), s.obs_pt[order]
+    starts = np.searchsorted(op, np.arange(s.n_pts + 1))
+    L = np.diff(starts)
+    keys = [np.arange(s.n_cams, dtype=np.int64) * (s.n_cams + 1)]
+    for dx in range(1, L.max()):
+        a = np.nonzero(L > dx)[0]
+        for off in range(0, L.max() - dx):
+            sel = a[L[a] > off + dx]
+            if len(sel) == 0:
+                break
+            keys.append(oc[starts[sel] + off] * s.n_cams + oc[starts[sel] + off + dx])
+    keys = np.unique(np.concatenate(keys))
+    got = np.repeat(np.arange(s.n_cams, dtype=np.int64), np.diff(row_ptr)) * s.n_cams + col
+    assert np.array_equal(np.sort(got), keys)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(s.n_cams, 5, replace=False)
+    pairs = [(int(i), int(i)) for i in rows]
+    for i in rows:
+        nb = row_ptr[i + 1] - row_ptr[i]
+        if nb > 1:
+            pairs.append((int(i), int(col[row_ptr[i] + 1 + rng.integers(0, nb - 1)])))
+    S_ref, b_ref = O.rcs_blocks_sampled(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics(), lam, pairs)
+    for (i, j) in pairs:
+        blk = row_ptr[i] + np.searchsorted(col[row_ptr[i]:row_ptr[i + 1]], j)
+        assert col[blk] == j
+        guard = 1e-3 * np.sqrt(np.linalg.norm(val[row_ptr[i]]) * np.linalg.norm(val[row_ptr[j]]))
+        den = max(np.linalg.norm(S_ref[(i, j)]), guard)
+        assert np.linalg.norm(val[blk] - S_ref[(i, j)]) / den <= tol, (i, j)
+    for i, bi in b_ref.items():
+        assert np.abs(b[i] - bi).max() <= 2e-3 * np.abs(bi).max()
+    info = g.lm_step()
+    assert info["accepted"] == 1 and info["cost_trial"] < info["cost_before"]
+    assert info["rcs_rel_resid"] <= 0.1
