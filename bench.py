@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: LM iterations per second of exact LM bundle adjustment on GB300.
+
+Workload (default ``aerial5k``): 5,000 nadir cameras on a 50 x 100 flight grid
+(60% forward / 30% side overlap), 1M points on sinusoidal terrain, tracks of
+2 + Geometric (mean 5, max 20) cameras, N(0, 1 px) noise; FP32 Jacobians,
+RCS assembly, SpMV and PCG with FP64 cost / gain-ratio sums and FP64
+refinement residual; PCG stop at the paper's inexact-Newton T = 0.1.
+
+A step is one LM iteration (linearize, RCS formation, PCG solve,
+back-substitution, trial evaluation, accept/reject) through the C ABI.  The
+timed steps are LM iterations 1..K from the initial state (the state is reset
+after the warm-up).  ``value`` is K / device time with all inputs resident in
+HBM; ``e2e`` is the same metric with each step's state copied in from host
+memory and the result copied back.  ``roofline`` is for the dominant kernel
+(RCS formation), from CUDA events the library records around each launch.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores (bounded
+samples of the same workload, scaled to the full observation count).
+Multi-GPU: independent replicas (one problem per rank), max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+METRIC = "LM iters/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return d, "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+def make_scene(workload: str, rank: int = 0):
+    import scenes
+    if workload == "aerial5k":
+        return scenes.aerial_scene(seed=2001 + rank)
+    if workload == "ring50":
+        return scenes.ring_scene(seed=1001 + rank)
+    if workload == "aerial_small":
+        return scenes.aerial_small(seed=2101 + rank)
+    raise ValueError(workload)
+
+
+def workload_opts(workload: str, B):
+    if workload == "ring50":
+        return dict(precision=B.BA_FP64, pcg_rel_tol=1e-10)
+    return dict(precision=B.BA_FP32, pcg_rel_tol=0.1, inner_rel_tol=1e-4)
+
+
+def workload_config(workload: str, s, opts):
+    return {"workload": workload, "n_cams": s.n_cams, "n_pts": s.n_pts, "n_obs": s.n_obs,
+            "mean_track": round(s.n_obs / s.n_pts, 3), "precision": "fp32+fp64-refine"
+            if opts.get("precision") == 1 else "fp64", "pcg_rel_tol": opts["pcg_rel_tol"],
+            "lm_iterations_timed": "1..K from the initial state",
+            "l2": "inputs larger than L2 (stored Jacobians %.0f MB > 129 MB)" % (s.n_obs * 80 / 1e6)}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def rcs_bytes_and_flops(st, esz=4):
+    """Algorithmic traffic and flops of one RCS-formation launch (K2).
+
+    reads: stored Jacobian rows (20 values / observation), the (a, b) product
+    list (4 B / product), local-block descriptors (4 B), track starts (4 B /
+    point), group descriptors (40 B); writes: sub-RCS partials (36 values)
+    and per-point L^-1, l_p (9 values)."""
+    m, P, pairs, npart, ng = st["n_obs"], st["n_pts"], st["n_pairs"], st["n_partials"], st["n_groups"]
+    byts = m * 20 * esz + pairs * 4 + npart * 4 + (P + 1) * 4 + ng * 40 + npart * 36 * esz + P * 9 * esz
+    offd = pairs - m
+    # per obs: V 9x2, l_p 6, P 2x6x... (30), e^ 12; per point: Cholesky ~40; per diag product 75 FMA,
+    # per off-diagonal product 108 FMA
+    flops = m * 2 * (9 + 6 + 15 + 6) + P * 60 + m * 2 * 75 + offd * 2 * 108
+    return byts, flops
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2307_08383_gb300 as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    s = make_scene(args.workload, rank)
+    opts = workload_opts(args.workload, B)
+    stream = torch.cuda.current_stream()
+    g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, stream=stream.cuda_stream, profile=1, **opts)
+    lam0 = g.opts.lambda0
+
+    for _ in range(args.warmup):
+        g.lm_step()
+    g.set_state(s.cams0, s.pts0, lam0, 2.0)
+    torch.cuda.synchronize()
+    g.reset_kernel_times()
+    st0 = g.stats()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    infos = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(g.lm_step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st1 = g.stats()
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    ktimes = g.kernel_times()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # ---- end-to-end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        g.set_state(s.cams0, s.pts0, lam0, 2.0)
+        hc = torch.empty((s.n_cams, 6), dtype=torch.float64, pin_memory=True).numpy()
+        hp = torch.empty((s.n_pts, 3), dtype=torch.float64, pin_memory=True).numpy()
+        hc[:] = s.cams0
+        hp[:] = s.pts0
+        lam, nu = lam0, 2.0
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.set_state(hc, hp, lam, nu)
+            g.lm_step()
+            B.ba_get_cameras(g.h, s.n_cams, hc)
+            B.ba_get_points(g.h, s.n_pts, hp)
+            lam, nu, _ = g.lm_state()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        td = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(td, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps / float(td.item()), "unit": "LM iters/s",
+               "h2d_bytes_per_step": int(hc.nbytes + hp.nbytes),
+               "d2h_bytes_per_step": int(hc.nbytes + hp.nbytes + 8)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks, peak_kind = load_peaks()
+    names = B.ba_kernel_names()
+    k = names.index("form_rcs")
+    n_l, tot = ktimes["form_rcs"]
+    esz = 4 if opts["precision"] == B.BA_FP32 else 8
+    byts, flops = rcs_bytes_and_flops(st1, esz)
+    avg_ms = tot / max(n_l, 1)
+    achieved = byts / (avg_ms / 1e3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "form_rcs_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tr = json.load(open(tr_path))
+            if tr.get("workload") == args.workload and tr.get("kernel_version") == KERNEL_VERSION:
+                traffic = tr["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    total_timed = sum(v[1] for v in ktimes.values())
+    roof = {"kernel": "form_rcs", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "peak_kind": peak_kind, "traffic": traffic, "algorithmic_bytes": int(byts),
+            "launches": n_l, "avg_ms": round(avg_ms, 4),
+            "fp32_tflops": round(flops / (avg_ms / 1e3) / 1e12, 2),
+            "share_of_timed_kernels": round(tot / total_timed, 3) if total_timed else None}
+    kernels = {nm: {"launches": v[0], "ms": round(v[1], 3)} for nm, v in ktimes.items() if v[0]}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload, s.n_obs)
+    acc = sum(i["accepted"] for i in infos)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "LM iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if opts["precision"] == B.BA_FP32 else "f64", "data": "synthetic",
+        "config": workload_config(args.workload, s, opts),
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "lm": {"accepted": acc, "pcg_iters": [i["pcg_iters"] for i in infos],
+               "cost": [infos[0]["cost_before"], infos[-1]["cost_after"]],
+               "rcs_rel_resid_max": max(i["rcs_rel_resid"] for i in infos)},
+        "kernels_ms": kernels, "impl": "ours",
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+KERNEL_VERSION = "form_rcs-v1"
+
+
+def _oracle_steps(workload, n_steps, sample_cams):
+    """Times n_steps oracle LM iterations on a sample of the workload."""
+    import oracle as O
+    import scenes
+    if workload == "ring50":
+        s = scenes.ring_scene(seed=1001)
+        tol = 1e-10
+    else:
+        na, nc = sample_cams
+        s = scenes.aerial_small(n_along=na, n_across=nc, pts_per_cam=200, seed=2101)
+        tol = 0.1
+    pb = O.Problem(s.n_cams, s.n_pts, s.obs_cam, s.obs_pt, s.obs_uv, pcg_tol=tol)
+    st = O.LMState(s.cams0.copy(), s.pts0.copy())
+    times = []
+    for _ in range(n_steps):
+        t0 = time.perf_counter()
+        st, _, _ = pb.step(st)
+        times.append(time.perf_counter() - t0)
+    return s, times
+
+
+def cpu_baseline(workload, m_full):
+    s, times = _oracle_steps(workload, 3, (20, 10))
+    per_obs = sum(times) / len(times) / s.n_obs
+    est = per_obs * m_full
+    return {"value": round(1.0 / est, 6), "unit": "LM iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"3 FP64 oracle LM iterations on a {s.n_cams}-camera, {s.n_pts}-point, {s.n_obs}-observation "
+                      f"sample of the same aerial layout ({sum(times):.1f} s), scaled to {m_full} observations "
+                      f"by time per observation"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import scenes
+    full = make_scene(args.workload) if args.workload == "ring50" else None
+    m_full = full.n_obs if full is not None else _aerial5k_obs()
+    sample = (10, 10)
+    s, w = _oracle_steps(args.workload, args.warmup, sample) if args.warmup else (None, [])
+    s, times = _oracle_steps(args.workload, args.steps, sample)
+    per_obs = sum(times) / len(times) / s.n_obs
+    est = per_obs * m_full
+    value = 1.0 / est
+    out = {"metric": METRIC, "value": round(value, 6), "unit": "LM iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(est * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "n_obs": m_full}, "impl": "reference",
+           "cpu_baseline": {"value": round(value, 6), "unit": "LM iters/s", "cores": 1, "kind": "oracle",
+                            "sample": f"each step one FP64 oracle LM iteration on a {s.n_cams}-camera, "
+                                      f"{s.n_obs}-observation sample, scaled to {m_full} observations"},
+           "e2e": {"value": round(value, 6), "unit": "LM iters/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def _aerial5k_obs():
+    # observation count of the full aerial workload (seeded, deterministic)
+    return make_scene("aerial5k").n_obs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="aerial5k", choices=["aerial5k", "ring50", "aerial_small"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -93,6 +93,7 @@ typedef struct {
     int64_t n_partials;      /* sub-RCS blocks written by the groups */
     int64_t n_pairs;         /* (obs, obs) products: sum_k L_k (L_k + 1) / 2 */
     int64_t device_bytes;    /* device memory held by the problem */
+    int64_t kernel_launches; /* kernels launched for this problem so far */
     int32_t precision;
 } ba_stats;
 

@@ -73,7 +73,8 @@ class ba_step_info(ctypes.Structure):
 class ba_stats(ctypes.Structure):
     _fields_ = [("n_cams", ctypes.c_int32), ("n_pts", ctypes.c_int64), ("n_obs", ctypes.c_int64),
                 ("nnzb", ctypes.c_int64), ("n_groups", ctypes.c_int64), ("n_partials", ctypes.c_int64),
-                ("n_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("precision", ctypes.c_int32)]
+                ("n_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("precision", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

@@ -709,6 +709,7 @@ ba_status ba_get_stats(const ba_problem *p, ba_stats *o) {
     o->n_partials = p->npart;
     o->n_pairs = p->hs.n_pairs;
     o->device_bytes = (int64_t)p->dev_bytes;
+    o->kernel_launches = p->launches;
     o->precision = p->opt.precision;
     return BA_OK;
 }

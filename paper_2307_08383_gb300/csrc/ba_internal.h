@@ -130,6 +130,7 @@ struct ba_problem {
     std::vector<Pending> pending;
     int64_t klaunch[ba::K_COUNT] = {};
     double kms[ba::K_COUNT] = {};
+    int64_t launches = 0;  // every kernel launched on behalf of this problem
 };
 
 namespace ba {

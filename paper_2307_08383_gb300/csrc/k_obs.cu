@@ -284,6 +284,7 @@ cudaError_t launch_prepare_state(ba_problem *p, StateBuf &s) {
         k_prepare_cams64<<<nb, 128, 0, p->st>>>(p->n, s.cams, (double *)s.camc);
     }
     ktimer_end(p, K_PREPARE, ev);
+    p->launches += p->fp32 ? 2 : 1;
     return cudaGetLastError();
 }
 
@@ -301,6 +302,7 @@ cudaError_t launch_linearize(ba_problem *p) {
                                                   p->cur.pts, nullptr, intr_of(p), hub, p->opt.huber_delta,
                                                   (double *)p->J);
     ktimer_end(p, K_LINEARIZE, ev);
+    p->launches += 1;
     return cudaGetLastError();
 }
 
@@ -318,6 +320,7 @@ cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial) {
                                              nullptr, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
                                              p->red, p->counters + 0);
     ktimer_end(p, K_COST, ev);
+    p->launches += 1;
     return cudaGetLastError();
 }
 
@@ -334,6 +337,7 @@ cudaError_t launch_apply_update(ba_problem *p) {
         k_update_pts<double><<<gp, 256, 0, p->st>>>(p->P, p->cur.pts, (const double *)p->dxp, p->trial.pts);
     }
     ktimer_end(p, K_UPDATE, ev);
+    p->launches += 2;
     return cudaGetLastError();
 }
 
@@ -353,6 +357,7 @@ cudaError_t launch_eval(ba_problem *p) {
                                              (const double *)p->dxp, intr_of(p), hub, p->opt.huber_delta, p->sc,
                                              p->red, p->counters + 1);
     ktimer_end(p, K_EVAL, ev);
+    p->launches += 1;
     return cudaGetLastError();
 }
 

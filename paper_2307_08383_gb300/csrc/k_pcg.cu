@@ -262,6 +262,7 @@ cudaError_t launch_pcg_init(ba_problem *p, const void *rhs, double tol, int max_
                                                  (double *)p->pv[3], (double *)p->pv[5], p->sc, tol * tol, max_iters,
                                                  p->red, p->counters + 2);
     ktimer_end(p, K_PCG_INIT, ev);
+    p->launches += 1;
     return cudaGetLastError();
 }
 
@@ -282,6 +283,7 @@ cudaError_t launch_pcg_iter(ba_problem *p, int it) {
                                                             (double *)dnew, (double *)p->pv[5], p->sc, p->red,
                                                             p->counters + 3);
     ktimer_end(p, K_SPMV, ev);
+    p->launches += 1;
     ktimer_begin(p, K_PCG_UPDATE, &ev);
     if (p->fp32)
         k_pcg_update<float><<<gv, 256, 0, p->st>>>(p->n, (const float *)p->Minv, (const float *)dnew,
@@ -292,6 +294,7 @@ cudaError_t launch_pcg_iter(ba_problem *p, int it) {
                                                     (double *)p->pv[5], (double *)p->pv[0], (double *)p->pv[1],
                                                     (double *)p->pv[2], p->sc, p->red, p->counters + 4);
     ktimer_end(p, K_PCG_UPDATE, ev);
+    p->launches += 1;
     return cudaGetLastError();
 }
 
@@ -318,6 +321,7 @@ cudaError_t launch_resid64(ba_problem *p, bool from_x64) {
         k_resid_fin<double><<<g, 256, 0, p->st>>>(p->n, (const double *)p->b, p->q64, p->r64, p->sc, p->red,
                                                   p->counters + 6);
     ktimer_end(p, K_RESID64, ev);
+    p->launches += from_x64 ? 2 : 1;
     return cudaGetLastError();
 }
 
@@ -329,6 +333,7 @@ cudaError_t launch_accumulate_solution(ba_problem *p, bool first) {
         k_acc64<float><<<g, 256, 0, p->st>>>(cnt, (const float *)p->pv[0], p->x64, first ? 1 : 0);
     else
         k_acc64<double><<<g, 256, 0, p->st>>>(cnt, (const double *)p->pv[0], p->x64, first ? 1 : 0);
+    p->launches += 1;
     return cudaGetLastError();
 }
 
@@ -340,6 +345,7 @@ cudaError_t launch_refine_rhs(ba_problem *p, void *rhs) {
         k_to_T<float><<<g, 256, 0, p->st>>>(cnt, p->r64, (float *)rhs);
     else
         k_to_T<double><<<g, 256, 0, p->st>>>(cnt, p->r64, (double *)rhs);
+    p->launches += 1;
     return cudaGetLastError();
 }
 
@@ -351,6 +357,7 @@ cudaError_t launch_solution_to_step(ba_problem *p) {
         k_to_T<float><<<g, 256, 0, p->st>>>(cnt, p->x64, (float *)p->dxc);
     else
         k_to_T<double><<<g, 256, 0, p->st>>>(cnt, p->x64, (double *)p->dxc);
+    p->launches += 1;
     return cudaGetLastError();
 }
 
@@ -367,6 +374,7 @@ cudaError_t launch_back_substitute(ba_problem *p) {
                                                  (const double *)p->dxc, (const double *)p->Linv,
                                                  (const double *)p->lp, (double *)p->dxp);
     ktimer_end(p, K_BACKSUB, ev);
+    p->launches += 1;
     return cudaGetLastError();
 }
 

@@ -259,6 +259,7 @@ cudaError_t launch_form_rcs(ba_problem *p, double lambda) {
             (double *)p->Linv, (double *)p->lp, p->sc, 0);
     }
     ktimer_end(p, K_FORM_RCS, ev);
+    p->launches += 1;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int64_t nval = p->nnzb * BW;
     ktimer_begin(p, K_RCS_REDUCE, &ev);
@@ -268,6 +269,7 @@ cudaError_t launch_form_rcs(ba_problem *p, double lambda) {
     else
         k_rcs_reduce<double><<<g, 256, 0, p->st>>>(nval, p->pptr, p->plist, (const double *)p->part, (double *)p->S);
     ktimer_end(p, K_RCS_REDUCE, ev);
+    p->launches += 1;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     ktimer_begin(p, K_RCS_DIAG, &ev);
     const int nb = (p->n + 127) / 128;
@@ -278,6 +280,7 @@ cudaError_t launch_form_rcs(ba_problem *p, double lambda) {
         k_rcs_diag<double><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (double *)p->S, (double *)p->b,
                                                   (double *)p->Minv, lambda, p->sc);
     ktimer_end(p, K_RCS_DIAG, ev);
+    p->launches += 1;
     return cudaGetLastError();
 }
 

@@ -113,9 +113,11 @@ def _finish(name, Rw2c, centers, pts, obs_cam, obs_pt, rng, sigma_px, rot_sd, t_
         uv[idx] = rng.uniform(0.0, IMG_PX, (k, 2))
         meta["n_outliers"] = k
     cams_gt = _pack_cams(Rw2c, centers)
-    cams0 = cams_gt.copy()
-    cams0[:, :3] += rng.normal(0.0, rot_sd, (len(cams0), 3))
-    cams0[:, 3:] += rng.normal(0.0, t_sd, (len(cams0), 3))
+    # initial poses: orientation perturbed by a rotation of N(0, rot_sd) rad per
+    # axis in the camera frame, camera centre moved by N(0, t_sd) m per axis
+    dR = Rotation.from_rotvec(rng.normal(0.0, rot_sd, (len(centers), 3))).as_matrix()
+    R0 = np.einsum("nij,njk->nik", dR, Rw2c)
+    cams0 = _pack_cams(R0, centers + rng.normal(0.0, t_sd, centers.shape))
     pts0 = pts + rng.normal(0.0, pt_sd, pts.shape)
     meta.setdefault("sigma_px", sigma_px)
     meta["mean_track"] = len(obs_cam) / len(pts)
