@@ -181,6 +181,39 @@ ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs,
                               const int32_t *obs_cam, const int64_t *obs_pt, int32_t *row_ptr,
                               int32_t *col, int64_t *nnzb);
 
+/* Allocation-free PCG for callers that cannot call cudaMalloc.
+ *
+ * The paper has no counterpart of this entry point; it serves callers that
+ * must not allocate device memory: code running while a framework owns the
+ * device memory pool (a caching allocator or a fixed arena), real-time loops
+ * that cannot take the allocator's lock or its implicit synchronisation, and
+ * hosts under a hard device-memory budget.  It solves S x = b by block-Jacobi
+ * PCG in FP32 (the iteration of ba_solve_rcs: y0 = 0, stop when
+ * ||r_k|| / ||r_0|| <= rel_tol or after max_iters iterations, 0 meaning
+ * max(1000, 6n)).
+ *
+ * All pointers are DEVICE pointers owned by the caller: row_ptr[n+1],
+ * col[nnzb] and val[nnzb x 36] are an FP32 BSMC matrix in the layout that
+ * ba_get_rcs returns (upper-triangle 6x6 blocks, row-major, the full diagonal
+ * block first in every row), b[n x 6] the right-hand side, x[n x 6] receives
+ * the solution.  iters_out and rel_resid_out (host pointers, may be NULL)
+ * receive the iteration count and the final ||r|| / ||r_0||.
+ *
+ * Scratch: one fixed array of about 2.2 MB in the library's device code,
+ * present on every GPU that loads the library until the process exits; n is
+ * limited to 8192 cameras (larger n returns BA_ERR_INVALID_ARG).  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU race on it.  Each call clears
+ * the parts that must start at zero.  The call allocates nothing (no
+ * cudaMalloc / cudaFree) and synchronises the stream every eight iterations
+ * to read the stop flag.  Errors: BA_ERR_INVALID_ARG, BA_ERR_NOT_SPD,
+ * BA_ERR_NO_CONVERGENCE (x holds the last iterate), BA_ERR_CUDA. */
+ba_status ba_pcg_solve_static(int32_t n, int64_t nnzb, const int32_t *row_ptr, const int32_t *col,
+                              const float *val, const float *b, float *x, double rel_tol,
+                              int32_t max_iters, void *cuda_stream, int32_t *iters_out,
+                              double *rel_resid_out);
+
 #ifdef __cplusplus
 }
 #endif

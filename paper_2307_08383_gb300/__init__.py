@@ -107,6 +107,8 @@ SIGNATURES = [
     ("ba_problem_destroy", None, [_P]),
     ("ba_last_error", ctypes.c_char_p, []),
     ("ba_symbolic_pattern", _S, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _I32, _I64, _I32, _I32, _I64]),
+    ("ba_pcg_solve_static", _S, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_double,
+                                 ctypes.c_int32, _P, _I32, _D]),
 ]
 
 _lib = None
@@ -376,3 +378,16 @@ class Problem:
 
     def reset_kernel_times(self):
         ba_reset_kernel_times(self.h)
+
+
+def ba_pcg_solve_static(n, nnzb, row_ptr, col, val, b, x, rel_tol, max_iters=0, stream=None):
+    """Allocation-free FP32 PCG on a BSMC system held in caller-owned device
+    buffers (addresses as ints, e.g. torch ``data_ptr()``); see include/ba.h.
+    Returns (status, iterations, final relative residual); raises BAError on
+    every status except BA_OK and BA_ERR_NO_CONVERGENCE."""
+    it = ctypes.c_int32()
+    rel = ctypes.c_double()
+    s = _check(lib().ba_pcg_solve_static(int(n), int(nnzb), row_ptr, col, val, b, x, float(rel_tol),
+                                         int(max_iters), stream, ctypes.byref(it), ctypes.byref(rel)),
+               allow=(BA_ERR_NO_CONVERGENCE,))
+    return s, it.value, rel.value

@@ -40,6 +40,8 @@ static ba_status fail(ba_status s, const std::string &m) {
 
 namespace ba {
 
+ba_status set_error(ba_status s, const char *msg) { return fail(s, msg); }
+
 const char *kernel_name(int k) {
     static const char *names[K_COUNT] = {"prepare_state", "linearize",  "cost",         "form_rcs",
                                          "rcs_reduce",    "rcs_diag",   "pcg_init",     "spmv",

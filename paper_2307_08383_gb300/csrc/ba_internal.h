@@ -135,6 +135,9 @@ struct ba_problem {
 
 namespace ba {
 
+// sets the calling thread's ba_last_error() message and returns s
+ba_status set_error(ba_status s, const char *msg);
+
 // kernel timing helpers (active when opt.profile != 0)
 void ktimer_begin(ba_problem *p, int k, cudaEvent_t *a);
 void ktimer_end(ba_problem *p, int k, cudaEvent_t a);
