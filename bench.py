@@ -54,6 +54,8 @@ def make_scene(workload: str, rank: int = 0):
         return scenes.ring_scene(seed=1001 + rank)
     if workload == "aerial_small":
         return scenes.aerial_small(seed=2101 + rank)
+    if workload == "aerial2400":
+        return scenes.aerial_small(n_along=60, n_across=40, pts_per_cam=200, seed=2201 + rank)
     raise ValueError(workload)
 
 
@@ -333,6 +335,31 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_kernel_case(args):
+    """A short driver for ncu captures: builds the problem for the workload,
+    linearizes once and runs the chosen kernel family three times."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2307_08383_gb300 as B
+    s = make_scene(args.workload)
+    opts = workload_opts(args.workload, B)
+    if args.pcg_tol:
+        opts.update(pcg_rel_tol=args.pcg_tol, inner_rel_tol=args.pcg_tol, refine_max=1)
+    g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, profile=2, **opts)
+    g.linearize()
+    for _ in range(3):
+        g.form_rcs(1e-6 if args.pcg_tol else 1e-4)
+        if args.kernel_case == "pcg":
+            g.solve_rcs()
+    torch.cuda.synchronize()
+    kt = {k: v for k, v in g.kernel_times().items() if v[0]}
+    print(json.dumps({"kernel_case": args.kernel_case, "workload": args.workload, "stats": g.stats(),
+                      "kernel_ms": kt}))
+    g.close()
+
+
 def _aerial5k_obs():
     # observation count of the full aerial workload (seeded, deterministic)
     return make_scene("aerial5k").n_obs
@@ -344,13 +371,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="aerial5k", choices=["aerial5k", "ring50", "aerial_small"])
+    ap.add_argument("--workload", default="aerial5k", choices=["aerial5k", "ring50", "aerial_small", "aerial2400"])
+    ap.add_argument("--kernel-case", default=None, choices=["form_rcs", "pcg"],
+                    help="profiling driver: run one kernel family a few times on the workload and exit")
+    ap.add_argument("--pcg-tol", type=float, default=None, help="kernel case: PCG relative tolerance")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.kernel_case:
+        run_kernel_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

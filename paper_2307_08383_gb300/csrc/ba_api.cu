@@ -43,16 +43,14 @@ namespace ba {
 ba_status set_error(ba_status s, const char *msg) { return fail(s, msg); }
 
 const char *kernel_name(int k) {
-    static const char *names[K_COUNT] = {"prepare_state", "linearize",  "cost",         "form_rcs",
-                                         "rcs_reduce",    "rcs_diag",   "pcg_init",     "spmv",
-                                         "pcg_update",    "resid64",    "back_substitute", "update",
-                                         "eval"};
+    static const char *names[K_COUNT] = {"prepare_state", "linearize", "cost",    "form_rcs",
+                                         "rcs_reduce",    "rcs_diag",  "pcg_init", "pcg_loop",
+                                         "resid64",       "back_substitute", "update", "eval"};
     return (k >= 0 && k < K_COUNT) ? names[k] : nullptr;
 }
 
 static bool timed(const ba_problem *p, int k) {
     if (!p->opt.profile) return false;
-    if (k == K_SPMV || k == K_PCG_UPDATE) return p->opt.profile >= 2;
     return true;
 }
 
@@ -252,7 +250,8 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     HostSetup &hs = p->hs;
     p->nnzb = (int64_t)hs.col.size();
     p->ngroups = (int64_t)hs.groups.size();
-    p->npart = (int64_t)hs.lb_info.size();
+    p->npart = (int64_t)hs.lb_gblk.size();
+    p->nitems = (int64_t)hs.items.size();
     const int64_t n = n_cams, P = n_pts, m = n_obs;
     const size_t E = p->esz;
 
@@ -260,9 +259,9 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     const size_t camc_w = p->fp32 ? 16 * 4 : 12 * 8;
     size_t plan = 2 * (n * 6 * 8 + P * 3 * 8 + n * camc_w + (p->fp32 ? P * 6 * 4 : 0)) +
                   m * 4 * 2 + (P + 1) * 4 + m * 16 + (p->fp32 ? m * 8 : 0) + m * JW * E + (n + 1) * 4 +
-                  p->nnzb * 4 + p->nnzb * BW * E + n * 6 * E + n * 36 * E + p->ngroups * sizeof(GroupDesc) +
-                  p->npart * 8 + hs.contrib.size() * 4 + (p->nnzb + 1) * 4 + p->npart * 4 + p->npart * BW * E +
-                  P * 9 * E + 7 * n * 6 * E + 3 * n * 6 * 8 + n * 6 * E + P * 3 * E + sizeof(DevScalars) +
+                  p->nnzb * 4 + 2 * (n + 1) * 4 + 2 * p->nnzb * 4 + (2 * p->nnzb - n) * 8 + p->nnzb * BW * E + n * 6 * E + n * 36 * E + p->ngroups * sizeof(GroupDesc) +
+                  p->nitems * 8 + hs.contrib.size() * 4 + (p->nnzb + 1) * 4 + p->npart * 4 + p->npart * BW * E +
+                  P * 9 * E + 8 * n * 6 * E + 3 * n * 6 * 8 + n * 6 * E + P * 3 * E + sizeof(DevScalars) +
                   RED_SLOTS * 8 + N_COUNTERS * 4;
     if (o.device_mem_cap && plan > o.device_mem_cap) {
         delete p;
@@ -305,18 +304,23 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     ALR(p->J, m * JW * E);
     AL(p->row_ptr, n + 1);
     AL(p->col, p->nnzb);
+    AL(p->ct_ptr, n + 1);
+    AL(p->ct_blk, p->nnzb - n);
+    AL(p->ct_row, p->nnzb - n);
+    AL(p->tw_ptr, n + 1);
+    AL(p->tw_ent, 2 * p->nnzb - n);
     ALR(p->S, p->nnzb * BW * E);
     ALR(p->b, n * 6 * E);
     ALR(p->Minv, n * 36 * E);
     AL(p->grp, p->ngroups);
-    AL(p->lb_info, p->npart);
+    AL(p->items, p->nitems);
     AL(p->contrib, hs.contrib.size());
     AL(p->pptr, p->nnzb + 1);
     AL(p->plist, p->npart);
     ALR(p->part, p->npart * BW * E);
     ALR(p->Linv, P * 6 * E);
     ALR(p->lp, P * 3 * E);
-    for (int k = 0; k < 6; ++k) ALR(p->pv[k], n * 6 * E);
+    for (int k = 0; k < 8; ++k) ALR(p->pv[k], n * 6 * E);
     AL(p->x64, n * 6);
     AL(p->r64, n * 6);
     AL(p->q64, n * 6);
@@ -357,8 +361,13 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     }
     up_ok(upload(p, p->row_ptr, hs.row_ptr.data(), n + 1));
     up_ok(upload(p, p->col, hs.col.data(), p->nnzb));
+    up_ok(upload(p, p->ct_ptr, hs.ct_ptr.data(), n + 1));
+    up_ok(upload(p, p->ct_blk, hs.ct_blk.data(), p->nnzb - n));
+    up_ok(upload(p, p->ct_row, hs.ct_row.data(), p->nnzb - n));
+    up_ok(upload(p, p->tw_ptr, hs.tw_ptr.data(), n + 1));
+    up_ok(upload(p, p->tw_ent, hs.tw_ent.data(), 2 * p->nnzb - n));
     up_ok(upload(p, p->grp, hs.groups.data(), p->ngroups));
-    up_ok(upload(p, p->lb_info, hs.lb_info.data(), p->npart));
+    up_ok(upload(p, p->items, hs.items.data(), p->nitems));
     up_ok(upload(p, p->contrib, hs.contrib.data(), hs.contrib.size()));
     up_ok(upload(p, p->pptr, hs.pptr.data(), p->nnzb + 1));
     up_ok(upload(p, p->plist, hs.plist.data(), p->npart));
@@ -370,13 +379,18 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     up_ok(cudaMemsetAsync(p->dxp, 0, P * 3 * E, p->st));
     // drop host copies that the device now holds (keep permutations and pattern)
     std::vector<GroupDesc>().swap(hs.groups);
-    std::vector<uint32_t>().swap(hs.lb_info);
+    std::vector<ItemDesc>().swap(hs.items);
     std::vector<int32_t>().swap(hs.lb_gblk);
     std::vector<uint32_t>().swap(hs.contrib);
     std::vector<int32_t>().swap(hs.pptr);
     std::vector<int32_t>().swap(hs.plist);
     std::vector<int32_t>().swap(hs.obs_pt);
     std::vector<int32_t>().swap(hs.trk_ptr);
+    std::vector<int32_t>().swap(hs.ct_ptr);
+    std::vector<int32_t>().swap(hs.ct_blk);
+    std::vector<int32_t>().swap(hs.ct_row);
+    std::vector<int32_t>().swap(hs.tw_ptr);
+    std::vector<int2>().swap(hs.tw_ent);
     if (e == cudaSuccess) e = launch_prepare_state(p, p->cur);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
     if (e != cudaSuccess) {
@@ -444,14 +458,12 @@ ba_status ba_form_rcs(ba_problem *p, double lambda) {
 
 static ba_status run_pcg(ba_problem *p, const void *rhs, double tol, int max_iters, int *iters) {
     CK(p, launch_pcg_init(p, rhs, tol, max_iters));
-    int it = 0;
-    const int chunk = 8;
-    for (;;) {
-        for (int c = 0; c < chunk; ++c, ++it) CK(p, launch_pcg_iter(p, it));
-        ba_status s = sync_scalars(p);
-        if (s) return s;
-        if (p->sc_host->done) break;
-        if (it > max_iters + 2 * chunk) return fail(BA_ERR_INTERNAL, "PCG did not stop");
+    CK(p, launch_pcg_loop(p));
+    ba_status s = sync_scalars(p);
+    if (s) return s;
+    if (p->sc_host->err == BA_ERR_TIMEOUT) {
+        p->dead = true;
+        return fail(BA_ERR_TIMEOUT, "PCG grid barrier timed out");
     }
     *iters = p->sc_host->iters;
     return BA_OK;

@@ -20,16 +20,27 @@ constexpr int BW = 36;
 constexpr int OBS_MAX_DEFAULT = 512;  // observations staged per point group
 constexpr int OBS_MAX_LIMIT = 1024;
 constexpr int LB_MAX = 2048;          // local blocks (sub-RCS blocks) per group
-constexpr int C_MAX = 16384;          // (obs, obs) products per group
+constexpr int C_MAX = 4096;           // (obs, obs) products per group (staged in shared memory)
+constexpr int ITEM_MAX = 8;           // products per work item
 constexpr int FORM_THREADS = 256;
 
 // A point group: a run of whole point tracks formed by one CTA (Sec. 6.1).
 struct GroupDesc {
-    int64_t c_begin;   // first (a, b) product in the contribution array
-    int64_t lb_begin;  // first local block == first partial written by the group
+    int64_t c_begin;     // first (a, b) product in the contribution array
+    int64_t part_begin;  // first partial written by the group
+    int64_t item_begin;  // first work item
     int32_t obs_begin, nobs;
     int32_t pt_begin, npts;
-    int32_t nlb, nc;
+    int32_t nitems, nc;
+};
+
+// A work item: up to ITEM_MAX products of one sub-RCS block.
+//   x: cbeg (16) | cnt (4) << 16 | diag << 20 | nfollow (5) << 21 | head << 26
+//   y: partial index (relative to the group) written by the head item
+// Items sit 32 to a warp in order; a block's consecutive items within a warp
+// form a run, summed by a segmented shuffle reduction into the run's head.
+struct ItemDesc {
+    uint32_t x, y;
 };
 
 // Device-resident scalars of the reductions and of the PCG recurrence.
@@ -45,7 +56,7 @@ constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
 
 enum KernelId {
     K_PREPARE = 0, K_LINEARIZE, K_COST, K_FORM_RCS, K_RCS_REDUCE, K_RCS_DIAG,
-    K_PCG_INIT, K_SPMV, K_PCG_UPDATE, K_RESID64, K_BACKSUB, K_UPDATE, K_EVAL, K_COUNT
+    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_EVAL, K_COUNT
 };
 const char *kernel_name(int k);
 
@@ -59,9 +70,14 @@ struct HostSetup {
     std::vector<int32_t> trk_ptr;    // P + 1
     std::vector<int32_t> row_ptr;    // n + 1
     std::vector<int32_t> col;        // nnzb
+    std::vector<int32_t> ct_ptr;     // n + 1: blocks (j < i, i) of column i ...
+    std::vector<int32_t> ct_blk;     // ... their BSMC ids, j ascending
+    std::vector<int32_t> ct_row;     // ... and their rows j
+    std::vector<int32_t> tw_ptr;     // n + 1: entries of row i for the SpMV ...
+    std::vector<int2> tw_ent;        // ... {block id | transposed << 31, column j}: row blocks, then column blocks
     std::vector<GroupDesc> groups;
-    std::vector<uint32_t> lb_info;   // cbeg | count << 16 | diag << 31 (relative to c_begin)
-    std::vector<int32_t> lb_gblk;    // global block of each local block
+    std::vector<ItemDesc> items;
+    std::vector<int32_t> lb_gblk;    // global block of each partial
     std::vector<uint32_t> contrib;   // a | b << 16 (observation offsets in the group)
     std::vector<int32_t> pptr;       // nnzb + 1: partials of each global block
     std::vector<int32_t> plist;
@@ -103,13 +119,18 @@ struct ba_problem {
     float *uv32 = nullptr;
     void *J = nullptr;
     int32_t *row_ptr = nullptr, *col = nullptr;
+    int32_t *ct_ptr = nullptr, *ct_blk = nullptr, *ct_row = nullptr;
+    int32_t *tw_ptr = nullptr;
+    int2 *tw_ent = nullptr;
     void *S = nullptr, *b = nullptr, *Minv = nullptr;
     ba::GroupDesc *grp = nullptr;
-    uint32_t *lb_info = nullptr, *contrib = nullptr;
+    ba::ItemDesc *items = nullptr;
+    uint32_t *contrib = nullptr;
+    int64_t nitems = 0;
     int32_t *pptr = nullptr, *plist = nullptr;
     void *part = nullptr;
     void *Linv = nullptr, *lp = nullptr;
-    void *pv[6] = {};  // y, r, z, d0, d1, q   (n x 6, mode precision)
+    void *pv[8] = {};  // y, r, z, d0, d1, q, r', q'   (n x 6, mode precision)
     double *x64 = nullptr, *r64 = nullptr, *q64 = nullptr;
     void *dxc = nullptr, *dxp = nullptr;
     ba::DevScalars *sc = nullptr;
@@ -149,7 +170,7 @@ cudaError_t launch_linearize(ba_problem *p);
 cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial);
 cudaError_t launch_form_rcs(ba_problem *p, double lambda);
 cudaError_t launch_pcg_init(ba_problem *p, const void *rhs_T, double tol, int max_iters);
-cudaError_t launch_pcg_iter(ba_problem *p, int it);
+cudaError_t launch_pcg_loop(ba_problem *p);
 cudaError_t launch_resid64(ba_problem *p, bool from_x64);
 cudaError_t launch_solution_to_step(ba_problem *p);
 cudaError_t launch_refine_rhs(ba_problem *p, void *rhs_T);

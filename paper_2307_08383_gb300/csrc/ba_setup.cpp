@@ -150,6 +150,34 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
     }
     if (pattern_only) return BA_OK;
 
+    // ---- column index of the upper triangle: for every column i the off-diagonal
+    //      blocks (j, i), j < i, in row order (the SpMV applies them transposed)
+    hs.ct_ptr.assign(n + 1, 0);
+    for (int32_t j = 0; j < n; ++j)
+        for (int32_t b = hs.row_ptr[j] + 1; b < hs.row_ptr[j + 1]; ++b) hs.ct_ptr[hs.col[b] + 1]++;
+    for (int32_t i = 0; i < n; ++i) hs.ct_ptr[i + 1] += hs.ct_ptr[i];
+    hs.ct_blk.assign(hs.ct_ptr[n], 0);
+    hs.ct_row.assign(hs.ct_ptr[n], 0);
+    {
+        std::vector<int32_t> fill(hs.ct_ptr.begin(), hs.ct_ptr.end() - 1);
+        for (int32_t j = 0; j < n; ++j)
+            for (int32_t b = hs.row_ptr[j] + 1; b < hs.row_ptr[j + 1]; ++b) {
+                const int32_t at = fill[hs.col[b]]++;
+                hs.ct_blk[at] = b;
+                hs.ct_row[at] = j;
+            }
+    }
+    // ---- two-sided SpMV entries of row i: (i, j >= i) as stored, then (j < i, i) transposed
+    hs.tw_ptr.assign(n + 1, 0);
+    hs.tw_ent.clear();
+    hs.tw_ent.reserve(2 * hs.col.size());
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t b = hs.row_ptr[i]; b < hs.row_ptr[i + 1]; ++b) hs.tw_ent.push_back(make_int2(b, hs.col[b]));
+        for (int32_t q = hs.ct_ptr[i]; q < hs.ct_ptr[i + 1]; ++q)
+            hs.tw_ent.push_back(make_int2((int32_t)((uint32_t)hs.ct_blk[q] | 0x80000000u), hs.ct_row[q]));
+        hs.tw_ptr[i + 1] = (int32_t)hs.tw_ent.size();
+    }
+
     // ---- point groups with their sub-RCS blocks (Sec. 6.1)
     const int64_t nnzb = (int64_t)hs.col.size();
     std::vector<int32_t> lb_stamp(nnzb, -1), lb_local(nnzb, 0);
@@ -157,7 +185,7 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
     std::vector<std::pair<int32_t, uint32_t>> g_c;  // (local block, a | b << 16)
     std::vector<int32_t> trk_g;                     // global ids of the current track's pairs
     hs.groups.clear();
-    hs.lb_info.clear();
+    hs.items.clear();
     hs.lb_gblk.clear();
     hs.contrib.clear();
     hs.n_pairs = 0;
@@ -167,37 +195,65 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
         if (g.npts == 0) return;
         const int32_t nlb = (int32_t)g_gblk.size();
         std::vector<int32_t> cnt(nlb, 0);
+        std::vector<char> is_diag(nlb, 0);
         for (auto &c : g_c) cnt[c.first]++;
-        // local blocks by contribution count (descending) so that neighbouring
-        // threads of the CTA run loops of similar length; ties by global id
+        for (int32_t b = 0; b < nlb; ++b) {
+            // a block is diagonal iff it is the first block of its row
+            auto it = std::upper_bound(hs.row_ptr.begin(), hs.row_ptr.end(), g_gblk[b]);
+            is_diag[b] = hs.row_ptr[(it - hs.row_ptr.begin()) - 1] == g_gblk[b];
+        }
+        // diagonal blocks first (one code path per warp), then by product count
+        // (descending) so that full items share warps; ties by global id
         std::vector<int32_t> ord(nlb);
         std::iota(ord.begin(), ord.end(), 0);
         std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
-            return cnt[x] > cnt[y] || (cnt[x] == cnt[y] && g_gblk[x] < g_gblk[y]);
+            if (is_diag[x] != is_diag[y]) return is_diag[x] > is_diag[y];
+            if (cnt[x] != cnt[y]) return cnt[x] > cnt[y];
+            return g_gblk[x] < g_gblk[y];
         });
         std::vector<int32_t> pos(nlb), start(nlb + 1, 0);
         for (int32_t r = 0; r < nlb; ++r) pos[ord[r]] = r;
         for (int32_t r = 0; r < nlb; ++r) start[r + 1] = start[r] + cnt[ord[r]];
         g.c_begin = (int64_t)hs.contrib.size();
-        g.lb_begin = (int64_t)hs.lb_info.size();
-        g.nlb = nlb;
+        g.part_begin = (int64_t)hs.lb_gblk.size();
+        g.item_begin = (int64_t)hs.items.size();
         g.nc = (int32_t)g_c.size();
-        hs.contrib.resize(hs.contrib.size() + g_c.size());
+        // each group's list starts on a 16-byte boundary and spans a multiple of 16 bytes (bulk copies)
+        hs.contrib.resize(hs.contrib.size() + ((g_c.size() + 3) & ~(size_t)3), 0u);
         std::vector<int32_t> fill(start.begin(), start.end() - 1);
         for (auto &c : g_c) hs.contrib[g.c_begin + fill[pos[c.first]]++] = c.second;  // stable: point order
+        // work items of <= ITEM_MAX products, sizes balanced within a block
+        struct It { int32_t blk, cbeg, cnt; };
+        std::vector<It> its;
         for (int32_t r = 0; r < nlb; ++r) {
-            int32_t gb = g_gblk[ord[r]];
-            int32_t i = 0;
-            // the block is diagonal iff its column is the first of its row
-            bool diag = false;
-            {
-                auto it = std::upper_bound(hs.row_ptr.begin(), hs.row_ptr.end(), gb);
-                i = (int32_t)(it - hs.row_ptr.begin()) - 1;
-                diag = (hs.row_ptr[i] == gb);
+            const int32_t c = cnt[ord[r]];
+            const int32_t k = (c + ITEM_MAX - 1) / ITEM_MAX;
+            int32_t off = start[r];
+            for (int32_t q = 0; q < k; ++q) {
+                const int32_t sz = c / k + (q < c % k ? 1 : 0);
+                its.push_back({r, off, sz});
+                off += sz;
             }
-            hs.lb_info.push_back((uint32_t)start[r] | ((uint32_t)cnt[ord[r]] << 16) | (diag ? 0x80000000u : 0u));
-            hs.lb_gblk.push_back(gb);
         }
+        // runs: consecutive items of one block inside one warp of 32
+        const int32_t nit = (int32_t)its.size();
+        int32_t npart = 0;
+        for (int32_t q = 0; q < nit;) {
+            int32_t e = q + 1;
+            while (e < nit && its[e].blk == its[q].blk && (e / 32) == (q / 32)) ++e;
+            for (int32_t t = q; t < e; ++t) {
+                ItemDesc d;
+                const bool dg = is_diag[ord[its[t].blk]];
+                d.x = (uint32_t)its[t].cbeg | ((uint32_t)its[t].cnt << 16) | ((uint32_t)dg << 20) |
+                      ((uint32_t)(e - 1 - t) << 21) | ((uint32_t)(t == q) << 26);
+                d.y = (t == q) ? (uint32_t)npart : 0u;
+                hs.items.push_back(d);
+            }
+            hs.lb_gblk.push_back(g_gblk[ord[its[q].blk]]);
+            ++npart;
+            q = e;
+        }
+        g.nitems = nit;
         hs.groups.push_back(g);
         g_gblk.clear();
         g_c.clear();
@@ -218,7 +274,7 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
             }
         if (L > obs_max || npair > C_MAX || npair > LB_MAX) {
             err = "point " + std::to_string(hs.pt_perm[k]) + " has a track of " + std::to_string(L) +
-                  " observations; the limit is " + std::to_string(std::min(obs_max, 180));
+                  " observations; the limit is " + std::to_string(std::min(obs_max, 90));
             return BA_ERR_INVALID_ARG;
         }
         if (g.npts > 0 && (g.nobs + L > obs_max || g.nc + npair > C_MAX || (int32_t)g_gblk.size() + fresh > LB_MAX))
@@ -242,7 +298,7 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
         hs.n_pairs += npair;
     }
     close_group();
-    if (hs.lb_info.size() >= (size_t)INT32_MAX) { err = "more than 2^31 partial blocks"; return BA_ERR_INVALID_ARG; }
+    if (hs.lb_gblk.size() >= (size_t)INT32_MAX) { err = "more than 2^31 partial blocks"; return BA_ERR_INVALID_ARG; }
     // ---- partials of each global block (segmented-reduction CSR), in group order
     hs.pptr.assign(nnzb + 1, 0);
     for (int32_t gb : hs.lb_gblk) hs.pptr[gb + 1]++;

@@ -9,8 +9,6 @@
 
 namespace ba {
 
-template <typename T> struct Vec;  // not used directly
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -76,6 +74,27 @@ template <typename T> __device__ __forceinline__ T dmax(T a, T b) { return a > b
 template <typename T> __device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
 
 __device__ __forceinline__ double clampd(double x) { return x < 1e-6 ? 1e-6 : (x > 1e32 ? 1e32 : x); }
+template <typename T> __device__ __forceinline__ T clampT(T x) { return x < T(1e-6) ? T(1e-6) : (x > T(1e32) ? T(1e32) : x); }
+
+// Per-thread running sum in the mode precision.  FP32: compensated
+// (Knuth TwoSum, error-free per step), so a thread's partial keeps about
+// twice FP32 precision without touching GB300's slow FP64 pipe; the
+// partials are then added across threads in FP64.  FP64: plain.
+template <typename T> struct RunSum;
+template <> struct RunSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x, z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+template <> struct RunSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
 
 // In-place Cholesky of a symmetric 6x6 (row-major, lower triangle used) and
 // the inverse A^-1 = L^-T L^-1 written full.  Returns false if not SPD.
@@ -174,5 +193,112 @@ __device__ __forceinline__ void quat_to_R(const double *q, double *R) {
 }
 
 template <typename T> __device__ __forceinline__ void red_add(T *p, T v) { atomicAdd(p, v); }
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).
+// bar[0] counts arrivals, bar[1] is the generation.  The wait is bounded by
+// about `limit_cycles` SM clocks; on timeout it sets *err = BA_ERR_TIMEOUT and
+// returns false, and the caller must leave the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, long long limit_cycles) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g0) {
+                if (clock64() - t0 > limit_cycles || *(volatile int *)err == (int)BA_ERR_TIMEOUT) {
+                    atomicExch(err, (int)BA_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Grid-wide all-reduce fused with a barrier (cooperative launch).  On entry
+// v holds this CTA's partial in thread 0; every CTA stores it, the last CTA
+// to arrive adds the partials in CTA order, publishes the totals in bcast and
+// releases the others; on return every thread holds the totals.  Waits are
+// bounded as in grid_barrier; returns false on timeout.
+__device__ __forceinline__ unsigned atom_add_release(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_allreduce(double (&v)[NV], double *part, double *bcast, unsigned *bar, int *err,
+                                               long long limit_cycles) {
+    __shared__ int s_last, s_ok;
+    __shared__ double s_tot[NV];
+    __shared__ double s_red[32 * NV];
+    unsigned g0 = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[blockIdx.x * NV + k] = v[k];
+        g0 = ld_acquire(bar + 1);
+        // release: the partial above is visible to whoever sees this arrival
+        const unsigned arrived = atom_add_release(bar, 1u);
+        s_last = (arrived == gridDim.x - 1);
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        if (threadIdx.x == 0) ld_acquire(bar);  // acquire: every CTA's partial is visible
+        __syncthreads();
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += __ldcg(part + b * NV + k);
+        block_sum<NV>(acc, s_red);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                __stcg(bcast + k, acc[k]);
+                s_tot[k] = acc[k];
+            }
+            atomicExch(bar, 0u);
+            atom_add_release(bar + 1, 1u);  // release: totals and the reset counter
+        }
+    } else if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        while (ld_acquire(bar + 1) == g0) {
+            if (clock64() - t0 > limit_cycles || *(volatile int *)err == (int)BA_ERR_TIMEOUT) {
+                atomicExch(err, (int)BA_ERR_TIMEOUT);
+                s_ok = 0;
+                break;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s_tot[k] = __ldcg(bcast + k);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = s_tot[k];
+    const bool ok = s_ok != 0;
+    __syncthreads();
+    return ok;
+}
 
 }  // namespace ba

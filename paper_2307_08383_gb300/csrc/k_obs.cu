@@ -90,9 +90,10 @@ __device__ __forceinline__ void cam_point(const float *camc, const double *, con
     for (int r = 0; r < 3; ++r) Xc[r] = R[3 * r] * D[0] + R[3 * r + 1] * D[1] + R[3 * r + 2] * D[2];
 }
 
-__device__ __forceinline__ double huber_rho(double s, int on, double delta) {
+template <typename T>
+__device__ __forceinline__ T huber_rho(T s, int on, T delta) {
     if (!on || s <= delta * delta) return s;
-    return 2.0 * delta * sqrt(s) - delta * delta;
+    return T(2) * delta * sqrt(s) - delta * delta;
 }
 
 // --------------------------------------------------------------------------
@@ -132,9 +133,9 @@ __global__ void __launch_bounds__(256) k_linearize(int64_t m, const int *__restr
             o[15 + c] = a1 * R[3 + c] + a3 * R[6 + c];
         }
         if (huber) {
-            const double s = (double)e0 * e0 + (double)e1 * e1;
-            if (s > delta * delta) {
-                const T sw = (T)sqrt(delta / sqrt(s));
+            const T s = e0 * e0 + e1 * e1, dl = (T)delta;
+            if (s > dl * dl) {
+                const T sw = sqrt(dl / sqrt(s));
 #pragma unroll
                 for (int q = 0; q < 18; ++q) o[q] *= sw;
                 e0 *= sw;
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
                                               const double *__restrict__ pts, const float *__restrict__ pts_hl,
                                               Intr in, int huber, double delta, DevScalars *sc, int trial,
                                               double *red, unsigned *ctr) {
-    double v[2] = {0.0, 0.0};
+    RunSum<T> f;
+    int ncheir = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
         const int i = obs_cam[a], k = obs_pt[a];
         T Xc[3], R[9];
@@ -173,9 +175,10 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
         const T iz = T(1) / Xc[2];
         const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
         const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
-        v[0] += huber_rho((double)e0 * e0 + (double)e1 * e1, huber, delta);
-        v[1] += (Xc[2] <= T(1e-6)) ? 1.0 : 0.0;
+        f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
+        ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
     }
+    double v[2] = {f.get(), (double)ncheir};
     grid_sum<2>(v, red, ctr, [&](double *t) {
         if (trial) {
             sc->cost_trial = 0.5 * t[0];
@@ -230,7 +233,8 @@ __global__ void __launch_bounds__(256) k_eval(int64_t m, const int *__restrict__
                                               const T *__restrict__ J, const T *__restrict__ dxc,
                                               const T *__restrict__ dxp, Intr in, int huber, double delta,
                                               DevScalars *sc, double *red, unsigned *ctr) {
-    double v[3] = {0.0, 0.0, 0.0};
+    RunSum<T> f, mdl;
+    int ncheir = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
         const int i = obs_cam[a], k = obs_pt[a];
         T Xc[3], R[9];
@@ -238,8 +242,8 @@ __global__ void __launch_bounds__(256) k_eval(int64_t m, const int *__restrict__
         const T iz = T(1) / Xc[2];
         const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
         const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
-        v[0] += huber_rho((double)e0 * e0 + (double)e1 * e1, huber, delta);
-        v[2] += (Xc[2] <= T(1e-6)) ? 1.0 : 0.0;
+        f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
+        ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
         const T *j = J + a * JW;
         T dc[6], dp[3];
 #pragma unroll
@@ -251,8 +255,9 @@ __global__ void __launch_bounds__(256) k_eval(int64_t m, const int *__restrict__
         for (int c = 0; c < 6; ++c) { jd0 += j[c] * dc[c]; jd1 += j[6 + c] * dc[c]; }
 #pragma unroll
         for (int c = 0; c < 3; ++c) { jd0 += j[12 + c] * dp[c]; jd1 += j[15 + c] * dp[c]; }
-        v[1] -= (double)jd0 * (2.0 * (double)j[18] + (double)jd0) + (double)jd1 * (2.0 * (double)j[19] + (double)jd1);
+        mdl.add(-(jd0 * (T(2) * j[18] + jd0) + jd1 * (T(2) * j[19] + jd1)));
     }
+    double v[3] = {f.get(), mdl.get(), (double)ncheir};
     grid_sum<3>(v, red, ctr, [&](double *t) {
         sc->cost_trial = 0.5 * t[0];
         sc->model = 0.5 * t[1];

@@ -6,96 +6,145 @@
 //   alpha = r^T M^-1 r / d^T S d, y += alpha d, r -= alpha S d,
 //   stop if ||r|| <= T ||r0||, beta = r+^T M^-1 r+ / r^T M^-1 r,
 //   d = M^-1 r+ + beta d.
-// Two kernels per iteration: the SpMV forms d = z + beta d_old on the fly
-// (double-buffered d), q = S d and d^T S d; the update kernel does the axpys,
-// z = M^-1 r and the two dot products.  Reductions end in the last CTA (no
-// waiting), and a device flag stops the recurrence, so a batch of iterations
-// is queued without host round trips.
+// The whole recurrence runs in one persistent cooperative kernel: per
+// iteration a BSMC SpMV phase forms d = z + beta d_old on the fly (double-
+// buffered d), q = S d and d^T S d; a grid barrier; an update phase does the
+// axpys, z = M^-1 r and the two dot products; a second barrier.  Every CTA
+// sums the per-CTA partials in the same order, so all CTAs take the same
+// alpha, beta and stop decision without a third barrier.  Barrier waits are
+// bounded; a timeout sets an error flag and every CTA leaves.
+#include <algorithm>
+
 #include "device_util.cuh"
 
 namespace ba {
 
-// q += S x over BSMC: a warp per block row; each lane takes blocks of the
-// row, adds S_ij x_j to its row sum and scatters S_ij^T x_i to q_j.
-// PCG variant: x_j = z_j + beta d_old_j, row owner stores d_new_i, and the
-// quadratic form d^T S d is accumulated (each off-diagonal block twice).
+// One 6x6 block (16-byte aligned) into registers, read-only path.
+template <typename TS, typename TV>
+__device__ __forceinline__ void load_block(const TS *__restrict__ Sb, TV (&v)[36]) {
+    if constexpr (sizeof(TS) == 4) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(Sb);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float4 t = __ldg(s4 + q);
+            v[4 * q] = (TV)t.x; v[4 * q + 1] = (TV)t.y; v[4 * q + 2] = (TV)t.z; v[4 * q + 3] = (TV)t.w;
+        }
+    } else {
+        const double2 *s2 = reinterpret_cast<const double2 *>(Sb);
+#pragma unroll
+        for (int q = 0; q < 18; ++q) {
+            const double2 t = __ldg(s2 + q);
+            v[2 * q] = (TV)t.x; v[2 * q + 1] = (TV)t.y;
+        }
+    }
+}
+
+// Six entries of a camera vector (24 B for FP32, 8-byte aligned; 48 B for FP64).
+__device__ __forceinline__ void load6(const float *p, float (&v)[6]) {
+    const float2 *p2 = reinterpret_cast<const float2 *>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float2 t = __ldcg(p2 + k);
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+__device__ __forceinline__ void load6(const double *p, double (&v)[6]) {
+    const double2 *p2 = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double2 t = __ldcg(p2 + k);
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+
+template <typename TV, bool PCG>
+__device__ __forceinline__ void gather_x(const TV *__restrict__ xz, const TV *__restrict__ dold, TV beta, int j,
+                                         TV (&x)[6]) {
+    load6(xz + 6 * j, x);
+    if (PCG) {
+        TV d[6];
+        load6(dold + 6 * j, d);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) x[c] += beta * d[c];
+    }
+}
+
+template <typename TV>
+__device__ __forceinline__ void block_apply(const TV (&Sv)[36], const TV (&x)[6], bool transposed, TV (&acc)[6]) {
+    if (!transposed) {
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[r] += Sv[6 * r + c] * x[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int r = 0; r < 6; ++r) acc[c] += Sv[6 * r + c] * x[r];
+    }
+}
+
+// q = S x over BSMC without atomics: a warp per block row i walks the row's
+// two-sided entry list - the stored blocks (i, j >= i), applied as S_ij x_j,
+// then the blocks (j < i, i) of column i, applied as S_ji^T x_j - so q_i is
+// one warp's sum: deterministic, no zeroing, no red.add.  (Fig. 13 reads each
+// block once and scatters; here each off-diagonal block is read twice, from
+// L2.)  A lane takes two entries at a time and issues all their loads before
+// any arithmetic, so one L2 round trip covers ~64 blocks of the row.
+// PCG variant: x_j = z_j + beta d_old_j, the row owner stores d_new_i, and the
+// function returns this thread's share of d^T S d = sum_i d_i^T q_i.
 template <typename TS, typename TV, bool PCG>
-__global__ void __launch_bounds__(256) k_spmv(int n, const int *__restrict__ row_ptr, const int *__restrict__ col,
-                                              const TS *__restrict__ S, const TV *__restrict__ xz,
-                                              const TV *__restrict__ dold, TV *__restrict__ dnew, TV *__restrict__ q,
-                                              DevScalars *sc, double *red, unsigned *ctr) {
-    if (PCG && sc->done) return;
-    const TV beta = PCG ? (TV)sc->beta : TV(0);
+__device__ __forceinline__ double spmv_rows(int n, const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
+                                            const TS *__restrict__ S, const TV *__restrict__ xz,
+                                            const TV *__restrict__ dold, TV *__restrict__ dnew, TV *__restrict__ q,
+                                            TV beta) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
-    double pap = 0.0;
+    TV pap = TV(0);
     for (int i = warp; i < n; i += nw) {
+        const int tb = __ldg(tw_ptr + i), te = __ldg(tw_ptr + i + 1);
         TV di[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) di[c] = PCG ? xz[6 * i + c] + beta * dold[6 * i + c] : xz[6 * i + c];
+        gather_x<TV, PCG>(xz, dold, beta, i, di);
         if (PCG) {
 #pragma unroll
             for (int c = 0; c < 6; ++c)
                 if (lane == c) dnew[6 * i + c] = di[c];
         }
         TV acc[6] = {0, 0, 0, 0, 0, 0};
-        const int rb = row_ptr[i], re = row_ptr[i + 1];
-        for (int blk = rb + lane; blk < re; blk += 32) {
-            const int j = col[blk];
-            const TS *Sb = S + (int64_t)blk * BW;
-            TV Sv[36];
-#pragma unroll
-            for (int t = 0; t < 36; ++t) Sv[t] = (TV)Sb[t];
-            TV dj[6];
-            if (j == i) {
-#pragma unroll
-                for (int c = 0; c < 6; ++c) dj[c] = di[c];
-            } else {
-#pragma unroll
-                for (int c = 0; c < 6; ++c) dj[c] = PCG ? xz[6 * j + c] + beta * dold[6 * j + c] : xz[6 * j + c];
-            }
-            double qf = 0.0;
-#pragma unroll
-            for (int r = 0; r < 6; ++r) {
-                TV t = TV(0);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) t += Sv[6 * r + c] * dj[c];
-                acc[r] += t;
-                qf += (double)di[r] * (double)t;
-            }
-            if (j != i) {
-                pap += 2.0 * qf;
-#pragma unroll
-                for (int c = 0; c < 6; ++c) {
-                    TV u = TV(0);
-#pragma unroll
-                    for (int r = 0; r < 6; ++r) u += Sv[6 * r + c] * di[r];
-                    atomicAdd(q + 6 * j + c, u);
-                }
-            } else {
-                pap += qf;
-            }
+        for (int t0 = tb + lane; t0 < te; t0 += 64) {
+            const int t1 = t0 + 32;
+            const bool has1 = t1 < te;
+            const int2 ea = __ldg(tw_ent + t0);
+            const int2 eb = has1 ? __ldg(tw_ent + t1) : ea;
+            TV Sa[36], Sb[36], xa[6], xb[6];
+            load_block<TS, TV>(S + (int64_t)(ea.x & 0x7fffffff) * BW, Sa);
+            load_block<TS, TV>(S + (int64_t)(eb.x & 0x7fffffff) * BW, Sb);
+            gather_x<TV, PCG>(xz, dold, beta, ea.y, xa);
+            gather_x<TV, PCG>(xz, dold, beta, eb.y, xb);
+            block_apply<TV>(Sa, xa, ea.x < 0, acc);
+            if (has1) block_apply<TV>(Sb, xb, eb.x < 0, acc);
         }
 #pragma unroll
         for (int r = 0; r < 6; ++r) acc[r] = warp_sum(acc[r]);
-        if (lane == 0)
 #pragma unroll
-            for (int r = 0; r < 6; ++r) atomicAdd(q + 6 * i + r, acc[r]);
+        for (int c = 0; c < 6; ++c)
+            if (lane == c) q[6 * i + c] = acc[c];
+        if (PCG && lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) pap += di[c] * acc[c];
+        }
     }
-    if (PCG) {
-        double v[1] = {pap};
-        grid_sum<1>(v, red, ctr, [&](double *t) {
-            sc->pAp = t[0];
-            if (!(t[0] > 0.0)) {
-                sc->done = 1;
-                sc->err = (int)BA_ERR_NOT_SPD;
-                sc->alpha = 0.0;
-            } else {
-                sc->alpha = sc->rz / t[0];
-            }
-        });
-    }
+    return (double)pap;
+}
+
+// q = S x with FP64 accumulation, for the refinement residual.
+template <typename TS>
+__global__ void __launch_bounds__(256) k_spmv64(int n, const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
+                                                const TS *__restrict__ S, const double *__restrict__ x, double *q) {
+    spmv_rows<TS, double, false>(n, tw_ptr, tw_ent, S, x, nullptr, nullptr, q, 0.0);
 }
 
 template <typename T>
@@ -112,9 +161,9 @@ __device__ __forceinline__ void apply_minv(const T *__restrict__ Minv, int i, co
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_pcg_init(int n, const T *__restrict__ rhs, const T *__restrict__ Minv, T *y, T *r,
-                                                  T *z, T *dold, T *q, DevScalars *sc, double tol2, int max_iters,
+                                                  T *z, T *dold, T *q, T *q1, DevScalars *sc, double tol2, int max_iters,
                                                   double *red, unsigned *ctr) {
-    double v[2] = {0.0, 0.0};
+    T rz_p = T(0), rr_p = T(0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         T ri[6], zi[6];
 #pragma unroll
@@ -123,16 +172,18 @@ __global__ void __launch_bounds__(256) k_pcg_init(int n, const T *__restrict__ r
             r[6 * i + c] = ri[c];
             y[6 * i + c] = T(0);
             q[6 * i + c] = T(0);
+            q1[6 * i + c] = T(0);
             dold[6 * i + c] = T(0);
         }
         apply_minv(Minv, i, ri, zi);
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             z[6 * i + c] = zi[c];
-            v[0] += (double)ri[c] * (double)zi[c];
-            v[1] += (double)ri[c] * (double)ri[c];
+            rz_p += ri[c] * zi[c];
+            rr_p += ri[c] * ri[c];
         }
     }
+    double v[2] = {(double)rz_p, (double)rr_p};
     grid_sum<2>(v, red, ctr, [&](double *t) {
         sc->rz = t[0];
         sc->rr = t[1];
@@ -146,40 +197,84 @@ __global__ void __launch_bounds__(256) k_pcg_init(int n, const T *__restrict__ r
     });
 }
 
+// The PCG recurrence from the state k_pcg_init left (alpha, beta, stop test
+// as in the header comment).  Cooperative launch: all CTAs are resident.
+// r is double-buffered by iteration parity: the update phase of iteration k
+// reads r_k (all six entries of a camera) and writes r_k+1.  The update runs one thread per vector entry
+// e = 6 i + a; each recomputes camera i's six new residual entries (reads
+// shared through L1) to form z_e = sum_c M^-1_i[a][c] r_i[c].
 template <typename T>
-__global__ void __launch_bounds__(256) k_pcg_update(int n, const T *__restrict__ Minv, const T *__restrict__ d, T *q,
-                                                    T *y, T *r, T *z, DevScalars *sc, double *red, unsigned *ctr) {
+__global__ void __launch_bounds__(256) k_pcg_persist(int n, const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
+                                                     const T *__restrict__ S, const T *__restrict__ Minv, T *y, T *r0,
+                                                     T *r1, T *z, T *d0, T *d1, T *q, DevScalars *sc, double *red,
+                                                     unsigned *bar, long long limit_cycles) {
+    __shared__ double sh[40];
     if (sc->done) return;
-    const T alpha = (T)sc->alpha;
-    double v[2] = {0.0, 0.0};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        T ri[6], zi[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            y[6 * i + c] += alpha * d[6 * i + c];
-            ri[c] = r[6 * i + c] - alpha * q[6 * i + c];
-            r[6 * i + c] = ri[c];
-            q[6 * i + c] = T(0);
+    double rz = sc->rz;
+    const double rr0 = sc->rr0, tol2 = sc->tol2;
+    const int max_iters = sc->max_iters;
+    double *redA = red, *redB = red + gridDim.x, *bcast = red + 3 * gridDim.x;
+    double beta = 0.0;
+    int it = 0;
+    const int ne = 6 * n;
+    for (;;) {
+        const bool odd = it & 1;
+        T *dold = odd ? d1 : d0, *dnew = odd ? d0 : d1;
+        T *rc = odd ? r1 : r0, *rn = odd ? r0 : r1;
+        // SpMV phase: d = z + beta d_old, q = S d, d^T S d
+        double v1[1] = {spmv_rows<T, T, true>(n, tw_ptr, tw_ent, S, z, dold, dnew, q, (T)beta)};
+        block_sum<1>(v1, sh);
+        if (!grid_allreduce<1>(v1, redA, bcast, bar, &sc->err, limit_cycles)) return;
+        const double pAp = v1[0];
+        if (!(pAp > 0.0)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                sc->err = (int)BA_ERR_NOT_SPD;
+                sc->done = 1;
+                sc->iters = it;
+            }
+            return;
         }
-        apply_minv(Minv, i, ri, zi);
+        const T alpha = (T)(rz / pAp);
+        // update phase: y += alpha d, r -= alpha q, z = M^-1 r, r^T z, r^T r
+        T rz_p = T(0), rr_p = T(0);
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+            const int i = e / 6, a = e - 6 * i;
+            T ri[6], qi[6];
+            load6(rc + 6 * i, ri);
+            load6(q + 6 * i, qi);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            z[6 * i + c] = zi[c];
-            v[0] += (double)ri[c] * (double)zi[c];
-            v[1] += (double)ri[c] * (double)ri[c];
+            for (int c = 0; c < 6; ++c) ri[c] -= alpha * qi[c];
+            const T *M = Minv + 36 * (int64_t)i + 6 * a;
+            T ze = T(0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) ze += __ldg(M + c) * ri[c];
+            T ra = ri[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c)
+                if (a == c) ra = ri[c];
+            y[e] += alpha * __ldcg(dnew + e);
+            rn[e] = ra;
+            z[e] = ze;
+            rz_p += ra * ze;
+            rr_p += ra * ra;
         }
+        double v2[2] = {(double)rz_p, (double)rr_p};
+        block_sum<2>(v2, sh);
+        if (!grid_allreduce<2>(v2, redB, bcast, bar, &sc->err, limit_cycles)) return;
+        const double rz_new = v2[0], rr = v2[1];
+        ++it;
+        if (rr <= tol2 * rr0 || it >= max_iters) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                sc->iters = it;
+                sc->rr = rr;
+                sc->rz = rz_new;
+                sc->done = 1;
+            }
+            return;
+        }
+        beta = rz_new / rz;
+        rz = rz_new;
     }
-    grid_sum<2>(v, red, ctr, [&](double *t) {
-        const int it = sc->iters + 1;
-        sc->iters = it;
-        sc->rr = t[1];
-        if (t[1] <= sc->tol2 * sc->rr0 || it >= sc->max_iters) {
-            sc->done = 1;
-        } else {
-            sc->beta = t[0] / sc->rz;
-            sc->rz = t[0];
-        }
-    });
 }
 
 // r64 = b - q64 (q64 = S x64 from the FP64 SpMV), q64 reset; ||r64||^2, ||b||^2.
@@ -247,7 +342,7 @@ static inline int grid_for(int64_t work, int threads, int cap) {
 }
 static constexpr int VEC_CAP = 152 * 4;
 
-// pv[]: 0 y, 1 r, 2 z, 3 d0, 4 d1, 5 q
+// pv[]: 0 y, 1 r, 2 z, 3 d0, 4 d1, 5 q, 6 r (odd iterations), 7 q (odd iterations)
 cudaError_t launch_pcg_init(ba_problem *p, const void *rhs, double tol, int max_iters) {
     cudaEvent_t ev;
     ktimer_begin(p, K_PCG_INIT, &ev);
@@ -255,46 +350,56 @@ cudaError_t launch_pcg_init(ba_problem *p, const void *rhs, double tol, int max_
     if (p->fp32)
         k_pcg_init<float><<<g, 256, 0, p->st>>>(p->n, (const float *)rhs, (const float *)p->Minv, (float *)p->pv[0],
                                                 (float *)p->pv[1], (float *)p->pv[2], (float *)p->pv[3],
-                                                (float *)p->pv[5], p->sc, tol * tol, max_iters, p->red, p->counters + 2);
+                                                (float *)p->pv[5], (float *)p->pv[7], p->sc, tol * tol, max_iters, p->red,
+                                                p->counters + 2);
     else
         k_pcg_init<double><<<g, 256, 0, p->st>>>(p->n, (const double *)rhs, (const double *)p->Minv,
                                                  (double *)p->pv[0], (double *)p->pv[1], (double *)p->pv[2],
-                                                 (double *)p->pv[3], (double *)p->pv[5], p->sc, tol * tol, max_iters,
-                                                 p->red, p->counters + 2);
+                                                 (double *)p->pv[3], (double *)p->pv[5], (double *)p->pv[7], p->sc,
+                                                 tol * tol, max_iters, p->red, p->counters + 2);
     ktimer_end(p, K_PCG_INIT, ev);
     p->launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_iter(ba_problem *p, int it) {
-    // even iterations read d0 and write d1, odd ones the reverse
-    void *dold = p->pv[3 + (it & 1)], *dnew = p->pv[4 - (it & 1)];
-    const int gs = grid_for((int64_t)p->n * 32, 256, 152 * 8);
-    const int gv = grid_for(p->n, 256, VEC_CAP);
+template <typename T>
+static cudaError_t pcg_loop_T(ba_problem *p) {
+    static int blocks_per_sm = -1, n_sm = 0;
+    cudaError_t e;
+    if (blocks_per_sm < 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pcg_persist<T>, 256, 0)) != cudaSuccess)
+            return e;
+        if (blocks_per_sm > 2) blocks_per_sm = 2;
+        if (blocks_per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    }
+    // enough warps for one block row each, at most what is co-resident
+    int64_t want = ((int64_t)p->n * 32 + 255) / 256;
+    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)blocks_per_sm * n_sm);
+    if ((e = cudaMemsetAsync(p->counters + 14, 0, 2 * sizeof(unsigned), p->st)) != cudaSuccess) return e;
+    int n = p->n;
+    const int *twp = p->tw_ptr;
+    const int2 *twe = p->tw_ent;
+    const T *S = (const T *)p->S, *Mi = (const T *)p->Minv;
+    T *y = (T *)p->pv[0], *r = (T *)p->pv[1], *z = (T *)p->pv[2], *d0 = (T *)p->pv[3], *d1 = (T *)p->pv[4];
+    T *q = (T *)p->pv[5], *r1 = (T *)p->pv[6];
+    DevScalars *sc = p->sc;
+    double *red = p->red;
+    unsigned *bar = p->counters + 14;
+    long long limit = 4000000000LL;  // ~2 s of SM clock per barrier wait
+    void *args[] = {&n, &twp, &twe, &S, &Mi, &y, &r, &r1, &z, &d0, &d1, &q, &sc, &red, &bar, &limit};
+    return cudaLaunchCooperativeKernel((const void *)k_pcg_persist<T>, dim3(grid), dim3(256), args, 0, p->st);
+}
+
+cudaError_t launch_pcg_loop(ba_problem *p) {
     cudaEvent_t ev;
-    ktimer_begin(p, K_SPMV, &ev);
-    if (p->fp32)
-        k_spmv<float, float, true><<<gs, 256, 0, p->st>>>(p->n, p->row_ptr, p->col, (const float *)p->S,
-                                                          (const float *)p->pv[2], (const float *)dold, (float *)dnew,
-                                                          (float *)p->pv[5], p->sc, p->red, p->counters + 3);
-    else
-        k_spmv<double, double, true><<<gs, 256, 0, p->st>>>(p->n, p->row_ptr, p->col, (const double *)p->S,
-                                                            (const double *)p->pv[2], (const double *)dold,
-                                                            (double *)dnew, (double *)p->pv[5], p->sc, p->red,
-                                                            p->counters + 3);
-    ktimer_end(p, K_SPMV, ev);
+    ktimer_begin(p, K_PCG_LOOP, &ev);
+    cudaError_t e = p->fp32 ? pcg_loop_T<float>(p) : pcg_loop_T<double>(p);
+    ktimer_end(p, K_PCG_LOOP, ev);
     p->launches += 1;
-    ktimer_begin(p, K_PCG_UPDATE, &ev);
-    if (p->fp32)
-        k_pcg_update<float><<<gv, 256, 0, p->st>>>(p->n, (const float *)p->Minv, (const float *)dnew,
-                                                   (float *)p->pv[5], (float *)p->pv[0], (float *)p->pv[1],
-                                                   (float *)p->pv[2], p->sc, p->red, p->counters + 4);
-    else
-        k_pcg_update<double><<<gv, 256, 0, p->st>>>(p->n, (const double *)p->Minv, (const double *)dnew,
-                                                    (double *)p->pv[5], (double *)p->pv[0], (double *)p->pv[1],
-                                                    (double *)p->pv[2], p->sc, p->red, p->counters + 4);
-    ktimer_end(p, K_PCG_UPDATE, ev);
-    p->launches += 1;
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -305,13 +410,9 @@ cudaError_t launch_resid64(ba_problem *p, bool from_x64) {
     if (from_x64) {
         const int gs = grid_for((int64_t)p->n * 32, 256, 152 * 8);
         if (p->fp32)
-            k_spmv<float, double, false><<<gs, 256, 0, p->st>>>(p->n, p->row_ptr, p->col, (const float *)p->S,
-                                                                p->x64, nullptr, nullptr, p->q64, p->sc, p->red,
-                                                                p->counters + 5);
+            k_spmv64<float><<<gs, 256, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const float *)p->S, p->x64, p->q64);
         else
-            k_spmv<double, double, false><<<gs, 256, 0, p->st>>>(p->n, p->row_ptr, p->col, (const double *)p->S,
-                                                                 p->x64, nullptr, nullptr, p->q64, p->sc, p->red,
-                                                                 p->counters + 5);
+            k_spmv64<double><<<gs, 256, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const double *)p->S, p->x64, p->q64);
     }
     const int g = grid_for((int64_t)p->n * 6, 256, VEC_CAP);
     if (p->fp32)

@@ -9,183 +9,303 @@
 //   S_(i_a, i_a) += J_c,a^T (I - P_a P_a^T) J_c,a      (U and -W V^-1 W^T)
 //   b_(i_a)      -= J_c,a^T e^_a                         (l_c - W V^-1 l_p)
 // which is W V^-1 W^T = (J_c^T P)(J_c^T P)^T written through the 2x2 middle
-// factors.  A CTA owns a group of whole tracks: it stages the group's
-// Jacobian rows in shared memory, turns J_p and e into P and e^ in place, then
-// each thread accumulates whole local blocks (sub-RCS blocks) in registers
-// over the precomputed (a, b) products of that block - no atomics - and writes
-// them as partials.  A segmented sum over the partials of each global block
+// factors.  Persistent CTAs walk the point groups (whole tracks, Sec. 6.1);
+// for each group a CTA copies the group's Jacobian rows and (a, b) product
+// list into shared memory with TMA bulk copies - double-buffered, the next
+// group's copy in flight while the current one is computed - turns J_p and e
+// into P and e^ in place, then sums the products of each sub-RCS block in
+// registers (work items of <= 8 products, joined by a warp-segmented shuffle
+// reduction) - no atomics - and writes them as partials.  A segmented sum over the partials of each global block
 // (precomputed CSR) then forms S, adds lambda clamp(diag U) on the diagonal,
 // and inverts the diagonal blocks for the preconditioner.
+#include <algorithm>
+
 #include "device_util.cuh"
 
 namespace ba {
 
 __host__ __device__ constexpr int up_idx(int r, int c) { return 6 * r - r * (r - 1) / 2 + (c - r); }
 
+// One staged observation row (JW values, 16-byte aligned) into registers.
+__device__ __forceinline__ void load_slot(const float *s, float (&v)[JW]) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(s);
+#pragma unroll
+    for (int q = 0; q < JW / 4; ++q) {
+        const float4 t = s4[q];
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_slot(const double *s, double (&v)[JW]) {
+    const double2 *s2 = reinterpret_cast<const double2 *>(s);
+#pragma unroll
+    for (int q = 0; q < JW / 2; ++q) {
+        const double2 t = s2[q];
+        v[2 * q] = t.x; v[2 * q + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// 1-D TMA bulk copy global -> shared, completion counted on the mbarrier.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for an mbarrier phase; false after ~limit SM clocks.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__restrict__ grp,
-                                                           const uint32_t *__restrict__ lb_info,
+__global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__restrict__ grp, int ngroups,
+                                                           const ItemDesc *__restrict__ items,
                                                            const uint32_t *__restrict__ contrib,
                                                            const int *__restrict__ trk_ptr, const T *__restrict__ J,
                                                            double lambda, T *__restrict__ part, T *__restrict__ Linv_out,
-                                                           T *__restrict__ lp_out, DevScalars *sc, int fp64_v) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *so = reinterpret_cast<T *>(smem_raw);  // [nobs][JW]: J_c (12) | J_p -> P (6) | e -> e^ (2)
-    const GroupDesc g = grp[blockIdx.x];
-
-    // 1) stage the group's Jacobian rows (contiguous, 16-byte aligned)
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(J + (int64_t)g.obs_begin * JW);
-        int4 *dst = reinterpret_cast<int4 *>(so);
-        const int nvec = g.nobs * JW * (int)sizeof(T) / 16;
-        for (int t = threadIdx.x; t < nvec; t += blockDim.x) dst[t] = __ldg(src + t);
+                                                           T *__restrict__ lp_out, DevScalars *sc, int fp64_v,
+                                                           int obs_max, long long limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ GroupDesc sdesc[2];
+    __shared__ int s_ok;
+    const size_t jbytes_max = (size_t)obs_max * JW * sizeof(T);
+    const size_t buf_bytes = jbytes_max + (size_t)C_MAX * sizeof(uint32_t);
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_proxy_async();
     }
     __syncthreads();
+    // thread 0: copy group gi's rows and product list into buffer b
+    auto issue = [&](int gi, int b) {
+        const GroupDesc d = grp[gi];
+        sdesc[b] = d;
+        unsigned char *dst = smem_raw + b * buf_bytes;
+        const uint32_t jb = (uint32_t)d.nobs * JW * (uint32_t)sizeof(T);
+        const uint32_t cb = (uint32_t)((d.nc + 3) & ~3) * 4u;
+        fence_proxy_async();  // earlier generic writes to this buffer before the async copy
+        mbar_expect_tx(&mbar[b], jb + cb);
+        bulk_g2s(dst, J + (int64_t)d.obs_begin * JW, jb, &mbar[b]);
+        if (cb) bulk_g2s(dst + jbytes_max, contrib + d.c_begin, cb, &mbar[b]);
+    };
+    uint32_t parity = 0u, pending = 0u;  // one bit per buffer
+    int gi = blockIdx.x;
+    if (threadIdx.x == 0 && gi < ngroups) issue(gi, 0);
+    if (gi < ngroups) pending |= 1u;
+    for (int k = 0; gi < ngroups; gi += gridDim.x, ++k) {
+        const int bsel = k & 1;
+        const int gn = gi + gridDim.x;
+        if (gn < ngroups) {
+            if (threadIdx.x == 0) issue(gn, bsel ^ 1);
+            pending |= 1u << (bsel ^ 1);
+        }
+        if (threadIdx.x == 0) s_ok = mbar_wait(&mbar[bsel], (parity >> bsel) & 1u, limit) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            // give up: flag it, let the copies still in flight land (bounded), leave
+            if (threadIdx.x == 0) {
+                atomicExch(&sc->err, (int)BA_ERR_TIMEOUT);
+                mbar_wait(&mbar[bsel], (parity >> bsel) & 1u, limit);
+                if ((pending >> (bsel ^ 1)) & 1u) mbar_wait(&mbar[bsel ^ 1], (parity >> (bsel ^ 1)) & 1u, limit);
+            }
+            return;
+        }
+        parity ^= 1u << bsel;
+        pending &= ~(1u << bsel);
+        const GroupDesc g = sdesc[bsel];
+        T *so = reinterpret_cast<T *>(smem_raw + bsel * buf_bytes);  // [nobs][JW]: J_c | J_p -> P | e -> e^
+        const uint32_t *sc_list = reinterpret_cast<const uint32_t *>(smem_raw + bsel * buf_bytes + jbytes_max);
 
-    // 2) per point: V_k, its Cholesky factor, q_k; J_p -> P and e -> e^ in place
-    for (int pl = threadIdx.x; pl < g.npts; pl += blockDim.x) {
-        const int k = g.pt_begin + pl;
-        const int a0 = trk_ptr[k] - g.obs_begin, a1 = trk_ptr[k + 1] - g.obs_begin;
-        T v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0, l0 = 0, l1 = 0, l2 = 0;
-        for (int a = a0; a < a1; ++a) {
-            const T *s = so + a * JW;
-            const T p0 = s[12], p1 = s[13], p2 = s[14], r0 = s[15], r1 = s[16], r2 = s[17], e0 = s[18], e1 = s[19];
-            v00 += p0 * p0 + r0 * r0; v01 += p0 * p1 + r0 * r1; v02 += p0 * p2 + r0 * r2;
-            v11 += p1 * p1 + r1 * r1; v12 += p1 * p2 + r1 * r2; v22 += p2 * p2 + r2 * r2;
-            l0 -= p0 * e0 + r0 * e1; l1 -= p1 * e0 + r1 * e1; l2 -= p2 * e0 + r2 * e1;
-        }
-        v00 += (T)(lambda * clampd((double)v00));
-        v11 += (T)(lambda * clampd((double)v11));
-        v22 += (T)(lambda * clampd((double)v22));
-        // Cholesky V = L L^T, then M = L^-1 (lower)
-        T m00, m10, m11, m20, m21, m22;
-        bool ok;
-        {
-            const T c00 = v00;
-            const T d0 = sqrt(c00);
-            const T c10 = v01 / d0, c20 = v02 / d0;
-            const T s11 = v11 - c10 * c10;
-            const T d1 = sqrt(s11);
-            const T c21 = (v12 - c20 * c10) / d1;
-            const T s22 = v22 - c20 * c20 - c21 * c21;
-            const T d2 = sqrt(s22);
-            ok = (c00 > T(0)) && (s11 > T(0)) && (s22 > T(0));
-            m00 = T(1) / d0; m11 = T(1) / d1; m22 = T(1) / d2;
-            m10 = -c10 * m00 * m11;
-            m21 = -c21 * m11 * m22;
-            m20 = -(c20 * m00 + c21 * m10) * m22;
-        }
-        if (fp64_v && ok) {
-            // FP32 mode: refactor in FP64 when kappa~ = ||V||_F ||V^-1||_F > 1e4
-            const T i00 = m00 * m00 + m10 * m10 + m20 * m20, i11 = m11 * m11 + m21 * m21, i22 = m22 * m22;
-            const T i01 = m10 * m11 + m20 * m21, i02 = m20 * m22, i12 = m21 * m22;
-            const T nv = v00 * v00 + v11 * v11 + v22 * v22 + 2 * (v01 * v01 + v02 * v02 + v12 * v12);
-            const T ni = i00 * i00 + i11 * i11 + i22 * i22 + 2 * (i01 * i01 + i02 * i02 + i12 * i12);
-            if (nv * ni > T(1e8)) {
-                double w00 = 0, w01 = 0, w02 = 0, w11 = 0, w12 = 0, w22 = 0;
-                for (int a = a0; a < a1; ++a) {
-                    const T *s = so + a * JW;
-                    const double p0 = s[12], p1 = s[13], p2 = s[14], r0 = s[15], r1 = s[16], r2 = s[17];
-                    w00 += p0 * p0 + r0 * r0; w01 += p0 * p1 + r0 * r1; w02 += p0 * p2 + r0 * r2;
-                    w11 += p1 * p1 + r1 * r1; w12 += p1 * p2 + r1 * r2; w22 += p2 * p2 + r2 * r2;
+        // 2) per point: V_k, its Cholesky factor, q_k; J_p -> P and e -> e^ in place
+        for (int pl = threadIdx.x; pl < g.npts; pl += blockDim.x) {
+            const int k = g.pt_begin + pl;
+            const int a0 = trk_ptr[k] - g.obs_begin, a1 = trk_ptr[k + 1] - g.obs_begin;
+            T v00 = 0, v01 = 0, v02 = 0, v11 = 0, v12 = 0, v22 = 0, l0 = 0, l1 = 0, l2 = 0;
+            for (int a = a0; a < a1; ++a) {
+                const T *s = so + a * JW;
+                const T p0 = s[12], p1 = s[13], p2 = s[14], r0 = s[15], r1 = s[16], r2 = s[17], e0 = s[18], e1 = s[19];
+                v00 += p0 * p0 + r0 * r0; v01 += p0 * p1 + r0 * r1; v02 += p0 * p2 + r0 * r2;
+                v11 += p1 * p1 + r1 * r1; v12 += p1 * p2 + r1 * r2; v22 += p2 * p2 + r2 * r2;
+                l0 -= p0 * e0 + r0 * e1; l1 -= p1 * e0 + r1 * e1; l2 -= p2 * e0 + r2 * e1;
+            }
+            const T lam = (T)lambda;
+            v00 += lam * clampT(v00);
+            v11 += lam * clampT(v11);
+            v22 += lam * clampT(v22);
+            // Cholesky V = L L^T, then M = L^-1 (lower)
+            T m00, m10, m11, m20, m21, m22;
+            bool ok;
+            {
+                const T c00 = v00;
+                const T d0 = sqrt(c00);
+                const T c10 = v01 / d0, c20 = v02 / d0;
+                const T s11 = v11 - c10 * c10;
+                const T d1 = sqrt(s11);
+                const T c21 = (v12 - c20 * c10) / d1;
+                const T s22 = v22 - c20 * c20 - c21 * c21;
+                const T d2 = sqrt(s22);
+                ok = (c00 > T(0)) && (s11 > T(0)) && (s22 > T(0));
+                m00 = T(1) / d0; m11 = T(1) / d1; m22 = T(1) / d2;
+                m10 = -c10 * m00 * m11;
+                m21 = -c21 * m11 * m22;
+                m20 = -(c20 * m00 + c21 * m10) * m22;
+            }
+            if (fp64_v && ok) {
+                // FP32 mode: refactor in FP64 when kappa~ = ||V||_F ||V^-1||_F > 1e4
+                const T i00 = m00 * m00 + m10 * m10 + m20 * m20, i11 = m11 * m11 + m21 * m21, i22 = m22 * m22;
+                const T i01 = m10 * m11 + m20 * m21, i02 = m20 * m22, i12 = m21 * m22;
+                const T nv = v00 * v00 + v11 * v11 + v22 * v22 + 2 * (v01 * v01 + v02 * v02 + v12 * v12);
+                const T ni = i00 * i00 + i11 * i11 + i22 * i22 + 2 * (i01 * i01 + i02 * i02 + i12 * i12);
+                if (nv * ni > T(1e8)) {
+                    double w00 = 0, w01 = 0, w02 = 0, w11 = 0, w12 = 0, w22 = 0;
+                    for (int a = a0; a < a1; ++a) {
+                        const T *s = so + a * JW;
+                        const double p0 = s[12], p1 = s[13], p2 = s[14], r0 = s[15], r1 = s[16], r2 = s[17];
+                        w00 += p0 * p0 + r0 * r0; w01 += p0 * p1 + r0 * r1; w02 += p0 * p2 + r0 * r2;
+                        w11 += p1 * p1 + r1 * r1; w12 += p1 * p2 + r1 * r2; w22 += p2 * p2 + r2 * r2;
+                    }
+                    w00 += lambda * clampd(w00); w11 += lambda * clampd(w11); w22 += lambda * clampd(w22);
+                    const double d0 = sqrt(w00), c10 = w01 / d0, c20 = w02 / d0;
+                    const double s11 = w11 - c10 * c10, d1 = sqrt(s11), c21 = (w12 - c20 * c10) / d1;
+                    const double s22 = w22 - c20 * c20 - c21 * c21, d2 = sqrt(s22);
+                    if (w00 > 0 && s11 > 0 && s22 > 0) {
+                        const double n00 = 1 / d0, n11 = 1 / d1, n22 = 1 / d2, n10 = -c10 * n00 * n11;
+                        const double n21 = -c21 * n11 * n22, n20 = -(c20 * n00 + c21 * n10) * n22;
+                        m00 = (T)n00; m10 = (T)n10; m11 = (T)n11; m20 = (T)n20; m21 = (T)n21; m22 = (T)n22;
+                        atomicAdd(&sc->n_v64, 1ull);
+                    } else {
+                        ok = false;
+                    }
                 }
-                w00 += lambda * clampd(w00); w11 += lambda * clampd(w11); w22 += lambda * clampd(w22);
-                const double d0 = sqrt(w00), c10 = w01 / d0, c20 = w02 / d0;
-                const double s11 = w11 - c10 * c10, d1 = sqrt(s11), c21 = (w12 - c20 * c10) / d1;
-                const double s22 = w22 - c20 * c20 - c21 * c21, d2 = sqrt(s22);
-                if (w00 > 0 && s11 > 0 && s22 > 0) {
-                    const double n00 = 1 / d0, n11 = 1 / d1, n22 = 1 / d2, n10 = -c10 * n00 * n11;
-                    const double n21 = -c21 * n11 * n22, n20 = -(c20 * n00 + c21 * n10) * n22;
-                    m00 = (T)n00; m10 = (T)n10; m11 = (T)n11; m20 = (T)n20; m21 = (T)n21; m22 = (T)n22;
-                    atomicAdd(&sc->n_v64, 1ull);
-                } else {
-                    ok = false;
+            }
+            if (!ok) {
+                atomicExch(&sc->err, (int)BA_ERR_NOT_SPD);
+                m00 = m10 = m11 = m20 = m21 = m22 = T(0);
+            }
+            const T q0 = m00 * l0, q1 = m10 * l0 + m11 * l1, q2 = m20 * l0 + m21 * l1 + m22 * l2;
+            T *lo = Linv_out + 6 * (int64_t)k;
+            lo[0] = m00; lo[1] = m10; lo[2] = m11; lo[3] = m20; lo[4] = m21; lo[5] = m22;
+            T *lpo = lp_out + 3 * (int64_t)k;
+            lpo[0] = l0; lpo[1] = l1; lpo[2] = l2;
+            for (int a = a0; a < a1; ++a) {
+                T *s = so + a * JW;
+    #pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const T j0 = s[12 + 3 * r], j1 = s[13 + 3 * r], j2 = s[14 + 3 * r];
+                    const T P0 = j0 * m00, P1 = j0 * m10 + j1 * m11, P2 = j0 * m20 + j1 * m21 + j2 * m22;
+                    s[12 + 3 * r] = P0; s[13 + 3 * r] = P1; s[14 + 3 * r] = P2;
+                    s[18 + r] += P0 * q0 + P1 * q1 + P2 * q2;
                 }
             }
         }
-        if (!ok) {
-            atomicExch(&sc->err, (int)BA_ERR_NOT_SPD);
-            m00 = m10 = m11 = m20 = m21 = m22 = T(0);
-        }
-        const T q0 = m00 * l0, q1 = m10 * l0 + m11 * l1, q2 = m20 * l0 + m21 * l1 + m22 * l2;
-        T *lo = Linv_out + 6 * (int64_t)k;
-        lo[0] = m00; lo[1] = m10; lo[2] = m11; lo[3] = m20; lo[4] = m21; lo[5] = m22;
-        T *lpo = lp_out + 3 * (int64_t)k;
-        lpo[0] = l0; lpo[1] = l1; lpo[2] = l2;
-        for (int a = a0; a < a1; ++a) {
-            T *s = so + a * JW;
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const T j0 = s[12 + 3 * r], j1 = s[13 + 3 * r], j2 = s[14 + 3 * r];
-                const T P0 = j0 * m00, P1 = j0 * m10 + j1 * m11, P2 = j0 * m20 + j1 * m21 + j2 * m22;
-                s[12 + 3 * r] = P0; s[13 + 3 * r] = P1; s[14 + 3 * r] = P2;
-                s[18 + r] += P0 * q0 + P1 * q1 + P2 * q2;
-            }
-        }
-    }
-    __syncthreads();
+        __syncthreads();
 
-    // 3) local blocks: one thread owns a whole sub-RCS block
-    const uint32_t *cg = contrib + g.c_begin;
-    for (int lb = threadIdx.x; lb < g.nlb; lb += blockDim.x) {
-        const uint32_t info = lb_info[g.lb_begin + lb];
-        const int cb = (int)(info & 0xffffu), cnt = (int)((info >> 16) & 0x7fffu);
-        T *out = part + (g.lb_begin + lb) * BW;
-        if (!(info >> 31)) {
+        // 3) work items: each lane sums <= ITEM_MAX products of one sub-RCS block in
+        //    registers; the items of a block that share a warp are added by a
+        //    segmented shuffle reduction and the run's head writes the partial.
+        const ItemDesc *itg = items + g.item_begin;
+        for (int base = 0; base < g.nitems; base += blockDim.x) {
+            const int it = base + threadIdx.x;
+            const ItemDesc d = it < g.nitems ? itg[it] : ItemDesc{0u, 0u};
+            const int cb = (int)(d.x & 0xffffu), cnt = (int)((d.x >> 16) & 0xfu);
+            const bool diag = (d.x >> 20) & 1u;
+            const int nfollow = (int)((d.x >> 21) & 31u);
+            const bool head = (d.x >> 26) & 1u;
             T acc[36];
-#pragma unroll
+    #pragma unroll
             for (int q = 0; q < 36; ++q) acc[q] = T(0);
-            for (int c = cb; c < cb + cnt; ++c) {
-                const uint32_t u = cg[c];
-                const T *sa = so + (u & 0xffffu) * JW, *sb = so + (u >> 16) * JW;
-                const T M00 = sa[12] * sb[12] + sa[13] * sb[13] + sa[14] * sb[14];
-                const T M01 = sa[12] * sb[15] + sa[13] * sb[16] + sa[14] * sb[17];
-                const T M10 = sa[15] * sb[12] + sa[16] * sb[13] + sa[17] * sb[14];
-                const T M11 = sa[15] * sb[15] + sa[16] * sb[16] + sa[17] * sb[17];
-                T t0[6], t1[6];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    t0[j] = M00 * sb[j] + M01 * sb[6 + j];
-                    t1[j] = M10 * sb[j] + M11 * sb[6 + j];
+            if (!diag) {
+                for (int c = cb; c < cb + cnt; ++c) {
+                    const uint32_t u = sc_list[c];
+                    T sa[JW], sb[JW];
+                    load_slot(so + (u & 0xffffu) * JW, sa);
+                    load_slot(so + (u >> 16) * JW, sb);
+                    const T M00 = sa[12] * sb[12] + sa[13] * sb[13] + sa[14] * sb[14];
+                    const T M01 = sa[12] * sb[15] + sa[13] * sb[16] + sa[14] * sb[17];
+                    const T M10 = sa[15] * sb[12] + sa[16] * sb[13] + sa[17] * sb[14];
+                    const T M11 = sa[15] * sb[15] + sa[16] * sb[16] + sa[17] * sb[17];
+                    T t0[6], t1[6];
+    #pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        t0[j] = M00 * sb[j] + M01 * sb[6 + j];
+                        t1[j] = M10 * sb[j] + M11 * sb[6 + j];
+                    }
+    #pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const T ai0 = sa[i], ai1 = sa[6 + i];
+    #pragma unroll
+                        for (int j = 0; j < 6; ++j) acc[6 * i + j] -= ai0 * t0[j] + ai1 * t1[j];
+                    }
                 }
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const T ai0 = sa[i], ai1 = sa[6 + i];
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) acc[6 * i + j] -= ai0 * t0[j] + ai1 * t1[j];
+            } else {
+                // packed [21 upper entries of U - W V^-1 W^T | 6 diag(J_c^T J_c) | 6 b | 3 zero]
+                for (int c = cb; c < cb + cnt; ++c) {
+                    T sa[JW];
+                    load_slot(so + (sc_list[c] & 0xffffu) * JW, sa);
+                    const T g00 = T(1) - (sa[12] * sa[12] + sa[13] * sa[13] + sa[14] * sa[14]);
+                    const T g01 = -(sa[12] * sa[15] + sa[13] * sa[16] + sa[14] * sa[17]);
+                    const T g11 = T(1) - (sa[15] * sa[15] + sa[16] * sa[16] + sa[17] * sa[17]);
+                    T t0[6], t1[6];
+    #pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        t0[j] = g00 * sa[j] + g01 * sa[6 + j];
+                        t1[j] = g01 * sa[j] + g11 * sa[6 + j];
+                    }
+    #pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const T ai0 = sa[i], ai1 = sa[6 + i];
+    #pragma unroll
+                        for (int j = i; j < 6; ++j) acc[up_idx(i, j)] += ai0 * t0[j] + ai1 * t1[j];
+                        acc[21 + i] += ai0 * ai0 + ai1 * ai1;
+                        acc[27 + i] -= ai0 * sa[18] + ai1 * sa[19];
+                    }
                 }
             }
-            for (int q = 0; q < 36; ++q) out[q] = acc[q];
-        } else {
-            T acc[21], du[6], bb[6];
-#pragma unroll
-            for (int q = 0; q < 21; ++q) acc[q] = T(0);
-#pragma unroll
-            for (int q = 0; q < 6; ++q) { du[q] = T(0); bb[q] = T(0); }
-            for (int c = cb; c < cb + cnt; ++c) {
-                const T *sa = so + (cg[c] & 0xffffu) * JW;
-                const T g00 = T(1) - (sa[12] * sa[12] + sa[13] * sa[13] + sa[14] * sa[14]);
-                const T g01 = -(sa[12] * sa[15] + sa[13] * sa[16] + sa[14] * sa[17]);
-                const T g11 = T(1) - (sa[15] * sa[15] + sa[16] * sa[16] + sa[17] * sa[17]);
-                T t0[6], t1[6];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    t0[j] = g00 * sa[j] + g01 * sa[6 + j];
-                    t1[j] = g01 * sa[j] + g11 * sa[6 + j];
-                }
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const T ai0 = sa[i], ai1 = sa[6 + i];
-#pragma unroll
-                    for (int j = i; j < 6; ++j) acc[up_idx(i, j)] += ai0 * t0[j] + ai1 * t1[j];
-                    du[i] += ai0 * ai0 + ai1 * ai1;
-                    bb[i] -= ai0 * sa[18] + ai1 * sa[19];
+            const unsigned maxnf = __reduce_max_sync(0xffffffffu, (unsigned)nfollow);
+            if (maxnf > 0) {
+                for (unsigned off = 1; off <= maxnf; off <<= 1) {
+    #pragma unroll
+                    for (int q = 0; q < 36; ++q) {
+                        const T v = __shfl_down_sync(0xffffffffu, acc[q], off);
+                        if (off <= (unsigned)nfollow) acc[q] += v;
+                    }
                 }
             }
-            for (int q = 0; q < 21; ++q) out[q] = acc[q];
-            for (int q = 0; q < 6; ++q) { out[21 + q] = du[q]; out[27 + q] = bb[q]; }
-            out[33] = out[34] = out[35] = T(0);
+            if (head) {
+                T *out = part + (g.part_begin + d.y) * BW;
+                if constexpr (sizeof(T) == 4) {
+                    float4 *o4 = reinterpret_cast<float4 *>(out);
+    #pragma unroll
+                    for (int q = 0; q < 9; ++q) o4[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+                } else {
+                    double2 *o2 = reinterpret_cast<double2 *>(out);
+    #pragma unroll
+                    for (int q = 0; q < 18; ++q) o2[q] = make_double2(acc[2 * q], acc[2 * q + 1]);
+                }
+            }
         }
+        __syncthreads();  // buffer free for the next copy
     }
 }
 
@@ -209,9 +329,9 @@ __global__ void k_rcs_diag(int n, const int *__restrict__ row_ptr, T *__restrict
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T *Sd = S + (int64_t)row_ptr[i] * BW;
-    double pk[36], A[36], Ai[36];
+    T pk[36], A[36], Ai[36];
 #pragma unroll
-    for (int q = 0; q < 36; ++q) pk[q] = (double)Sd[q];
+    for (int q = 0; q < 36; ++q) pk[q] = Sd[q];
 #pragma unroll
     for (int r = 0; r < 6; ++r)
 #pragma unroll
@@ -219,22 +339,20 @@ __global__ void k_rcs_diag(int n, const int *__restrict__ row_ptr, T *__restrict
             A[6 * r + c] = pk[up_idx(r, c)];
             A[6 * c + r] = pk[up_idx(r, c)];
         }
+    const T lam = (T)lambda;
 #pragma unroll
-    for (int r = 0; r < 6; ++r) A[7 * r] += lambda * clampd(pk[21 + r]);
+    for (int r = 0; r < 6; ++r) A[7 * r] += lam * clampT(pk[21 + r]);
 #pragma unroll
-    for (int q = 0; q < 36; ++q) Sd[q] = (T)A[q];
+    for (int q = 0; q < 36; ++q) Sd[q] = A[q];
 #pragma unroll
-    for (int r = 0; r < 6; ++r) b[6 * i + r] = (T)pk[27 + r];
-    // precondition with the diagonal block as stored (rounded to T)
-#pragma unroll
-    for (int q = 0; q < 36; ++q) A[q] = (double)(T)A[q];
-    if (!spd_inverse6<double>(A, Ai)) {
+    for (int r = 0; r < 6; ++r) b[6 * i + r] = pk[27 + r];
+    if (!spd_inverse6<T>(A, Ai)) {
         atomicExch(&sc->err, (int)BA_ERR_NOT_SPD);
 #pragma unroll
-        for (int q = 0; q < 36; ++q) Ai[q] = 0.0;
+        for (int q = 0; q < 36; ++q) Ai[q] = T(0);
     }
 #pragma unroll
-    for (int q = 0; q < 36; ++q) Minv[36 * (int64_t)i + q] = (T)Ai[q];
+    for (int q = 0; q < 36; ++q) Minv[36 * (int64_t)i + q] = Ai[q];
 }
 
 static inline int grid_for(int64_t work, int threads, int cap) {
@@ -242,22 +360,38 @@ static inline int grid_for(int64_t work, int threads, int cap) {
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
+template <typename T>
+static cudaError_t form_rcs_T(ba_problem *p, double lambda, size_t smem, long long limit) {
+    static int ctas_per_sm = -1, n_sm = 0;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_form_rcs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    if (ctas_per_sm < 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_form_rcs<T>, FORM_THREADS, smem)) !=
+            cudaSuccess)
+            return e;
+        if (ctas_per_sm < 1) ctas_per_sm = 1;
+    }
+    const int grid = (int)std::min<int64_t>(p->ngroups, (int64_t)ctas_per_sm * n_sm);
+    k_form_rcs<T><<<grid, FORM_THREADS, smem, p->st>>>(p->grp, (int)p->ngroups, p->items, p->contrib, p->trk_ptr,
+                                                      (const T *)p->J, lambda, (T *)p->part, (T *)p->Linv, (T *)p->lp,
+                                                      p->sc, p->fp32 ? 1 : 0, p->obs_max, limit);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_form_rcs(ba_problem *p, double lambda) {
     cudaError_t err;
     cudaEvent_t ev;
-    const size_t smem = (size_t)p->obs_max * JW * p->esz;
+    const size_t smem = 2 * ((size_t)p->obs_max * JW * p->esz + (size_t)C_MAX * sizeof(uint32_t));
+    const long long limit = 4000000000LL;  // ~2 s of SM clock per copy wait
     ktimer_begin(p, K_FORM_RCS, &ev);
-    if (p->fp32) {
-        cudaFuncSetAttribute(k_form_rcs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_form_rcs<float><<<(unsigned)p->ngroups, FORM_THREADS, smem, p->st>>>(
-            p->grp, p->lb_info, p->contrib, p->trk_ptr, (const float *)p->J, lambda, (float *)p->part,
-            (float *)p->Linv, (float *)p->lp, p->sc, 1);
-    } else {
-        cudaFuncSetAttribute(k_form_rcs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_form_rcs<double><<<(unsigned)p->ngroups, FORM_THREADS, smem, p->st>>>(
-            p->grp, p->lb_info, p->contrib, p->trk_ptr, (const double *)p->J, lambda, (double *)p->part,
-            (double *)p->Linv, (double *)p->lp, p->sc, 0);
-    }
+    if (p->fp32)
+        err = form_rcs_T<float>(p, lambda, smem, limit);
+    else
+        err = form_rcs_T<double>(p, lambda, smem, limit);
     ktimer_end(p, K_FORM_RCS, ev);
     p->launches += 1;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(B):
 
 def test_kernel_names(B):
     names = B.ba_kernel_names()
-    assert "form_rcs" in names and "spmv" in names and "linearize" in names
+    assert "form_rcs" in names and "pcg_loop" in names and "linearize" in names
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
