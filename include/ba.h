@@ -181,6 +181,62 @@ ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs,
                               const int32_t *obs_cam, const int64_t *obs_pt, int32_t *row_ptr,
                               int32_t *col, int64_t *nnzb);
 
+/* ---- Learned block-Jacobi correction (not in the paper) ------------------
+ * The paper preconditions PCG with the block diagonal of the RCS (Sec. 3.2).
+ * A small network corrects each block's inverse while keeping it SPD:
+ *   S_ii = L_i L_i^T,  M_i^-1 = L_i^-T T_i T_i^T L_i^-1,
+ * T_i lower triangular with T_kk = exp(0.1 o_kk), T_kl = 0.1 o_kl (k > l), o_i the
+ * 21 outputs of two message-passing layers (hidden 64, BF16 weights on the
+ * tensor cores, FP32 accumulation) over the camera co-visibility graph: nodes
+ * are cameras, edges the off-diagonal BSMC blocks with weight
+ * ||S_ij||_F / sqrt(||S_ii||_F ||S_jj||_F).  Node features: the 15 correlations
+ * of S_ii, its 6 log-diagonals centred over cameras, log(1 + degree), summed
+ * edge weight, 1.  Layer: h' = relu([h | mean_w(neighbours' h)] W + b).
+ * Zero output weights give exactly block-Jacobi.
+ * Parameters (FP32 master, packed): W1 (48 x 64), b1 (64), W2 (128 x 64),
+ * b2 (64), Wo (64 x 21), bo (21), row-major. */
+typedef struct ba_precond_net ba_precond_net;
+
+int32_t ba_precond_net_num_params(void);
+
+/* params: host array of ba_precond_net_num_params() floats, or NULL for a
+ * seeded He-normal initialisation with a zero output layer. */
+ba_status ba_precond_net_create(const float *params, uint64_t seed, void *cuda_stream, ba_precond_net **out);
+void ba_precond_net_destroy(ba_precond_net *net);
+ba_status ba_precond_net_get_params(const ba_precond_net *net, float *out);
+ba_status ba_precond_net_set_params(ba_precond_net *net, const float *params);
+
+/* Attach a network to a problem (NULL detaches): ba_solve_rcs then uses the
+ * corrected M^-1, and falls back to plain block-Jacobi (info->used_fallback = 1)
+ * if the learned PCG breaks down or misses its tolerance.  The network must
+ * outlive the attachment. */
+ba_status ba_set_precond_net(ba_problem *p, ba_precond_net *net);
+
+/* Forward pass on the problem's last formed RCS: out_o (n x 21) and out_minv
+ * (n x 36), host buffers, either may be NULL. */
+ba_status ba_precond_net_forward(ba_precond_net *net, ba_problem *p, float *out_o, double *out_minv);
+
+/* Training step on the problem's last formed RCS with kp probe vectors W
+ * (host array kp x n x 6, or NULL for Rademacher probes from seed):
+ *   loss = sum_i ||M_i^-1 (S W)_i - W_i||^2 / ||W||^2,
+ * gradients by the network's backward pass (tensor-core GEMMs); if lr > 0 an
+ * Adam step (0.9, 0.999, 1e-8) updates the parameters.  loss and grads (host,
+ * num_params floats) may be NULL. */
+ba_status ba_precond_net_train_step(ba_precond_net *net, ba_problem *p, int32_t kp, const float *probes,
+                                    uint64_t seed, double lr, double *loss, float *grads);
+
+/* Small GEMM on the tensor cores (the operation of the learned preconditioner's
+ * dense layers): C[M x N] = A[M x K] * B[K x N], or C += A * B when
+ * accumulate != 0.  Device pointers; element (r, c) of A is A[r * a_rs + c * a_cs]
+ * (likewise B, C), so transposed operands need no copy.  A and B are rounded to
+ * BF16 and multiplied on the 5th-generation tensor cores (tcgen05) with FP32
+ * accumulation.  N must be 32, 64, 96 or 128; M and K are free (K is split in
+ * chunks of 128 whose results are added atomically).  err_dev (device int, may
+ * be NULL) receives BA_ERR_TIMEOUT if a bounded device wait gave up. */
+ba_status ba_tc_gemm(int32_t M, int32_t N, int32_t K, const float *A, int64_t a_rs, int64_t a_cs,
+                     const float *B, int64_t b_rs, int64_t b_cs, float *C, int64_t c_rs, int64_t c_cs,
+                     int32_t accumulate, int32_t *err_dev, void *cuda_stream);
+
 /* Allocation-free PCG for callers that cannot call cudaMalloc.
  *
  * The paper has no counterpart of this entry point; it serves callers that

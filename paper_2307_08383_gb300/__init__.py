@@ -109,6 +109,17 @@ SIGNATURES = [
     ("ba_symbolic_pattern", _S, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _I32, _I64, _I32, _I32, _I64]),
     ("ba_pcg_solve_static", _S, [ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_double,
                                  ctypes.c_int32, _P, _I32, _D]),
+    ("ba_precond_net_num_params", ctypes.c_int32, []),
+    ("ba_precond_net_create", _S, [ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
+    ("ba_precond_net_destroy", None, [_P]),
+    ("ba_precond_net_get_params", _S, [_P, ctypes.POINTER(ctypes.c_float)]),
+    ("ba_precond_net_set_params", _S, [_P, ctypes.POINTER(ctypes.c_float)]),
+    ("ba_set_precond_net", _S, [_P, _P]),
+    ("ba_precond_net_forward", _S, [_P, _P, ctypes.POINTER(ctypes.c_float), _D]),
+    ("ba_precond_net_train_step", _S, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), ctypes.c_uint64,
+                                       ctypes.c_double, _D, ctypes.POINTER(ctypes.c_float)]),
+    ("ba_tc_gemm", _S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int64, _P,
+                        ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P, _P]),
 ]
 
 _lib = None
@@ -391,3 +402,87 @@ def ba_pcg_solve_static(n, nnzb, row_ptr, col, val, b, x, rel_tol, max_iters=0, 
                                          int(max_iters), stream, ctypes.byref(it), ctypes.byref(rel)),
                allow=(BA_ERR_NO_CONVERGENCE,))
     return s, it.value, rel.value
+
+
+def ba_tc_gemm(M, N, K, A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs, accumulate=False, err=None, stream=None):
+    """C = A @ B (or C += A @ B) on the tensor cores; addresses are device
+    pointers (ints), strides in elements; see include/ba.h."""
+    _check(lib().ba_tc_gemm(int(M), int(N), int(K), A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs,
+                            1 if accumulate else 0, err, stream))
+
+
+_F = ctypes.POINTER(ctypes.c_float)
+
+
+def _fp(a):
+    return a.ctypes.data_as(_F) if a is not None else None
+
+
+class PrecondNet:
+    """The learned block-Jacobi correction (see include/ba.h)."""
+
+    def __init__(self, params=None, seed=0, stream="current"):
+        if stream == "current":
+            stream = _default_stream()
+        self.nparams = lib().ba_precond_net_num_params()
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        if p is not None and p.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters")
+        h = _P()
+        _check(lib().ba_precond_net_create(_fp(p), int(seed), stream, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ba_precond_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(self.nparams, np.float32)
+        _check(lib().ba_precond_net_get_params(self.h, _fp(out)))
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().ba_precond_net_set_params(self.h, _fp(p)))
+
+    def forward(self, problem):
+        o = np.empty((problem.n, 21), np.float32)
+        minv = np.empty((problem.n, 6, 6))
+        _check(lib().ba_precond_net_forward(self.h, problem.h, _fp(o), _dp(minv)))
+        return o, minv
+
+    def train_step(self, problem, kp=4, probes=None, seed=0, lr=0.0, want_grads=False):
+        pr = None if probes is None else np.ascontiguousarray(probes, dtype=np.float32)
+        loss = ctypes.c_double()
+        g = np.empty(self.nparams, np.float32) if want_grads else None
+        _check(lib().ba_precond_net_train_step(self.h, problem.h, int(kp), _fp(pr), int(seed), float(lr),
+                                               ctypes.byref(loss), _fp(g)))
+        return (loss.value, g) if want_grads else loss.value
+
+
+def ba_set_precond_net(problem, net):
+    _check(lib().ba_set_precond_net(problem.h, None if net is None else net.h))
+
+
+def unpack_params(p):
+    """Packed parameters -> dict of the oracle's layout (W1, b1, W2, b2, Wo, bo)."""
+    p = np.asarray(p, dtype=np.float64)
+    out, off = {}, 0
+    for name, shape in (("W1", (48, 64)), ("b1", (64,)), ("W2", (128, 64)), ("b2", (64,)), ("Wo", (64, 21)),
+                        ("bo", (21,))):
+        cnt = int(np.prod(shape))
+        out[name] = p[off:off + cnt].reshape(shape)
+        off += cnt
+    return out
+
+
+def pack_params(d):
+    return np.concatenate([np.asarray(d[k], dtype=np.float32).reshape(-1) for k in ("W1", "b1", "W2", "b2", "Wo",
+                                                                                      "bo")])

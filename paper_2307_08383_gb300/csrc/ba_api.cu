@@ -406,6 +406,8 @@ void ba_problem_destroy(ba_problem *p) {
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st);
     else cudaDeviceSynchronize();
+    gnn_free(p);
+    if (p->Minv_bj) cudaFree(p->Minv_bj);
     free_all(p);
     delete p;
 }
@@ -469,9 +471,8 @@ static ba_status run_pcg(ba_problem *p, const void *rhs, double tol, int max_ite
     return BA_OK;
 }
 
-ba_status ba_solve_rcs(ba_problem *p, ba_step_info *info) {
-    LIVE(p);
-    if (!p->rcs_formed) return fail(BA_ERR_STATE, "ba_solve_rcs needs ba_form_rcs first");
+// One solve with the current M^-1 (no learned-preconditioner logic).
+static ba_status solve_once(ba_problem *p, ba_step_info *info) {
     const int max_iters = p->opt.pcg_max_iters > 0 ? p->opt.pcg_max_iters : std::max(1000, 6 * p->n);
     const double tol = p->opt.pcg_rel_tol;
     int total = 0, refine = 0;
@@ -523,6 +524,37 @@ ba_status ba_solve_rcs(ba_problem *p, ba_step_info *info) {
     }
     if (!converged) return fail(BA_ERR_NO_CONVERGENCE, "PCG reached its iteration cap");
     return BA_OK;
+}
+
+ba_status ba_solve_rcs(ba_problem *p, ba_step_info *info) {
+    LIVE(p);
+    if (!p->rcs_formed) return fail(BA_ERR_STATE, "ba_solve_rcs needs ba_form_rcs first");
+    ba_step_info loc;
+    std::memset(&loc, 0, sizeof(loc));
+    ba_status s;
+    p->last_used_fallback = 0;
+    if (p->net) {
+        if ((s = gnn_apply(p))) return s;
+        s = solve_once(p, &loc);
+        if (s == BA_ERR_NOT_SPD || s == BA_ERR_NO_CONVERGENCE) {
+            // the learned M^-1 failed: plain block-Jacobi PCG
+            if ((s = gnn_restore_block_jacobi(p))) return s;
+            const int it = loc.pcg_iters;
+            s = solve_once(p, &loc);
+            loc.pcg_iters += it;
+            p->last_used_fallback = 1;
+        }
+    } else {
+        s = solve_once(p, &loc);
+    }
+    loc.used_fallback = p->last_used_fallback;
+    if (info) {
+        info->pcg_iters = loc.pcg_iters;
+        info->refine_steps = loc.refine_steps;
+        info->rcs_rel_resid = loc.rcs_rel_resid;
+        info->used_fallback = loc.used_fallback;
+    }
+    return s;
 }
 
 ba_status ba_back_substitute(ba_problem *p) {

@@ -100,6 +100,9 @@ struct StateBuf {
 
 }  // namespace ba
 
+struct ba_precond_net;
+namespace ba { struct GnnWork; }
+
 struct ba_problem {
     ba_options opt{};
     cudaStream_t st = nullptr;
@@ -152,6 +155,12 @@ struct ba_problem {
     int64_t klaunch[ba::K_COUNT] = {};
     double kms[ba::K_COUNT] = {};
     int64_t launches = 0;  // every kernel launched on behalf of this problem
+
+    // learned preconditioner (optional)
+    ba_precond_net *net = nullptr;
+    ba::GnnWork *gw = nullptr;
+    void *Minv_bj = nullptr;  // block-Jacobi copy kept for the fallback
+    int last_used_fallback = 0;
 };
 
 namespace ba {
@@ -177,5 +186,12 @@ cudaError_t launch_refine_rhs(ba_problem *p, void *rhs_T);
 cudaError_t launch_back_substitute(ba_problem *p);
 cudaError_t launch_apply_update(ba_problem *p);
 cudaError_t launch_eval(ba_problem *p);
+// y = S x for one FP32 vector (learned-preconditioner probes)
+cudaError_t launch_spmv_f32(ba_problem *p, const float *x, float *y);
+// learned preconditioner: M^-1 of the last formed RCS from the attached net
+// (the block-Jacobi M^-1 is saved first); restore the block-Jacobi M^-1
+ba_status gnn_apply(ba_problem *p);
+ba_status gnn_restore_block_jacobi(ba_problem *p);
+void gnn_free(ba_problem *p);
 
 }  // namespace ba

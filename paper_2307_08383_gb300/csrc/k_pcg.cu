@@ -462,6 +462,22 @@ cudaError_t launch_solution_to_step(ba_problem *p) {
     return cudaGetLastError();
 }
 
+template <typename TS>
+__global__ void __launch_bounds__(256) k_spmv_f32(int n, const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
+                                                  const TS *__restrict__ S, const float *__restrict__ x, float *y) {
+    spmv_rows<TS, float, false>(n, tw_ptr, tw_ent, S, x, nullptr, nullptr, y, 0.f);
+}
+
+cudaError_t launch_spmv_f32(ba_problem *p, const float *x, float *y) {
+    const int gs = grid_for((int64_t)p->n * 32, 256, 152 * 8);
+    if (p->fp32)
+        k_spmv_f32<float><<<gs, 256, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const float *)p->S, x, y);
+    else
+        k_spmv_f32<double><<<gs, 256, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const double *)p->S, x, y);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_back_substitute(ba_problem *p) {
     cudaEvent_t ev;
     ktimer_begin(p, K_BACKSUB, &ev);

@@ -1,0 +1,91 @@
+"""GPU parity of the learned block-Jacobi correction against its FP64 oracle:
+forward outputs and M^-1, the probe loss and every gradient (BF16 weights and
+activations on the tensor cores vs FP64 with BF16-rounded weights), the zero
+output layer (exactly block-Jacobi), and that training lowers the loss."""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.precond_net as N
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2307_08383_gb300.build import build
+    build()
+    import paper_2307_08383_gb300 as B
+    s = scenes.aerial_small(n_along=12, n_across=8, pts_per_cam=80, seed=81)
+    g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, precision=B.BA_FP32, pcg_rel_tol=1e-6)
+    g.linearize()
+    g.form_rcs(1e-3)
+    row_ptr, col, val, b = g.rcs()
+    diag, src, dst, w = N.graph_from_bsmc(row_ptr, col, val)
+    return torch, B, g, (row_ptr, col, val, b), (diag, src, dst, w)
+
+
+def _random_net(B, seed):
+    rng = np.random.default_rng(seed)
+    Wt = N.init_weights(seed)
+    Wt["Wo"] = N.bf16_round(rng.normal(0, 0.3, Wt["Wo"].shape))
+    Wt["bo"] = rng.normal(0, 0.3, Wt["bo"].shape)
+    Wt["b1"] = rng.normal(0, 0.1, 64)
+    Wt["b2"] = rng.normal(0, 0.1, 64)
+    return B.PrecondNet(params=B.pack_params(Wt)), Wt
+
+
+def test_forward_matches_oracle(env):
+    torch, B, g, (row_ptr, col, val, b), (diag, src, dst, w) = env
+    net, Wt = _random_net(B, 1)
+    o, minv = net.forward(g)
+    x = N.node_features(diag, src, dst, w)
+    o_ref, _ = N.forward(Wt, x, src, dst, w)
+    scale = np.abs(o_ref).max()
+    assert np.abs(o - o_ref).max() <= 3e-2 * scale, np.abs(o - o_ref).max() / scale
+    m_ref, _, _ = N.precond_blocks(diag, o.astype(np.float64))  # same outputs -> M^-1 in FP32 vs FP64
+    rel = np.linalg.norm((minv - m_ref).reshape(len(diag), -1), axis=1) / np.linalg.norm(m_ref.reshape(len(diag), -1), axis=1)
+    assert rel.max() <= 1e-3
+
+
+def test_zero_output_layer_is_block_jacobi(env):
+    torch, B, g, (row_ptr, col, val, b), (diag, src, dst, w) = env
+    net = B.PrecondNet(seed=3)
+    o, minv = net.forward(g)
+    assert np.abs(o).max() == 0.0
+    ref = np.linalg.inv(diag)
+    rel = np.linalg.norm((minv - ref).reshape(len(diag), -1), axis=1) / np.linalg.norm(ref.reshape(len(diag), -1), axis=1)
+    assert rel.max() <= 1e-4
+    # PCG with the attached untrained net takes block-Jacobi's iterations
+    g.form_rcs(1e-3)
+    i_bj, _ = g.solve_rcs()
+    B.ba_set_precond_net(g, net)
+    g.form_rcs(1e-3)
+    i_nn, _ = g.solve_rcs()
+    B.ba_set_precond_net(g, None)
+    assert abs(i_nn["pcg_iters"] - i_bj["pcg_iters"]) <= 1 and i_nn["used_fallback"] == 0
+
+
+def test_loss_and_gradients_match_oracle(env):
+    torch, B, g, (row_ptr, col, val, b), (diag, src, dst, w) = env
+    net, Wt = _random_net(B, 2)
+    kp = 3
+    Wp = N.probes(len(diag), kp, 5)                      # (n, 6, kp)
+    probes = np.ascontiguousarray(np.transpose(Wp, (2, 0, 1)), dtype=np.float32)  # (kp, n, 6)
+    loss, grads = net.train_step(g, kp=kp, probes=probes, lr=0.0, want_grads=True)
+    Up = N.apply_S_blocks(row_ptr, col, val, Wp)
+    loss_ref, g_ref = N.loss_and_grad(Wt, diag, src, dst, w, Wp, Up)
+    assert abs(loss - loss_ref) <= 2e-2 * loss_ref, (loss, loss_ref)
+    gd = B.unpack_params(grads)
+    for name in ("Wo", "bo", "W2", "b2", "W1", "b1"):
+        err = np.linalg.norm(gd[name] - g_ref[name]) / max(np.linalg.norm(g_ref[name]), 1e-30)
+        assert err <= 5e-2, (name, err)
+
+
+def test_training_lowers_the_loss(env):
+    torch, B, g, (row_ptr, col, val, b), (diag, src, dst, w) = env
+    net = B.PrecondNet(seed=4)
+    losses = [net.train_step(g, kp=4, seed=s, lr=3e-3) for s in range(60)]
+    assert np.mean(losses[-10:]) < 0.97 * np.mean(losses[:5]), (losses[:5], losses[-10:])
