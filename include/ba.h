@@ -66,6 +66,9 @@ typedef struct {
     size_t device_mem_cap;   /* 0 = none; creation fails with BA_ERR_OOM above it */
     int32_t group_max_obs;   /* observations per point group (0 = default) */
     int32_t profile;         /* nonzero: time every kernel launch with CUDA events */
+    int32_t solve_precision; /* FP64 problems only: BA_FP32 solves S x = b with FP32 inner
+                                PCG on a demoted copy of S (demotion timed inside the
+                                solve) and FP64 refinement with the FP64 S; 0 = as precision */
 } ba_options;
 
 typedef struct {
@@ -111,6 +114,18 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
                             int64_t n_pts, const double *pts, int64_t n_obs,
                             const int32_t *obs_cam, const int64_t *obs_pt,
                             const double *obs_uv, ba_problem **out);
+
+/* Creates a problem that holds a reduced camera system only (no observations),
+ * for solving and for the learned preconditioner: row_ptr[n+1], col[nnzb],
+ * val[nnzb x 36] (host, BSMC upper triangle of Sec. 4 with the full diagonal
+ * block first in every row, columns ascending), b[n x 6].  The block-Jacobi
+ * M^-1 is formed at creation.  ba_solve_rcs, the getters of the RCS and of
+ * dx_c, ba_set_precond_net and the network calls work; the LM calls return
+ * BA_ERR_STATE.  Rejected with BA_ERR_INVALID_ARG: a malformed pattern;
+ * BA_ERR_NONFINITE: a NaN/Inf value; BA_ERR_NOT_SPD: a diagonal block that is
+ * not positive definite. */
+ba_status ba_problem_create_rcs(const ba_options *opt, int32_t n, int64_t nnzb, const int32_t *row_ptr,
+                                const int32_t *col, const double *val, const double *b, ba_problem **out);
 
 /* Residuals and Jacobians at the current state (Eq. 1's e and J, weighted by
  * sqrt(rho') under the Huber loss), stored on the device.  *cost_out (may be
@@ -216,10 +231,12 @@ ba_status ba_set_precond_net(ba_problem *p, ba_precond_net *net);
  * (n x 36), host buffers, either may be NULL. */
 ba_status ba_precond_net_forward(ba_precond_net *net, ba_problem *p, float *out_o, double *out_minv);
 
-/* Training step on the problem's last formed RCS with kp probe vectors W
- * (host array kp x n x 6, or NULL for Rademacher probes from seed):
- *   loss = sum_i ||M_i^-1 (S W)_i - W_i||^2 / ||W||^2,
- * gradients by the network's backward pass (tensor-core GEMMs); if lr > 0 an
+/* Training step on the problem's last formed RCS with kp probe vectors w_p
+ * (host array kp x n x 6, or NULL for Rademacher probes from seed).  The loss
+ * is the S-norm error left by one preconditioned Richardson step with the
+ * optimal step length:  u_p = S w_p, z_p = M^-1 u_p, a = sum z_p^T u_p,
+ * c = sum z_p^T S z_p, e = sum w_p^T u_p, loss = 1 - a^2 / (c e).
+ * Gradients by the network's backward pass (tensor-core GEMMs); if lr > 0 an
  * Adam step (0.9, 0.999, 1e-8) updates the parameters.  loss and grads (host,
  * num_params floats) may be NULL. */
 ba_status ba_precond_net_train_step(ba_precond_net *net, ba_problem *p, int32_t kp, const float *probes,

@@ -24,9 +24,15 @@ then o_i = h2_i W_o + b_o (64 -> 21).  Layer 1 reads 24 node features, so its
 input is [x_i | m_i] of width 48.  Weights are rounded to BF16 on both sides
 (the GPU keeps BF16 weights); all arithmetic here is FP64.
 
-Training loss (probe form of ||M^-1 S - I||_F^2 restricted to the probes):
+Training loss: the energy-norm error left by one preconditioned Richardson
+step with the optimal step length, on probe vectors W (columns w_p):
 
-    loss = sum_i ||M_i^-1 u_i - w_i||^2 / sum_i ||w_i||^2,   U = S W.
+    u_p = S w_p,  z_p = M^-1 u_p,  a = sum_p z_p^T u_p,  c = sum_p z_p^T S z_p,
+    e = sum_p w_p^T u_p,  loss = 1 - a^2 / (c e)  in [0, 1],
+
+i.e. min_alpha sum_p ||w_p - alpha M^-1 S w_p||_S^2 / sum_p ||w_p||_S^2: small
+when M^-1 acts like S^-1 in the S-norm on the probes.  It is invariant to a
+common scale of M^-1 and sees the off-diagonal blocks through S z_p.
 """
 from __future__ import annotations
 
@@ -136,21 +142,25 @@ def precond_blocks(diag, o):
     return G @ np.swapaxes(G, 1, 2), G, Li
 
 
-def loss_and_grad(Wt, diag, src, dst, w, Wp, Up):
-    """Loss of the probe form and its gradient w.r.t. every weight.
+def loss_and_grad(Wt, diag, src, dst, w, Wp, Up, Sapply):
+    """Energy loss and its gradient w.r.t. every weight.
 
-    Wp, Up: (n, 6, k) probes and S @ probes per camera block."""
+    Wp, Up: (n, 6, k) probes and S @ probes per camera block; Sapply(Z) = S Z."""
     x = node_features(diag, src, dst, w)
     n = len(x)
     o, (a1, z1, h1, a2, z2, h2) = forward(Wt, x, src, dst, w)
     Minv, G, Li = precond_blocks(diag, o)
-    R = Minv @ Up - Wp
-    den = float(np.sum(Wp * Wp))
-    loss = float(np.sum(R * R)) / den
-    # d loss / d Minv = 2 R U^T / den;  Minv = G G^T -> dG = (dM + dM^T) G
-    dM = 2.0 * R @ np.swapaxes(Up, 1, 2) / den
+    Z = Minv @ Up
+    V = Sapply(Z)
+    a = float(np.sum(Z * Up))
+    c = float(np.sum(Z * V))
+    e = float(np.sum(Wp * Up))
+    loss = 1.0 - a * a / (c * e)
+    # d loss / d Z = (2a/(ce)) ((a/c) V - U); Z = Minv U -> dMinv = dZ U^T
+    dZ = (2.0 * a / (c * e)) * ((a / c) * V - Up)
+    dM = dZ @ np.swapaxes(Up, 1, 2)
+    # Minv = G G^T -> dG = (dM + dM^T) G;  G = Li^T T -> dT = Li dG (lower part used)
     dG = (dM + np.swapaxes(dM, 1, 2)) @ G
-    # G = Li^T T -> dT = Li dG (lower-triangular part used)
     dT = Li @ dG
     T = tri_from_out(o)
     do = np.zeros_like(o)
@@ -176,7 +186,7 @@ def probes(n, k, seed):
 
 
 def apply_S_blocks(row_ptr, col, val, Wp):
-    """U = S W for probes W (n, 6, k) from the upper-triangle BSMC."""
+    """U = S W for probe blocks W (n, 6, k) from the upper-triangle BSMC (Fig. 13)."""
     n = len(row_ptr) - 1
     U = np.zeros_like(Wp)
     for i in range(n):

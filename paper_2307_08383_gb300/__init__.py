@@ -52,7 +52,8 @@ class ba_options(ctypes.Structure):
                 ("pcg_max_iters", ctypes.c_int32), ("inner_rel_tol", ctypes.c_double),
                 ("refine_max", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("device_mem_cap", ctypes.c_size_t),
-                ("group_max_obs", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("group_max_obs", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("solve_precision", ctypes.c_int32)]
 
 
 class ba_step_info(ctypes.Structure):
@@ -88,6 +89,8 @@ SIGNATURES = [
     ("ba_options_default", None, [ctypes.POINTER(ba_options)]),
     ("ba_problem_create", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _D, ctypes.c_int64, _D,
                                ctypes.c_int64, _I32, _I64, _D, ctypes.POINTER(_P)]),
+    ("ba_problem_create_rcs", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, ctypes.c_int64, _I32, _I32, _D, _D,
+                                   ctypes.POINTER(_P)]),
     ("ba_linearize", _S, [_P, _D]),
     ("ba_form_rcs", _S, [_P, ctypes.c_double]),
     ("ba_solve_rcs", _S, [_P, ctypes.POINTER(ba_step_info)]),
@@ -322,6 +325,20 @@ def ba_symbolic_pattern(n_cams, n_pts, obs_cam, obs_pt):
     return row_ptr, col
 
 
+def ba_problem_create_rcs(opts, row_ptr, col, val, b):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64).reshape(-1, 36)
+    b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1, 6)
+    n = len(row_ptr) - 1
+    if len(b) != n or len(val) != len(col):
+        raise ValueError("inconsistent BSMC arrays")
+    h = _P()
+    _check(lib().ba_problem_create_rcs(ctypes.byref(opts), n, len(col), row_ptr.ctypes.data_as(_I32),
+                                       col.ctypes.data_as(_I32), _dp(val), _dp(b), ctypes.byref(h)))
+    return h
+
+
 class Problem:
     """A libba problem handle with numpy in / out."""
 
@@ -333,6 +350,19 @@ class Problem:
         self.P = len(pts)
         self.m = len(obs_cam)
         self.h = ba_problem_create(self.opts, cams, pts, obs_cam, obs_pt, obs_uv)
+
+    @classmethod
+    def from_rcs(cls, row_ptr, col, val, b, stream="current", **opts):
+        """A problem holding only a reduced camera system (see ba_problem_create_rcs)."""
+        self = cls.__new__(cls)
+        if stream == "current":
+            stream = _default_stream()
+        self.opts = ba_options_default(cuda_stream=stream, **opts)
+        self.n = len(row_ptr) - 1
+        self.P = 0
+        self.m = 0
+        self.h = ba_problem_create_rcs(self.opts, row_ptr, col, val, b)
+        return self
 
     def close(self):
         if getattr(self, "h", None):

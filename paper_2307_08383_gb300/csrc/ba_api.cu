@@ -45,7 +45,8 @@ ba_status set_error(ba_status s, const char *msg) { return fail(s, msg); }
 const char *kernel_name(int k) {
     static const char *names[K_COUNT] = {"prepare_state", "linearize", "cost",    "form_rcs",
                                          "rcs_reduce",    "rcs_diag",  "pcg_init", "pcg_loop",
-                                         "resid64",       "back_substitute", "update", "eval"};
+                                         "resid64",       "back_substitute", "update", "eval",
+                                         "demote"};
     return (k >= 0 && k < K_COUNT) ? names[k] : nullptr;
 }
 
@@ -158,6 +159,13 @@ static void to_double(const void *src, bool fp32, double *dst, size_t cnt) {
     }
 }
 
+static void default_view(ba_problem *p) {
+    p->sv.f32 = p->fp32;
+    p->sv.S = p->S;
+    p->sv.Minv = p->Minv;
+    for (int k = 0; k < 8; ++k) p->sv.pv[k] = p->pv[k];
+}
+
 // device array of the mode precision -> host doubles
 static ba_status fetch(ba_problem *p, const void *dev, size_t cnt, std::vector<double> &out) {
     std::vector<unsigned char> raw(cnt * p->esz);
@@ -191,6 +199,7 @@ void ba_options_default(ba_options *o) {
     o->device_mem_cap = 0;
     o->group_max_obs = 0;
     o->profile = 0;
+    o->solve_precision = 0;
 }
 
 const char *ba_last_error(void) { return g_err.c_str(); }
@@ -391,12 +400,108 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     std::vector<int32_t>().swap(hs.ct_row);
     std::vector<int32_t>().swap(hs.tw_ptr);
     std::vector<int2>().swap(hs.tw_ent);
+    default_view(p);
     if (e == cudaSuccess) e = launch_prepare_state(p, p->cur);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
     if (e != cudaSuccess) {
         free_all(p);
         delete p;
         return fail(BA_ERR_CUDA, std::string("problem upload: ") + cudaGetErrorString(e));
+    }
+    *out = p;
+    return BA_OK;
+}
+
+ba_status ba_problem_create_rcs(const ba_options *opt, int32_t n, int64_t nnzb, const int32_t *row_ptr,
+                                const int32_t *col, const double *val, const double *b, ba_problem **out) {
+    if (!out) return fail(BA_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    ba_options o;
+    if (opt) o = *opt; else ba_options_default(&o);
+    if (n <= 0 || nnzb < n || nnzb >= (int64_t)INT32_MAX) return fail(BA_ERR_INVALID_ARG, "need 0 < n <= nnzb < 2^31");
+    if (!row_ptr || !col || !val || !b) return fail(BA_ERR_INVALID_ARG, "null input array");
+    if (o.precision != BA_FP64 && o.precision != BA_FP32) return fail(BA_ERR_INVALID_ARG, "bad precision");
+    if (!(o.pcg_rel_tol > 0) || !(o.inner_rel_tol > 0) || o.pcg_max_iters < 0 || o.refine_max < 1)
+        return fail(BA_ERR_INVALID_ARG, "bad solver option");
+    if (row_ptr[0] != 0 || row_ptr[n] != nnzb) return fail(BA_ERR_INVALID_ARG, "row_ptr must run from 0 to nnzb");
+    for (int32_t i = 0; i < n; ++i) {
+        if (row_ptr[i + 1] <= row_ptr[i]) return fail(BA_ERR_INVALID_ARG, "every row needs its diagonal block");
+        if (col[row_ptr[i]] != i) return fail(BA_ERR_INVALID_ARG, "the first block of row i must be (i, i)");
+        for (int32_t q = row_ptr[i] + 1; q < row_ptr[i + 1]; ++q)
+            if (col[q] <= col[q - 1] || col[q] >= n) return fail(BA_ERR_INVALID_ARG, "columns must ascend within [i, n)");
+    }
+    if (!finite_all(val, (size_t)nnzb * 36) || !finite_all(b, (size_t)n * 6))
+        return fail(BA_ERR_NONFINITE, "non-finite RCS value");
+    ba_problem *p = new ba_problem();
+    p->opt = o;
+    p->st = (cudaStream_t)o.cuda_stream;
+    p->n = n;
+    p->P = 0;
+    p->m = 0;
+    p->fp32 = (o.precision == BA_FP32);
+    p->esz = p->fp32 ? 4 : 8;
+    p->rcs_only = true;
+    p->nnzb = nnzb;
+    p->hs.row_ptr.assign(row_ptr, row_ptr + n + 1);
+    p->hs.col.assign(col, col + nnzb);
+    build_twosided(p->hs, n);
+    const size_t E = p->esz;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void **q, size_t bytes) { if (e == cudaSuccess) e = dalloc_raw(p, q, bytes); };
+    A((void **)&p->row_ptr, (n + 1) * 4);
+    A((void **)&p->col, nnzb * 4);
+    A((void **)&p->tw_ptr, (n + 1) * 4);
+    A((void **)&p->tw_ent, (2 * nnzb - n) * 8);
+    A(&p->S, nnzb * BW * E);
+    A(&p->b, (size_t)n * 6 * E);
+    A(&p->Minv, (size_t)n * 36 * E);
+    for (int k = 0; k < 8; ++k) A(&p->pv[k], (size_t)n * 6 * E);
+    A((void **)&p->x64, (size_t)n * 6 * 8);
+    A((void **)&p->r64, (size_t)n * 6 * 8);
+    A((void **)&p->q64, (size_t)n * 6 * 8);
+    A(&p->dxc, (size_t)n * 6 * E);
+    A((void **)&p->sc, sizeof(DevScalars));
+    A((void **)&p->red, RED_SLOTS * 8);
+    A((void **)&p->counters, N_COUNTERS * 4);
+    if (e == cudaSuccess && cudaMallocHost((void **)&p->sc_host, sizeof(DevScalars)) != cudaSuccess)
+        e = cudaErrorMemoryAllocation;
+    auto up_ok = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    up_ok(upload(p, p->row_ptr, row_ptr, n + 1));
+    up_ok(upload(p, p->col, col, nnzb));
+    up_ok(upload(p, p->tw_ptr, p->hs.tw_ptr.data(), n + 1));
+    up_ok(upload(p, p->tw_ent, p->hs.tw_ent.data(), 2 * nnzb - n));
+    if (p->fp32) {
+        std::vector<float> t((size_t)nnzb * 36);
+        for (size_t k = 0; k < t.size(); ++k) t[k] = (float)val[k];
+        up_ok(upload(p, (float *)p->S, t.data(), t.size()));
+        std::vector<float> tb((size_t)n * 6);
+        for (size_t k = 0; k < tb.size(); ++k) tb[k] = (float)b[k];
+        up_ok(upload(p, (float *)p->b, tb.data(), tb.size()));
+    } else {
+        up_ok(upload(p, (double *)p->S, val, (size_t)nnzb * 36));
+        up_ok(upload(p, (double *)p->b, b, (size_t)n * 6));
+    }
+    up_ok(cudaMemsetAsync(p->q64, 0, (size_t)n * 6 * 8, p->st));
+    up_ok(cudaMemsetAsync(p->x64, 0, (size_t)n * 6 * 8, p->st));
+    up_ok(cudaMemsetAsync(p->sc, 0, sizeof(DevScalars), p->st));
+    up_ok(cudaMemsetAsync(p->counters, 0, N_COUNTERS * 4, p->st));
+    std::vector<int2>().swap(p->hs.tw_ent);
+    std::vector<int32_t>().swap(p->hs.tw_ptr);
+    if (e == cudaSuccess) e = launch_block_jacobi(p);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess) {
+        free_all(p);
+        delete p;
+        return fail(e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA,
+                    std::string("RCS problem creation: ") + cudaGetErrorString(e));
+    }
+    default_view(p);
+    p->rcs_formed = true;
+    p->lambda = 0.0;
+    if (sync_scalars(p) == BA_OK && p->sc_host->err == BA_ERR_NOT_SPD) {
+        free_all(p);
+        delete p;
+        return fail(BA_ERR_NOT_SPD, "a diagonal block of the RCS is not positive definite");
     }
     *out = p;
     return BA_OK;
@@ -436,6 +541,7 @@ static ba_status ensure_cost(ba_problem *p) {
 
 ba_status ba_linearize(ba_problem *p, double *cost_out) {
     LIVE(p);
+    if (p->rcs_only) return fail(BA_ERR_STATE, "ba_linearize: the problem holds an RCS only");
     CK(p, launch_linearize(p));
     p->linearized = true;
     p->rcs_formed = p->solved = p->backsub = false;
@@ -449,6 +555,7 @@ ba_status ba_linearize(ba_problem *p, double *cost_out) {
 
 ba_status ba_form_rcs(ba_problem *p, double lambda) {
     LIVE(p);
+    if (p->rcs_only) return fail(BA_ERR_STATE, "ba_form_rcs: the problem holds an RCS only");
     if (!p->linearized) return fail(BA_ERR_STATE, "ba_form_rcs needs ba_linearize first");
     if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and >= 0");
     CK(p, launch_form_rcs(p, lambda));
@@ -472,13 +579,45 @@ static ba_status run_pcg(ba_problem *p, const void *rhs, double tol, int max_ite
 }
 
 // One solve with the current M^-1 (no learned-preconditioner logic).
+static ba_status ensure_shadows(ba_problem *p) {
+    if (p->S32) return BA_OK;
+    CK(p, dalloc_raw(p, &p->S32, (size_t)p->nnzb * BW * 4));
+    CK(p, dalloc_raw(p, &p->Minv32, (size_t)p->n * 36 * 4));
+    for (int k = 0; k < 8; ++k) CK(p, dalloc_raw(p, &p->pv32[k], (size_t)p->n * 6 * 4));
+    return BA_OK;
+}
+
+static ba_status solve_once_view(ba_problem *p, ba_step_info *info);
+
+// One solve with the current M^-1 (no learned-preconditioner logic).  An FP64
+// problem with solve_precision = BA_FP32 demotes S and M^-1 to FP32 shadows
+// (timed as part of the solve), runs the inner PCG in FP32 and refines with
+// the FP64 residual b - S x of the FP64 system.
 static ba_status solve_once(ba_problem *p, ba_step_info *info) {
+    const bool mixed = !p->fp32 && p->opt.solve_precision == BA_FP32;
+    ba_status s;
+    if (mixed) {
+        if ((s = ensure_shadows(p))) return s;
+        CK(p, launch_demote(p));
+        p->sv.f32 = true;
+        p->sv.S = p->S32;
+        p->sv.Minv = p->Minv32;
+        for (int k = 0; k < 8; ++k) p->sv.pv[k] = p->pv32[k];
+    } else {
+        default_view(p);
+    }
+    s = solve_once_view(p, info);
+    default_view(p);
+    return s;
+}
+
+static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
     const int max_iters = p->opt.pcg_max_iters > 0 ? p->opt.pcg_max_iters : std::max(1000, 6 * p->n);
     const double tol = p->opt.pcg_rel_tol;
     int total = 0, refine = 0;
     bool converged = false;
     ba_status s;
-    if (!p->fp32) {
+    if (!p->sv.f32) {
         int it = 0;
         if ((s = run_pcg(p, p->b, tol, max_iters, &it))) return s;
         if ((s = check_err_flag(p))) return s;
@@ -495,9 +634,9 @@ static ba_status solve_once(ba_problem *p, ba_step_info *info) {
         for (int o = 0; o < p->opt.refine_max; ++o) {
             if (p->sc_host->rr64 <= tol * tol * p->sc_host->bb64) { converged = true; break; }
             if (p->sc_host->bb64 == 0.0) { converged = true; break; }
-            CK(p, launch_refine_rhs(p, p->pv[1]));  // r buffer doubles as the rhs (copied by init)
+            CK(p, launch_refine_rhs(p, p->sv.pv[1]));  // r buffer doubles as the rhs (copied by init)
             int it = 0;
-            if ((s = run_pcg(p, p->pv[1], inner, max_iters, &it))) return s;
+            if ((s = run_pcg(p, p->sv.pv[1], inner, max_iters, &it))) return s;
             if ((s = check_err_flag(p))) return s;
             total += it;
             ++refine;
@@ -559,6 +698,7 @@ ba_status ba_solve_rcs(ba_problem *p, ba_step_info *info) {
 
 ba_status ba_back_substitute(ba_problem *p) {
     LIVE(p);
+    if (p->rcs_only) return fail(BA_ERR_STATE, "ba_back_substitute: the problem holds an RCS only");
     if (!p->solved) return fail(BA_ERR_STATE, "ba_back_substitute needs ba_solve_rcs first");
     CK(p, launch_back_substitute(p));
     p->backsub = true;
@@ -567,6 +707,7 @@ ba_status ba_back_substitute(ba_problem *p) {
 
 ba_status ba_lm_step(ba_problem *p, ba_step_info *info) {
     LIVE(p);
+    if (p->rcs_only) return fail(BA_ERR_STATE, "ba_lm_step: the problem holds an RCS only");
     ba_step_info loc;
     std::memset(&loc, 0, sizeof(loc));
     cudaEvent_t ev[6];

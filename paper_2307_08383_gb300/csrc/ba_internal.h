@@ -56,7 +56,7 @@ constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
 
 enum KernelId {
     K_PREPARE = 0, K_LINEARIZE, K_COST, K_FORM_RCS, K_RCS_REDUCE, K_RCS_DIAG,
-    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_EVAL, K_COUNT
+    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_EVAL, K_DEMOTE, K_COUNT
 };
 const char *kernel_name(int k);
 
@@ -84,6 +84,9 @@ struct HostSetup {
     int64_t n_pairs = 0;
 };
 
+// Column index and two-sided SpMV entry lists from hs.row_ptr / hs.col.
+void build_twosided(HostSetup &hs, int32_t n);
+
 // Validates the observation set and builds everything above.  Returns BA_OK or
 // BA_ERR_INVALID_ARG with a message.
 ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam,
@@ -101,7 +104,16 @@ struct StateBuf {
 }  // namespace ba
 
 struct ba_precond_net;
-namespace ba { struct GnnWork; }
+namespace ba {
+struct GnnWork;
+// The buffers a PCG solve runs on: the problem's own, or FP32 shadows of an
+// FP64 problem's system (mixed-precision solve).
+struct SolverView {
+    bool f32 = false;
+    void *S = nullptr, *Minv = nullptr;
+    void *pv[8] = {};
+};
+}  // namespace ba
 
 struct ba_problem {
     ba_options opt{};
@@ -156,6 +168,11 @@ struct ba_problem {
     double kms[ba::K_COUNT] = {};
     int64_t launches = 0;  // every kernel launched on behalf of this problem
 
+    // solve view and FP32 shadows (FP64 problems solved in mixed precision)
+    ba::SolverView sv;
+    void *S32 = nullptr, *Minv32 = nullptr, *pv32[8] = {};
+    bool rcs_only = false;  // created from a BSMC system: no observations
+
     // learned preconditioner (optional)
     ba_precond_net *net = nullptr;
     ba::GnnWork *gw = nullptr;
@@ -186,6 +203,8 @@ cudaError_t launch_refine_rhs(ba_problem *p, void *rhs_T);
 cudaError_t launch_back_substitute(ba_problem *p);
 cudaError_t launch_apply_update(ba_problem *p);
 cudaError_t launch_eval(ba_problem *p);
+cudaError_t launch_block_jacobi(ba_problem *p);               // Minv from the diagonal blocks of S
+cudaError_t launch_demote(ba_problem *p);                     // S32, Minv32 from the FP64 S, Minv
 // y = S x for one FP32 vector (learned-preconditioner probes)
 cudaError_t launch_spmv_f32(ba_problem *p, const float *x, float *y);
 // learned preconditioner: M^-1 of the last formed RCS from the attached net

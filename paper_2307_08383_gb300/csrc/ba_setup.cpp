@@ -69,6 +69,37 @@ static int32_t find_block(const std::vector<int32_t> &row_ptr, const std::vector
     return (int32_t)(it - col.begin());
 }
 
+void build_twosided(HostSetup &hs, int32_t n) {
+    // column index of the upper triangle: for every column i the off-diagonal
+    //      blocks (j, i), j < i, in row order (the SpMV applies them transposed)
+    hs.ct_ptr.assign(n + 1, 0);
+    for (int32_t j = 0; j < n; ++j)
+        for (int32_t b = hs.row_ptr[j] + 1; b < hs.row_ptr[j + 1]; ++b) hs.ct_ptr[hs.col[b] + 1]++;
+    for (int32_t i = 0; i < n; ++i) hs.ct_ptr[i + 1] += hs.ct_ptr[i];
+    hs.ct_blk.assign(hs.ct_ptr[n], 0);
+    hs.ct_row.assign(hs.ct_ptr[n], 0);
+    {
+        std::vector<int32_t> fill(hs.ct_ptr.begin(), hs.ct_ptr.end() - 1);
+        for (int32_t j = 0; j < n; ++j)
+            for (int32_t b = hs.row_ptr[j] + 1; b < hs.row_ptr[j + 1]; ++b) {
+                const int32_t at = fill[hs.col[b]]++;
+                hs.ct_blk[at] = b;
+                hs.ct_row[at] = j;
+            }
+    }
+    // two-sided SpMV entries of row i: (i, j >= i) as stored, then (j < i, i) transposed
+    hs.tw_ptr.assign(n + 1, 0);
+    hs.tw_ent.clear();
+    hs.tw_ent.reserve(2 * hs.col.size());
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t b = hs.row_ptr[i]; b < hs.row_ptr[i + 1]; ++b) hs.tw_ent.push_back(make_int2(b, hs.col[b]));
+        for (int32_t q = hs.ct_ptr[i]; q < hs.ct_ptr[i + 1]; ++q)
+            hs.tw_ent.push_back(make_int2((int32_t)((uint32_t)hs.ct_blk[q] | 0x80000000u), hs.ct_row[q]));
+        hs.tw_ptr[i + 1] = (int32_t)hs.tw_ent.size();
+    }
+
+}
+
 ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam,
                          const int64_t *obs_pt, const double *pts, int obs_max, bool pattern_only,
                          HostSetup &hs, std::string &err) {
@@ -150,33 +181,7 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
     }
     if (pattern_only) return BA_OK;
 
-    // ---- column index of the upper triangle: for every column i the off-diagonal
-    //      blocks (j, i), j < i, in row order (the SpMV applies them transposed)
-    hs.ct_ptr.assign(n + 1, 0);
-    for (int32_t j = 0; j < n; ++j)
-        for (int32_t b = hs.row_ptr[j] + 1; b < hs.row_ptr[j + 1]; ++b) hs.ct_ptr[hs.col[b] + 1]++;
-    for (int32_t i = 0; i < n; ++i) hs.ct_ptr[i + 1] += hs.ct_ptr[i];
-    hs.ct_blk.assign(hs.ct_ptr[n], 0);
-    hs.ct_row.assign(hs.ct_ptr[n], 0);
-    {
-        std::vector<int32_t> fill(hs.ct_ptr.begin(), hs.ct_ptr.end() - 1);
-        for (int32_t j = 0; j < n; ++j)
-            for (int32_t b = hs.row_ptr[j] + 1; b < hs.row_ptr[j + 1]; ++b) {
-                const int32_t at = fill[hs.col[b]]++;
-                hs.ct_blk[at] = b;
-                hs.ct_row[at] = j;
-            }
-    }
-    // ---- two-sided SpMV entries of row i: (i, j >= i) as stored, then (j < i, i) transposed
-    hs.tw_ptr.assign(n + 1, 0);
-    hs.tw_ent.clear();
-    hs.tw_ent.reserve(2 * hs.col.size());
-    for (int32_t i = 0; i < n; ++i) {
-        for (int32_t b = hs.row_ptr[i]; b < hs.row_ptr[i + 1]; ++b) hs.tw_ent.push_back(make_int2(b, hs.col[b]));
-        for (int32_t q = hs.ct_ptr[i]; q < hs.ct_ptr[i + 1]; ++q)
-            hs.tw_ent.push_back(make_int2((int32_t)((uint32_t)hs.ct_blk[q] | 0x80000000u), hs.ct_row[q]));
-        hs.tw_ptr[i + 1] = (int32_t)hs.tw_ent.size();
-    }
+    build_twosided(hs, n);
 
     // ---- point groups with their sub-RCS blocks (Sec. 6.1)
     const int64_t nnzb = (int64_t)hs.col.size();

@@ -257,95 +257,139 @@ __global__ void k_precond(int n, const int *__restrict__ row_ptr, const T *__res
         }
 }
 
-// Probe loss and its gradient w.r.t. the 21 outputs; thread per camera.
-//   R = Minv U - W, loss = sum ||R||^2 / den, dM = 2 R U^T / den,
-//   dG = (dM + dM^T) G, dT = Li dG, dO from dT.
+// M_i^-1, G_i = L_i^-T T_i and L_i^-1 of camera i from S_ii and its outputs.
 template <typename T>
-__global__ void k_probe_loss(int n, int kp, const int *__restrict__ row_ptr, const T *__restrict__ S,
-                             const float *__restrict__ O, const float *__restrict__ Wp, const float *__restrict__ Up,
-                             float inv_den, float *__restrict__ dO, double *red, unsigned *ctr, double *loss_out) {
-    double acc[1] = {0.0};
+__device__ __forceinline__ void precond_parts(const T *__restrict__ d, const float *__restrict__ o, float *M, float *G,
+                                              float *Li, float *Tm) {
+    float A[36];
+#pragma unroll
+    for (int q = 0; q < 36; ++q) A[q] = (float)d[q];
+    chol6_inv(A, Li);
+    tri_from_out(o, Tm);
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s += Li[6 * k + r] * Tm[6 * k + c];
+            G[6 * r + c] = s;
+        }
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s += G[6 * r + k] * G[6 * c + k];
+            M[6 * r + c] = s;
+        }
+}
+
+// Energy loss, stage 1: z_p = M^-1 u_p per camera; a = sum z^T u, e = sum w^T u.
+template <typename T>
+__global__ void k_energy_z(int n, int kp, const int *__restrict__ row_ptr, const T *__restrict__ S,
+                           const float *__restrict__ O, const float *__restrict__ Wp, const float *__restrict__ Up,
+                           float *__restrict__ Zp, double *red, unsigned *ctr, double *scal) {
+    RunSum<float> sa, se;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float A[36], Li[36], Tm[36], G[36], M[36], dM[36];
-        const T *d = S + (int64_t)row_ptr[i] * BW;
-#pragma unroll
-        for (int q = 0; q < 36; ++q) A[q] = (float)d[q];
-        chol6_inv(A, Li);
-        tri_from_out(O + (int64_t)i * NOP, Tm);
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                float s = 0.f;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) s += Li[6 * k + r] * Tm[6 * k + c];
-                G[6 * r + c] = s;
-            }
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                float s = 0.f;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) s += G[6 * r + k] * G[6 * c + k];
-                M[6 * r + c] = s;
-            }
-#pragma unroll
-        for (int q = 0; q < 36; ++q) dM[q] = 0.f;
-        float l = 0.f;
+        float M[36], G[36], Li[36], Tm[36];
+        precond_parts<T>(S + (int64_t)row_ptr[i] * BW, O + (int64_t)i * NOP, M, G, Li, Tm);
         for (int p = 0; p < kp; ++p) {
-            const float *u = Up + ((int64_t)p * n + i) * 6, *w = Wp + ((int64_t)p * n + i) * 6;
-            float uu[6], R[6];
+            const int64_t o6 = ((int64_t)p * n + i) * 6;
+            float u[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) uu[c] = u[c];
+            for (int c = 0; c < 6; ++c) u[c] = Up[o6 + c];
 #pragma unroll
             for (int r = 0; r < 6; ++r) {
-                float s = -w[r];
+                float z = 0.f;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) s += M[6 * r + c] * uu[c];
-                R[r] = s;
-                l += s * s;
+                for (int c = 0; c < 6; ++c) z += M[6 * r + c] * u[c];
+                Zp[o6 + r] = z;
+                sa.add(z * u[r]);
+                se.add(Wp[o6 + r] * u[r]);
             }
-#pragma unroll
-            for (int r = 0; r < 6; ++r)
-#pragma unroll
-                for (int c = 0; c < 6; ++c) dM[6 * r + c] += 2.f * inv_den * R[r] * uu[c];
         }
-        acc[0] += (double)l;
-        float S2[36], dG[36], dT[36];
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) S2[6 * r + c] = dM[6 * r + c] + dM[6 * c + r];
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                float s = 0.f;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) s += S2[6 * r + k] * G[6 * k + c];
-                dG[6 * r + c] = s;
-            }
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                float s = 0.f;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) s += Li[6 * r + k] * dG[6 * k + c];
-                dT[6 * r + c] = s;
-            }
-        float *g = dO + (int64_t)i * NOP;
-        int q = 0;
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-#pragma unroll
-            for (int l2 = 0; l2 <= k; ++l2, ++q)
-                g[q] = dT[6 * k + l2] * (k == l2 ? OUT_SCALE * Tm[7 * k] : OUT_SCALE);
-#pragma unroll
-        for (int q2 = NO; q2 < NOP; ++q2) g[q2] = 0.f;
     }
-    grid_sum<1>(acc, red, ctr, [&](double *t) { *loss_out = t[0] * (double)inv_den; });
+    double v[2] = {sa.get(), se.get()};
+    grid_sum<2>(v, red, ctr, [&](double *t) {
+        scal[1] = t[0];  // a
+        scal[3] = t[1];  // e
+    });
+}
+
+// Energy loss, stage 2: c = sum z^T (S z); loss = 1 - a^2 / (c e).
+__global__ void k_energy_c(int64_t cnt, const float *__restrict__ Zp, const float *__restrict__ Vp, double *red,
+                           unsigned *ctr, double *scal) {
+    RunSum<float> sc;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < cnt; x += (int64_t)gridDim.x * blockDim.x)
+        sc.add(Zp[x] * Vp[x]);
+    double v[1] = {sc.get()};
+    grid_sum<1>(v, red, ctr, [&](double *t) {
+        scal[2] = t[0];  // c
+        scal[0] = 1.0 - scal[1] * scal[1] / (t[0] * scal[3]);
+    });
+}
+
+// Energy loss, stage 3: d loss / d o per camera.
+//   dz_p = (2a/(ce)) ((a/c) v_p - u_p),  dM = sum_p dz_p u_p^T,
+//   dG = (dM + dM^T) G,  dT = L^-1 dG,  dO from dT.
+template <typename T>
+__global__ void k_energy_grad(int n, int kp, const int *__restrict__ row_ptr, const T *__restrict__ S,
+                              const float *__restrict__ O, const float *__restrict__ Up, const float *__restrict__ Vp,
+                              const double *__restrict__ scal, float *__restrict__ dO) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = scal[1], c = scal[2], e = scal[3];
+    const float f1 = (float)(2.0 * a / (c * e)), f2 = (float)(a / c);
+    float M[36], G[36], Li[36], Tm[36], dM[36];
+    precond_parts<T>(S + (int64_t)row_ptr[i] * BW, O + (int64_t)i * NOP, M, G, Li, Tm);
+#pragma unroll
+    for (int q = 0; q < 36; ++q) dM[q] = 0.f;
+    for (int p = 0; p < kp; ++p) {
+        const int64_t o6 = ((int64_t)p * n + i) * 6;
+        float u[6], dz[6];
+#pragma unroll
+        for (int c2 = 0; c2 < 6; ++c2) {
+            u[c2] = Up[o6 + c2];
+            dz[c2] = f1 * (f2 * Vp[o6 + c2] - u[c2]);
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int c2 = 0; c2 < 6; ++c2) dM[6 * r + c2] += dz[r] * u[c2];
+    }
+    float S2[36], dG[36], dT[36];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c2 = 0; c2 < 6; ++c2) S2[6 * r + c2] = dM[6 * r + c2] + dM[6 * c2 + r];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c2 = 0; c2 < 6; ++c2) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s2 += S2[6 * r + k] * G[6 * k + c2];
+            dG[6 * r + c2] = s2;
+        }
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c2 = 0; c2 < 6; ++c2) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s2 += Li[6 * r + k] * dG[6 * k + c2];
+            dT[6 * r + c2] = s2;
+        }
+    float *g = dO + (int64_t)i * NOP;
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int l2 = 0; l2 <= k; ++l2, ++q) g[q] = dT[6 * k + l2] * (k == l2 ? OUT_SCALE * Tm[7 * k] : OUT_SCALE);
+#pragma unroll
+    for (int q2 = NO; q2 < NOP; ++q2) g[q2] = 0.f;
 }
 
 // Rademacher probes from a counter-based hash (splitmix64 of seed, index).
@@ -410,7 +454,7 @@ struct ba_precond_net {
     int64_t step = 0;
     cudaStream_t st = nullptr;
     int *err = nullptr;
-    double *loss = nullptr;
+    double *loss = nullptr;  // [loss, a, c, e] of the last training step
 };
 
 namespace ba {
@@ -420,7 +464,7 @@ struct GnnWork {
     float *dn = nullptr, *logd = nullptr, *logd_mean = nullptr, *wb = nullptr;
     float *A1 = nullptr, *Z1 = nullptr, *A2 = nullptr, *Z2 = nullptr, *H2 = nullptr, *O = nullptr;
     float *dO = nullptr, *dZ2 = nullptr, *dA2 = nullptr, *dZ1 = nullptr;
-    float *Wp = nullptr, *Up = nullptr;
+    float *Wp = nullptr, *Up = nullptr, *Zp = nullptr, *Vp = nullptr;
     std::vector<void *> bufs;
 };
 
@@ -457,7 +501,10 @@ static cudaError_t ensure_work(ba_problem *p, int kp) {
     A(&w->dn, n); A(&w->logd, 6 * n); A(&w->logd_mean, 8); A(&w->wb, p->nnzb);
     A(&w->A1, n * 2 * NF); A(&w->Z1, n * H); A(&w->A2, n * 2 * H); A(&w->Z2, n * H); A(&w->H2, n * H);
     A(&w->O, n * NOP); A(&w->dO, n * NOP); A(&w->dZ2, n * H); A(&w->dA2, n * 2 * H); A(&w->dZ1, n * H);
-    if (kp > 0) { A(&w->Wp, (size_t)kp * n * 6); A(&w->Up, (size_t)kp * n * 6); }
+    if (kp > 0) {
+        A(&w->Wp, (size_t)kp * n * 6); A(&w->Up, (size_t)kp * n * 6);
+        A(&w->Zp, (size_t)kp * n * 6); A(&w->Vp, (size_t)kp * n * 6);
+    }
     return e;
 }
 
@@ -539,13 +586,19 @@ static cudaError_t loss_grad_T(ba_problem *p, ba_precond_net *net, int kp) {
     const int n = p->n;
     cudaStream_t st = p->st;
     cudaError_t e;
-    // U = S W for each probe
+    // U = S W, Z = M^-1 U, V = S Z for each probe; energy loss and d loss / d o
     for (int k = 0; k < kp; ++k)
         if ((e = launch_spmv_f32(p, w->Wp + (int64_t)k * n * 6, w->Up + (int64_t)k * n * 6)) != cudaSuccess) return e;
-    const float inv_den = 1.f / (float)((double)kp * n * 6);  // Rademacher probes: ||W||^2 = 6 n kp
     const int gv = (int)std::min<int64_t>((n + 127) / 128, 152 * 4);
-    k_probe_loss<T><<<gv, 128, 0, st>>>(n, kp, p->row_ptr, (const T *)p->S, w->O, w->Wp, w->Up, inv_den, w->dO, p->red,
-                                        p->counters + 9, net->loss);
+    k_energy_z<T><<<gv, 128, 0, st>>>(n, kp, p->row_ptr, (const T *)p->S, w->O, w->Wp, w->Up, w->Zp, p->red,
+                                      p->counters + 9, net->loss);
+    for (int k = 0; k < kp; ++k)
+        if ((e = launch_spmv_f32(p, w->Zp + (int64_t)k * n * 6, w->Vp + (int64_t)k * n * 6)) != cudaSuccess) return e;
+    const int64_t cnt = (int64_t)kp * n * 6;
+    k_energy_c<<<(int)std::min<int64_t>((cnt + 255) / 256, 1024), 256, 0, st>>>(cnt, w->Zp, w->Vp, p->red,
+                                                                                  p->counters + 10, net->loss);
+    k_energy_grad<T><<<(n + 127) / 128, 128, 0, st>>>(n, kp, p->row_ptr, (const T *)p->S, w->O, w->Up, w->Vp,
+                                                      net->loss, w->dO);
     if ((e = cudaMemsetAsync(net->g, 0, sizeof(float) * (NPARAM + H * NOP + NOP), st)) != cudaSuccess) return e;
     float *gwo_pad = net->g + NPARAM, *gbo_pad = gwo_pad + H * NOP;
     // output layer: dWo = H2^T dO, dbo = colsum(dO), dH2 = dO Wo^T masked by Z2 > 0 -> dZ2
@@ -652,7 +705,7 @@ ba_status ba_precond_net_create(const float *params, uint64_t seed, void *cuda_s
     auto A = [&](void **q, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(q, bytes); };
     A((void **)&net->w, np * 4); A((void **)&net->g, (np + extra) * 4); A((void **)&net->m, np * 4);
     A((void **)&net->v, np * 4); A((void **)&net->wo_pad, extra * 4); A((void **)&net->err, sizeof(int));
-    A((void **)&net->loss, sizeof(double));
+    A((void **)&net->loss, 4 * sizeof(double));
     if (e == cudaSuccess) {
         net->bo_pad = net->wo_pad + gnn::H * gnn::NOP;
         std::vector<float> h(np, 0.f);

@@ -347,15 +347,15 @@ cudaError_t launch_pcg_init(ba_problem *p, const void *rhs, double tol, int max_
     cudaEvent_t ev;
     ktimer_begin(p, K_PCG_INIT, &ev);
     const int g = grid_for(p->n, 256, VEC_CAP);
-    if (p->fp32)
-        k_pcg_init<float><<<g, 256, 0, p->st>>>(p->n, (const float *)rhs, (const float *)p->Minv, (float *)p->pv[0],
-                                                (float *)p->pv[1], (float *)p->pv[2], (float *)p->pv[3],
-                                                (float *)p->pv[5], (float *)p->pv[7], p->sc, tol * tol, max_iters, p->red,
+    if (p->sv.f32)
+        k_pcg_init<float><<<g, 256, 0, p->st>>>(p->n, (const float *)rhs, (const float *)p->sv.Minv, (float *)p->sv.pv[0],
+                                                (float *)p->sv.pv[1], (float *)p->sv.pv[2], (float *)p->sv.pv[3],
+                                                (float *)p->sv.pv[5], (float *)p->sv.pv[7], p->sc, tol * tol, max_iters, p->red,
                                                 p->counters + 2);
     else
-        k_pcg_init<double><<<g, 256, 0, p->st>>>(p->n, (const double *)rhs, (const double *)p->Minv,
-                                                 (double *)p->pv[0], (double *)p->pv[1], (double *)p->pv[2],
-                                                 (double *)p->pv[3], (double *)p->pv[5], (double *)p->pv[7], p->sc,
+        k_pcg_init<double><<<g, 256, 0, p->st>>>(p->n, (const double *)rhs, (const double *)p->sv.Minv,
+                                                 (double *)p->sv.pv[0], (double *)p->sv.pv[1], (double *)p->sv.pv[2],
+                                                 (double *)p->sv.pv[3], (double *)p->sv.pv[5], (double *)p->sv.pv[7], p->sc,
                                                  tol * tol, max_iters, p->red, p->counters + 2);
     ktimer_end(p, K_PCG_INIT, ev);
     p->launches += 1;
@@ -382,9 +382,9 @@ static cudaError_t pcg_loop_T(ba_problem *p) {
     int n = p->n;
     const int *twp = p->tw_ptr;
     const int2 *twe = p->tw_ent;
-    const T *S = (const T *)p->S, *Mi = (const T *)p->Minv;
-    T *y = (T *)p->pv[0], *r = (T *)p->pv[1], *z = (T *)p->pv[2], *d0 = (T *)p->pv[3], *d1 = (T *)p->pv[4];
-    T *q = (T *)p->pv[5], *r1 = (T *)p->pv[6];
+    const T *S = (const T *)p->sv.S, *Mi = (const T *)p->sv.Minv;
+    T *y = (T *)p->sv.pv[0], *r = (T *)p->sv.pv[1], *z = (T *)p->sv.pv[2], *d0 = (T *)p->sv.pv[3], *d1 = (T *)p->sv.pv[4];
+    T *q = (T *)p->sv.pv[5], *r1 = (T *)p->sv.pv[6];
     DevScalars *sc = p->sc;
     double *red = p->red;
     unsigned *bar = p->counters + 14;
@@ -396,7 +396,7 @@ static cudaError_t pcg_loop_T(ba_problem *p) {
 cudaError_t launch_pcg_loop(ba_problem *p) {
     cudaEvent_t ev;
     ktimer_begin(p, K_PCG_LOOP, &ev);
-    cudaError_t e = p->fp32 ? pcg_loop_T<float>(p) : pcg_loop_T<double>(p);
+    cudaError_t e = p->sv.f32 ? pcg_loop_T<float>(p) : pcg_loop_T<double>(p);
     ktimer_end(p, K_PCG_LOOP, ev);
     p->launches += 1;
     if (e != cudaSuccess) return e;
@@ -430,10 +430,10 @@ cudaError_t launch_resid64(ba_problem *p, bool from_x64) {
 cudaError_t launch_accumulate_solution(ba_problem *p, bool first) {
     const int64_t cnt = (int64_t)p->n * 6;
     const int g = grid_for(cnt, 256, VEC_CAP);
-    if (p->fp32)
-        k_acc64<float><<<g, 256, 0, p->st>>>(cnt, (const float *)p->pv[0], p->x64, first ? 1 : 0);
+    if (p->sv.f32)
+        k_acc64<float><<<g, 256, 0, p->st>>>(cnt, (const float *)p->sv.pv[0], p->x64, first ? 1 : 0);
     else
-        k_acc64<double><<<g, 256, 0, p->st>>>(cnt, (const double *)p->pv[0], p->x64, first ? 1 : 0);
+        k_acc64<double><<<g, 256, 0, p->st>>>(cnt, (const double *)p->sv.pv[0], p->x64, first ? 1 : 0);
     p->launches += 1;
     return cudaGetLastError();
 }
@@ -442,7 +442,7 @@ cudaError_t launch_accumulate_solution(ba_problem *p, bool first) {
 cudaError_t launch_refine_rhs(ba_problem *p, void *rhs) {
     const int64_t cnt = (int64_t)p->n * 6;
     const int g = grid_for(cnt, 256, VEC_CAP);
-    if (p->fp32)
+    if (p->sv.f32)
         k_to_T<float><<<g, 256, 0, p->st>>>(cnt, p->r64, (float *)rhs);
     else
         k_to_T<double><<<g, 256, 0, p->st>>>(cnt, p->r64, (double *)rhs);
@@ -475,6 +475,23 @@ cudaError_t launch_spmv_f32(ba_problem *p, const float *x, float *y) {
     else
         k_spmv_f32<double><<<gs, 256, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const double *)p->S, x, y);
     p->launches += 1;
+    return cudaGetLastError();
+}
+
+__global__ void k_demote(int64_t cnt, const double *__restrict__ a, float *__restrict__ o) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < cnt; x += (int64_t)gridDim.x * blockDim.x)
+        o[x] = (float)a[x];
+}
+
+// FP32 shadows of an FP64 problem's S and M^-1 (mixed-precision solve)
+cudaError_t launch_demote(ba_problem *p) {
+    cudaEvent_t ev;
+    ktimer_begin(p, K_DEMOTE, &ev);
+    const int64_t cs = p->nnzb * BW, cm = (int64_t)p->n * 36;
+    k_demote<<<grid_for(cs, 256, 152 * 16), 256, 0, p->st>>>(cs, (const double *)p->S, (float *)p->S32);
+    k_demote<<<grid_for(cm, 256, 152 * 4), 256, 0, p->st>>>(cm, (const double *)p->Minv, (float *)p->Minv32);
+    ktimer_end(p, K_DEMOTE, ev);
+    p->launches += 2;
     return cudaGetLastError();
 }
 

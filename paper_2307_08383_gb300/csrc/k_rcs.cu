@@ -355,6 +355,25 @@ __global__ void k_rcs_diag(int n, const int *__restrict__ row_ptr, T *__restrict
     for (int q = 0; q < 36; ++q) Minv[36 * (int64_t)i + q] = Ai[q];
 }
 
+// Block-Jacobi only: M_i^-1 = S_ii^-1 (diagonal blocks stored full, first in each row).
+template <typename T>
+__global__ void k_block_jacobi(int n, const int *__restrict__ row_ptr, const T *__restrict__ S, T *__restrict__ Minv,
+                               DevScalars *sc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T A[36], Ai[36];
+    const T *d = S + (int64_t)row_ptr[i] * BW;
+#pragma unroll
+    for (int q = 0; q < 36; ++q) A[q] = d[q];
+    if (!spd_inverse6<T>(A, Ai)) {
+        atomicExch(&sc->err, (int)BA_ERR_NOT_SPD);
+#pragma unroll
+        for (int q = 0; q < 36; ++q) Ai[q] = T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 36; ++q) Minv[36 * (int64_t)i + q] = Ai[q];
+}
+
 static inline int grid_for(int64_t work, int threads, int cap) {
     int64_t g = (work + threads - 1) / threads;
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -379,6 +398,16 @@ static cudaError_t form_rcs_T(ba_problem *p, double lambda, size_t smem, long lo
     k_form_rcs<T><<<grid, FORM_THREADS, smem, p->st>>>(p->grp, (int)p->ngroups, p->items, p->contrib, p->trk_ptr,
                                                       (const T *)p->J, lambda, (T *)p->part, (T *)p->Linv, (T *)p->lp,
                                                       p->sc, p->fp32 ? 1 : 0, p->obs_max, limit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_jacobi(ba_problem *p) {
+    const int nb = (p->n + 127) / 128;
+    if (p->fp32)
+        k_block_jacobi<float><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const float *)p->S, (float *)p->Minv, p->sc);
+    else
+        k_block_jacobi<double><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const double *)p->S, (double *)p->Minv, p->sc);
+    p->launches += 1;
     return cudaGetLastError();
 }
 

@@ -119,3 +119,30 @@ def test_null_problem_calls_fail_cleanly(B):
     assert B.lib().ba_linearize(None, None) == B.BA_ERR_INVALID_ARG
     assert B.lib().ba_lm_step(None, None) == B.BA_ERR_INVALID_ARG
     B.lib().ba_problem_destroy(None)
+
+
+@pytest.mark.parametrize("case", ["no_diag_first", "descending", "col_range", "row_ptr_end", "nan"])
+def test_create_rcs_rejects_malformed_input_without_gpu(B, case):
+    row_ptr = np.array([0, 2, 3], np.int32)
+    col = np.array([0, 1, 1], np.int32)
+    val = np.tile(np.eye(6).reshape(1, 36), (3, 1))
+    b = np.ones((2, 6))
+    want = B.BA_ERR_INVALID_ARG
+    if case == "no_diag_first":
+        col = np.array([1, 0, 1], np.int32)
+    elif case == "descending":
+        row_ptr = np.array([0, 3, 4], np.int32)
+        col = np.array([0, 1, 1, 1], np.int32)
+        val = np.tile(np.eye(6).reshape(1, 36), (4, 1))
+    elif case == "col_range":
+        col = np.array([0, 5, 1], np.int32)
+    elif case == "row_ptr_end":
+        row_ptr = np.array([0, 2, 2], np.int32)
+    elif case == "nan":
+        val = val.copy()
+        val[1, 3] = np.nan
+        want = B.BA_ERR_NONFINITE
+    o = B.ba_options_default()
+    with pytest.raises(B.BAError) as ei:
+        B.ba_problem_create_rcs(o, row_ptr, col, val, b)
+    assert ei.value.status == want

@@ -1,5 +1,5 @@
 """GPU parity of the learned block-Jacobi correction against its FP64 oracle:
-forward outputs and M^-1, the probe loss and every gradient (BF16 weights and
+forward outputs and M^-1, the energy loss and every gradient (BF16 weights and
 activations on the tensor cores vs FP64 with BF16-rounded weights), the zero
 output layer (exactly block-Jacobi), and that training lowers the loss."""
 import numpy as np
@@ -76,7 +76,8 @@ def test_loss_and_gradients_match_oracle(env):
     probes = np.ascontiguousarray(np.transpose(Wp, (2, 0, 1)), dtype=np.float32)  # (kp, n, 6)
     loss, grads = net.train_step(g, kp=kp, probes=probes, lr=0.0, want_grads=True)
     Up = N.apply_S_blocks(row_ptr, col, val, Wp)
-    loss_ref, g_ref = N.loss_and_grad(Wt, diag, src, dst, w, Wp, Up)
+    Sap = lambda Z: N.apply_S_blocks(row_ptr, col, val, Z)
+    loss_ref, g_ref = N.loss_and_grad(Wt, diag, src, dst, w, Wp, Up, Sap)
     assert abs(loss - loss_ref) <= 2e-2 * loss_ref, (loss, loss_ref)
     gd = B.unpack_params(grads)
     for name in ("Wo", "bo", "W2", "b2", "W1", "b1"):
