@@ -256,6 +256,8 @@ def run_ours(args):
             "share_of_timed_kernels": round(tot / total_timed, 3) if total_timed else None}
     kernels = {nm: {"launches": v[0], "ms": round(v[1], 3)} for nm, v in ktimes.items() if v[0]}
     cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload, s.n_obs)
+    g.close()
+    solver = None if args.no_solver else solver_bench(B, torch)
     acc = sum(i["accepted"] for i in infos)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "LM iters/s", "n_gpus": world,
@@ -268,7 +270,7 @@ def run_ours(args):
         "lm": {"accepted": acc, "pcg_iters": [i["pcg_iters"] for i in infos],
                "cost": [infos[0]["cost_before"], infos[-1]["cost_after"]],
                "rcs_rel_resid_max": max(i["rcs_rel_resid"] for i in infos)},
-        "kernels_ms": kernels, "impl": "ours",
+        "kernels_ms": kernels, "solver": solver, "impl": "ours",
     }
     print(json.dumps(out))
     if dist:
@@ -276,6 +278,51 @@ def run_ours(args):
 
 
 KERNEL_VERSION = "form_rcs-v1"
+
+
+def solver_bench(B, torch, seed=200, repeats=5):
+    """PCG time to a true relative residual of 1e-8 on the RCS of a held-out
+    aerial-shaped scene (LM iterations 0 and 1): FP64 block-Jacobi PCG against
+    FP32 PCG inside FP64 refinement, with block-Jacobi and with the packaged
+    learned correction.  Times are host wall-clock around synchronised calls
+    (the solve synchronises internally), median over repeats."""
+    from paper_2307_08383_gb300.precond_training import _instances_of_scene
+    _, insts = _instances_of_scene(seed)
+    net = B.PrecondNet.load()
+    arms = {"fp64_block_jacobi": (dict(precision=B.BA_FP64), False),
+            "fp32_block_jacobi": (dict(precision=B.BA_FP64, solve_precision=B.BA_FP32, inner_rel_tol=1e-4), False),
+            "fp32_learned": (dict(precision=B.BA_FP64, solve_precision=B.BA_FP32, inner_rel_tol=1e-4), True)}
+    res = {k: {"ms": [], "pcg_iters": [], "true_rel_resid": [], "used_fallback": []} for k in arms}
+    for row_ptr, col, val, b, lam in insts:
+        for name, (kw, use_net) in arms.items():
+            g = B.Problem.from_rcs(row_ptr, col, val, b, pcg_rel_tol=1e-8, pcg_max_iters=50000, **kw)
+            if use_net:
+                B.ba_set_precond_net(g, net)
+            g.solve_rcs()
+            ts = []
+            for _ in range(repeats):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info, conv = g.solve_rcs()
+                torch.cuda.synchronize()
+                ts.append((time.perf_counter() - t0) * 1e3)
+                if not conv:
+                    raise RuntimeError(f"{name} did not reach 1e-8")
+            ts.sort()
+            r = res[name]
+            r["ms"].append(round(ts[len(ts) // 2], 3))
+            r["pcg_iters"].append(info["pcg_iters"])
+            r["true_rel_resid"].append(info["rcs_rel_resid"])
+            r["used_fallback"].append(info["used_fallback"])
+            B.ba_set_precond_net(g, None)
+            g.close()
+    net.close()
+    t64 = sum(res["fp64_block_jacobi"]["ms"])
+    tl = sum(res["fp32_learned"]["ms"])
+    return {"metric": "PCG time to true rel. residual 1e-8", "unit": "ms", "scene_seed": seed,
+            "n_cams": len(insts[0][0]) - 1, "nnzb": int(len(insts[0][1])), "lambdas": [x[4] for x in insts],
+            "arms": res, "speedup_fp32_learned_vs_fp64": round(t64 / tl, 3),
+            "speedup_fp32_block_jacobi_vs_fp64": round(t64 / sum(res["fp32_block_jacobi"]["ms"]), 3)}
 
 
 def _oracle_steps(workload, n_steps, sample_cams):
@@ -347,16 +394,24 @@ def run_kernel_case(args):
     opts = workload_opts(args.workload, B)
     if args.pcg_tol:
         opts.update(pcg_rel_tol=args.pcg_tol, inner_rel_tol=args.pcg_tol, refine_max=1)
+    if args.pcg_variant:
+        opts["pcg_variant"] = {"standard": B.BA_PCG_STANDARD, "split": B.BA_PCG_SPLIT}[args.pcg_variant]
     g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, profile=2, **opts)
     g.linearize()
+    iters = []
     for _ in range(3):
         g.form_rcs(1e-6 if args.pcg_tol else 1e-4)
         if args.kernel_case == "pcg":
-            g.solve_rcs()
+            info, _ = g.solve_rcs()
+            iters.append(info["pcg_iters"])
     torch.cuda.synchronize()
     kt = {k: v for k, v in g.kernel_times().items() if v[0]}
-    print(json.dumps({"kernel_case": args.kernel_case, "workload": args.workload, "stats": g.stats(),
-                      "kernel_ms": kt}))
+    out = {"kernel_case": args.kernel_case, "workload": args.workload, "stats": g.stats(), "kernel_ms": kt}
+    if iters:
+        n_l, ms = kt["pcg_loop"]
+        out.update(pcg_iters=iters, pcg_variant=args.pcg_variant or "auto",
+                   us_per_iteration=round(1e3 * ms / max(sum(iters), 1), 2))
+    print(json.dumps(out))
     g.close()
 
 
@@ -375,8 +430,10 @@ def main():
     ap.add_argument("--kernel-case", default=None, choices=["form_rcs", "pcg"],
                     help="profiling driver: run one kernel family a few times on the workload and exit")
     ap.add_argument("--pcg-tol", type=float, default=None, help="kernel case: PCG relative tolerance")
+    ap.add_argument("--pcg-variant", default=None, choices=["standard", "split"], help="kernel case: PCG variant")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solver", action="store_true", help="skip the PCG time-to-1e-8 comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -47,6 +47,7 @@ typedef enum {
 enum { BA_FP64 = 0, BA_FP32 = 1 };            /* ba_options.precision */
 enum { BA_LOSS_PLAIN = 0, BA_LOSS_HUBER = 1 }; /* ba_options.robust */
 enum { BA_PC_BLOCK_JACOBI = 0, BA_PC_LEARNED = 1 };
+enum { BA_PCG_AUTO = 0, BA_PCG_STANDARD = 1, BA_PCG_SPLIT = 2 }; /* ba_options.pcg_variant */
 
 typedef struct {
     int32_t precision;       /* BA_FP64: everything in FP64.  BA_FP32: Jacobians,
@@ -59,7 +60,9 @@ typedef struct {
     double lambda0;          /* initial LM damping (1e-4) */
     double pcg_rel_tol;      /* stop when ||b - S x|| / ||b|| <= tol (1e-10) */
     int32_t pcg_max_iters;   /* 0: max(1000, 6n) */
-    double inner_rel_tol;    /* FP32 mode: tolerance of each inner FP32 PCG (1e-4) */
+    double inner_rel_tol;    /* FP32 mode: tolerance of each inner FP32 PCG (1e-4); a sweep that
+                                needs less (0.5 * pcg_rel_tol / current rel. residual,
+                                at most 0.5) asks for that instead */
     int32_t refine_max;      /* FP32 mode: outer refinement steps (20) */
     int32_t preconditioner;  /* BA_PC_BLOCK_JACOBI (only this value is accepted) */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream */
@@ -69,6 +72,11 @@ typedef struct {
     int32_t solve_precision; /* FP64 problems only: BA_FP32 solves S x = b with FP32 inner
                                 PCG on a demoted copy of S (demotion timed inside the
                                 solve) and FP64 refinement with the FP64 S; 0 = as precision */
+    int32_t pcg_variant;     /* FP32 solves: BA_PCG_AUTO (0) or BA_PCG_SPLIT run CG on the
+                                split system G^T S G (M^-1 = G G^T per camera; the same
+                                iterates as block-Jacobi PCG in exact arithmetic) with one
+                                grid-wide reduction per iteration; BA_PCG_STANDARD runs the
+                                Sec. 3.2 recurrence as written.  FP64 solves always run it. */
 } ba_options;
 
 typedef struct {

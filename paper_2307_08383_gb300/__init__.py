@@ -30,6 +30,7 @@ BA_ERR_STATE = 8
 BA_ERR_INTERNAL = 9
 BA_FP64 = 0
 BA_FP32 = 1
+BA_PCG_AUTO, BA_PCG_STANDARD, BA_PCG_SPLIT = 0, 1, 2
 BA_LOSS_PLAIN = 0
 BA_LOSS_HUBER = 1
 BA_PC_BLOCK_JACOBI = 0
@@ -53,7 +54,8 @@ class ba_options(ctypes.Structure):
                 ("refine_max", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("device_mem_cap", ctypes.c_size_t),
                 ("group_max_obs", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("solve_precision", ctypes.c_int32)]
+                ("solve_precision", ctypes.c_int32),
+                ("pcg_variant", ctypes.c_int32)]
 
 
 class ba_step_info(ctypes.Structure):
@@ -461,6 +463,15 @@ class PrecondNet:
         h = _P()
         _check(lib().ba_precond_net_create(_fp(p), int(seed), stream, ctypes.byref(h)))
         self.h = h
+
+    @classmethod
+    def load(cls, path=None, stream="current"):
+        """A net with the weights stored by the training module (default: the
+        packaged weights trained on aerial-shaped systems)."""
+        path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                    "precond_net_aerial.npz")
+        with np.load(path, allow_pickle=False) as d:
+            return cls(params=d["params"], stream=stream)
 
     def close(self):
         if getattr(self, "h", None):

@@ -46,7 +46,7 @@ const char *kernel_name(int k) {
     static const char *names[K_COUNT] = {"prepare_state", "linearize", "cost",    "form_rcs",
                                          "rcs_reduce",    "rcs_diag",  "pcg_init", "pcg_loop",
                                          "resid64",       "back_substitute", "update", "eval",
-                                         "demote"};
+                                         "demote",        "split_prepare"};
     return (k >= 0 && k < K_COUNT) ? names[k] : nullptr;
 }
 
@@ -200,6 +200,7 @@ void ba_options_default(ba_options *o) {
     o->group_max_obs = 0;
     o->profile = 0;
     o->solve_precision = 0;
+    o->pcg_variant = BA_PCG_AUTO;
 }
 
 const char *ba_last_error(void) { return g_err.c_str(); }
@@ -229,7 +230,8 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     if (o.precision != BA_FP64 && o.precision != BA_FP32) return fail(BA_ERR_INVALID_ARG, "precision must be BA_FP64 or BA_FP32");
     if (o.robust != BA_LOSS_PLAIN && o.robust != BA_LOSS_HUBER) return fail(BA_ERR_INVALID_ARG, "robust must be BA_LOSS_PLAIN or BA_LOSS_HUBER");
     if (o.robust == BA_LOSS_HUBER && !(o.huber_delta > 0)) return fail(BA_ERR_INVALID_ARG, "huber_delta must be > 0");
-    if (!(o.lambda0 >= 0) || !(o.pcg_rel_tol > 0) || !(o.inner_rel_tol > 0) || o.pcg_max_iters < 0 || o.refine_max < 1)
+    if (!(o.lambda0 >= 0) || !(o.pcg_rel_tol > 0) || !(o.inner_rel_tol > 0) || o.pcg_max_iters < 0 || o.refine_max < 1 ||
+        o.pcg_variant < BA_PCG_AUTO || o.pcg_variant > BA_PCG_SPLIT)
         return fail(BA_ERR_INVALID_ARG, "bad solver option");
     if (!(o.fx > 0) || !(o.fy > 0) || !std::isfinite(o.cx) || !std::isfinite(o.cy))
         return fail(BA_ERR_INVALID_ARG, "bad intrinsics");
@@ -421,7 +423,8 @@ ba_status ba_problem_create_rcs(const ba_options *opt, int32_t n, int64_t nnzb, 
     if (n <= 0 || nnzb < n || nnzb >= (int64_t)INT32_MAX) return fail(BA_ERR_INVALID_ARG, "need 0 < n <= nnzb < 2^31");
     if (!row_ptr || !col || !val || !b) return fail(BA_ERR_INVALID_ARG, "null input array");
     if (o.precision != BA_FP64 && o.precision != BA_FP32) return fail(BA_ERR_INVALID_ARG, "bad precision");
-    if (!(o.pcg_rel_tol > 0) || !(o.inner_rel_tol > 0) || o.pcg_max_iters < 0 || o.refine_max < 1)
+    if (!(o.pcg_rel_tol > 0) || !(o.inner_rel_tol > 0) || o.pcg_max_iters < 0 || o.refine_max < 1 ||
+        o.pcg_variant < BA_PCG_AUTO || o.pcg_variant > BA_PCG_SPLIT)
         return fail(BA_ERR_INVALID_ARG, "bad solver option");
     if (row_ptr[0] != 0 || row_ptr[n] != nnzb) return fail(BA_ERR_INVALID_ARG, "row_ptr must run from 0 to nnzb");
     for (int32_t i = 0; i < n; ++i) {
@@ -559,6 +562,7 @@ ba_status ba_form_rcs(ba_problem *p, double lambda) {
     if (!p->linearized) return fail(BA_ERR_STATE, "ba_form_rcs needs ba_linearize first");
     if (!(lambda >= 0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and >= 0");
     CK(p, launch_form_rcs(p, lambda));
+    p->minv_learned = false;
     p->rcs_formed = true;
     p->rcs_lambda = lambda;
     p->solved = p->backsub = false;
@@ -579,26 +583,45 @@ static ba_status run_pcg(ba_problem *p, const void *rhs, double tol, int max_ite
 }
 
 // One solve with the current M^-1 (no learned-preconditioner logic).
-static ba_status ensure_shadows(ba_problem *p) {
-    if (p->S32) return BA_OK;
-    CK(p, dalloc_raw(p, &p->S32, (size_t)p->nnzb * BW * 4));
-    CK(p, dalloc_raw(p, &p->Minv32, (size_t)p->n * 36 * 4));
-    for (int k = 0; k < 8; ++k) CK(p, dalloc_raw(p, &p->pv32[k], (size_t)p->n * 6 * 4));
+static ba_status ensure_shadows(ba_problem *p, bool matrix) {
+    if (!p->pv32[0])
+        for (int k = 0; k < 8; ++k) CK(p, dalloc_raw(p, &p->pv32[k], (size_t)p->n * 6 * 4));
+    if (matrix && !p->S32) {
+        CK(p, dalloc_raw(p, &p->S32, (size_t)p->nnzb * BW * 4));
+        CK(p, dalloc_raw(p, &p->Minv32, (size_t)p->n * 36 * 4));
+    }
+    return BA_OK;
+}
+
+static bool split_cg(const ba_problem *p) { return p->sv.f32 && p->opt.pcg_variant != BA_PCG_STANDARD; }
+
+static ba_status run_pcg_split(ba_problem *p, const void *rhs, double tol, int max_iters, int *iters) {
+    CK(p, launch_split_init(p, (const float *)rhs, tol, max_iters));
+    CK(p, launch_pcg_split(p));
+    ba_status s = sync_scalars(p);
+    if (s) return s;
+    if (p->sc_host->err == BA_ERR_TIMEOUT) {
+        p->dead = true;
+        return fail(BA_ERR_TIMEOUT, "PCG grid all-reduce timed out");
+    }
+    *iters = p->sc_host->iters;
     return BA_OK;
 }
 
 static ba_status solve_once_view(ba_problem *p, ba_step_info *info);
 
 // One solve with the current M^-1 (no learned-preconditioner logic).  An FP64
-// problem with solve_precision = BA_FP32 demotes S and M^-1 to FP32 shadows
-// (timed as part of the solve), runs the inner PCG in FP32 and refines with
-// the FP64 residual b - S x of the FP64 system.
+// problem with solve_precision = BA_FP32 runs the inner PCG in FP32 - on the
+// split system G^T S G formed from the FP64 S, or (standard variant) on a
+// demoted copy of S and M^-1 - and refines with the FP64 residual b - S x of
+// the FP64 system; the FP32 copies are made inside the timed solve.
 static ba_status solve_once(ba_problem *p, ba_step_info *info) {
     const bool mixed = !p->fp32 && p->opt.solve_precision == BA_FP32;
     ba_status s;
     if (mixed) {
-        if ((s = ensure_shadows(p))) return s;
-        CK(p, launch_demote(p));
+        const bool standard = p->opt.pcg_variant == BA_PCG_STANDARD;
+        if ((s = ensure_shadows(p, standard))) return s;
+        if (standard) CK(p, launch_demote(p));
         p->sv.f32 = true;
         p->sv.S = p->S32;
         p->sv.Minv = p->Minv32;
@@ -626,8 +649,13 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
         CK(p, launch_accumulate_solution(p, true));
         CK(p, launch_resid64(p, true));
     } else {
-        // FP32 inner PCG + FP64 iterative refinement on r = b - S x
-        const double inner = std::max(p->opt.inner_rel_tol, 0.5 * tol);
+        const bool split = split_cg(p);
+        if (split) CK(p, launch_split_prepare(p, p->minv_learned));
+        // FP32 inner PCG + FP64 iterative refinement on r = b - S x.  Each
+        // sweep asks its inner solve for inner_rel_tol, or for just the
+        // reduction still missing (half of tol / rho, rho = |r|/|b| now) when
+        // that is looser, so a last sweep that needs a factor of a few takes
+        // a few iterations rather than a full inner solve.
         CK(p, launch_resid64(p, false));  // r64 = b, x64 implicit 0
         if ((s = sync_scalars(p))) return s;
         bool first = true;
@@ -635,12 +663,16 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
             if (p->sc_host->rr64 <= tol * tol * p->sc_host->bb64) { converged = true; break; }
             if (p->sc_host->bb64 == 0.0) { converged = true; break; }
             CK(p, launch_refine_rhs(p, p->sv.pv[1]));  // r buffer doubles as the rhs (copied by init)
+            const double rho = std::sqrt(p->sc_host->rr64 / p->sc_host->bb64);
+            const double inner = std::min(0.5, std::max(p->opt.inner_rel_tol, 0.5 * tol / rho));
             int it = 0;
-            if ((s = run_pcg(p, p->sv.pv[1], inner, max_iters, &it))) return s;
+            if ((s = split ? run_pcg_split(p, p->sv.pv[1], inner, max_iters, &it)
+                           : run_pcg(p, p->sv.pv[1], inner, max_iters, &it)))
+                return s;
             if ((s = check_err_flag(p))) return s;
             total += it;
             ++refine;
-            CK(p, launch_accumulate_solution(p, first));
+            CK(p, split ? launch_accumulate_split(p, first) : launch_accumulate_solution(p, first));
             first = false;
             CK(p, launch_resid64(p, true));
             if ((s = sync_scalars(p))) return s;
@@ -652,6 +684,8 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
     if ((s = sync_scalars(p))) return s;
     const double bb = p->sc_host->bb64;
     p->last_true_rel = bb > 0 ? std::sqrt(p->sc_host->rr64 / bb) : 0.0;
+    // a learned M^-1 is judged by the true residual, not PCG's recurrence
+    if (p->net && !p->sv.f32 && p->last_true_rel > 10.0 * tol) converged = false;
     p->last_pcg_iters = total;
     p->last_refine = refine;
     p->solved = true;
@@ -724,6 +758,7 @@ ba_status ba_lm_step(ba_problem *p, ba_step_info *info) {
     p->linearized = true;
     CK(p, cudaEventRecord(ev[1], p->st));
     CK(p, launch_form_rcs(p, p->lambda));
+    p->minv_learned = false;
     p->rcs_formed = true;
     p->rcs_lambda = p->lambda;
     CK(p, cudaEventRecord(ev[2], p->st));

@@ -56,7 +56,7 @@ constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
 
 enum KernelId {
     K_PREPARE = 0, K_LINEARIZE, K_COST, K_FORM_RCS, K_RCS_REDUCE, K_RCS_DIAG,
-    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_EVAL, K_DEMOTE, K_COUNT
+    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_EVAL, K_DEMOTE, K_SPLIT_PREP, K_COUNT
 };
 const char *kernel_name(int k);
 
@@ -178,6 +178,11 @@ struct ba_problem {
     ba::GnnWork *gw = nullptr;
     void *Minv_bj = nullptr;  // block-Jacobi copy kept for the fallback
     int last_used_fallback = 0;
+
+    // split-preconditioned FP32 CG: per-camera factors G, H = G^-T (n x 36)
+    // and S^ = G^T S G (nnzb x 36), allocated on the first such solve
+    float *Gs = nullptr, *Hs = nullptr, *Sh = nullptr;
+    bool minv_learned = false;  // Minv holds the learned M^-1 (else block-Jacobi)
 };
 
 namespace ba {
@@ -205,6 +210,13 @@ cudaError_t launch_apply_update(ba_problem *p);
 cudaError_t launch_eval(ba_problem *p);
 cudaError_t launch_block_jacobi(ba_problem *p);               // Minv from the diagonal blocks of S
 cudaError_t launch_demote(ba_problem *p);                     // S32, Minv32 from the FP64 S, Minv
+// split-preconditioned FP32 CG: G, H and S^ = G^T S G from the problem's S
+// (block-Jacobi) or its current M^-1 (from_minv); init, the persistent loop
+// and x64 (+)= G x^
+cudaError_t launch_split_prepare(ba_problem *p, bool from_minv);
+cudaError_t launch_split_init(ba_problem *p, const float *rhs, double tol, int max_iters);
+cudaError_t launch_pcg_split(ba_problem *p);
+cudaError_t launch_accumulate_split(ba_problem *p, bool first);
 // y = S x for one FP32 vector (learned-preconditioner probes)
 cudaError_t launch_spmv_f32(ba_problem *p, const float *x, float *y);
 // learned preconditioner: M^-1 of the last formed RCS from the attached net

@@ -301,4 +301,67 @@ __device__ __forceinline__ bool grid_allreduce(double (&v)[NV], double *part, do
     return ok;
 }
 
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Symmetric deterministic grid all-reduce for persistent cooperative kernels.
+// `bar` is an arrival counter that starts at 0 for the launch and only grows;
+// `gen` numbers this kernel's calls 0, 1, 2, ...  Each CTA stores its NV
+// partials (v, valid in warp 0 as block_sum leaves them) in half (gen & 1)
+// of `part` (2 * gridDim.x * AR_NV_MAX doubles), announces itself with a release
+// add, waits (bounded) until (gen + 1) * gridDim.x arrivals, and then adds
+// all partials itself in CTA order with a fixed lane order and shuffle tree,
+// so every CTA obtains the same bits without a broadcast round trip.  A half
+// is written again only two calls later, by a CTA that has passed call
+// gen + 1, which every CTA enters after reading the partials of call gen.
+// On return every thread holds the totals; false on timeout.
+constexpr int AR_NV_MAX = 4;
+template <int NV>
+__device__ __forceinline__ bool grid_allreduce_sym(double (&v)[NV], double *part, unsigned gen, unsigned *bar,
+                                                   int *err, long long limit_cycles) {
+    static_assert(NV <= AR_NV_MAX, "too many values");
+    __shared__ double s_tot[NV];
+    __shared__ int s_ok;
+    double *half = part + (size_t)(gen & 1u) * gridDim.x * AR_NV_MAX;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) __stcg(half + blockIdx.x * AR_NV_MAX + k, v[k]);
+        red_add_release(bar, 1u);
+        const unsigned target = (gen + 1u) * gridDim.x;
+        const long long t0 = clock64();
+        int ok = 1;
+        while (ld_acquire(bar) < target) {
+            if (clock64() - t0 > limit_cycles || *(volatile int *)err == (int)BA_ERR_TIMEOUT) {
+                atomicExch(err, (int)BA_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        s_ok = ok;
+    }
+    if (threadIdx.x < 32) {
+        __syncwarp();
+        const int lane = threadIdx.x;
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        if (s_ok)
+            for (unsigned b = lane; b < gridDim.x; b += 32)
+#pragma unroll
+                for (int k = 0; k < NV; ++k) acc[k] += __ldcg(half + b * AR_NV_MAX + k);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s_tot[k] = acc[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = s_tot[k];
+    const bool ok = s_ok != 0;
+    __syncthreads();
+    return ok;
+}
+
 }  // namespace ba

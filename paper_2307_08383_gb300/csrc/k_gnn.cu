@@ -648,7 +648,9 @@ ba_status gnn_apply(ba_problem *p) {
         e = cudaMalloc(&q, (size_t)p->n * 36 * p->esz);
         if (e == cudaSuccess) p->Minv_bj = q;
     }
-    if (e == cudaSuccess)
+    // keep the block-Jacobi M^-1 for the fallback (not a learned one left by
+    // an earlier solve of the same RCS)
+    if (e == cudaSuccess && !p->minv_learned)
         e = cudaMemcpyAsync(p->Minv_bj, p->Minv, (size_t)p->n * 36 * p->esz, cudaMemcpyDeviceToDevice, p->st);
     if (e == cudaSuccess) e = forward(p, net);
     if (e == cudaSuccess) {
@@ -666,10 +668,12 @@ ba_status gnn_apply(ba_problem *p) {
         p->dead = true;
         return set_error(BA_ERR_CUDA, cudaGetErrorString(e));
     }
+    p->minv_learned = true;
     return BA_OK;
 }
 
 ba_status gnn_restore_block_jacobi(ba_problem *p) {
+    p->minv_learned = false;
     if (!p->Minv_bj) return BA_OK;
     cudaError_t e = cudaMemcpyAsync(p->Minv, p->Minv_bj, (size_t)p->n * 36 * p->esz, cudaMemcpyDeviceToDevice, p->st);
     if (e != cudaSuccess) {

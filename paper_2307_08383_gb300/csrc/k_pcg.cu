@@ -13,6 +13,13 @@
 // sums the per-CTA partials in the same order, so all CTAs take the same
 // alpha, beta and stop decision without a third barrier.  Barrier waits are
 // bounded; a timeout sets an error flag and every CTA leaves.
+//
+// FP32 solves instead run CG on the split-preconditioned system
+// S^ = G^T S G (M^-1 = G G^T per camera, G from a Cholesky factor), which is
+// block-Jacobi PCG in other variables, in the Chronopoulos-Gear arrangement:
+// both dot products of an iteration come after its one SpMV, and the SpMV
+// forms each neighbour's new residual r_j - alpha (w_j + beta s_j) itself, so
+// an iteration is one phase and one grid all-reduce (see k_pcg_split).
 #include <algorithm>
 
 #include "device_util.cuh"
@@ -95,6 +102,30 @@ __device__ __forceinline__ void block_apply(const TV (&Sv)[36], const TV (&x)[6]
 // any arithmetic, so one L2 round trip covers ~64 blocks of the row.
 // PCG variant: x_j = z_j + beta d_old_j, the row owner stores d_new_i, and the
 // function returns this thread's share of d^T S d = sum_i d_i^T q_i.
+template <typename TS, typename TV, class GX>
+__device__ __forceinline__ void spmv_row(int i, int lane, const int *__restrict__ tw_ptr,
+                                         const int2 *__restrict__ tw_ent, const TS *__restrict__ S, GX gx,
+                                         TV (&acc)[6]) {
+    const int tb = __ldg(tw_ptr + i), te = __ldg(tw_ptr + i + 1);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] = TV(0);
+    for (int t0 = tb + lane; t0 < te; t0 += 64) {
+        const int t1 = t0 + 32;
+        const bool has1 = t1 < te;
+        const int2 ea = __ldg(tw_ent + t0);
+        const int2 eb = has1 ? __ldg(tw_ent + t1) : ea;
+        TV Sa[36], Sb[36], xa[6], xb[6];
+        load_block<TS, TV>(S + (int64_t)(ea.x & 0x7fffffff) * BW, Sa);
+        load_block<TS, TV>(S + (int64_t)(eb.x & 0x7fffffff) * BW, Sb);
+        gx(ea.y, xa);
+        gx(eb.y, xb);
+        block_apply<TV>(Sa, xa, ea.x < 0, acc);
+        if (has1) block_apply<TV>(Sb, xb, eb.x < 0, acc);
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) acc[r] = warp_sum(acc[r]);
+}
+
 template <typename TS, typename TV, bool PCG>
 __device__ __forceinline__ double spmv_rows(int n, const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
                                             const TS *__restrict__ S, const TV *__restrict__ xz,
@@ -105,7 +136,6 @@ __device__ __forceinline__ double spmv_rows(int n, const int *__restrict__ tw_pt
     const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
     TV pap = TV(0);
     for (int i = warp; i < n; i += nw) {
-        const int tb = __ldg(tw_ptr + i), te = __ldg(tw_ptr + i + 1);
         TV di[6];
         gather_x<TV, PCG>(xz, dold, beta, i, di);
         if (PCG) {
@@ -113,22 +143,9 @@ __device__ __forceinline__ double spmv_rows(int n, const int *__restrict__ tw_pt
             for (int c = 0; c < 6; ++c)
                 if (lane == c) dnew[6 * i + c] = di[c];
         }
-        TV acc[6] = {0, 0, 0, 0, 0, 0};
-        for (int t0 = tb + lane; t0 < te; t0 += 64) {
-            const int t1 = t0 + 32;
-            const bool has1 = t1 < te;
-            const int2 ea = __ldg(tw_ent + t0);
-            const int2 eb = has1 ? __ldg(tw_ent + t1) : ea;
-            TV Sa[36], Sb[36], xa[6], xb[6];
-            load_block<TS, TV>(S + (int64_t)(ea.x & 0x7fffffff) * BW, Sa);
-            load_block<TS, TV>(S + (int64_t)(eb.x & 0x7fffffff) * BW, Sb);
-            gather_x<TV, PCG>(xz, dold, beta, ea.y, xa);
-            gather_x<TV, PCG>(xz, dold, beta, eb.y, xb);
-            block_apply<TV>(Sa, xa, ea.x < 0, acc);
-            if (has1) block_apply<TV>(Sb, xb, eb.x < 0, acc);
-        }
-#pragma unroll
-        for (int r = 0; r < 6; ++r) acc[r] = warp_sum(acc[r]);
+        TV acc[6];
+        spmv_row<TS, TV>(i, lane, tw_ptr, tw_ent, S,
+                         [&](int j, TV(&x)[6]) { gather_x<TV, PCG>(xz, dold, beta, j, x); }, acc);
 #pragma unroll
         for (int c = 0; c < 6; ++c)
             if (lane == c) q[6 * i + c] = acc[c];
@@ -213,9 +230,9 @@ __global__ void __launch_bounds__(256) k_pcg_persist(int n, const int *__restric
     double rz = sc->rz;
     const double rr0 = sc->rr0, tol2 = sc->tol2;
     const int max_iters = sc->max_iters;
-    double *redA = red, *redB = red + gridDim.x, *bcast = red + 3 * gridDim.x;
     double beta = 0.0;
     int it = 0;
+    unsigned gen = 0;
     const int ne = 6 * n;
     for (;;) {
         const bool odd = it & 1;
@@ -224,7 +241,7 @@ __global__ void __launch_bounds__(256) k_pcg_persist(int n, const int *__restric
         // SpMV phase: d = z + beta d_old, q = S d, d^T S d
         double v1[1] = {spmv_rows<T, T, true>(n, tw_ptr, tw_ent, S, z, dold, dnew, q, (T)beta)};
         block_sum<1>(v1, sh);
-        if (!grid_allreduce<1>(v1, redA, bcast, bar, &sc->err, limit_cycles)) return;
+        if (!grid_allreduce_sym<1>(v1, red, gen++, bar, &sc->err, limit_cycles)) return;
         const double pAp = v1[0];
         if (!(pAp > 0.0)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -260,7 +277,7 @@ __global__ void __launch_bounds__(256) k_pcg_persist(int n, const int *__restric
         }
         double v2[2] = {(double)rz_p, (double)rr_p};
         block_sum<2>(v2, sh);
-        if (!grid_allreduce<2>(v2, redB, bcast, bar, &sc->err, limit_cycles)) return;
+        if (!grid_allreduce_sym<2>(v2, red, gen++, bar, &sc->err, limit_cycles)) return;
         const double rz_new = v2[0], rr = v2[1];
         ++it;
         if (rr <= tol2 * rr0 || it >= max_iters) {
@@ -331,6 +348,315 @@ __global__ void __launch_bounds__(256) k_back_sub(int64_t P, const int *__restri
         dxp[3 * k + 1] = m[2] * u1 + m[4] * u2;
         dxp[3 * k + 2] = m[5] * u2;
     }
+}
+
+// --------------------------------------------------------------------------
+// Split-preconditioned CG for FP32 solves
+// --------------------------------------------------------------------------
+
+// Cholesky A = L L^T of a symmetric 6x6 (row-major, lower triangle read) and
+// L^-1, both packed lower (index k(k+1)/2 + l).  False if A is not SPD.
+__device__ bool chol6_with_inverse(const double *A, double *L, double *Li) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * 6 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i * (i + 1) / 2 + k] * L[j * (j + 1) / 2 + k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i * (i + 1) / 2 + i] = sqrt(s);
+            } else {
+                L[i * (i + 1) / 2 + j] = s / L[j * (j + 1) / 2 + j];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        Li[i * (i + 1) / 2 + i] = 1.0 / L[i * (i + 1) / 2 + i];
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = j; k < i; ++k) s += L[i * (i + 1) / 2 + k] * Li[k * (k + 1) / 2 + j];
+            Li[i * (i + 1) / 2 + j] = -s * Li[i * (i + 1) / 2 + i];
+        }
+    }
+    return true;
+}
+
+// Per camera, in FP64, a factor G_i with M_i^-1 = G_i G_i^T and H_i = G_i^-T
+// (H r^ gives back the residual of the original system):
+//   block-Jacobi (from_minv = 0): S_ii = L L^T, G = L^-T, H = L;
+//   a given M^-1 (from_minv = 1):  M^-1 = C C^T, G = C,   H = C^-T.
+// Stored row-major FP32, n x 36 each.
+template <typename T>
+__global__ void __launch_bounds__(128) k_split_factor(int n, const int *__restrict__ row_ptr, const T *__restrict__ S,
+                                                      const T *__restrict__ Minv, int from_minv, float *__restrict__ G,
+                                                      float *__restrict__ H, DevScalars *sc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T *src = from_minv ? Minv + 36 * (int64_t)i : S + (int64_t)__ldg(row_ptr + i) * BW;
+    double A[36], L[21], Li[21];
+#pragma unroll
+    for (int k = 0; k < 36; ++k) A[k] = (double)src[k];
+    float *g = G + 36 * (int64_t)i, *h = H + 36 * (int64_t)i;
+    if (!chol6_with_inverse(A, L, Li)) {
+        atomicExch(&sc->err, (int)BA_ERR_NOT_SPD);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) g[k] = h[k] = (k % 7 == 0) ? 1.f : 0.f;
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const double low = a >= c ? L[a * (a + 1) / 2 + c] : 0.0;    // L[a][c]
+            const double lit = c >= a ? Li[c * (c + 1) / 2 + a] : 0.0;   // (L^-1)^T[a][c]
+            g[6 * a + c] = (float)(from_minv ? low : lit);
+            h[6 * a + c] = (float)(from_minv ? lit : low);
+        }
+}
+
+// S^_ij = G_i^T S_ij G_j for every stored block (FP32 out); a warp per block
+// row, a lane per block.
+template <typename TS>
+__global__ void __launch_bounds__(128) k_split_scale(int n, const int *__restrict__ row_ptr,
+                                                     const int *__restrict__ col, const TS *__restrict__ S,
+                                                     const float *__restrict__ G, float *__restrict__ Sh) {
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const float *gi = G + 36 * (int64_t)i;
+    for (int b = __ldg(row_ptr + i) + lane; b < __ldg(row_ptr + i + 1); b += 32) {
+        const float *gj = G + 36 * (int64_t)__ldg(col + b);
+        const TS *sb = S + (int64_t)b * BW;
+        float T1[36];  // S_ij G_j
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            float srow[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) srow[k] = (float)sb[6 * a + k];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                float t = 0.f;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) t = __fmaf_rn(srow[k], __ldg(gj + 6 * k + c), t);
+                T1[6 * a + c] = t;
+            }
+        }
+        float4 *o4 = reinterpret_cast<float4 *>(Sh + (int64_t)b * BW);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            float o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int a = (4 * q + u) / 6, c = (4 * q + u) % 6;
+                float t = 0.f;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) t = __fmaf_rn(__ldg(gi + 6 * k + a), T1[6 * k + c], t);
+                o[u] = t;
+            }
+            o4[q] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
+// r^_0 = G^T rhs per camera (rhs may alias r0), x^ = p = s = 0, and the
+// scalars of the solve.
+template <typename TR>
+__global__ void __launch_bounds__(256) k_split_init(int n, const TR *rhs, const float *__restrict__ G, float *r0,
+                                                    float *x, float *p, float *s0, float *s1, DevScalars *sc,
+                                                    double tol2, int max_iters) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float b6[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) b6[c] = (float)rhs[6 * i + c];
+        const float *g = G + 36 * (int64_t)i;
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            float t = 0.f;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) t = __fmaf_rn(__ldg(g + 6 * c + a), b6[c], t);
+            r0[6 * i + a] = t;
+            x[6 * i + a] = 0.f;
+            p[6 * i + a] = 0.f;
+            s0[6 * i + a] = 0.f;
+            s1[6 * i + a] = 0.f;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->tol2 = tol2;
+        sc->max_iters = max_iters;
+        sc->iters = 0;
+        sc->alpha = 0.0;
+        sc->beta = 0.0;
+        sc->done = max_iters <= 0 ? 1 : 0;
+    }
+}
+
+// The new residual of a camera from the previous iteration's vectors: the row
+// owner and every row that gathers it evaluate exactly these two FMAs.
+__device__ __forceinline__ float next_r(float r, float w, float s, float a, float b) {
+    return __fmaf_rn(-a, __fmaf_rn(b, s, w), r);
+}
+
+__device__ __forceinline__ float sel6(const float (&v)[6], int c) {
+    float o = v[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k)
+        if (c == k) o = v[k];
+    return o;
+}
+
+// CG on S^ x^ = r^_0 (Chronopoulos-Gear), with per iteration k
+//   p = r + beta p,  s = w + beta s,  x^ += alpha p,  r -= alpha s,  w = S^ r,
+//   gamma = r.r, delta = w.r, beta' = gamma'/gamma,
+//   alpha' = gamma' / (delta' - beta' gamma' / alpha),
+// one phase per iteration: a warp per block row gathers r_j(new) for its
+// neighbours (next_r), forms w_i = sum S^_ij r_j, and lanes 0-5 update the
+// row's own p, s, x^, r, w.  r, w and s are double-buffered by parity.  The
+// stop test uses the original residual norm ||H r^|| (block-Jacobi: ||L r^||).
+// One grid all-reduce of (gamma, delta, ||H r||^2) ends each phase.
+__global__ void __launch_bounds__(256) k_pcg_split(int n, const int *__restrict__ tw_ptr,
+                                                   const int2 *__restrict__ tw_ent, const float *__restrict__ Sh,
+                                                   const float *__restrict__ H, float *x, float *r0, float *r1,
+                                                   float *w0, float *w1, float *s0, float *s1, float *p,
+                                                   DevScalars *sc, double *red, unsigned *bar, long long limit_cycles) {
+    __shared__ double sh[40];
+    if (sc->done) return;
+    const double tol2 = sc->tol2;
+    const int max_iters = sc->max_iters;
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    unsigned gen = 0;
+    double gamma, delta, rr;
+    {  // prologue: w_0 = S^ r_0 and the dot products of iteration 0
+        RunSum<float> gp, dp, rp;
+        for (int i = warp; i < n; i += nw) {
+            float acc[6];
+            spmv_row<float, float>(i, lane, tw_ptr, tw_ent, Sh, [&](int j, float(&v)[6]) { load6(r0 + 6 * j, v); },
+                                   acc);
+            float rv[6];
+            load6(r0 + 6 * i, rv);
+            if (lane < 6) {
+                const int c = lane;
+                const float wc = sel6(acc, c), rc = sel6(rv, c);
+                w0[6 * i + c] = wc;
+                const float *h = H + 36 * (int64_t)i + 6 * c;
+                float hr = 0.f;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) hr = __fmaf_rn(__ldg(h + k), rv[k], hr);
+                gp.add(rc * rc);
+                dp.add(wc * rc);
+                rp.add(hr * hr);
+            }
+        }
+        double v[3] = {gp.get(), dp.get(), rp.get()};
+        block_sum<3>(v, sh);
+        if (!grid_allreduce_sym<3>(v, red, gen++, bar, &sc->err, limit_cycles)) return;
+        gamma = v[0];
+        delta = v[1];
+        rr = v[2];
+    }
+    const double rr0 = rr;
+    double alpha_prev = 0.0, gamma_prev = 0.0;
+    int it = 0;
+    for (;;) {
+        if (rr <= tol2 * rr0 || it >= max_iters) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                sc->iters = it;
+                sc->rr = rr;
+                sc->rr0 = rr0;
+                sc->rz = gamma;
+                sc->done = 1;
+            }
+            return;
+        }
+        double alpha, beta;
+        if (it == 0) {
+            beta = 0.0;
+            alpha = gamma / delta;
+        } else {
+            beta = gamma / gamma_prev;
+            alpha = gamma / (delta - beta * gamma / alpha_prev);
+        }
+        if (!(alpha > 0.0) || !(alpha < 1e300)) {  // p^T S^ p <= 0 or not finite
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                sc->err = (int)BA_ERR_NOT_SPD;
+                sc->done = 1;
+                sc->iters = it;
+            }
+            return;
+        }
+        const bool odd = it & 1;
+        const float *rc = odd ? r1 : r0, *wc = odd ? w1 : w0, *scur = odd ? s1 : s0;
+        float *rn = odd ? r0 : r1, *wn = odd ? w0 : w1, *sn = odd ? s0 : s1;
+        const float a = (float)alpha, b = (float)beta;
+        RunSum<float> gp, dp, rp;
+        for (int i = warp; i < n; i += nw) {
+            float acc[6];
+            spmv_row<float, float>(i, lane, tw_ptr, tw_ent, Sh,
+                                   [&](int j, float(&v)[6]) {
+                                       float rj[6], wj[6], sj[6];
+                                       load6(rc + 6 * j, rj);
+                                       load6(wc + 6 * j, wj);
+                                       load6(scur + 6 * j, sj);
+#pragma unroll
+                                       for (int c = 0; c < 6; ++c) v[c] = next_r(rj[c], wj[c], sj[c], a, b);
+                                   },
+                                   acc);
+            if (lane < 6) {
+                const int c = lane, e = 6 * i + c;
+                float rv[6], wv[6], sv[6], rnew[6];
+                load6(rc + 6 * i, rv);
+                load6(wc + 6 * i, wv);
+                load6(scur + 6 * i, sv);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) rnew[k] = next_r(rv[k], wv[k], sv[k], a, b);
+                const float rold = sel6(rv, c), wold = sel6(wv, c), sold = sel6(sv, c);
+                const float pval = __fmaf_rn(b, __ldcg(p + e), rold);
+                const float sval = __fmaf_rn(b, sold, wold);
+                x[e] = __fmaf_rn(a, pval, __ldcg(x + e));
+                p[e] = pval;
+                sn[e] = sval;
+                const float r_e = sel6(rnew, c), w_e = sel6(acc, c);
+                rn[e] = r_e;
+                wn[e] = w_e;
+                const float *h = H + 36 * (int64_t)i + 6 * c;
+                float hr = 0.f;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) hr = __fmaf_rn(__ldg(h + k), rnew[k], hr);
+                gp.add(r_e * r_e);
+                dp.add(w_e * r_e);
+                rp.add(hr * hr);
+            }
+        }
+        double v[3] = {gp.get(), dp.get(), rp.get()};
+        block_sum<3>(v, sh);
+        if (!grid_allreduce_sym<3>(v, red, gen++, bar, &sc->err, limit_cycles)) return;
+        gamma_prev = gamma;
+        alpha_prev = alpha;
+        gamma = v[0];
+        delta = v[1];
+        rr = v[2];
+        ++it;
+    }
+}
+
+// x64 (+)= G x^ per camera (the solution of the original system)
+__global__ void k_acc64_split(int n, const float *__restrict__ G, const float *__restrict__ xh, double *x64,
+                              int first) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 6 * n) return;
+    const int i = e / 6, a = e - 6 * i;
+    const float *g = G + 36 * (int64_t)i + 6 * a;
+    float t = 0.f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t = __fmaf_rn(__ldg(g + c), __ldcg(xh + 6 * i + c), t);
+    x64[e] = (first ? 0.0 : x64[e]) + (double)t;
 }
 
 // --------------------------------------------------------------------------
@@ -492,6 +818,102 @@ cudaError_t launch_demote(ba_problem *p) {
     k_demote<<<grid_for(cm, 256, 152 * 4), 256, 0, p->st>>>(cm, (const double *)p->Minv, (float *)p->Minv32);
     ktimer_end(p, K_DEMOTE, ev);
     p->launches += 2;
+    return cudaGetLastError();
+}
+
+static cudaError_t split_alloc(ba_problem *p) {
+    cudaError_t e = cudaSuccess;
+    auto al = [&](float **q, size_t cnt) {
+        if (e == cudaSuccess && !*q) {
+            void *v = nullptr;
+            e = cudaMalloc(&v, cnt * sizeof(float));
+            if (e == cudaSuccess) {
+                *q = (float *)v;
+                p->allocs.push_back(v);
+                p->dev_bytes += cnt * sizeof(float);
+            }
+        }
+    };
+    al(&p->Gs, (size_t)p->n * 36);
+    al(&p->Hs, (size_t)p->n * 36);
+    al(&p->Sh, (size_t)p->nnzb * BW);
+    return e;
+}
+
+cudaError_t launch_split_prepare(ba_problem *p, bool from_minv) {
+    cudaError_t e = split_alloc(p);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t ev;
+    ktimer_begin(p, K_SPLIT_PREP, &ev);
+    const int nb = (p->n + 127) / 128, ns = (int)(((int64_t)p->n * 32 + 127) / 128);
+    if (p->fp32) {
+        k_split_factor<float><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const float *)p->S, (const float *)p->Minv,
+                                                     from_minv ? 1 : 0, p->Gs, p->Hs, p->sc);
+        k_split_scale<float><<<ns, 128, 0, p->st>>>(p->n, p->row_ptr, p->col, (const float *)p->S, p->Gs, p->Sh);
+    } else {
+        k_split_factor<double><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const double *)p->S,
+                                                      (const double *)p->Minv, from_minv ? 1 : 0, p->Gs, p->Hs, p->sc);
+        k_split_scale<double><<<ns, 128, 0, p->st>>>(p->n, p->row_ptr, p->col, (const double *)p->S, p->Gs, p->Sh);
+    }
+    ktimer_end(p, K_SPLIT_PREP, ev);
+    p->launches += 2;
+    return cudaGetLastError();
+}
+
+// vectors of the active FP32 view: 0 x^, 1 r, 6 r', 3 w, 4 w', 5 s, 7 s', 2 p
+cudaError_t launch_split_init(ba_problem *p, const float *rhs, double tol, int max_iters) {
+    cudaEvent_t ev;
+    ktimer_begin(p, K_PCG_INIT, &ev);
+    float **v = (float **)p->sv.pv;
+    k_split_init<float><<<grid_for(p->n, 256, VEC_CAP), 256, 0, p->st>>>(p->n, rhs, p->Gs, v[1], v[0], v[2], v[5],
+                                                                         v[7], p->sc, tol * tol, max_iters);
+    ktimer_end(p, K_PCG_INIT, ev);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_split(ba_problem *p) {
+    static int blocks_per_sm = -1, n_sm = 0;
+    cudaError_t e;
+    cudaEvent_t ev;
+    if (blocks_per_sm < 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pcg_split, 256, 0)) != cudaSuccess)
+            return e;
+        if (blocks_per_sm > 2) blocks_per_sm = 2;
+        if (blocks_per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    }
+    int64_t want = ((int64_t)p->n * 32 + 255) / 256;
+    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)blocks_per_sm * n_sm);
+    ktimer_begin(p, K_PCG_LOOP, &ev);
+    e = cudaMemsetAsync(p->counters + 14, 0, 2 * sizeof(unsigned), p->st);
+    if (e == cudaSuccess) {
+        int n = p->n;
+        const int *twp = p->tw_ptr;
+        const int2 *twe = p->tw_ent;
+        const float *Sh = p->Sh, *H = p->Hs;
+        float **v = (float **)p->sv.pv;
+        float *x = v[0], *r0 = v[1], *r1 = v[6], *w0 = v[3], *w1 = v[4], *s0 = v[5], *s1 = v[7], *pp = v[2];
+        DevScalars *sc = p->sc;
+        double *red = p->red;
+        unsigned *bar = p->counters + 14;
+        long long limit = 4000000000LL;  // ~2 s of SM clock per all-reduce wait
+        void *args[] = {&n, &twp, &twe, &Sh, &H, &x, &r0, &r1, &w0, &w1, &s0, &s1, &pp, &sc, &red, &bar, &limit};
+        e = cudaLaunchCooperativeKernel((const void *)k_pcg_split, dim3(grid), dim3(256), args, 0, p->st);
+    }
+    ktimer_end(p, K_PCG_LOOP, ev);
+    p->launches += 1;
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_split(ba_problem *p, bool first) {
+    const int cnt = p->n * 6;
+    k_acc64_split<<<(cnt + 255) / 256, 256, 0, p->st>>>(p->n, p->Gs, (const float *)p->sv.pv[0], p->x64,
+                                                        first ? 1 : 0);
+    p->launches += 1;
     return cudaGetLastError();
 }
 

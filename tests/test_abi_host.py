@@ -70,7 +70,7 @@ def _valid():
 
 
 @pytest.mark.parametrize("case", ["cam_range", "pt_range", "duplicate", "single_obs", "idle_camera", "nan_uv",
-                                  "inf_cam", "bad_precision", "bad_delta", "bad_tol"])
+                                  "inf_cam", "bad_precision", "bad_delta", "bad_tol", "bad_pcg_variant"])
 def test_create_rejects_bad_input_without_gpu(B, case):
     s = _valid()
     kw = {}
@@ -103,6 +103,8 @@ def test_create_rejects_bad_input_without_gpu(B, case):
         kw["huber_delta"] = -1.0
     elif case == "bad_tol":
         kw["pcg_rel_tol"] = 0.0
+    elif case == "bad_pcg_variant":
+        kw["pcg_variant"] = 3
     with pytest.raises(B.BAError) as ei:
         _create(B, s, **kw)
     assert ei.value.status == want

@@ -1,0 +1,106 @@
+"""The split-preconditioned CG of FP32 solves against the Sec. 3.2
+recurrence: CG on G^T S G with M^-1 = G G^T takes the iterates of
+block-Jacobi PCG in exact arithmetic, so its iteration counts match the FP64
+oracle's PCG on the same system, its solutions reach the same true residual,
+and FP64 solves (always the standard recurrence) ignore the option."""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.precond_net as N
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2307_08383_gb300.build import build
+    build()
+    import paper_2307_08383_gb300 as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def scene():
+    return scenes.aerial_small(n_along=12, n_across=6, pts_per_cam=150, seed=52)
+
+
+def _solve(B, s, lam, **kw):
+    g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, **kw)
+    g.linearize()
+    g.form_rcs(lam)
+    info, conv = g.solve_rcs()
+    dxc, _ = g.step()
+    rcs = g.rcs()
+    g.close()
+    return info, conv, dxc, rcs
+
+
+@pytest.mark.parametrize("tol", [1e-1, 1e-3])
+def test_split_iterations_follow_block_jacobi_pcg(B, scene, tol):
+    """One inner sweep (tol above inner_rel_tol): the sweep runs to
+    max(inner_rel_tol, tol / 2), and its iteration count equals the FP64
+    oracle's block-Jacobi PCG to that tolerance on the GPU's own FP32 system."""
+    info, conv, dxc, (row_ptr, col, val, b) = _solve(B, scene, 1e-4, precision=B.BA_FP32, pcg_rel_tol=tol,
+                                                     pcg_variant=B.BA_PCG_SPLIT)
+    assert conv and info["refine_steps"] == 1
+    A = O.BSMC(row_ptr, col, val)
+    ref = O.pcg(A, b.reshape(-1), O.block_jacobi(A), max(1e-4, 0.5 * tol))
+    assert abs(info["pcg_iters"] - ref.iters) <= 1, (info["pcg_iters"], ref.iters)
+    # same iterate up to FP32 rounding: compare with the oracle's y
+    assert np.linalg.norm(dxc.reshape(-1) - ref.y) <= 2e-3 * np.linalg.norm(ref.y)
+
+
+def test_split_and_standard_reach_the_same_tight_residual(B, scene):
+    out = {}
+    for name, v in (("standard", B.BA_PCG_STANDARD), ("split", B.BA_PCG_SPLIT)):
+        info, conv, dxc, (row_ptr, col, val, b) = _solve(B, scene, 1e-4, precision=B.BA_FP32, pcg_rel_tol=1e-8,
+                                                         pcg_variant=v)
+        A = O.BSMC(row_ptr, col, val)
+        r = b.reshape(-1) - O.bsmc_spmv(A, dxc.reshape(-1).astype(np.float64))
+        assert conv and info["rcs_rel_resid"] <= 1e-8
+        assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(b)
+        out[name] = (info, dxc)
+    # the unpreconditioned residual norm of CG is not monotone, so the loose
+    # last refinement sweep stops wherever it first dips below its target:
+    # totals of two roundings of the same method differ by a few tens
+    it_s, it_p = out["standard"][0]["pcg_iters"], out["split"][0]["pcg_iters"]
+    print({"standard": it_s, "split": it_p})
+    assert it_p <= 1.5 * it_s + 10 and it_s <= 1.5 * it_p + 10, (it_s, it_p)
+    # both solve the same system to 1e-8: they differ by up to kappa(S) * 1e-8
+    # relative, so compare them through S (FP32 storage of dx_c adds ~1e-7)
+    d_s, d_p = out["standard"][1].reshape(-1), out["split"][1].reshape(-1)
+    assert np.linalg.norm(O.bsmc_spmv(A, d_s - d_p)) <= 2e-6 * np.linalg.norm(b)
+
+
+def test_fp64_solves_ignore_the_variant(B, scene):
+    a = _solve(B, scene, 1e-4, precision=B.BA_FP64, pcg_rel_tol=1e-10, pcg_variant=B.BA_PCG_STANDARD)
+    b = _solve(B, scene, 1e-4, precision=B.BA_FP64, pcg_rel_tol=1e-10, pcg_variant=B.BA_PCG_SPLIT)
+    assert a[0]["pcg_iters"] == b[0]["pcg_iters"]
+    assert np.array_equal(a[2], b[2])
+
+
+def test_split_with_a_learned_preconditioner(B, scene):
+    """A learned (non block-Jacobi) M^-1 enters the split system through its
+    own Cholesky factor: iterations match the standard recurrence's."""
+    rng = np.random.default_rng(4)
+    Wt = N.init_weights(4)
+    Wt["Wo"] = N.bf16_round(rng.normal(0, 0.2, Wt["Wo"].shape))
+    Wt["bo"] = rng.normal(0, 0.2, Wt["bo"].shape)
+    net = B.PrecondNet(params=B.pack_params(Wt))
+    its = {}
+    for name, v in (("standard", B.BA_PCG_STANDARD), ("split", B.BA_PCG_SPLIT)):
+        s = scene
+        g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, precision=B.BA_FP32, pcg_rel_tol=1e-3,
+                      pcg_variant=v)
+        g.linearize()
+        g.form_rcs(1e-4)
+        B.ba_set_precond_net(g, net)
+        info, conv = g.solve_rcs()
+        B.ba_set_precond_net(g, None)
+        g.close()
+        assert conv and info["used_fallback"] == 0
+        its[name] = info["pcg_iters"]
+    assert abs(its["standard"] - its["split"]) <= 2, its
+    net.close()
