@@ -106,6 +106,9 @@ typedef struct {
     int64_t device_bytes;    /* device memory held by the problem */
     int64_t kernel_launches; /* kernels launched for this problem so far */
     int32_t precision;
+    double pcg_phase_us[3];  /* profile >= 2: split CG iteration phases, mean over CTAs and
+                                iterations of all solves so far, in us: SpMV passes (to the
+                                CTA barrier), row combine and update, grid all-reduce */
 } ba_stats;
 
 /* Fills *o with the defaults listed above. */

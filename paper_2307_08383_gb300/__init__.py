@@ -77,7 +77,7 @@ class ba_stats(ctypes.Structure):
     _fields_ = [("n_cams", ctypes.c_int32), ("n_pts", ctypes.c_int64), ("n_obs", ctypes.c_int64),
                 ("nnzb", ctypes.c_int64), ("n_groups", ctypes.c_int64), ("n_partials", ctypes.c_int64),
                 ("n_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("pcg_phase_us", ctypes.c_double * 3)]
 
 
 _P = ctypes.c_void_p
@@ -232,7 +232,9 @@ def ba_lm_step(h) -> dict:
 def ba_get_stats(h) -> dict:
     s = ba_stats()
     _check(lib().ba_get_stats(h, ctypes.byref(s)))
-    return {f: getattr(s, f) for f, _ in s._fields_}
+    out = {f: getattr(s, f) for f, _ in s._fields_}
+    out["pcg_phase_us"] = list(out["pcg_phase_us"])
+    return out
 
 
 def ba_get_cameras(h, n, out=None):

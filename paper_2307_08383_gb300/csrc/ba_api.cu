@@ -593,13 +593,19 @@ static ba_status ensure_shadows(ba_problem *p, bool matrix) {
     return BA_OK;
 }
 
-static bool split_cg(const ba_problem *p) { return p->sv.f32 && p->opt.pcg_variant != BA_PCG_STANDARD; }
+// FP32 solves run the split CG unless the standard recurrence is asked for
+// or the problem is too large for the balanced SpMV's shared memory
+static bool split_cg(ba_problem *p) {
+    return p->sv.f32 && p->opt.pcg_variant != BA_PCG_STANDARD && split_available(p);
+}
 
 static ba_status run_pcg_split(ba_problem *p, const void *rhs, double tol, int max_iters, int *iters) {
     CK(p, launch_split_init(p, (const float *)rhs, tol, max_iters));
     CK(p, launch_pcg_split(p));
     ba_status s = sync_scalars(p);
     if (s) return s;
+    if (p->opt.profile >= 2)
+        for (int k = 0; k < 4; ++k) p->ph_sum[k] += p->sc_host->ph[k];
     if (p->sc_host->err == BA_ERR_TIMEOUT) {
         p->dead = true;
         return fail(BA_ERR_TIMEOUT, "PCG grid all-reduce timed out");
@@ -619,7 +625,7 @@ static ba_status solve_once(ba_problem *p, ba_step_info *info) {
     const bool mixed = !p->fp32 && p->opt.solve_precision == BA_FP32;
     ba_status s;
     if (mixed) {
-        const bool standard = p->opt.pcg_variant == BA_PCG_STANDARD;
+        const bool standard = p->opt.pcg_variant == BA_PCG_STANDARD || !split_available(p);
         if ((s = ensure_shadows(p, standard))) return s;
         if (standard) CK(p, launch_demote(p));
         p->sv.f32 = true;
@@ -933,6 +939,7 @@ ba_status ba_get_stats(const ba_problem *p, ba_stats *o) {
     o->device_bytes = (int64_t)p->dev_bytes;
     o->kernel_launches = p->launches;
     o->precision = p->opt.precision;
+    for (int k = 0; k < 3; ++k) o->pcg_phase_us[k] = p->ph_sum[3] > 0 ? p->ph_sum[k] / p->ph_sum[3] / 1e3 : 0.0;
     return BA_OK;
 }
 

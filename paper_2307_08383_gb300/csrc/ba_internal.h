@@ -50,6 +50,8 @@ struct DevScalars {
     double rr64, bb64;
     unsigned long long n_cheir, n_cheir_trial, n_v64;
     int iters, done, max_iters, err;
+    int prof_on;   // split CG: time its phases (profile >= 2)
+    double ph[4];  // split CG phase ns summed over CTAs and iterations; ph[3] = CTA iterations
 };
 constexpr int N_COUNTERS = 16;
 constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
@@ -179,9 +181,16 @@ struct ba_problem {
     void *Minv_bj = nullptr;  // block-Jacobi copy kept for the fallback
     int last_used_fallback = 0;
 
-    // split-preconditioned FP32 CG: per-camera factors G, H = G^-T (n x 36)
-    // and S^ = G^T S G (nnzb x 36), allocated on the first such solve
-    float *Gs = nullptr, *Hs = nullptr, *Sh = nullptr;
+    // split-preconditioned FP32 CG: per-camera factors G, H = G^-T (n x 36),
+    // S^ = G^T S G in two-sided entry order (one block per entry), the vector
+    // records; allocated on the first such solve
+    float *Gs = nullptr, *Hs = nullptr, *Sh = nullptr, *srec = nullptr;
+    int32_t *cta_rows = nullptr;   // row range of each CTA of the balanced SpMV
+    uint16_t *tw_lrow = nullptr;   // local row of each two-sided entry
+    int *tw_col = nullptr;         // column of each two-sided entry
+    int split_grid = 0;            // 0: not partitioned yet, < 0: unavailable
+    size_t split_smem = 0;
+    double ph_sum[4] = {};  // split CG phase totals over solves (profile >= 2)
     bool minv_learned = false;  // Minv holds the learned M^-1 (else block-Jacobi)
 };
 
@@ -214,6 +223,7 @@ cudaError_t launch_demote(ba_problem *p);                     // S32, Minv32 fro
 // (block-Jacobi) or its current M^-1 (from_minv); init, the persistent loop
 // and x64 (+)= G x^
 cudaError_t launch_split_prepare(ba_problem *p, bool from_minv);
+bool split_available(ba_problem *p);  // partitions on first use
 cudaError_t launch_split_init(ba_problem *p, const float *rhs, double tol, int max_iters);
 cudaError_t launch_pcg_split(ba_problem *p);
 cudaError_t launch_accumulate_split(ba_problem *p, bool first);

@@ -21,8 +21,10 @@
 // forms each neighbour's new residual r_j - alpha (w_j + beta s_j) itself, so
 // an iteration is one phase and one grid all-reduce (see k_pcg_split).
 #include <algorithm>
+#include <vector>
 
 #include "device_util.cuh"
+#include "tma_util.cuh"
 
 namespace ba {
 
@@ -419,71 +421,94 @@ __global__ void __launch_bounds__(128) k_split_factor(int n, const int *__restri
         }
 }
 
-// S^_ij = G_i^T S_ij G_j for every stored block (FP32 out); a warp per block
-// row, a lane per block.
+// S^ in two-sided entry order: entry t of block row i (column j = the
+// entry's y) gets S^_ij = G_i^T S_ij G_j, with S_ij the stored block or, for
+// the entries of column i, the transpose of the stored block (j, i).  Every
+// off-diagonal block is thus held twice, already transposed where needed, so
+// the entries of consecutive rows are one contiguous, 16-byte aligned range
+// that a bulk copy moves.  Also writes the entry's column (tw_col).  A warp
+// per block row, a lane per entry.
 template <typename TS>
-__global__ void __launch_bounds__(128) k_split_scale(int n, const int *__restrict__ row_ptr,
-                                                     const int *__restrict__ col, const TS *__restrict__ S,
-                                                     const float *__restrict__ G, float *__restrict__ Sh) {
+__global__ void __launch_bounds__(128) k_split_scale(int n, const int *__restrict__ tw_ptr,
+                                                     const int2 *__restrict__ tw_ent, const TS *__restrict__ S,
+                                                     const float *__restrict__ G, float *__restrict__ Sh,
+                                                     int *__restrict__ tw_col) {
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
     const float *gi = G + 36 * (int64_t)i;
-    for (int b = __ldg(row_ptr + i) + lane; b < __ldg(row_ptr + i + 1); b += 32) {
-        const float *gj = G + 36 * (int64_t)__ldg(col + b);
-        const TS *sb = S + (int64_t)b * BW;
+    for (int t = __ldg(tw_ptr + i) + lane; t < __ldg(tw_ptr + i + 1); t += 32) {
+        const int2 e = __ldg(tw_ent + t);
+        const bool tr = e.x < 0;
+        const TS *sb = S + (int64_t)(e.x & 0x7fffffff) * BW;
+        const float *gj = G + 36 * (int64_t)e.y;
+        tw_col[t] = e.y;
         float T1[36];  // S_ij G_j
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
             float srow[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) srow[k] = (float)sb[6 * a + k];
+            for (int k = 0; k < 6; ++k) srow[k] = (float)(tr ? sb[6 * k + a] : sb[6 * a + k]);
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                float t = 0.f;
+                float v = 0.f;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) t = __fmaf_rn(srow[k], __ldg(gj + 6 * k + c), t);
-                T1[6 * a + c] = t;
+                for (int k = 0; k < 6; ++k) v = __fmaf_rn(srow[k], __ldg(gj + 6 * k + c), v);
+                T1[6 * a + c] = v;
             }
         }
-        float4 *o4 = reinterpret_cast<float4 *>(Sh + (int64_t)b * BW);
+        float4 *o4 = reinterpret_cast<float4 *>(Sh + (int64_t)t * BW);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             float o[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int a = (4 * q + u) / 6, c = (4 * q + u) % 6;
-                float t = 0.f;
+                float v = 0.f;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) t = __fmaf_rn(__ldg(gi + 6 * k + a), T1[6 * k + c], t);
-                o[u] = t;
+                for (int k = 0; k < 6; ++k) v = __fmaf_rn(__ldg(gi + 6 * k + a), T1[6 * k + c], v);
+                o[u] = v;
             }
             o4[q] = make_float4(o[0], o[1], o[2], o[3]);
         }
     }
 }
 
-// r^_0 = G^T rhs per camera (rhs may alias r0), x^ = p = s = 0, and the
-// scalars of the solve.
-template <typename TR>
-__global__ void __launch_bounds__(256) k_split_init(int n, const TR *rhs, const float *__restrict__ G, float *r0,
-                                                    float *x, float *p, float *s0, float *s1, DevScalars *sc,
-                                                    double tol2, int max_iters) {
+// Vector records of the split CG, double-buffered by iteration parity: per
+// camera 20 floats [r (6), w (6), s (6), pad (2)], 80 B and 16-byte aligned,
+// so a gather of a neighbour's three vectors is five float4 loads.
+constexpr int SREC = 20;
+
+__device__ __forceinline__ void load_rec(const float *rec, int j, float (&v)[20]) {
+    const float4 *q = reinterpret_cast<const float4 *>(rec + (int64_t)SREC * j);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float4 t = __ldcg(q + k);
+        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+    }
+}
+
+// r^_0 = G^T rhs per camera into record 0, s = 0 in both records, x^ = p = 0,
+// and the scalars of the solve.
+__global__ void __launch_bounds__(256) k_split_init(int n, const float *__restrict__ rhs, const float *__restrict__ G,
+                                                    float *rec0, float *rec1, float *x, float *p, DevScalars *sc,
+                                                    double tol2, int max_iters, int prof) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float b6[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) b6[c] = (float)rhs[6 * i + c];
+        for (int c = 0; c < 6; ++c) b6[c] = rhs[6 * i + c];
         const float *g = G + 36 * (int64_t)i;
+        float *q0 = rec0 + (int64_t)SREC * i, *q1 = rec1 + (int64_t)SREC * i;
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
             float t = 0.f;
 #pragma unroll
             for (int c = 0; c < 6; ++c) t = __fmaf_rn(__ldg(g + 6 * c + a), b6[c], t);
-            r0[6 * i + a] = t;
+            q0[a] = t;
+            q0[12 + a] = 0.f;
+            q1[12 + a] = 0.f;
             x[6 * i + a] = 0.f;
             p[6 * i + a] = 0.f;
-            s0[6 * i + a] = 0.f;
-            s1[6 * i + a] = 0.f;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -493,7 +518,15 @@ __global__ void __launch_bounds__(256) k_split_init(int n, const TR *rhs, const 
         sc->alpha = 0.0;
         sc->beta = 0.0;
         sc->done = max_iters <= 0 ? 1 : 0;
+        sc->prof_on = prof;
+        for (int k = 0; k < 4; ++k) sc->ph[k] = 0.0;
     }
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // The new residual of a camera from the previous iteration's vectors: the row
@@ -502,61 +535,230 @@ __device__ __forceinline__ float next_r(float r, float w, float s, float a, floa
     return __fmaf_rn(-a, __fmaf_rn(b, s, w), r);
 }
 
-__device__ __forceinline__ float sel6(const float (&v)[6], int c) {
-    float o = v[0];
+// Balanced, bulk-copied SpMV of the split CG.  CTA c owns block rows
+// [rb, re) (chosen on the host for about equal work) and their entries
+// [eb, ee), cut into passes of 32 consecutive entries; warp w takes passes
+// w, w + 8, ...  The S^ blocks of a pass (4.6 KB, contiguous in entry order)
+// arrive in shared memory by a 1-D bulk copy into one of the warp's two
+// buffers; since S^ does not change during the solve, each refill fetches
+// the warp's pass two positions ahead, wrapping into the next iteration, so
+// the copies for an iteration are already in flight when it starts.  A lane
+// applies one entry to its gathered neighbour vector (a plain, L1-cached
+// load: records change only between grid all-reduces, whose acquire orders
+// them); a segmented shuffle scan over the pass (entries are sorted by row)
+// leaves each row segment's sum in its last lane, which stores it in shared
+// memory: slot (q, 0) if the segment opens pass q, slot (q, 1) if it closes
+// it, else the row's own slot (a row inside one pass).  The sums depend only
+// on the entry order: deterministic.
+constexpr int SPLIT_WARPS = 8;
+constexpr int PASS_BYTES = 32 * BW * 4;                           // 4608
+constexpr int SPLIT_STAGE_BYTES = SPLIT_WARPS * 2 * PASS_BYTES;   // 73728
+
+struct SplitPipe {
+    float *stage;    // [warp][2][32 * 36]
+    uint64_t *mbar;  // [warp][2]
+    const float *Sh;
+    int eb, ee, m;   // entry range; passes of this warp
+    uint32_t seq;    // passes this warp has consumed so far
+};
+
+// lane 0: refill buffer (s & 1) with the warp's pass number (s mod m)
+__device__ __forceinline__ void split_issue(const SplitPipe &pp, uint32_t s) {
+    const int wid = threadIdx.x >> 5;
+    const int q = wid + SPLIT_WARPS * (int)(s % (uint32_t)pp.m);
+    const int cnt = min(32, pp.ee - pp.eb - 32 * q);
+    const uint32_t bytes = (uint32_t)cnt * BW * 4;
+    uint64_t *bar = pp.mbar + 2 * wid + (s & 1);
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(pp.stage + (size_t)(2 * wid + (s & 1)) * 32 * BW, pp.Sh + (int64_t)(pp.eb + 32 * q) * BW, bytes, bar);
+}
+
+// lane 0: wait (bounded) for the copies still in flight before the CTA leaves
+__device__ __forceinline__ void split_drain(const SplitPipe &pp, long long limit) {
+    if ((threadIdx.x & 31) != 0 || pp.m == 0) return;
+    const int wid = threadIdx.x >> 5;
+    for (uint32_t s = pp.seq; s < pp.seq + 2; ++s) mbar_wait(pp.mbar + 2 * wid + (s & 1), (s >> 1) & 1u, limit);
+}
+
+__device__ __forceinline__ void load_rec_l1(const float *rec, int j, float (&v)[20]) {
+    const float4 *q = reinterpret_cast<const float4 *>(rec + (int64_t)SREC * j);
 #pragma unroll
-    for (int k = 1; k < 6; ++k)
-        if (c == k) o = v[k];
-    return o;
+    for (int k = 0; k < 5; ++k) {
+        const float4 t = q[k];
+        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+    }
+}
+
+// One sweep of the warp's passes.  xf(record, x) forms the vector the SpMV
+// applies from a neighbour's record.  False on an mbarrier timeout (then the
+// warp stops; callers agree CTA-wide with __syncthreads_and and leave).
+template <class XF>
+__device__ __forceinline__ bool split_passes(SplitPipe &pp, int rb, const int *__restrict__ tw_ptr,
+                                             const int *__restrict__ tw_col, const uint16_t *__restrict__ tw_lrow,
+                                             const float *rec, XF xf, float *slot, float *rowacc, int *err,
+                                             long long limit) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (pp.m == 0) return true;
+    const int eb = pp.eb, ee = pp.ee;
+    int t = eb + 32 * wid + lane;
+    bool valid = t < ee;
+    int lr = valid ? (int)__ldg(tw_lrow + t) : 0xFFFF;
+    float rv[20];
+    if (valid) load_rec_l1(rec, __ldg(tw_col + t), rv);
+    for (int k = 0; k < pp.m; ++k) {
+        const int q = wid + SPLIT_WARPS * k;
+        // the next pass's gather goes out before this pass is applied
+        const int tn = t + 32 * SPLIT_WARPS;
+        const bool vn = k + 1 < pp.m && tn < ee;
+        int lrn = 0xFFFF;
+        float rn[20];
+        if (vn) {
+            lrn = (int)__ldg(tw_lrow + tn);
+            load_rec_l1(rec, __ldg(tw_col + tn), rn);
+        }
+        const uint32_t b = pp.seq & 1;
+        // every lane observes the copy's completion; the verdict is warp-uniform
+        if (!__all_sync(0xffffffffu, mbar_wait(pp.mbar + 2 * wid + b, (pp.seq >> 1) & 1u, limit))) {
+            if (lane == 0) atomicExch(err, (int)BA_ERR_TIMEOUT);
+            return false;
+        }
+        float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid) {
+            float x[6];
+            xf(rv, x);
+            const float4 *s4 = reinterpret_cast<const float4 *>(pp.stage + (size_t)(2 * wid + b) * 32 * BW +
+                                                                lane * BW);
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {  // two block rows (12 floats) at a time
+                const float4 u0 = s4[3 * h], u1 = s4[3 * h + 1], u2 = s4[3 * h + 2];
+                const float ra[6] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y};
+                const float rb6[6] = {u1.z, u1.w, u2.x, u2.y, u2.z, u2.w};
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    y[2 * h] = __fmaf_rn(ra[c], x[c], y[2 * h]);
+                    y[2 * h + 1] = __fmaf_rn(rb6[c], x[c], y[2 * h + 1]);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) split_issue(pp, pp.seq + 2);  // this buffer is free again
+        ++pp.seq;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int lu = __shfl_up_sync(0xffffffffu, lr, d);
+            float yu[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) yu[c] = __shfl_up_sync(0xffffffffu, y[c], d);
+            if (lane >= d && lu == lr)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) y[c] += yu[c];
+        }
+        const int ld = __shfl_down_sync(0xffffffffu, lr, 1);
+        if (valid && (lane == 31 || ld != lr)) {
+            const int i = rb + lr;
+            const int rs = __ldg(tw_ptr + i), rend = __ldg(tw_ptr + i + 1);
+            const int ps = eb + 32 * q, pe = min(ps + 32, ee);
+            float *dst = rs <= ps ? slot + 12 * q : (rend >= pe ? slot + 12 * q + 6 : rowacc + 6 * lr);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) dst[c] = y[c];
+        }
+        t = tn;
+        valid = vn;
+        lr = lrn;
+#pragma unroll
+        for (int c = 0; c < 20; ++c) rv[c] = rn[c];
+    }
+    return true;
+}
+
+// Component c of (S^ x)_i for local row lr after split_passes and a
+// __syncthreads: the row's segment sums in pass order.
+__device__ __forceinline__ float split_combine(int lr, int c, int rb, int eb, int ee,
+                                               const int *__restrict__ tw_ptr, const float *slot,
+                                               const float *rowacc) {
+    const int i = rb + lr;
+    const int rs = __ldg(tw_ptr + i), rend = __ldg(tw_ptr + i + 1);
+    float w = 0.f;
+    for (int q = (rs - eb) >> 5; q <= (rend - 1 - eb) >> 5; ++q) {
+        const int ps = eb + 32 * q, pe = min(ps + 32, ee);
+        const float *src = rs <= ps ? slot + 12 * q : (rend >= pe ? slot + 12 * q + 6 : rowacc + 6 * lr);
+        w += src[c];
+    }
+    return w;
 }
 
 // CG on S^ x^ = r^_0 (Chronopoulos-Gear), with per iteration k
 //   p = r + beta p,  s = w + beta s,  x^ += alpha p,  r -= alpha s,  w = S^ r,
 //   gamma = r.r, delta = w.r, beta' = gamma'/gamma,
 //   alpha' = gamma' / (delta' - beta' gamma' / alpha),
-// one phase per iteration: a warp per block row gathers r_j(new) for its
-// neighbours (next_r), forms w_i = sum S^_ij r_j, and lanes 0-5 update the
-// row's own p, s, x^, r, w.  r, w and s are double-buffered by parity.  The
-// stop test uses the original residual norm ||H r^|| (block-Jacobi: ||L r^||).
-// One grid all-reduce of (gamma, delta, ||H r||^2) ends each phase.
-__global__ void __launch_bounds__(256) k_pcg_split(int n, const int *__restrict__ tw_ptr,
-                                                   const int2 *__restrict__ tw_ent, const float *__restrict__ Sh,
-                                                   const float *__restrict__ H, float *x, float *r0, float *r1,
-                                                   float *w0, float *w1, float *s0, float *s1, float *p,
-                                                   DevScalars *sc, double *red, unsigned *bar, long long limit_cycles) {
+// one phase per iteration: the SpMV gathers r_j(new) = next_r(...) from the
+// previous records, then a thread per (row, component) of the CTA's rows
+// combines w_i and updates the row's own p, s, x^, r, w.  The stop test uses
+// the original residual norm ||H r^|| (block-Jacobi: ||L r^||).  One grid
+// all-reduce of (gamma, delta, ||H r||^2) ends each phase.
+__global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ cta_rows, const int *__restrict__ tw_ptr,
+                                                      const int *__restrict__ tw_col,
+                                                      const uint16_t *__restrict__ tw_lrow,
+                                                      const float *__restrict__ Sh, const float *__restrict__ H,
+                                                      float *x, float *p, float *rec0, float *rec1, DevScalars *sc,
+                                                      double *red, unsigned *bar, long long limit_cycles) {
+    extern __shared__ __align__(16) float sdyn[];
+    __shared__ uint64_t mbar[2 * SPLIT_WARPS];
     __shared__ double sh[40];
     if (sc->done) return;
     const double tol2 = sc->tol2;
     const int max_iters = sc->max_iters;
-    const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int rb = __ldg(cta_rows + blockIdx.x), re = __ldg(cta_rows + blockIdx.x + 1);
+    const int eb = __ldg(tw_ptr + rb), ee = __ldg(tw_ptr + re);
+    const int R = re - rb, P = (ee - eb + 31) >> 5, wid = threadIdx.x >> 5;
+    float *slot = sdyn + SPLIT_STAGE_BYTES / 4, *rowacc = slot + 12 * P;
+    SplitPipe pp{sdyn, mbar, Sh, eb, ee, wid < P ? (P - 1 - wid) / SPLIT_WARPS + 1 : 0, 0u};
+    if (threadIdx.x < 2 * SPLIT_WARPS) mbar_init(&mbar[threadIdx.x], 1);
+    fence_proxy_async();
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0 && pp.m > 0) {
+        split_issue(pp, 0);
+        split_issue(pp, 1);
+    }
     unsigned gen = 0;
     double gamma, delta, rr;
     {  // prologue: w_0 = S^ r_0 and the dot products of iteration 0
-        RunSum<float> gp, dp, rp;
-        for (int i = warp; i < n; i += nw) {
-            float acc[6];
-            spmv_row<float, float>(i, lane, tw_ptr, tw_ent, Sh, [&](int j, float(&v)[6]) { load6(r0 + 6 * j, v); },
-                                   acc);
-            float rv[6];
-            load6(r0 + 6 * i, rv);
-            if (lane < 6) {
-                const int c = lane;
-                const float wc = sel6(acc, c), rc = sel6(rv, c);
-                w0[6 * i + c] = wc;
-                const float *h = H + 36 * (int64_t)i + 6 * c;
-                float hr = 0.f;
+        const bool ok = __syncthreads_and(split_passes(
+            pp, rb, tw_ptr, tw_col, tw_lrow, rec0,
+            [](const float(&v)[20], float(&xx)[6]) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) hr = __fmaf_rn(__ldg(h + k), rv[k], hr);
-                gp.add(rc * rc);
-                dp.add(wc * rc);
-                rp.add(hr * hr);
-            }
+                for (int k = 0; k < 6; ++k) xx[k] = v[k];
+            },
+            slot, rowacc, &sc->err, limit_cycles));
+        if (!ok) {
+            split_drain(pp, limit_cycles);
+            return;
+        }
+        RunSum<float> gp, dp, rp;
+        for (int u = threadIdx.x; u < 6 * R; u += blockDim.x) {
+            const int lr = u / 6, c = u - 6 * lr, i = rb + lr;
+            const float wc = split_combine(lr, c, rb, eb, ee, tw_ptr, slot, rowacc);
+            float v[20];
+            load_rec(rec0, i, v);
+            rec0[(int64_t)SREC * i + 6 + c] = wc;
+            const float *h = H + 36 * (int64_t)i + 6 * c;
+            float hr = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) hr = __fmaf_rn(__ldg(h + k), v[k], hr);
+            float rc = v[0];
+#pragma unroll
+            for (int k = 1; k < 6; ++k)
+                if (c == k) rc = v[k];
+            gp.add(rc * rc);
+            dp.add(wc * rc);
+            rp.add(hr * hr);
         }
         double v[3] = {gp.get(), dp.get(), rp.get()};
         block_sum<3>(v, sh);
-        if (!grid_allreduce_sym<3>(v, red, gen++, bar, &sc->err, limit_cycles)) return;
+        if (!grid_allreduce_sym<3>(v, red, gen++, bar, &sc->err, limit_cycles)) {
+            split_drain(pp, limit_cycles);
+            return;
+        }
         gamma = v[0];
         delta = v[1];
         rr = v[2];
@@ -564,6 +766,9 @@ __global__ void __launch_bounds__(256) k_pcg_split(int n, const int *__restrict_
     const double rr0 = rr;
     double alpha_prev = 0.0, gamma_prev = 0.0;
     int it = 0;
+    // phase timing (thread 0 of each CTA, profile >= 2): passes, combine, all-reduce
+    const bool prof = sc->prof_on != 0 && threadIdx.x == 0;
+    unsigned long long t_pass = 0, t_comb = 0, t_red = 0, t0 = 0, t1 = 0, t2 = 0;
     for (;;) {
         if (rr <= tol2 * rr0 || it >= max_iters) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -573,6 +778,13 @@ __global__ void __launch_bounds__(256) k_pcg_split(int n, const int *__restrict_
                 sc->rz = gamma;
                 sc->done = 1;
             }
+            if (prof) {
+                atomicAdd(&sc->ph[0], (double)t_pass);
+                atomicAdd(&sc->ph[1], (double)t_comb);
+                atomicAdd(&sc->ph[2], (double)t_red);
+                atomicAdd(&sc->ph[3], (double)it);
+            }
+            split_drain(pp, limit_cycles);
             return;
         }
         double alpha, beta;
@@ -589,54 +801,71 @@ __global__ void __launch_bounds__(256) k_pcg_split(int n, const int *__restrict_
                 sc->done = 1;
                 sc->iters = it;
             }
+            split_drain(pp, limit_cycles);
             return;
         }
-        const bool odd = it & 1;
-        const float *rc = odd ? r1 : r0, *wc = odd ? w1 : w0, *scur = odd ? s1 : s0;
-        float *rn = odd ? r0 : r1, *wn = odd ? w0 : w1, *sn = odd ? s0 : s1;
+        const float *rc = (it & 1) ? rec1 : rec0;
+        float *rn = (it & 1) ? rec0 : rec1;
         const float a = (float)alpha, b = (float)beta;
+        if (prof) t0 = global_ns();
+        const bool ok = __syncthreads_and(split_passes(
+            pp, rb, tw_ptr, tw_col, tw_lrow, rc,
+            [a, b](const float(&v)[20], float(&xx)[6]) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) xx[k] = next_r(v[k], v[6 + k], v[12 + k], a, b);
+            },
+            slot, rowacc, &sc->err, limit_cycles));
+        if (!ok) {
+            split_drain(pp, limit_cycles);
+            return;
+        }
+        if (prof) t1 = global_ns();
         RunSum<float> gp, dp, rp;
-        for (int i = warp; i < n; i += nw) {
-            float acc[6];
-            spmv_row<float, float>(i, lane, tw_ptr, tw_ent, Sh,
-                                   [&](int j, float(&v)[6]) {
-                                       float rj[6], wj[6], sj[6];
-                                       load6(rc + 6 * j, rj);
-                                       load6(wc + 6 * j, wj);
-                                       load6(scur + 6 * j, sj);
+        for (int u = threadIdx.x; u < 6 * R; u += blockDim.x) {
+            const int lr = u / 6, c = u - 6 * lr, i = rb + lr, e = 6 * i + c;
+            const float w_e = split_combine(lr, c, rb, eb, ee, tw_ptr, slot, rowacc);
+            float t[20], rnew[6];
+            load_rec(rc, i, t);
 #pragma unroll
-                                       for (int c = 0; c < 6; ++c) v[c] = next_r(rj[c], wj[c], sj[c], a, b);
-                                   },
-                                   acc);
-            if (lane < 6) {
-                const int c = lane, e = 6 * i + c;
-                float rv[6], wv[6], sv[6], rnew[6];
-                load6(rc + 6 * i, rv);
-                load6(wc + 6 * i, wv);
-                load6(scur + 6 * i, sv);
+            for (int k = 0; k < 6; ++k) rnew[k] = next_r(t[k], t[6 + k], t[12 + k], a, b);
+            float rold = t[0], wold = t[6], sold = t[12], r_e = rnew[0];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) rnew[k] = next_r(rv[k], wv[k], sv[k], a, b);
-                const float rold = sel6(rv, c), wold = sel6(wv, c), sold = sel6(sv, c);
-                const float pval = __fmaf_rn(b, __ldcg(p + e), rold);
-                const float sval = __fmaf_rn(b, sold, wold);
-                x[e] = __fmaf_rn(a, pval, __ldcg(x + e));
-                p[e] = pval;
-                sn[e] = sval;
-                const float r_e = sel6(rnew, c), w_e = sel6(acc, c);
-                rn[e] = r_e;
-                wn[e] = w_e;
-                const float *h = H + 36 * (int64_t)i + 6 * c;
-                float hr = 0.f;
+            for (int k = 1; k < 6; ++k)
+                if (c == k) {
+                    rold = t[k];
+                    wold = t[6 + k];
+                    sold = t[12 + k];
+                    r_e = rnew[k];
+                }
+            const float pval = __fmaf_rn(b, __ldcg(p + e), rold);
+            const float sval = __fmaf_rn(b, sold, wold);
+            x[e] = __fmaf_rn(a, pval, __ldcg(x + e));
+            p[e] = pval;
+            float *o = rn + (int64_t)SREC * i;
+            o[c] = r_e;
+            o[6 + c] = w_e;
+            o[12 + c] = sval;
+            const float *h = H + 36 * (int64_t)i + 6 * c;
+            float hr = 0.f;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) hr = __fmaf_rn(__ldg(h + k), rnew[k], hr);
-                gp.add(r_e * r_e);
-                dp.add(w_e * r_e);
-                rp.add(hr * hr);
-            }
+            for (int k = 0; k < 6; ++k) hr = __fmaf_rn(__ldg(h + k), rnew[k], hr);
+            gp.add(r_e * r_e);
+            dp.add(w_e * r_e);
+            rp.add(hr * hr);
         }
         double v[3] = {gp.get(), dp.get(), rp.get()};
         block_sum<3>(v, sh);
-        if (!grid_allreduce_sym<3>(v, red, gen++, bar, &sc->err, limit_cycles)) return;
+        if (prof) t2 = global_ns();
+        if (!grid_allreduce_sym<3>(v, red, gen++, bar, &sc->err, limit_cycles)) {
+            split_drain(pp, limit_cycles);
+            return;
+        }
+        if (prof) {
+            const unsigned long long t3 = global_ns();
+            t_pass += t1 - t0;
+            t_comb += t2 - t1;
+            t_red += t3 - t2;
+        }
         gamma_prev = gamma;
         alpha_prev = alpha;
         gamma = v[0];
@@ -836,7 +1065,18 @@ static cudaError_t split_alloc(ba_problem *p) {
     };
     al(&p->Gs, (size_t)p->n * 36);
     al(&p->Hs, (size_t)p->n * 36);
-    al(&p->Sh, (size_t)p->nnzb * BW);
+    const size_t E = (size_t)(2 * p->nnzb - p->n);
+    al(&p->Sh, E * BW);
+    al(&p->srec, (size_t)2 * SREC * p->n);
+    if (e == cudaSuccess && !p->tw_col) {
+        void *v = nullptr;
+        e = cudaMalloc(&v, E * sizeof(int));
+        if (e == cudaSuccess) {
+            p->tw_col = (int *)v;
+            p->allocs.push_back(v);
+            p->dev_bytes += E * sizeof(int);
+        }
+    }
     return e;
 }
 
@@ -849,59 +1089,140 @@ cudaError_t launch_split_prepare(ba_problem *p, bool from_minv) {
     if (p->fp32) {
         k_split_factor<float><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const float *)p->S, (const float *)p->Minv,
                                                      from_minv ? 1 : 0, p->Gs, p->Hs, p->sc);
-        k_split_scale<float><<<ns, 128, 0, p->st>>>(p->n, p->row_ptr, p->col, (const float *)p->S, p->Gs, p->Sh);
+        k_split_scale<float><<<ns, 128, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const float *)p->S, p->Gs, p->Sh,
+                                                    p->tw_col);
     } else {
         k_split_factor<double><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const double *)p->S,
                                                       (const double *)p->Minv, from_minv ? 1 : 0, p->Gs, p->Hs, p->sc);
-        k_split_scale<double><<<ns, 128, 0, p->st>>>(p->n, p->row_ptr, p->col, (const double *)p->S, p->Gs, p->Sh);
+        k_split_scale<double><<<ns, 128, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const double *)p->S, p->Gs, p->Sh,
+                                                     p->tw_col);
     }
     ktimer_end(p, K_SPLIT_PREP, ev);
     p->launches += 2;
     return cudaGetLastError();
 }
 
-// vectors of the active FP32 view: 0 x^, 1 r, 6 r', 3 w, 4 w', 5 s, 7 s', 2 p
+// Work partition of the balanced split SpMV, made once per problem: the grid
+// size, each CTA's row range (contiguous rows, about equal entries + a fixed
+// cost per row), the local row of every two-sided entry, and the dynamic
+// shared memory of the busiest CTA (the warps' copy buffers, two 6-float
+// slots per 32-entry pass, one per row).  Problems whose largest CTA would
+// need more than 200 KB keep the standard recurrence (split_grid < 0).
+static cudaError_t split_partition(ba_problem *p) {
+    if (p->split_grid != 0) return cudaSuccess;
+    cudaError_t e;
+    const int n = p->n;
+    std::vector<int32_t> twp(n + 1);
+    if ((e = cudaMemcpy(twp.data(), p->tw_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    const int64_t E = twp[n];
+    int dev = 0, n_sm = 0, bps = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    constexpr int SMEM_MAX = 200 * 1024, ROW_COST = 8;
+    if ((e = cudaFuncSetAttribute(k_pcg_split, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX)) != cudaSuccess)
+        return e;
+    std::vector<int32_t> rows;
+    size_t smem = SPLIT_STAGE_BYTES;
+    int G = 0;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pcg_split, 256, smem)) != cudaSuccess) return e;
+        bps = std::min(bps, 2);
+        if (bps < 1) break;
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * n_sm, (E + 255) / 256));
+        if (g == G) break;
+        G = g;
+        rows.assign(G + 1, n);
+        rows[0] = 0;
+        const double total = (double)E + (double)ROW_COST * n;
+        int c = 1;
+        double acc = 0.0;
+        for (int i = 0; i < n && c < G; ++i) {
+            acc += (double)(twp[i + 1] - twp[i]) + ROW_COST;
+            while (c < G && acc >= total * c / G) rows[c++] = i + 1;
+        }
+        smem = SPLIT_STAGE_BYTES;
+        for (int k = 0; k < G; ++k) {
+            const int64_t P = ((int64_t)twp[rows[k + 1]] - twp[rows[k]] + 31) / 32;
+            smem = std::max(smem, SPLIT_STAGE_BYTES + (size_t)(12 * P + 6 * (int64_t)(rows[k + 1] - rows[k])) * sizeof(float));
+        }
+        if (smem > (size_t)SMEM_MAX) break;
+    }
+    if (bps < 1 || smem > (size_t)SMEM_MAX || G < 1) {
+        p->split_grid = -1;
+        return cudaSuccess;
+    }
+    // the occupancy at the final shared-memory size must keep the grid resident
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pcg_split, 256, smem)) != cudaSuccess) return e;
+    if ((int64_t)bps * n_sm < G) {
+        p->split_grid = -1;
+        return cudaSuccess;
+    }
+    std::vector<uint16_t> lrow(E);
+    for (int k = 0; k < G; ++k)
+        for (int i = rows[k]; i < rows[k + 1]; ++i)
+            for (int t = twp[i]; t < twp[i + 1]; ++t) lrow[t] = (uint16_t)(i - rows[k]);
+    for (int k = 0; k < G; ++k)
+        if (rows[k + 1] - rows[k] > 0xFFFE) {  // local row ids are 16-bit
+            p->split_grid = -1;
+            return cudaSuccess;
+        }
+    void *d_rows = nullptr, *d_lrow = nullptr;
+    if ((e = cudaMalloc(&d_rows, (G + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+    p->allocs.push_back(d_rows);
+    if ((e = cudaMalloc(&d_lrow, std::max<int64_t>(E, 1) * sizeof(uint16_t))) != cudaSuccess) return e;
+    p->allocs.push_back(d_lrow);
+    p->dev_bytes += (G + 1) * sizeof(int32_t) + E * sizeof(uint16_t);
+    if ((e = cudaMemcpy(d_rows, rows.data(), (G + 1) * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if (E && (e = cudaMemcpy(d_lrow, lrow.data(), E * sizeof(uint16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    p->cta_rows = (int32_t *)d_rows;
+    p->tw_lrow = (uint16_t *)d_lrow;
+    p->split_smem = smem;
+    p->split_grid = G;
+    return cudaSuccess;
+}
+
+bool split_available(ba_problem *p) {
+    if (split_partition(p) != cudaSuccess) {
+        cudaGetLastError();
+        p->split_grid = -1;
+    }
+    return p->split_grid > 0;
+}
+
+// vectors: pv[0] x^, pv[2] p of the active FP32 view; records in p->srec
 cudaError_t launch_split_init(ba_problem *p, const float *rhs, double tol, int max_iters) {
     cudaEvent_t ev;
     ktimer_begin(p, K_PCG_INIT, &ev);
     float **v = (float **)p->sv.pv;
-    k_split_init<float><<<grid_for(p->n, 256, VEC_CAP), 256, 0, p->st>>>(p->n, rhs, p->Gs, v[1], v[0], v[2], v[5],
-                                                                         v[7], p->sc, tol * tol, max_iters);
+    float *rec0 = p->srec, *rec1 = p->srec + (size_t)SREC * p->n;
+    k_split_init<<<grid_for(p->n, 256, VEC_CAP), 256, 0, p->st>>>(p->n, rhs, p->Gs, rec0, rec1, v[0], v[2], p->sc,
+                                                                  tol * tol, max_iters, p->opt.profile >= 2);
     ktimer_end(p, K_PCG_INIT, ev);
     p->launches += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_split(ba_problem *p) {
-    static int blocks_per_sm = -1, n_sm = 0;
-    cudaError_t e;
     cudaEvent_t ev;
-    if (blocks_per_sm < 0) {
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pcg_split, 256, 0)) != cudaSuccess)
-            return e;
-        if (blocks_per_sm > 2) blocks_per_sm = 2;
-        if (blocks_per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    }
-    int64_t want = ((int64_t)p->n * 32 + 255) / 256;
-    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)blocks_per_sm * n_sm);
     ktimer_begin(p, K_PCG_LOOP, &ev);
-    e = cudaMemsetAsync(p->counters + 14, 0, 2 * sizeof(unsigned), p->st);
+    cudaError_t e = cudaMemsetAsync(p->counters + 14, 0, 2 * sizeof(unsigned), p->st);
     if (e == cudaSuccess) {
-        int n = p->n;
-        const int *twp = p->tw_ptr;
-        const int2 *twe = p->tw_ent;
+        const int *cr = p->cta_rows, *twp = p->tw_ptr, *twc = p->tw_col;
+        const uint16_t *lr = p->tw_lrow;
         const float *Sh = p->Sh, *H = p->Hs;
         float **v = (float **)p->sv.pv;
-        float *x = v[0], *r0 = v[1], *r1 = v[6], *w0 = v[3], *w1 = v[4], *s0 = v[5], *s1 = v[7], *pp = v[2];
+        float *x = v[0], *pp = v[2];
+        float *rec0 = p->srec, *rec1 = p->srec + (size_t)SREC * p->n;
         DevScalars *sc = p->sc;
         double *red = p->red;
         unsigned *bar = p->counters + 14;
         long long limit = 4000000000LL;  // ~2 s of SM clock per all-reduce wait
-        void *args[] = {&n, &twp, &twe, &Sh, &H, &x, &r0, &r1, &w0, &w1, &s0, &s1, &pp, &sc, &red, &bar, &limit};
-        e = cudaLaunchCooperativeKernel((const void *)k_pcg_split, dim3(grid), dim3(256), args, 0, p->st);
+        void *args[] = {&cr, &twp, &twc, &lr, &Sh, &H, &x, &pp, &rec0, &rec1, &sc, &red, &bar, &limit};
+        e = cudaLaunchCooperativeKernel((const void *)k_pcg_split, dim3(p->split_grid), dim3(256), args,
+                                        p->split_smem, p->st);
     }
     ktimer_end(p, K_PCG_LOOP, ev);
     p->launches += 1;
