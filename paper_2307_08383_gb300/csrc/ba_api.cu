@@ -823,16 +823,37 @@ ba_status ba_get_cameras(const ba_problem *p, double *out) {
     return BA_OK;
 }
 
+// Staging buffer and permutation for caller-order point I/O (first use).
+static ba_status ensure_point_io(ba_problem *p) {
+    if (p->stage_pts) return BA_OK;
+    std::vector<int32_t> perm(p->P);
+    for (int64_t k = 0; k < p->P; ++k) perm[k] = (int32_t)p->hs.pt_perm[k];
+    void *a = nullptr, *b = nullptr, *c = nullptr;
+    CK(p, dalloc_raw(p, &a, (size_t)p->P * sizeof(int32_t)));
+    CK(p, dalloc_raw(p, &b, (size_t)p->P * 3 * sizeof(double)));
+    CK(p, dalloc_raw(p, &c, 256));
+    CK(p, cudaMemcpyAsync(a, perm.data(), (size_t)p->P * sizeof(int32_t), cudaMemcpyHostToDevice, p->st));
+    CK(p, cudaStreamSynchronize(p->st));
+    p->d_perm = (int32_t *)a;
+    p->io_flag = (unsigned *)c;
+    p->stage_pts = (double *)b;
+    return BA_OK;
+}
+
+// P x 3 internal-order values (FP64 or FP32) to the caller's order in out
+static ba_status fetch_points(ba_problem *p, const void *internal, bool fp32, double *out) {
+    ba_status s;
+    if ((s = ensure_point_io(p))) return s;
+    CK(p, launch_scatter_pts(p, internal, fp32, p->stage_pts));
+    CK(p, cudaMemcpyAsync(out, p->stage_pts, p->P * 3 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CK(p, cudaStreamSynchronize(p->st));
+    return BA_OK;
+}
+
 ba_status ba_get_points(const ba_problem *p, double *out) {
     LIVE(p);
     if (!out) return fail(BA_ERR_INVALID_ARG, "null output");
-    ba_problem *q = const_cast<ba_problem *>(p);
-    std::vector<double> tmp(p->P * 3);
-    CK(q, cudaMemcpyAsync(tmp.data(), p->cur.pts, p->P * 3 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
-    CK(q, cudaStreamSynchronize(p->st));
-    for (int64_t k = 0; k < p->P; ++k)
-        for (int d = 0; d < 3; ++d) out[3 * p->hs.pt_perm[k] + d] = tmp[3 * k + d];
-    return BA_OK;
+    return fetch_points(const_cast<ba_problem *>(p), p->cur.pts, false, out);
 }
 
 ba_status ba_get_rcs(const ba_problem *p, int64_t *nnzb, int32_t *row_ptr, int32_t *col, double *val, double *b) {
@@ -864,11 +885,7 @@ ba_status ba_get_step(const ba_problem *p, double *dxc, double *dxp) {
         if ((s = fetch(q, p->dxc, p->n * 6, tmp))) return s;
         std::memcpy(dxc, tmp.data(), tmp.size() * 8);
     }
-    if (dxp) {
-        if ((s = fetch(q, p->dxp, p->P * 3, tmp))) return s;
-        for (int64_t k = 0; k < p->P; ++k)
-            for (int d = 0; d < 3; ++d) dxp[3 * p->hs.pt_perm[k] + d] = tmp[3 * k + d];
-    }
+    if (dxp && (s = fetch_points(q, p->dxp, p->fp32, dxp))) return s;
     return BA_OK;
 }
 
@@ -898,12 +915,18 @@ ba_status ba_set_state(ba_problem *p, const double *cams, const double *pts, dou
         CK(p, cudaMemcpyAsync(p->cur.cams, cams, p->n * 6 * 8, cudaMemcpyHostToDevice, p->st));
     }
     if (pts) {
-        if (!finite_all(pts, p->P * 3)) return fail(BA_ERR_NONFINITE, "non-finite point");
-        std::vector<double> tmp(p->P * 3);
-        for (int64_t k = 0; k < p->P; ++k)
-            for (int d = 0; d < 3; ++d) tmp[3 * k + d] = pts[3 * p->hs.pt_perm[k] + d];
-        CK(p, cudaMemcpyAsync(p->cur.pts, tmp.data(), p->P * 3 * 8, cudaMemcpyHostToDevice, p->st));
+        // caller's order to the staging buffer, checked there; the state
+        // changes only when every value is finite
+        ba_status s;
+        if ((s = ensure_point_io(p))) return s;
+        CK(p, cudaMemcpyAsync(p->stage_pts, pts, p->P * 3 * 8, cudaMemcpyHostToDevice, p->st));
+        CK(p, cudaMemsetAsync(p->io_flag, 0, sizeof(unsigned), p->st));
+        CK(p, launch_count_nonfinite(p, p->stage_pts, p->P * 3, p->io_flag));
+        unsigned bad = 0;
+        CK(p, cudaMemcpyAsync(&bad, p->io_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, p->st));
         CK(p, cudaStreamSynchronize(p->st));
+        if (bad) return fail(BA_ERR_NONFINITE, "non-finite point");
+        CK(p, launch_gather_pts(p, p->stage_pts, p->cur.pts));
     }
     CK(p, launch_prepare_state(p, p->cur));
     p->lambda = lambda;

@@ -192,6 +192,12 @@ struct ba_problem {
     size_t split_smem = 0;
     double ph_sum[4] = {};  // split CG phase totals over solves (profile >= 2)
     bool minv_learned = false;  // Minv holds the learned M^-1 (else block-Jacobi)
+
+    // caller-order point I/O on the device, allocated on first use: the
+    // internal -> caller permutation, a P x 3 staging buffer, a flag word
+    int32_t *d_perm = nullptr;
+    double *stage_pts = nullptr;
+    unsigned *io_flag = nullptr;
 };
 
 namespace ba {
@@ -206,6 +212,10 @@ ba_status ktimer_flush(ba_problem *p);
 
 // launchers (kernels in the .cu files); each returns cudaGetLastError()
 cudaError_t launch_prepare_state(ba_problem *p, StateBuf &s);
+// caller-order point I/O through a device staging buffer (d_perm, stage_pts)
+cudaError_t launch_count_nonfinite(ba_problem *p, const double *a, int64_t cnt, unsigned *bad);
+cudaError_t launch_gather_pts(ba_problem *p, const double *user, double *internal);
+cudaError_t launch_scatter_pts(ba_problem *p, const void *internal, bool internal_fp32, double *user);
 cudaError_t launch_linearize(ba_problem *p);
 cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial);
 cudaError_t launch_form_rcs(ba_problem *p, double lambda);

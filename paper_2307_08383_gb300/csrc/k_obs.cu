@@ -278,6 +278,53 @@ static constexpr int GRID_CAP = 152 * 8;  // 152 SMs x 8 resident 256-thread CTA
 
 static Intr intr_of(const ba_problem *p) { return Intr{p->opt.fx, p->opt.fy, p->opt.cx, p->opt.cy}; }
 
+// Points between the caller's order and the internal (Morton) one:
+// internal point k is the caller's point perm[k].
+__global__ void k_count_nonfinite(int64_t cnt, const double *__restrict__ a, unsigned *bad) {
+    unsigned local = 0;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < cnt; x += (int64_t)gridDim.x * blockDim.x)
+        local |= isfinite(a[x]) ? 0u : 1u;
+    if (__any_sync(0xffffffffu, local) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+__global__ void k_gather_pts(int64_t P, const int32_t *__restrict__ perm, const double *__restrict__ user,
+                             double *__restrict__ internal) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = __ldg(perm + k);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) internal[3 * k + d] = user[3 * u + d];
+    }
+}
+template <typename T>
+__global__ void k_scatter_pts(int64_t P, const int32_t *__restrict__ perm, const T *__restrict__ internal,
+                              double *__restrict__ user) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = __ldg(perm + k);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) user[3 * u + d] = (double)internal[3 * k + d];
+    }
+}
+
+cudaError_t launch_count_nonfinite(ba_problem *p, const double *a, int64_t cnt, unsigned *bad) {
+    k_count_nonfinite<<<grid_for(cnt, 256, GRID_CAP), 256, 0, p->st>>>(cnt, a, bad);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+cudaError_t launch_gather_pts(ba_problem *p, const double *user, double *internal) {
+    k_gather_pts<<<grid_for(p->P, 256, GRID_CAP), 256, 0, p->st>>>(p->P, p->d_perm, user, internal);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+cudaError_t launch_scatter_pts(ba_problem *p, const void *internal, bool internal_fp32, double *user) {
+    if (internal_fp32)
+        k_scatter_pts<float><<<grid_for(p->P, 256, GRID_CAP), 256, 0, p->st>>>(p->P, p->d_perm,
+                                                                              (const float *)internal, user);
+    else
+        k_scatter_pts<double><<<grid_for(p->P, 256, GRID_CAP), 256, 0, p->st>>>(p->P, p->d_perm,
+                                                                               (const double *)internal, user);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prepare_state(ba_problem *p, StateBuf &s) {
     cudaEvent_t ev;
     ktimer_begin(p, K_PREPARE, &ev);

@@ -282,6 +282,30 @@ def test_set_state_roundtrip(B):
     assert abs(F - O.cost(s.cams_gt, s.pts_gt, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics())) <= 1e-9 * F
 
 
+def test_set_state_rejects_non_finite_points_and_keeps_the_state(B):
+    """The point upload is checked on the device before the state changes;
+    the step (dx_p) comes back in the caller's point order."""
+    s = scenes.shuffled(scenes.ring_scene(n_cams=8, n_pts=120, seed=58), 5)
+    g = _gpu(B, s, precision=B.BA_FP64, pcg_rel_tol=1e-10)
+    bad = s.pts_gt.copy()
+    bad[17, 1] = np.nan
+    with pytest.raises(B.BAError) as ei:
+        g.set_state(s.cams_gt, bad, 1e-2, 4.0)
+    assert ei.value.status == B.BA_ERR_NONFINITE
+    assert np.array_equal(g.points(), s.pts0)
+    # dx_p in caller order: Eq. 5 from the oracle with the GPU's own dx_c
+    g.linearize()
+    g.form_rcs(1e-3)
+    g.solve_rcs()
+    g.back_substitute()
+    dxc, dxp = g.step()
+    pb = _oracle(s)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    blk, A, b = pb.rcs(e, Jc, Jp, 1e-3)
+    ref = O.back_substitute(blk, pb.obs_cam, pb.obs_pt, s.n_pts, dxc)
+    assert np.abs(dxp - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
 # ----------------------------------------------------------------------------- full size
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-4)])
