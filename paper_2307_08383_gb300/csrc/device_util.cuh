@@ -364,4 +364,95 @@ __device__ __forceinline__ bool grid_allreduce_sym(double (&v)[NV], double *part
     return ok;
 }
 
+// Double-float (hi + lo, both FP32) values for reductions on the FP32 pipe:
+// the sum of two is formed with an error-free TwoSum, so it is exact to about
+// 2^-44 relative and, TwoSum being symmetric, a xor-butterfly gives every lane
+// the same bits.
+struct df32 {
+    float hi, lo;
+};
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+    const float s = a.hi + b.hi, bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float hi = s + e;
+    return {hi, e - (hi - s)};
+}
+__device__ __forceinline__ df32 warp_sum_df(df32 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const df32 u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, u);
+    }
+    return v;
+}
+
+// Block sum of NV double-floats; the totals are valid in every lane of warp 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_df(df32 (&v)[NV], float2 *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum_df(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[w * NV + i] = make_float2(v[i].hi, v[i].lo);
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const float2 t = lane < nw ? sh[lane * NV + i] : make_float2(0.f, 0.f);
+            v[i] = warp_sum_df(df32{t.x, t.y});
+        }
+    }
+    __syncthreads();
+}
+
+// grid_allreduce_sym for double-floats (partials stored as float2 in the same
+// slots): every CTA adds all partials itself in CTA order.  On return the
+// totals are valid in thread 0 only (as doubles, hi + lo); false on timeout.
+template <int NV>
+__device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, unsigned gen, unsigned *bar,
+                                                  int *err, long long limit_cycles, double (&tot)[NV]) {
+    static_assert(NV <= AR_NV_MAX, "too many values");
+    __shared__ int s_ok;
+    float2 *half = reinterpret_cast<float2 *>(part + (size_t)(gen & 1u) * gridDim.x * AR_NV_MAX);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) __stcg(half + blockIdx.x * AR_NV_MAX + k, make_float2(v[k].hi, v[k].lo));
+        red_add_release(bar, 1u);
+        const unsigned target = (gen + 1u) * gridDim.x;
+        const long long t0 = clock64();
+        int ok = 1;
+        while (ld_acquire(bar) < target) {
+            if (clock64() - t0 > limit_cycles || *(volatile int *)err == (int)BA_ERR_TIMEOUT) {
+                atomicExch(err, (int)BA_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        s_ok = ok;
+    }
+    bool ok = true;
+    if (threadIdx.x < 32) {
+        __syncwarp();
+        ok = s_ok != 0;
+        df32 acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = df32{0.f, 0.f};
+        if (ok)
+            for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const float2 t = __ldcg(half + b * AR_NV_MAX + k);
+                    acc[k] = df_add(acc[k], df32{t.x, t.y});
+                }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            acc[k] = warp_sum_df(acc[k]);
+            tot[k] = (double)acc[k].hi + (double)acc[k].lo;
+        }
+    }
+    return ok;
+}
+
 }  // namespace ba

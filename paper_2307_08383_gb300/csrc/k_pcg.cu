@@ -560,7 +560,9 @@ struct SplitPipe {
     const float *Sh;
     int eb, ee, m;   // entry range; passes of this warp
     uint32_t seq;    // passes this warp has consumed so far
+    uint32_t iter;   // parity of the current iteration (which records are current)
 };
+__device__ __forceinline__ uint32_t it_parity(const SplitPipe &pp) { return pp.iter; }
 
 // lane 0: refill buffer (s & 1) with the warp's pass number (s mod m)
 __device__ __forceinline__ void split_issue(const SplitPipe &pp, uint32_t s) {
@@ -704,15 +706,12 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
                                                       double *red, unsigned *bar, long long limit_cycles) {
     extern __shared__ __align__(16) float sdyn[];
     __shared__ uint64_t mbar[2 * SPLIT_WARPS];
-    __shared__ double sh[40];
     if (sc->done) return;
-    const double tol2 = sc->tol2;
-    const int max_iters = sc->max_iters;
     const int rb = __ldg(cta_rows + blockIdx.x), re = __ldg(cta_rows + blockIdx.x + 1);
     const int eb = __ldg(tw_ptr + rb), ee = __ldg(tw_ptr + re);
     const int R = re - rb, P = (ee - eb + 31) >> 5, wid = threadIdx.x >> 5;
     float *slot = sdyn + SPLIT_STAGE_BYTES / 4, *rowacc = slot + 12 * P;
-    SplitPipe pp{sdyn, mbar, Sh, eb, ee, wid < P ? (P - 1 - wid) / SPLIT_WARPS + 1 : 0, 0u};
+    SplitPipe pp{sdyn, mbar, Sh, eb, ee, wid < P ? (P - 1 - wid) / SPLIT_WARPS + 1 : 0, 0u, 0u};
     if (threadIdx.x < 2 * SPLIT_WARPS) mbar_init(&mbar[threadIdx.x], 1);
     fence_proxy_async();
     __syncthreads();
@@ -721,7 +720,53 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
         split_issue(pp, 1);
     }
     unsigned gen = 0;
-    double gamma, delta, rr;
+    // The recurrence's FP64 scalars live in thread 0, which decides alpha,
+    // beta and the stop after each all-reduce and publishes them here (GB300's
+    // FP64 rate is far below FP32: no other thread does FP64 arithmetic).
+    __shared__ float2 sh_df[3 * SPLIT_WARPS];
+    __shared__ int s_ctl;        // 0 go on, 1 stop, 2 not SPD, 3 timeout
+    __shared__ float s_ab[2];
+    double gamma = 0.0, delta = 0.0, rr = 0.0, rr0 = 0.0, alpha_prev = 0.0, gamma_prev = 0.0;
+    int it = 0;
+    // thread 0, after an all-reduce with totals (gamma', delta', rr'): the next step
+    auto decide = [&](bool ok, const double (&t)[3], bool first) {
+        if (!ok) {
+            s_ctl = 3;
+            return;
+        }
+        if (first) {
+            rr0 = t[2];
+        } else {
+            gamma_prev = gamma;
+            ++it;
+        }
+        gamma = t[0];
+        delta = t[1];
+        rr = t[2];
+        if (rr <= sc->tol2 * rr0 || it >= sc->max_iters) {
+            s_ctl = 1;
+            return;
+        }
+        double alpha, beta;
+        if (it == 0) {
+            beta = 0.0;
+            alpha = gamma / delta;
+        } else {
+            beta = gamma / gamma_prev;
+            alpha = gamma / (delta - beta * gamma / alpha_prev);
+        }
+        alpha_prev = alpha;
+        if (!(alpha > 0.0) || !(alpha < 1e300)) {  // p^T S^ p <= 0 or not finite
+            s_ctl = 2;
+            return;
+        }
+        s_ctl = 0;
+        s_ab[0] = (float)alpha;
+        s_ab[1] = (float)beta;
+    };
+    // phase timing (thread 0 of each CTA, profile >= 2): passes, combine, all-reduce
+    const bool prof = sc->prof_on != 0 && threadIdx.x == 0;
+    unsigned long long t_pass = 0, t_comb = 0, t_red = 0, t0 = 0, t1 = 0, t2 = 0;
     {  // prologue: w_0 = S^ r_0 and the dot products of iteration 0
         const bool ok = __syncthreads_and(split_passes(
             pp, rb, tw_ptr, tw_col, tw_lrow, rec0,
@@ -753,60 +798,38 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
             dp.add(wc * rc);
             rp.add(hr * hr);
         }
-        double v[3] = {gp.get(), dp.get(), rp.get()};
-        block_sum<3>(v, sh);
-        if (!grid_allreduce_sym<3>(v, red, gen++, bar, &sc->err, limit_cycles)) {
-            split_drain(pp, limit_cycles);
-            return;
-        }
-        gamma = v[0];
-        delta = v[1];
-        rr = v[2];
+        df32 v[3] = {{gp.s, gp.c}, {dp.s, dp.c}, {rp.s, rp.c}};
+        block_sum_df<3>(v, sh_df);
+        double t[3];
+        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t);
+        if (threadIdx.x == 0) decide(ok2, t, true);
+        __syncthreads();
     }
-    const double rr0 = rr;
-    double alpha_prev = 0.0, gamma_prev = 0.0;
-    int it = 0;
-    // phase timing (thread 0 of each CTA, profile >= 2): passes, combine, all-reduce
-    const bool prof = sc->prof_on != 0 && threadIdx.x == 0;
-    unsigned long long t_pass = 0, t_comb = 0, t_red = 0, t0 = 0, t1 = 0, t2 = 0;
     for (;;) {
-        if (rr <= tol2 * rr0 || it >= max_iters) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                sc->iters = it;
-                sc->rr = rr;
-                sc->rr0 = rr0;
-                sc->rz = gamma;
-                sc->done = 1;
-            }
-            if (prof) {
-                atomicAdd(&sc->ph[0], (double)t_pass);
-                atomicAdd(&sc->ph[1], (double)t_comb);
-                atomicAdd(&sc->ph[2], (double)t_red);
-                atomicAdd(&sc->ph[3], (double)it);
-            }
-            split_drain(pp, limit_cycles);
-            return;
-        }
-        double alpha, beta;
-        if (it == 0) {
-            beta = 0.0;
-            alpha = gamma / delta;
-        } else {
-            beta = gamma / gamma_prev;
-            alpha = gamma / (delta - beta * gamma / alpha_prev);
-        }
-        if (!(alpha > 0.0) || !(alpha < 1e300)) {  // p^T S^ p <= 0 or not finite
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                sc->err = (int)BA_ERR_NOT_SPD;
-                sc->done = 1;
-                sc->iters = it;
+        const int ctl = s_ctl;
+        if (ctl != 0) {
+            if (threadIdx.x == 0) {
+                if (blockIdx.x == 0 && ctl != 3) {
+                    if (ctl == 2) sc->err = (int)BA_ERR_NOT_SPD;
+                    sc->iters = it;
+                    sc->rr = rr;
+                    sc->rr0 = rr0;
+                    sc->rz = gamma;
+                    sc->done = 1;
+                }
+                if (prof) {
+                    atomicAdd(&sc->ph[0], (double)t_pass);
+                    atomicAdd(&sc->ph[1], (double)t_comb);
+                    atomicAdd(&sc->ph[2], (double)t_red);
+                    atomicAdd(&sc->ph[3], (double)it);
+                }
             }
             split_drain(pp, limit_cycles);
             return;
         }
-        const float *rc = (it & 1) ? rec1 : rec0;
-        float *rn = (it & 1) ? rec0 : rec1;
-        const float a = (float)alpha, b = (float)beta;
+        const float a = s_ab[0], b = s_ab[1];
+        const float *rc = (it_parity(pp) & 1) ? rec1 : rec0;
+        float *rn = (it_parity(pp) & 1) ? rec0 : rec1;
         if (prof) t0 = global_ns();
         const bool ok = __syncthreads_and(split_passes(
             pp, rb, tw_ptr, tw_col, tw_lrow, rc,
@@ -853,25 +876,22 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
             dp.add(w_e * r_e);
             rp.add(hr * hr);
         }
-        double v[3] = {gp.get(), dp.get(), rp.get()};
-        block_sum<3>(v, sh);
+        df32 v[3] = {{gp.s, gp.c}, {dp.s, dp.c}, {rp.s, rp.c}};
+        block_sum_df<3>(v, sh_df);
         if (prof) t2 = global_ns();
-        if (!grid_allreduce_sym<3>(v, red, gen++, bar, &sc->err, limit_cycles)) {
-            split_drain(pp, limit_cycles);
-            return;
+        double t[3];
+        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t);
+        if (threadIdx.x == 0) {
+            if (prof) {
+                const unsigned long long t3 = global_ns();
+                t_pass += t1 - t0;
+                t_comb += t2 - t1;
+                t_red += t3 - t2;
+            }
+            decide(ok2, t, false);
         }
-        if (prof) {
-            const unsigned long long t3 = global_ns();
-            t_pass += t1 - t0;
-            t_comb += t2 - t1;
-            t_red += t3 - t2;
-        }
-        gamma_prev = gamma;
-        alpha_prev = alpha;
-        gamma = v[0];
-        delta = v[1];
-        rr = v[2];
-        ++it;
+        __syncthreads();
+        pp.iter ^= 1u;
     }
 }
 
