@@ -192,6 +192,7 @@ struct ba_problem {
     size_t split_smem = 0;
     double ph_sum[4] = {};  // split CG phase totals over solves (profile >= 2)
     bool minv_learned = false;  // Minv holds the learned M^-1 (else block-Jacobi)
+    float2 *xs = nullptr;  // x64 split in FP32 pairs (refinement residual of FP32 problems)
 
     // caller-order point I/O on the device, allocated on first use: the
     // internal -> caller permutation, a P x 3 staging buffer, a flag word

@@ -166,6 +166,61 @@ __global__ void __launch_bounds__(256) k_spmv64(int n, const int *__restrict__ t
     spmv_rows<TS, double, false>(n, tw_ptr, tw_ent, S, x, nullptr, nullptr, q, 0.0);
 }
 
+// q = S x to about 2^-44 relative on the FP32 pipe, for the refinement
+// residual of FP32 problems (FP64 arithmetic runs at a small fraction of the
+// FP32 rate on GB300).  x arrives split in FP32 pairs (xh + xl, k_split_x);
+// S is FP32.  Each product is the exact s xh (FMA TwoProd) plus s xl, added
+// with TwoSum (double-float).  A warp per block row over its two-sided
+// entries.
+__device__ __forceinline__ void split_f64(double v, float &h, float &l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+__global__ void k_split_x(int64_t cnt, const double *__restrict__ x, float2 *__restrict__ xs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        float h, l;
+        split_f64(x[i], h, l);
+        xs[i] = make_float2(h, l);
+    }
+}
+__global__ void __launch_bounds__(256) k_spmv_df(int n, const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
+                                                 const float *__restrict__ S, const float2 *__restrict__ xs, double *q) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    for (int i = warp; i < n; i += nw) {
+        df32 acc[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) acc[r] = df32{0.f, 0.f};
+        for (int t = __ldg(tw_ptr + i) + lane; t < __ldg(tw_ptr + i + 1); t += 32) {
+            const int2 e = __ldg(tw_ent + t);
+            const bool tr = e.x < 0;
+            const float *sb = S + (int64_t)(e.x & 0x7fffffff) * BW;
+            float xh[6], xl[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const float2 v = __ldcg(xs + 6 * (int64_t)e.y + c);
+                xh[c] = v.x;
+                xl[c] = v.y;
+            }
+#pragma unroll
+            for (int r = 0; r < 6; ++r)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const float sv = __ldg(sb + (tr ? 6 * c + r : 6 * r + c));
+                    const float ph = sv * xh[c];
+                    const float pl = __fmaf_rn(sv, xh[c], -ph) + sv * xl[c];
+                    acc[r] = df_add(acc[r], df32{ph, pl});
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r) acc[r] = warp_sum_df(acc[r]);
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+            if (lane == r) q[6 * (int64_t)i + r] = (double)acc[r].hi + (double)acc[r].lo;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void apply_minv(const T *__restrict__ Minv, int i, const T *r, T *z) {
     const T *M = Minv + 36 * (int64_t)i;
@@ -978,16 +1033,36 @@ cudaError_t launch_pcg_loop(ba_problem *p) {
     return cudaGetLastError();
 }
 
+static cudaError_t ensure_xs(ba_problem *p) {
+    if (p->xs) return cudaSuccess;
+    void *v = nullptr;
+    const size_t bytes = (size_t)p->n * 6 * sizeof(float2);
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) return e;
+    p->xs = (float2 *)v;
+    p->allocs.push_back(v);
+    p->dev_bytes += bytes;
+    return cudaSuccess;
+}
+
 // from_x64: r64 = b - S x64; else r64 = b (x64 = 0).
 cudaError_t launch_resid64(ba_problem *p, bool from_x64) {
     cudaEvent_t ev;
     ktimer_begin(p, K_RESID64, &ev);
     if (from_x64) {
         const int gs = grid_for((int64_t)p->n * 32, 256, 152 * 8);
-        if (p->fp32)
-            k_spmv64<float><<<gs, 256, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const float *)p->S, p->x64, p->q64);
-        else
+        // FP32 problems: double-float products on the FP32 pipe; FP64
+        // problems keep FP64 arithmetic (their S is FP64)
+        if (p->fp32) {
+            cudaError_t e = ensure_xs(p);
+            if (e != cudaSuccess) return e;
+            const int64_t cnt = (int64_t)p->n * 6;
+            k_split_x<<<grid_for(cnt, 256, VEC_CAP), 256, 0, p->st>>>(cnt, p->x64, p->xs);
+            k_spmv_df<<<gs, 256, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const float *)p->S, p->xs, p->q64);
+            p->launches += 1;
+        } else {
             k_spmv64<double><<<gs, 256, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const double *)p->S, p->x64, p->q64);
+        }
     }
     const int g = grid_for((int64_t)p->n * 6, 256, VEC_CAP);
     if (p->fp32)
