@@ -287,7 +287,7 @@ def run_ours(args):
 
 # Versions of the two kernels whose DRAM traffic was captured with ncu; the
 # captured bytes are reported only while the kernel is the one measured.
-PCG_KERNEL_VERSION = "pcg_split-bulk-v1"
+PCG_KERNEL_VERSION = "pcg_split-halo-v2"
 RCS_KERNEL_VERSION = "form_rcs-v3"
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum, profiles/pcg_split_aerial5k.md

@@ -186,9 +186,10 @@ struct ba_problem {
     // records; allocated on the first such solve
     float *Gs = nullptr, *Hs = nullptr, *Sh = nullptr, *srec = nullptr;
     int32_t *cta_rows = nullptr;   // row range of each CTA of the balanced SpMV
-    uint16_t *tw_lrow = nullptr;   // local row of each two-sided entry
-    int *tw_col = nullptr;         // column of each two-sided entry
+    uint32_t *tw_meta = nullptr;   // per entry: local row | halo index << 16 (per-CTA aligned)
+    int32_t *meta_off = nullptr, *halo_ptr = nullptr, *halo_col = nullptr, *own_base = nullptr;
     int split_grid = 0;            // 0: not partitioned yet, < 0: unavailable
+    int split_slot_floats = 0;
     size_t split_smem = 0;
     double ph_sum[4] = {};  // split CG phase totals over solves (profile >= 2)
     bool minv_learned = false;  // Minv holds the learned M^-1 (else block-Jacobi)

@@ -364,6 +364,25 @@ __device__ __forceinline__ bool grid_allreduce_sym(double (&v)[NV], double *part
     return ok;
 }
 
+// One stored linearization row (JW values, 16-byte aligned, read-only) into
+// registers with vector loads.
+__device__ __forceinline__ void load_jrow(const float *__restrict__ s, float (&v)[JW]) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(s);
+#pragma unroll
+    for (int q = 0; q < JW / 4; ++q) {
+        const float4 t = __ldg(s4 + q);
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_jrow(const double *__restrict__ s, double (&v)[JW]) {
+    const double2 *s2 = reinterpret_cast<const double2 *>(s);
+#pragma unroll
+    for (int q = 0; q < JW / 2; ++q) {
+        const double2 t = __ldg(s2 + q);
+        v[2 * q] = t.x; v[2 * q + 1] = t.y;
+    }
+}
+
 // Double-float (hi + lo, both FP32) values for reductions on the FP32 pipe:
 // the sum of two is formed with an error-free TwoSum, so it is exact to about
 // 2^-44 relative and, TwoSum being symmetric, a xor-butterfly gives every lane

@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(256) k_eval(int64_t m, const int *__restrict__
         const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
         f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
         ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
-        const T *j = J + a * JW;
+        T j[JW];
+        load_jrow(J + a * JW, j);
         T dc[6], dp[3];
 #pragma unroll
         for (int c = 0; c < 6; ++c) dc[c] = dxc[6 * i + c];

@@ -390,7 +390,8 @@ __global__ void __launch_bounds__(256) k_back_sub(int64_t P, const int *__restri
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
         T s0 = lp[3 * k], s1 = lp[3 * k + 1], s2 = lp[3 * k + 2];
         for (int a = trk_ptr[k]; a < trk_ptr[k + 1]; ++a) {
-            const T *j = J + (int64_t)a * JW;
+            T j[JW];
+            load_jrow(J + (int64_t)a * JW, j);
             const T *dc = dxc + 6 * obs_cam[a];
             T t0 = T(0), t1 = T(0);
 #pragma unroll
@@ -481,13 +482,11 @@ __global__ void __launch_bounds__(128) k_split_factor(int n, const int *__restri
 // the entries of column i, the transpose of the stored block (j, i).  Every
 // off-diagonal block is thus held twice, already transposed where needed, so
 // the entries of consecutive rows are one contiguous, 16-byte aligned range
-// that a bulk copy moves.  Also writes the entry's column (tw_col).  A warp
-// per block row, a lane per entry.
+// that a bulk copy moves.  A warp per block row, a lane per entry.
 template <typename TS>
 __global__ void __launch_bounds__(128) k_split_scale(int n, const int *__restrict__ tw_ptr,
                                                      const int2 *__restrict__ tw_ent, const TS *__restrict__ S,
-                                                     const float *__restrict__ G, float *__restrict__ Sh,
-                                                     int *__restrict__ tw_col) {
+                                                     const float *__restrict__ G, float *__restrict__ Sh) {
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -497,7 +496,6 @@ __global__ void __launch_bounds__(128) k_split_scale(int n, const int *__restric
         const bool tr = e.x < 0;
         const TS *sb = S + (int64_t)(e.x & 0x7fffffff) * BW;
         const float *gj = G + 36 * (int64_t)e.y;
-        tw_col[t] = e.y;
         float T1[36];  // S_ij G_j
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
@@ -584,50 +582,67 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// a / b (b > 0) in FP32 for any FP64 magnitudes: both are scaled by the same
+// power of two, taken from b's exponent, before the FP32 division.
+__device__ __forceinline__ float ratio32(double a, double b) {
+    int e = (int)((__double_as_longlong(b) >> 52) & 0x7FF) - 1023;
+    e = e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+    const double sc = __longlong_as_double((long long)(1023 - e) << 52);  // 2^-e
+    return (float)(a * sc) / (float)(b * sc);
+}
+
 // The new residual of a camera from the previous iteration's vectors: the row
 // owner and every row that gathers it evaluate exactly these two FMAs.
 __device__ __forceinline__ float next_r(float r, float w, float s, float a, float b) {
     return __fmaf_rn(-a, __fmaf_rn(b, s, w), r);
 }
 
-// Balanced, bulk-copied SpMV of the split CG.  CTA c owns block rows
-// [rb, re) (chosen on the host for about equal work) and their entries
-// [eb, ee), cut into passes of 32 consecutive entries; warp w takes passes
-// w, w + 8, ...  The S^ blocks of a pass (4.6 KB, contiguous in entry order)
-// arrive in shared memory by a 1-D bulk copy into one of the warp's two
-// buffers; since S^ does not change during the solve, each refill fetches
-// the warp's pass two positions ahead, wrapping into the next iteration, so
-// the copies for an iteration are already in flight when it starts.  A lane
-// applies one entry to its gathered neighbour vector (a plain, L1-cached
-// load: records change only between grid all-reduces, whose acquire orders
-// them); a segmented shuffle scan over the pass (entries are sorted by row)
-// leaves each row segment's sum in its last lane, which stores it in shared
-// memory: slot (q, 0) if the segment opens pass q, slot (q, 1) if it closes
-// it, else the row's own slot (a row inside one pass).  The sums depend only
-// on the entry order: deterministic.
-constexpr int SPLIT_WARPS = 8;
-constexpr int PASS_BYTES = 32 * BW * 4;                           // 4608
-constexpr int SPLIT_STAGE_BYTES = SPLIT_WARPS * 2 * PASS_BYTES;   // 73728
+// Balanced SpMV of the split CG with a shared-memory halo.  CTA c owns block
+// rows [rb, re) (chosen on the host for about equal work) and their entries
+// [eb, ee), cut into passes of 32 consecutive entries; warp w of the nine
+// takes passes w, w + 9, ...  The cameras the CTA's entries reference (its halo, about a
+// hundred at the benchmark size) are gathered once per iteration from the
+// previous iteration's records, each transformed once into the vector the
+// SpMV applies, x_j = r_j - alpha (w_j + beta s_j), and kept in shared
+// memory.  A pass's 32 S^ blocks (4.6 KB, contiguous in entry order) and the
+// entries' packed (local row, halo index) arrive by 1-D bulk copies into one
+// of the warp's two buffers; since S^ does not change during the solve, each
+// refill fetches the warp's pass two positions ahead, wrapping into the next
+// iteration.  The pass loop thus reads shared memory only.  A segmented
+// shuffle scan over the pass (entries are sorted by row) leaves each row
+// segment's sum in its last lane, which stores it in a slot: (q, 0) if the
+// segment opens pass q, (q, 1) if it closes it, else the row's own slot.  The
+// sums depend only on the entry order: deterministic.
+constexpr int SPLIT_WARPS = 9;
+constexpr int PASS_S_BYTES = 32 * BW * 4;                        // 4608
+constexpr int PASS_BYTES = PASS_S_BYTES + 32 * 4;                // + packed metadata
+constexpr int SPLIT_STAGE_BYTES = SPLIT_WARPS * 2 * PASS_BYTES;  // 75776
+constexpr int HX = 8;                                            // floats per halo vector
 
 struct SplitPipe {
-    float *stage;    // [warp][2][32 * 36]
+    float *stage;    // [warp][2][32 * 36 floats + 32 u32]
     uint64_t *mbar;  // [warp][2]
     const float *Sh;
+    const uint32_t *meta;  // this CTA's packed entry metadata (16-byte aligned base)
     int eb, ee, m;   // entry range; passes of this warp
     uint32_t seq;    // passes this warp has consumed so far
-    uint32_t iter;   // parity of the current iteration (which records are current)
 };
-__device__ __forceinline__ uint32_t it_parity(const SplitPipe &pp) { return pp.iter; }
+
+__device__ __forceinline__ float *pass_buf(const SplitPipe &pp, uint32_t s) {
+    return pp.stage + (size_t)(2 * (threadIdx.x >> 5) + (s & 1)) * (PASS_BYTES / 4);
+}
 
 // lane 0: refill buffer (s & 1) with the warp's pass number (s mod m)
 __device__ __forceinline__ void split_issue(const SplitPipe &pp, uint32_t s) {
     const int wid = threadIdx.x >> 5;
     const int q = wid + SPLIT_WARPS * (int)(s % (uint32_t)pp.m);
     const int cnt = min(32, pp.ee - pp.eb - 32 * q);
-    const uint32_t bytes = (uint32_t)cnt * BW * 4;
+    const uint32_t sbytes = (uint32_t)cnt * BW * 4, mbytes = (uint32_t)((cnt + 3) & ~3) * 4;
     uint64_t *bar = pp.mbar + 2 * wid + (s & 1);
-    mbar_expect_tx(bar, bytes);
-    bulk_g2s(pp.stage + (size_t)(2 * wid + (s & 1)) * 32 * BW, pp.Sh + (int64_t)(pp.eb + 32 * q) * BW, bytes, bar);
+    float *buf = pass_buf(pp, s);
+    mbar_expect_tx(bar, sbytes + mbytes);
+    bulk_g2s(buf, pp.Sh + (int64_t)(pp.eb + 32 * q) * BW, sbytes, bar);
+    bulk_g2s(buf + PASS_S_BYTES / 4, pp.meta + 32 * q, mbytes, bar);
 }
 
 // lane 0: wait (bounded) for the copies still in flight before the CTA leaves
@@ -637,54 +652,33 @@ __device__ __forceinline__ void split_drain(const SplitPipe &pp, long long limit
     for (uint32_t s = pp.seq; s < pp.seq + 2; ++s) mbar_wait(pp.mbar + 2 * wid + (s & 1), (s >> 1) & 1u, limit);
 }
 
-__device__ __forceinline__ void load_rec_l1(const float *rec, int j, float (&v)[20]) {
-    const float4 *q = reinterpret_cast<const float4 *>(rec + (int64_t)SREC * j);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const float4 t = q[k];
-        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
-    }
-}
-
-// One sweep of the warp's passes.  xf(record, x) forms the vector the SpMV
-// applies from a neighbour's record.  False on an mbarrier timeout (then the
-// warp stops; callers agree CTA-wide with __syncthreads_and and leave).
-template <class XF>
-__device__ __forceinline__ bool split_passes(SplitPipe &pp, int rb, const int *__restrict__ tw_ptr,
-                                             const int *__restrict__ tw_col, const uint16_t *__restrict__ tw_lrow,
-                                             const float *rec, XF xf, float *slot, float *rowacc, int *err,
-                                             long long limit) {
+// One sweep of the warp's passes over the halo vectors hx.  False on an
+// mbarrier timeout (then the warp stops; callers agree CTA-wide with
+// __syncthreads_and and leave).
+__device__ __forceinline__ bool split_passes(SplitPipe &pp, int rb, const int *__restrict__ tw_ptr, const float *hx,
+                                             float *slot, float *rowacc, int *err, long long limit) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (pp.m == 0) return true;
     const int eb = pp.eb, ee = pp.ee;
-    int t = eb + 32 * wid + lane;
-    bool valid = t < ee;
-    int lr = valid ? (int)__ldg(tw_lrow + t) : 0xFFFF;
-    float rv[20];
-    if (valid) load_rec_l1(rec, __ldg(tw_col + t), rv);
     for (int k = 0; k < pp.m; ++k) {
         const int q = wid + SPLIT_WARPS * k;
-        // the next pass's gather goes out before this pass is applied
-        const int tn = t + 32 * SPLIT_WARPS;
-        const bool vn = k + 1 < pp.m && tn < ee;
-        int lrn = 0xFFFF;
-        float rn[20];
-        if (vn) {
-            lrn = (int)__ldg(tw_lrow + tn);
-            load_rec_l1(rec, __ldg(tw_col + tn), rn);
-        }
+        const int t = eb + 32 * q + lane;
+        const bool valid = t < ee;
         const uint32_t b = pp.seq & 1;
         // every lane observes the copy's completion; the verdict is warp-uniform
         if (!__all_sync(0xffffffffu, mbar_wait(pp.mbar + 2 * wid + b, (pp.seq >> 1) & 1u, limit))) {
             if (lane == 0) atomicExch(err, (int)BA_ERR_TIMEOUT);
             return false;
         }
+        const float *buf = pass_buf(pp, pp.seq);
+        int lr = 0xFFFF;
         float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (valid) {
-            float x[6];
-            xf(rv, x);
-            const float4 *s4 = reinterpret_cast<const float4 *>(pp.stage + (size_t)(2 * wid + b) * 32 * BW +
-                                                                lane * BW);
+            const uint32_t md = reinterpret_cast<const uint32_t *>(buf + PASS_S_BYTES / 4)[lane];
+            lr = (int)(md & 0xFFFFu);
+            const float4 *x4 = reinterpret_cast<const float4 *>(hx + HX * (md >> 16));
+            const float4 xa = x4[0], xb = x4[1];
+            const float x[6] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y};
+            const float4 *s4 = reinterpret_cast<const float4 *>(buf + lane * BW);
 #pragma unroll
             for (int h = 0; h < 3; ++h) {  // two block rows (12 floats) at a time
                 const float4 u0 = s4[3 * h], u1 = s4[3 * h + 1], u2 = s4[3 * h + 2];
@@ -719,22 +713,14 @@ __device__ __forceinline__ bool split_passes(SplitPipe &pp, int rb, const int *_
 #pragma unroll
             for (int c = 0; c < 6; ++c) dst[c] = y[c];
         }
-        t = tn;
-        valid = vn;
-        lr = lrn;
-#pragma unroll
-        for (int c = 0; c < 20; ++c) rv[c] = rn[c];
     }
     return true;
 }
 
 // Component c of (S^ x)_i for local row lr after split_passes and a
 // __syncthreads: the row's segment sums in pass order.
-__device__ __forceinline__ float split_combine(int lr, int c, int rb, int eb, int ee,
-                                               const int *__restrict__ tw_ptr, const float *slot,
+__device__ __forceinline__ float split_combine(int lr, int c, int rs, int rend, int eb, int ee, const float *slot,
                                                const float *rowacc) {
-    const int i = rb + lr;
-    const int rs = __ldg(tw_ptr + i), rend = __ldg(tw_ptr + i + 1);
     float w = 0.f;
     for (int q = (rs - eb) >> 5; q <= (rend - 1 - eb) >> 5; ++q) {
         const int ps = eb + 32 * q, pe = min(ps + 32, ee);
@@ -744,18 +730,51 @@ __device__ __forceinline__ float split_combine(int lr, int c, int rb, int eb, in
     return w;
 }
 
+// Halo gather: for each halo camera the vector the SpMV applies (x = r for
+// the prologue, else next_r of its record), and for the CTA's own rows the
+// old r, w, s (own[lr][0..17]).
+__device__ __forceinline__ void split_halo(const int *__restrict__ halo_col, int hb, int H, int ob, int R,
+                                           const float *rec, bool first, float a, float b, float *hx, float *own) {
+    for (int h = threadIdx.x; h < H; h += blockDim.x) {
+        const int j = __ldg(halo_col + hb + h);
+        const float4 *q = reinterpret_cast<const float4 *>(rec + (int64_t)SREC * j);
+        float t[20];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float4 v = __ldcg(q + k);
+            t[4 * k] = v.x; t[4 * k + 1] = v.y; t[4 * k + 2] = v.z; t[4 * k + 3] = v.w;
+        }
+        float x[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x[k] = first ? t[k] : next_r(t[k], t[6 + k], t[12 + k], a, b);
+        float4 *o = reinterpret_cast<float4 *>(hx + HX * h);
+        o[0] = make_float4(x[0], x[1], x[2], x[3]);
+        o[1] = make_float4(x[4], x[5], 0.f, 0.f);
+        const int lr = h - ob;
+        if (lr >= 0 && lr < R) {
+            float4 *w4 = reinterpret_cast<float4 *>(own + 20 * lr);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) w4[k] = make_float4(t[4 * k], t[4 * k + 1], t[4 * k + 2], t[4 * k + 3]);
+        }
+    }
+}
+
 // CG on S^ x^ = r^_0 (Chronopoulos-Gear), with per iteration k
 //   p = r + beta p,  s = w + beta s,  x^ += alpha p,  r -= alpha s,  w = S^ r,
 //   gamma = r.r, delta = w.r, beta' = gamma'/gamma,
 //   alpha' = gamma' / (delta' - beta' gamma' / alpha),
-// one phase per iteration: the SpMV gathers r_j(new) = next_r(...) from the
-// previous records, then a thread per (row, component) of the CTA's rows
-// combines w_i and updates the row's own p, s, x^, r, w.  The stop test uses
-// the original residual norm ||H r^|| (block-Jacobi: ||L r^||).  One grid
-// all-reduce of (gamma, delta, ||H r||^2) ends each phase.
-__global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ cta_rows, const int *__restrict__ tw_ptr,
-                                                      const int *__restrict__ tw_col,
-                                                      const uint16_t *__restrict__ tw_lrow,
+// one phase per iteration: the halo gather, the SpMV passes, then a thread
+// per (row, component) of the CTA's rows combines w_i and updates the row's
+// own p, s, x^, r, w (a thread's first element keeps p, x^ and its row of H
+// in registers across iterations).  The stop test uses the original
+// residual norm ||H r^|| (block-Jacobi: ||L r^||).  One grid all-reduce of
+// (gamma, delta, ||H r||^2) ends each phase.
+__global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__restrict__ cta_rows, const int *__restrict__ tw_ptr,
+                                                      const uint32_t *__restrict__ tw_meta,
+                                                      const int *__restrict__ meta_off,
+                                                      const int *__restrict__ halo_ptr,
+                                                      const int *__restrict__ halo_col,
+                                                      const int *__restrict__ own_base, int slot_floats,
                                                       const float *__restrict__ Sh, const float *__restrict__ H,
                                                       float *x, float *p, float *rec0, float *rec1, DevScalars *sc,
                                                       double *red, unsigned *bar, long long limit_cycles) {
@@ -764,9 +783,14 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
     if (sc->done) return;
     const int rb = __ldg(cta_rows + blockIdx.x), re = __ldg(cta_rows + blockIdx.x + 1);
     const int eb = __ldg(tw_ptr + rb), ee = __ldg(tw_ptr + re);
+    const int hb = __ldg(halo_ptr + blockIdx.x), NH = __ldg(halo_ptr + blockIdx.x + 1) - hb;
+    const int ob = __ldg(own_base + blockIdx.x);
     const int R = re - rb, P = (ee - eb + 31) >> 5, wid = threadIdx.x >> 5;
+    // dynamic shared memory: copy buffers | slots + row sums | halo vectors | own records
     float *slot = sdyn + SPLIT_STAGE_BYTES / 4, *rowacc = slot + 12 * P;
-    SplitPipe pp{sdyn, mbar, Sh, eb, ee, wid < P ? (P - 1 - wid) / SPLIT_WARPS + 1 : 0, 0u, 0u};
+    float *hx = slot + slot_floats, *own = hx + HX * NH;
+    SplitPipe pp{sdyn, mbar, Sh, tw_meta + __ldg(meta_off + blockIdx.x), eb, ee,
+                 wid < P ? (P - 1 - wid) / SPLIT_WARPS + 1 : 0, 0u};
     if (threadIdx.x < 2 * SPLIT_WARPS) mbar_init(&mbar[threadIdx.x], 1);
     fence_proxy_async();
     __syncthreads();
@@ -774,17 +798,34 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
         split_issue(pp, 0);
         split_issue(pp, 1);
     }
+    // this thread's first (row, component): p, x^, its row of H and the row's
+    // entry range stay in registers
+    const int u0 = threadIdx.x;
+    const bool has0 = u0 < 6 * R;
+    const int lr0 = u0 / 6, c0 = u0 - 6 * lr0;
+    float p0 = 0.f, x0 = 0.f, h0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int rs0 = 0, re0 = 0;
+    if (has0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) h0[k] = __ldg(H + 36 * (int64_t)(rb + lr0) + 6 * c0 + k);
+        rs0 = __ldg(tw_ptr + rb + lr0);
+        re0 = __ldg(tw_ptr + rb + lr0 + 1);
+    }
     unsigned gen = 0;
     // The recurrence's FP64 scalars live in thread 0, which decides alpha,
     // beta and the stop after each all-reduce and publishes them here (GB300's
     // FP64 rate is far below FP32: no other thread does FP64 arithmetic).
     __shared__ float2 sh_df[3 * SPLIT_WARPS];
-    __shared__ int s_ctl;        // 0 go on, 1 stop, 2 not SPD, 3 timeout
+    __shared__ int s_ctl;  // 0 go on, 1 stop, 2 not SPD, 3 timeout
     __shared__ float s_ab[2];
-    double gamma = 0.0, delta = 0.0, rr = 0.0, rr0 = 0.0, alpha_prev = 0.0, gamma_prev = 0.0;
+    double gamma = 0.0, delta = 0.0, rr = 0.0, rr0 = 0.0, gamma_prev = 0.0, ga_prev = 0.0;
     int it = 0;
-    // thread 0, after an all-reduce with totals (gamma', delta', rr'): the next step
-    auto decide = [&](bool ok, const double (&t)[3], bool first) {
+    const double tol2 = threadIdx.x == 0 ? sc->tol2 : 0.0;
+    const int max_iters = threadIdx.x == 0 ? sc->max_iters : 0;
+    // alpha = gamma / (delta - gamma^2 / (gamma_prev alpha_prev)): the
+    // difference (p^T S^ p, prone to cancellation) in FP64 with one division;
+    // alpha and beta, applied in FP32, by FP32 divisions
+    auto decide = [&](bool ok, const double(&t)[3], bool first) {
         if (!ok) {
             s_ctl = 3;
             return;
@@ -798,57 +839,49 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
         gamma = t[0];
         delta = t[1];
         rr = t[2];
-        if (rr <= sc->tol2 * rr0 || it >= sc->max_iters) {
+        if (rr <= tol2 * rr0 || it >= max_iters) {
             s_ctl = 1;
             return;
         }
-        double alpha, beta;
-        if (it == 0) {
-            beta = 0.0;
-            alpha = gamma / delta;
-        } else {
-            beta = gamma / gamma_prev;
-            alpha = gamma / (delta - beta * gamma / alpha_prev);
-        }
-        alpha_prev = alpha;
-        if (!(alpha > 0.0) || !(alpha < 1e300)) {  // p^T S^ p <= 0 or not finite
+        const double den = it == 0 ? delta : delta - gamma * gamma / ga_prev;
+        const float alpha = den > 0.0 ? ratio32(gamma, den) : 0.f;
+        const float beta = it == 0 ? 0.f : ratio32(gamma, gamma_prev);
+        ga_prev = gamma * (double)alpha;
+        if (!(den > 0.0) || !(alpha > 0.f) || !(alpha < 1e30f)) {  // p^T S^ p <= 0 or not finite
             s_ctl = 2;
             return;
         }
         s_ctl = 0;
-        s_ab[0] = (float)alpha;
-        s_ab[1] = (float)beta;
+        s_ab[0] = alpha;
+        s_ab[1] = beta;
+    };
+    auto leave = [&]() {
+        if (has0) x[6 * (int64_t)(rb + lr0) + c0] = x0;
+        split_drain(pp, limit_cycles);
     };
     // phase timing (thread 0 of each CTA, profile >= 2): passes, combine, all-reduce
     const bool prof = sc->prof_on != 0 && threadIdx.x == 0;
     unsigned long long t_pass = 0, t_comb = 0, t_red = 0, t0 = 0, t1 = 0, t2 = 0;
     {  // prologue: w_0 = S^ r_0 and the dot products of iteration 0
-        const bool ok = __syncthreads_and(split_passes(
-            pp, rb, tw_ptr, tw_col, tw_lrow, rec0,
-            [](const float(&v)[20], float(&xx)[6]) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) xx[k] = v[k];
-            },
-            slot, rowacc, &sc->err, limit_cycles));
+        split_halo(halo_col, hb, NH, ob, R, rec0, true, 0.f, 0.f, hx, own);
+        __syncthreads();
+        const bool ok = __syncthreads_and(split_passes(pp, rb, tw_ptr, hx, slot, rowacc, &sc->err, limit_cycles));
         if (!ok) {
-            split_drain(pp, limit_cycles);
+            leave();
             return;
         }
         RunSum<float> gp, dp, rp;
         for (int u = threadIdx.x; u < 6 * R; u += blockDim.x) {
             const int lr = u / 6, c = u - 6 * lr, i = rb + lr;
-            const float wc = split_combine(lr, c, rb, eb, ee, tw_ptr, slot, rowacc);
-            float v[20];
-            load_rec(rec0, i, v);
+            const int rs = u == u0 ? rs0 : __ldg(tw_ptr + i), rend = u == u0 ? re0 : __ldg(tw_ptr + i + 1);
+            const float wc = split_combine(lr, c, rs, rend, eb, ee, slot, rowacc);
+            const float *r6 = hx + HX * (ob + lr);
             rec0[(int64_t)SREC * i + 6 + c] = wc;
-            const float *h = H + 36 * (int64_t)i + 6 * c;
             float hr = 0.f;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) hr = __fmaf_rn(__ldg(h + k), v[k], hr);
-            float rc = v[0];
-#pragma unroll
-            for (int k = 1; k < 6; ++k)
-                if (c == k) rc = v[k];
+            for (int k = 0; k < 6; ++k)
+                hr = __fmaf_rn(u == u0 ? h0[k] : __ldg(H + 36 * (int64_t)i + 6 * c + k), r6[k], hr);
+            const float rc = r6[c];
             gp.add(rc * rc);
             dp.add(wc * rc);
             rp.add(hr * hr);
@@ -860,6 +893,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
         if (threadIdx.x == 0) decide(ok2, t, true);
         __syncthreads();
     }
+    uint32_t par = 0;  // parity of the current iteration's records
     for (;;) {
         const int ctl = s_ctl;
         if (ctl != 0) {
@@ -879,54 +913,48 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
                     atomicAdd(&sc->ph[3], (double)it);
                 }
             }
-            split_drain(pp, limit_cycles);
+            leave();
             return;
         }
         const float a = s_ab[0], b = s_ab[1];
-        const float *rc = (it_parity(pp) & 1) ? rec1 : rec0;
-        float *rn = (it_parity(pp) & 1) ? rec0 : rec1;
+        const float *rc = par ? rec1 : rec0;
+        float *rn = par ? rec0 : rec1;
         if (prof) t0 = global_ns();
-        const bool ok = __syncthreads_and(split_passes(
-            pp, rb, tw_ptr, tw_col, tw_lrow, rc,
-            [a, b](const float(&v)[20], float(&xx)[6]) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) xx[k] = next_r(v[k], v[6 + k], v[12 + k], a, b);
-            },
-            slot, rowacc, &sc->err, limit_cycles));
+        split_halo(halo_col, hb, NH, ob, R, rc, false, a, b, hx, own);
+        __syncthreads();
+        const bool ok = __syncthreads_and(split_passes(pp, rb, tw_ptr, hx, slot, rowacc, &sc->err, limit_cycles));
         if (!ok) {
-            split_drain(pp, limit_cycles);
+            leave();
             return;
         }
         if (prof) t1 = global_ns();
         RunSum<float> gp, dp, rp;
         for (int u = threadIdx.x; u < 6 * R; u += blockDim.x) {
             const int lr = u / 6, c = u - 6 * lr, i = rb + lr, e = 6 * i + c;
-            const float w_e = split_combine(lr, c, rb, eb, ee, tw_ptr, slot, rowacc);
-            float t[20], rnew[6];
-            load_rec(rc, i, t);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) rnew[k] = next_r(t[k], t[6 + k], t[12 + k], a, b);
-            float rold = t[0], wold = t[6], sold = t[12], r_e = rnew[0];
-#pragma unroll
-            for (int k = 1; k < 6; ++k)
-                if (c == k) {
-                    rold = t[k];
-                    wold = t[6 + k];
-                    sold = t[12 + k];
-                    r_e = rnew[k];
-                }
-            const float pval = __fmaf_rn(b, __ldcg(p + e), rold);
+            const bool first = u == u0;
+            const int rs = first ? rs0 : __ldg(tw_ptr + i), rend = first ? re0 : __ldg(tw_ptr + i + 1);
+            const float w_e = split_combine(lr, c, rs, rend, eb, ee, slot, rowacc);
+            const float *rnew = hx + HX * (ob + lr);  // this row's new residual (all six components)
+            const float *o6 = own + 20 * lr;
+            const float r_e = rnew[c], rold = o6[c], wold = o6[6 + c], sold = o6[12 + c];
+            const float pval = __fmaf_rn(b, first ? p0 : __ldcg(p + e), rold);
             const float sval = __fmaf_rn(b, sold, wold);
-            x[e] = __fmaf_rn(a, pval, __ldcg(x + e));
-            p[e] = pval;
+            const float xval = __fmaf_rn(a, pval, first ? x0 : __ldcg(x + e));
+            if (first) {
+                p0 = pval;
+                x0 = xval;
+            } else {
+                p[e] = pval;
+                x[e] = xval;
+            }
             float *o = rn + (int64_t)SREC * i;
             o[c] = r_e;
             o[6 + c] = w_e;
             o[12 + c] = sval;
-            const float *h = H + 36 * (int64_t)i + 6 * c;
             float hr = 0.f;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) hr = __fmaf_rn(__ldg(h + k), rnew[k], hr);
+            for (int k = 0; k < 6; ++k)
+                hr = __fmaf_rn(first ? h0[k] : __ldg(H + 36 * (int64_t)i + 6 * c + k), rnew[k], hr);
             gp.add(r_e * r_e);
             dp.add(w_e * r_e);
             rp.add(hr * hr);
@@ -946,7 +974,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_split(const int *__restrict__ ct
             decide(ok2, t, false);
         }
         __syncthreads();
-        pp.iter ^= 1u;
+        par ^= 1u;
     }
 }
 
@@ -1163,15 +1191,6 @@ static cudaError_t split_alloc(ba_problem *p) {
     const size_t E = (size_t)(2 * p->nnzb - p->n);
     al(&p->Sh, E * BW);
     al(&p->srec, (size_t)2 * SREC * p->n);
-    if (e == cudaSuccess && !p->tw_col) {
-        void *v = nullptr;
-        e = cudaMalloc(&v, E * sizeof(int));
-        if (e == cudaSuccess) {
-            p->tw_col = (int *)v;
-            p->allocs.push_back(v);
-            p->dev_bytes += E * sizeof(int);
-        }
-    }
     return e;
 }
 
@@ -1184,25 +1203,26 @@ cudaError_t launch_split_prepare(ba_problem *p, bool from_minv) {
     if (p->fp32) {
         k_split_factor<float><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const float *)p->S, (const float *)p->Minv,
                                                      from_minv ? 1 : 0, p->Gs, p->Hs, p->sc);
-        k_split_scale<float><<<ns, 128, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const float *)p->S, p->Gs, p->Sh,
-                                                    p->tw_col);
+        k_split_scale<float><<<ns, 128, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const float *)p->S, p->Gs, p->Sh);
     } else {
         k_split_factor<double><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const double *)p->S,
                                                       (const double *)p->Minv, from_minv ? 1 : 0, p->Gs, p->Hs, p->sc);
-        k_split_scale<double><<<ns, 128, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const double *)p->S, p->Gs, p->Sh,
-                                                     p->tw_col);
+        k_split_scale<double><<<ns, 128, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const double *)p->S, p->Gs, p->Sh);
     }
     ktimer_end(p, K_SPLIT_PREP, ev);
     p->launches += 2;
     return cudaGetLastError();
 }
 
-// Work partition of the balanced split SpMV, made once per problem: the grid
-// size, each CTA's row range (contiguous rows, about equal entries + a fixed
-// cost per row), the local row of every two-sided entry, and the dynamic
-// shared memory of the busiest CTA (the warps' copy buffers, two 6-float
-// slots per 32-entry pass, one per row).  Problems whose largest CTA would
-// need more than 200 KB keep the standard recurrence (split_grid < 0).
+// Work partition of the split CG, made once per problem on the host: the
+// grid size; each CTA's row range (contiguous rows, about equal entries + a
+// fixed cost per row); its halo (the sorted distinct columns of its entries;
+// its own rows are one contiguous stretch of it, starting at own_base); the
+// packed metadata of every entry (local row | halo index << 16), laid out
+// per CTA from a 16-byte aligned offset; and the dynamic shared memory of
+// the busiest CTA (copy buffers, pass slots and row sums, halo vectors, own
+// records).  Problems that need more than 200 KB in a CTA keep the standard
+// recurrence (split_grid < 0).
 static cudaError_t split_partition(ba_problem *p) {
     if (p->split_grid != 0) return cudaSuccess;
     cudaError_t e;
@@ -1211,19 +1231,26 @@ static cudaError_t split_partition(ba_problem *p) {
     if ((e = cudaMemcpy(twp.data(), p->tw_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return e;
     const int64_t E = twp[n];
+    std::vector<int2> twe(E);
+    if (E && (e = cudaMemcpy(twe.data(), p->tw_ent, E * sizeof(int2), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
     int dev = 0, n_sm = 0, bps = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     constexpr int SMEM_MAX = 200 * 1024, ROW_COST = 8;
     if ((e = cudaFuncSetAttribute(k_pcg_split, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX)) != cudaSuccess)
         return e;
-    std::vector<int32_t> rows;
+    auto unavailable = [&]() {
+        p->split_grid = -1;
+        return cudaSuccess;
+    };
+    std::vector<int32_t> rows, hptr, hcol, obase;
     size_t smem = SPLIT_STAGE_BYTES;
-    int G = 0;
+    int slot_floats = 0, G = 0;
     for (int attempt = 0; attempt < 4; ++attempt) {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pcg_split, 256, smem)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pcg_split, SPLIT_WARPS * 32, smem)) != cudaSuccess) return e;
         bps = std::min(bps, 2);
-        if (bps < 1) break;
+        if (bps < 1) return unavailable();
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * n_sm, (E + 255) / 256));
         if (g == G) break;
         G = g;
@@ -1236,44 +1263,68 @@ static cudaError_t split_partition(ba_problem *p) {
             acc += (double)(twp[i + 1] - twp[i]) + ROW_COST;
             while (c < G && acc >= total * c / G) rows[c++] = i + 1;
         }
-        smem = SPLIT_STAGE_BYTES;
+        // halos
+        hptr.assign(G + 1, 0);
+        hcol.clear();
+        obase.assign(G, 0);
+        int Hmax = 0, Rmax = 0;
+        slot_floats = 0;
+        std::vector<int32_t> cols;
         for (int k = 0; k < G; ++k) {
+            cols.clear();
+            for (int64_t t = twp[rows[k]]; t < twp[rows[k + 1]]; ++t) cols.push_back(twe[t].y);
+            std::sort(cols.begin(), cols.end());
+            cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+            obase[k] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), rows[k]) - cols.begin());
+            hcol.insert(hcol.end(), cols.begin(), cols.end());
+            hptr[k + 1] = (int32_t)hcol.size();
+            const int R = rows[k + 1] - rows[k];
             const int64_t P = ((int64_t)twp[rows[k + 1]] - twp[rows[k]] + 31) / 32;
-            smem = std::max(smem, SPLIT_STAGE_BYTES + (size_t)(12 * P + 6 * (int64_t)(rows[k + 1] - rows[k])) * sizeof(float));
+            Hmax = std::max(Hmax, (int)cols.size());
+            Rmax = std::max(Rmax, R);
+            slot_floats = std::max(slot_floats, (int)(12 * P + 6 * R + 3) & ~3);
         }
-        if (smem > (size_t)SMEM_MAX) break;
-    }
-    if (bps < 1 || smem > (size_t)SMEM_MAX || G < 1) {
-        p->split_grid = -1;
-        return cudaSuccess;
+        smem = SPLIT_STAGE_BYTES + ((size_t)slot_floats + (size_t)HX * Hmax + 20 * (size_t)Rmax) * sizeof(float);
+        if (smem > (size_t)SMEM_MAX || Hmax > 0xFFFF || Rmax > 0xFFFE) return unavailable();
     }
     // the occupancy at the final shared-memory size must keep the grid resident
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pcg_split, 256, smem)) != cudaSuccess) return e;
-    if ((int64_t)bps * n_sm < G) {
-        p->split_grid = -1;
-        return cudaSuccess;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pcg_split, SPLIT_WARPS * 32, smem)) != cudaSuccess) return e;
+    if (G < 1 || (int64_t)bps * n_sm < G) return unavailable();
+    // packed entry metadata, per CTA from a 16-byte aligned offset (+ padding
+    // for the rounded-up copy of a CTA's last pass)
+    std::vector<int32_t> moff(G);
+    int64_t mtotal = 0;
+    for (int k = 0; k < G; ++k) {
+        moff[k] = (int32_t)mtotal;
+        mtotal += ((int64_t)twp[rows[k + 1]] - twp[rows[k]] + 3) & ~3;
     }
-    std::vector<uint16_t> lrow(E);
-    for (int k = 0; k < G; ++k)
+    mtotal += 4;
+    std::vector<uint32_t> meta(mtotal, 0u);
+    for (int k = 0; k < G; ++k) {
+        const int32_t *hc = hcol.data() + hptr[k];
+        const int H = hptr[k + 1] - hptr[k];
         for (int i = rows[k]; i < rows[k + 1]; ++i)
-            for (int t = twp[i]; t < twp[i + 1]; ++t) lrow[t] = (uint16_t)(i - rows[k]);
-    for (int k = 0; k < G; ++k)
-        if (rows[k + 1] - rows[k] > 0xFFFE) {  // local row ids are 16-bit
-            p->split_grid = -1;
-            return cudaSuccess;
-        }
-    void *d_rows = nullptr, *d_lrow = nullptr;
-    if ((e = cudaMalloc(&d_rows, (G + 1) * sizeof(int32_t))) != cudaSuccess) return e;
-    p->allocs.push_back(d_rows);
-    if ((e = cudaMalloc(&d_lrow, std::max<int64_t>(E, 1) * sizeof(uint16_t))) != cudaSuccess) return e;
-    p->allocs.push_back(d_lrow);
-    p->dev_bytes += (G + 1) * sizeof(int32_t) + E * sizeof(uint16_t);
-    if ((e = cudaMemcpy(d_rows, rows.data(), (G + 1) * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
-    if (E && (e = cudaMemcpy(d_lrow, lrow.data(), E * sizeof(uint16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
-    p->cta_rows = (int32_t *)d_rows;
-    p->tw_lrow = (uint16_t *)d_lrow;
+            for (int64_t t = twp[i]; t < twp[i + 1]; ++t) {
+                const uint32_t h = (uint32_t)(std::lower_bound(hc, hc + H, twe[t].y) - hc);
+                meta[moff[k] + (t - twp[rows[k]])] = (uint32_t)(i - rows[k]) | (h << 16);
+            }
+    }
+    std::vector<std::pair<void **, std::pair<const void *, size_t>>> up = {
+        {(void **)&p->cta_rows, {rows.data(), rows.size() * sizeof(int32_t)}},
+        {(void **)&p->tw_meta, {meta.data(), meta.size() * sizeof(uint32_t)}},
+        {(void **)&p->meta_off, {moff.data(), moff.size() * sizeof(int32_t)}},
+        {(void **)&p->halo_ptr, {hptr.data(), hptr.size() * sizeof(int32_t)}},
+        {(void **)&p->halo_col, {hcol.data(), std::max<size_t>(hcol.size(), 1) * sizeof(int32_t)}},
+        {(void **)&p->own_base, {obase.data(), obase.size() * sizeof(int32_t)}}};
+    for (auto &u : up) {
+        void *d = nullptr;
+        if ((e = cudaMalloc(&d, u.second.second)) != cudaSuccess) return e;
+        p->allocs.push_back(d);
+        p->dev_bytes += u.second.second;
+        if ((e = cudaMemcpy(d, u.second.first, u.second.second, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        *u.first = d;
+    }
+    p->split_slot_floats = slot_floats;
     p->split_smem = smem;
     p->split_grid = G;
     return cudaSuccess;
@@ -1305,8 +1356,10 @@ cudaError_t launch_pcg_split(ba_problem *p) {
     ktimer_begin(p, K_PCG_LOOP, &ev);
     cudaError_t e = cudaMemsetAsync(p->counters + 14, 0, 2 * sizeof(unsigned), p->st);
     if (e == cudaSuccess) {
-        const int *cr = p->cta_rows, *twp = p->tw_ptr, *twc = p->tw_col;
-        const uint16_t *lr = p->tw_lrow;
+        const int *cr = p->cta_rows, *twp = p->tw_ptr, *mo = p->meta_off, *hp = p->halo_ptr, *hc = p->halo_col,
+                  *ob = p->own_base;
+        const uint32_t *meta = p->tw_meta;
+        int sf = p->split_slot_floats;
         const float *Sh = p->Sh, *H = p->Hs;
         float **v = (float **)p->sv.pv;
         float *x = v[0], *pp = v[2];
@@ -1314,9 +1367,10 @@ cudaError_t launch_pcg_split(ba_problem *p) {
         DevScalars *sc = p->sc;
         double *red = p->red;
         unsigned *bar = p->counters + 14;
-        long long limit = 4000000000LL;  // ~2 s of SM clock per all-reduce wait
-        void *args[] = {&cr, &twp, &twc, &lr, &Sh, &H, &x, &pp, &rec0, &rec1, &sc, &red, &bar, &limit};
-        e = cudaLaunchCooperativeKernel((const void *)k_pcg_split, dim3(p->split_grid), dim3(256), args,
+        long long limit = 4000000000LL;  // ~2 s of SM clock per wait
+        void *args[] = {&cr, &twp, &meta, &mo, &hp, &hc, &ob, &sf, &Sh, &H, &x, &pp, &rec0, &rec1, &sc, &red, &bar,
+                        &limit};
+        e = cudaLaunchCooperativeKernel((const void *)k_pcg_split, dim3(p->split_grid), dim3(SPLIT_WARPS * 32), args,
                                         p->split_smem, p->st);
     }
     ktimer_end(p, K_PCG_LOOP, ev);
