@@ -56,12 +56,19 @@ def make_scene(workload: str, rank: int = 0):
         return scenes.aerial_small(seed=2101 + rank)
     if workload == "aerial2400":
         return scenes.aerial_small(n_along=60, n_across=40, pts_per_cam=200, seed=2201 + rank)
+    if workload == "blocks50k":
+        # 20 overlapping 50 x 50 aerial blocks, 10M points, tracks 2 + Geom (mean 6, max 40),
+        # 1% outlier observations
+        return scenes.blocks_scene(seed=3001 + rank)
     raise ValueError(workload)
 
 
 def workload_opts(workload: str, B):
     if workload == "ring50":
         return dict(precision=B.BA_FP64, pcg_rel_tol=1e-10)
+    if workload == "blocks50k":
+        return dict(precision=B.BA_FP32, pcg_rel_tol=0.1, inner_rel_tol=1e-4, robust=B.BA_LOSS_HUBER,
+                    huber_delta=2.0)
     return dict(precision=B.BA_FP32, pcg_rel_tol=0.1, inner_rel_tol=1e-4)
 
 
@@ -70,6 +77,7 @@ def workload_config(workload: str, s, opts):
             "mean_track": round(s.n_obs / s.n_pts, 3), "precision": "fp32+fp64-refine"
             if opts.get("precision") == 1 else "fp64", "pcg_rel_tol": opts["pcg_rel_tol"],
             "lm_iterations_timed": "1..K from the initial state",
+            "robust": "huber 2 px" if opts.get("robust") else "none",
             "l2": "inputs larger than L2 (stored Jacobians %.0f MB > 129 MB)" % (s.n_obs * 80 / 1e6)}
 
 
@@ -247,7 +255,8 @@ def run_ours(args):
             "peak_kind": peak_kind, "traffic": traffic, "per": "PCG iteration",
             "algorithmic_bytes": int(per_iter), "iterations": iters, "launches": n_pcg,
             "us_per_iteration": round(us_iter, 2),
-            "note": "S (23 MB) stays in L2 at this size: DRAM traffic is the vectors only",
+            "note": ("S (%.0f MB) fits in L2: its DRAM traffic is the vectors" % (st1["nnzb"] * 36 * esz / 1e6))
+            if st1["nnzb"] * 36 * esz < 100e6 else "S (%.0f MB) streams from HBM" % (st1["nnzb"] * 36 * esz / 1e6),
             "share_of_timed_kernels": round(t_pcg / total_timed, 3) if total_timed else None}
     # RCS assembly (K2), the metric's second figure
     n_l, tot = ktimes["form_rcs"]
@@ -291,7 +300,7 @@ PCG_KERNEL_VERSION = "pcg_split-halo-v2"
 RCS_KERNEL_VERSION = "form_rcs-v3"
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum, profiles/pcg_split_aerial5k.md
-    "pcg_split": {"version": "pcg_split-bulk-v1", "workload": "aerial5k", "bytes_per_unit": 1_174_800},
+    "pcg_split": {"version": "pcg_split-halo-v2", "workload": "aerial5k", "bytes_per_unit": 1_157_700},
     # profiles/form_rcs_aerial.md
     "form_rcs": {"version": "form_rcs-v3", "workload": "aerial5k", "bytes_per_unit": 784_956_672},
 }
@@ -420,6 +429,8 @@ def run_kernel_case(args):
         opts.update(pcg_rel_tol=args.pcg_tol, inner_rel_tol=args.pcg_tol, refine_max=1)
     if args.pcg_variant:
         opts["pcg_variant"] = {"standard": B.BA_PCG_STANDARD, "split": B.BA_PCG_SPLIT}[args.pcg_variant]
+    if args.group_obs:
+        opts["group_max_obs"] = args.group_obs
     g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, profile=2, **opts)
     g.linearize()
     iters = []
@@ -431,6 +442,11 @@ def run_kernel_case(args):
     torch.cuda.synchronize()
     kt = {k: v for k, v in g.kernel_times().items() if v[0]}
     out = {"kernel_case": args.kernel_case, "workload": args.workload, "stats": g.stats(), "kernel_ms": kt}
+    if args.kernel_case == "form_rcs":
+        st = g.stats()
+        out["rcs_phase_us_per_group"] = [round(x, 2) for x in st["rcs_phase_us"]]
+        out["form_rcs_us"] = round(1e3 * kt["form_rcs"][1] / kt["form_rcs"][0], 1)
+        out["rcs_reduce_us"] = round(1e3 * kt["rcs_reduce"][1] / kt["rcs_reduce"][0], 1)
     if iters:
         n_l, ms = kt["pcg_loop"]
         out.update(pcg_iters=iters, pcg_variant=args.pcg_variant or "auto",
@@ -451,11 +467,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="aerial5k", choices=["aerial5k", "ring50", "aerial_small", "aerial2400"])
+    ap.add_argument("--workload", default="aerial5k",
+                    choices=["aerial5k", "ring50", "aerial_small", "aerial2400", "blocks50k"])
     ap.add_argument("--kernel-case", default=None, choices=["form_rcs", "pcg"],
                     help="profiling driver: run one kernel family a few times on the workload and exit")
     ap.add_argument("--pcg-tol", type=float, default=None, help="kernel case: PCG relative tolerance")
     ap.add_argument("--pcg-variant", default=None, choices=["standard", "split"], help="kernel case: PCG variant")
+    ap.add_argument("--group-obs", type=int, default=0, help="kernel case: observations per point group")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solver", action="store_true", help="skip the PCG time-to-1e-8 comparison")

@@ -109,6 +109,9 @@ typedef struct {
     double pcg_phase_us[3];  /* profile >= 2: split CG iteration phases, mean over CTAs and
                                 iterations of all solves so far, in us: SpMV passes (to the
                                 CTA barrier), row combine and update, grid all-reduce */
+    double rcs_phase_us[3];  /* profile >= 2: RCS formation per point group, mean over the
+                                groups formed so far, in us: wait for the group's copy,
+                                per-point work (V_k, Cholesky, P, e^), products and write-out */
 } ba_stats;
 
 /* Fills *o with the defaults listed above. */

@@ -77,7 +77,8 @@ class ba_stats(ctypes.Structure):
     _fields_ = [("n_cams", ctypes.c_int32), ("n_pts", ctypes.c_int64), ("n_obs", ctypes.c_int64),
                 ("nnzb", ctypes.c_int64), ("n_groups", ctypes.c_int64), ("n_partials", ctypes.c_int64),
                 ("n_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("precision", ctypes.c_int32), ("pcg_phase_us", ctypes.c_double * 3)]
+                ("precision", ctypes.c_int32), ("pcg_phase_us", ctypes.c_double * 3),
+                ("rcs_phase_us", ctypes.c_double * 3)]
 
 
 _P = ctypes.c_void_p
@@ -234,6 +235,7 @@ def ba_get_stats(h) -> dict:
     _check(lib().ba_get_stats(h, ctypes.byref(s)))
     out = {f: getattr(s, f) for f, _ in s._fields_}
     out["pcg_phase_us"] = list(out["pcg_phase_us"])
+    out["rcs_phase_us"] = list(out["rcs_phase_us"])
     return out
 
 

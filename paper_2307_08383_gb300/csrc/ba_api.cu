@@ -952,6 +952,10 @@ ba_status ba_get_lm_state(const ba_problem *p, double *lambda, double *nu, doubl
 ba_status ba_get_stats(const ba_problem *p, ba_stats *o) {
     LIVE(p);
     if (!o) return fail(BA_ERR_INVALID_ARG, "null output");
+    if (p->opt.profile >= 2) {  // the device-side phase totals
+        ba_status s = sync_scalars(const_cast<ba_problem *>(p));
+        if (s) return s;
+    }
     o->n_cams = p->n;
     o->n_pts = p->P;
     o->n_obs = p->m;
@@ -963,6 +967,8 @@ ba_status ba_get_stats(const ba_problem *p, ba_stats *o) {
     o->kernel_launches = p->launches;
     o->precision = p->opt.precision;
     for (int k = 0; k < 3; ++k) o->pcg_phase_us[k] = p->ph_sum[3] > 0 ? p->ph_sum[k] / p->ph_sum[3] / 1e3 : 0.0;
+    for (int k = 0; k < 3; ++k)
+        o->rcs_phase_us[k] = p->sc_host->ph_rcs[3] > 0 ? p->sc_host->ph_rcs[k] / p->sc_host->ph_rcs[3] / 1e3 : 0.0;
     return BA_OK;
 }
 

@@ -52,6 +52,7 @@ struct DevScalars {
     int iters, done, max_iters, err;
     int prof_on;   // split CG: time its phases (profile >= 2)
     double ph[4];  // split CG phase ns summed over CTAs and iterations; ph[3] = CTA iterations
+    double ph_rcs[4];  // RCS formation phase ns summed over groups (profile >= 2); [3] = groups
 };
 constexpr int N_COUNTERS = 16;
 constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
@@ -194,6 +195,7 @@ struct ba_problem {
     double ph_sum[4] = {};  // split CG phase totals over solves (profile >= 2)
     bool minv_learned = false;  // Minv holds the learned M^-1 (else block-Jacobi)
     float2 *xs = nullptr;  // x64 split in FP32 pairs (refinement residual of FP32 problems)
+    unsigned *ar_bar = nullptr;  // arrival counters of the split CG's all-reduce (one per line)
 
     // caller-order point I/O on the device, allocated on first use: the
     // internal -> caller permutation, a P x 3 staging buffer, a flag word

@@ -427,34 +427,42 @@ __device__ __forceinline__ void block_sum_df(df32 (&v)[NV], float2 *sh) {
 }
 
 // grid_allreduce_sym for double-floats (partials stored as float2 in the same
-// slots): every CTA adds all partials itself in CTA order.  On return the
-// totals are valid in thread 0 only (as doubles, hi + lo); false on timeout.
+// slots): every CTA adds all partials itself in CTA order.  Arrivals are
+// spread over AR_SUB counters, one per 128-byte line (CTA c announces itself
+// on counter c % AR_SUB), so the release adds of a large grid do not queue on
+// one address; lanes 0..AR_SUB-1 of warp 0 each poll one counter.  `bar`
+// holds AR_SUB * 32 words, zero at launch.  On return the totals are valid
+// in thread 0 only (as doubles, hi + lo); false on timeout.
+constexpr int AR_SUB = 16;
 template <int NV>
 __device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, unsigned gen, unsigned *bar,
                                                   int *err, long long limit_cycles, double (&tot)[NV]) {
     static_assert(NV <= AR_NV_MAX, "too many values");
-    __shared__ int s_ok;
     float2 *half = reinterpret_cast<float2 *>(part + (size_t)(gen & 1u) * gridDim.x * AR_NV_MAX);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) __stcg(half + blockIdx.x * AR_NV_MAX + k, make_float2(v[k].hi, v[k].lo));
-        red_add_release(bar, 1u);
-        const unsigned target = (gen + 1u) * gridDim.x;
-        const long long t0 = clock64();
-        int ok = 1;
-        while (ld_acquire(bar) < target) {
-            if (clock64() - t0 > limit_cycles || *(volatile int *)err == (int)BA_ERR_TIMEOUT) {
-                atomicExch(err, (int)BA_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-        }
-        s_ok = ok;
+        red_add_release(bar + 32 * (blockIdx.x % AR_SUB), 1u);
     }
     bool ok = true;
     if (threadIdx.x < 32) {
-        __syncwarp();
-        ok = s_ok != 0;
+        const int lane = threadIdx.x;
+        int lane_ok = 1;
+        if (lane < AR_SUB) {
+            // CTAs that announce themselves on this lane's counter
+            const unsigned per = gridDim.x / AR_SUB + ((unsigned)lane < gridDim.x % AR_SUB ? 1u : 0u);
+            const unsigned target = (gen + 1u) * per;
+            const long long t0 = clock64();
+            while (ld_acquire(bar + 32 * lane) < target) {
+                if (clock64() - t0 > limit_cycles || *(volatile int *)err == (int)BA_ERR_TIMEOUT) {
+                    lane_ok = 0;
+                    break;
+                }
+            }
+        }
+        ok = __all_sync(0xffffffffu, lane_ok) != 0;
+        __syncwarp();  // each lane's acquire orders the partial reads of every lane
+        if (!ok && lane == 0) atomicExch(err, (int)BA_ERR_TIMEOUT);
         df32 acc[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) acc[k] = df32{0.f, 0.f};

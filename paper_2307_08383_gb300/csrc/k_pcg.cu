@@ -1353,8 +1353,16 @@ cudaError_t launch_split_init(ba_problem *p, const float *rhs, double tol, int m
 
 cudaError_t launch_pcg_split(ba_problem *p) {
     cudaEvent_t ev;
+    cudaError_t e = cudaSuccess;
+    if (!p->ar_bar) {
+        void *v = nullptr;
+        if ((e = cudaMalloc(&v, AR_SUB * 32 * sizeof(unsigned))) != cudaSuccess) return e;
+        p->ar_bar = (unsigned *)v;
+        p->allocs.push_back(v);
+        p->dev_bytes += AR_SUB * 32 * sizeof(unsigned);
+    }
     ktimer_begin(p, K_PCG_LOOP, &ev);
-    cudaError_t e = cudaMemsetAsync(p->counters + 14, 0, 2 * sizeof(unsigned), p->st);
+    e = cudaMemsetAsync(p->ar_bar, 0, AR_SUB * 32 * sizeof(unsigned), p->st);
     if (e == cudaSuccess) {
         const int *cr = p->cta_rows, *twp = p->tw_ptr, *mo = p->meta_off, *hp = p->halo_ptr, *hc = p->halo_col,
                   *ob = p->own_base;
@@ -1366,7 +1374,7 @@ cudaError_t launch_pcg_split(ba_problem *p) {
         float *rec0 = p->srec, *rec1 = p->srec + (size_t)SREC * p->n;
         DevScalars *sc = p->sc;
         double *red = p->red;
-        unsigned *bar = p->counters + 14;
+        unsigned *bar = p->ar_bar;
         long long limit = 4000000000LL;  // ~2 s of SM clock per wait
         void *args[] = {&cr, &twp, &meta, &mo, &hp, &hc, &ob, &sf, &Sh, &H, &x, &pp, &rec0, &rec1, &sc, &red, &bar,
                         &limit};

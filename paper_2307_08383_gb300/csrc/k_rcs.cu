@@ -45,6 +45,12 @@ __device__ __forceinline__ void load_slot(const double *s, double (&v)[JW]) {
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns_rcs() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__restrict__ grp, int ngroups,
                                                            const ItemDesc *__restrict__ items,
@@ -52,7 +58,7 @@ __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__re
                                                            const int *__restrict__ trk_ptr, const T *__restrict__ J,
                                                            double lambda, T *__restrict__ part, T *__restrict__ Linv_out,
                                                            T *__restrict__ lp_out, DevScalars *sc, int fp64_v,
-                                                           int obs_max, long long limit) {
+                                                           int obs_max, long long limit, int prof) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ GroupDesc sdesc[2];
@@ -78,6 +84,9 @@ __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__re
         if (cb) bulk_g2s(dst + jbytes_max, contrib + d.c_begin, cb, &mbar[b]);
     };
     uint32_t parity = 0u, pending = 0u;  // one bit per buffer
+    // phase timing (thread 0, prof): copy wait, per-point work, products + write-out
+    const bool tm = prof && threadIdx.x == 0;
+    unsigned long long ta = 0, tb = 0, tc = 0, t_wait = 0, t_pts = 0, t_prod = 0, ngr = 0;
     int gi = blockIdx.x;
     if (threadIdx.x == 0 && gi < ngroups) issue(gi, 0);
     if (gi < ngroups) pending |= 1u;
@@ -88,8 +97,10 @@ __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__re
             if (threadIdx.x == 0) issue(gn, bsel ^ 1);
             pending |= 1u << (bsel ^ 1);
         }
+        if (tm) ta = global_ns_rcs();
         if (threadIdx.x == 0) s_ok = mbar_wait(&mbar[bsel], (parity >> bsel) & 1u, limit) ? 1 : 0;
         __syncthreads();
+        if (tm) tb = global_ns_rcs();
         if (!s_ok) {
             // give up: flag it, let the copies still in flight land (bounded), leave
             if (threadIdx.x == 0) {
@@ -188,6 +199,7 @@ __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__re
             }
         }
         __syncthreads();
+        if (tm) tc = global_ns_rcs();
 
         // 3) work items: each lane sums <= ITEM_MAX products of one sub-RCS block in
         //    registers; the items of a block that share a warp are added by a
@@ -274,6 +286,19 @@ __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__re
             }
         }
         __syncthreads();  // buffer free for the next copy
+        if (tm) {
+            const unsigned long long td = global_ns_rcs();
+            t_wait += tb - ta;
+            t_pts += tc - tb;
+            t_prod += td - tc;
+            ++ngr;
+        }
+    }
+    if (tm && ngr) {
+        atomicAdd(&sc->ph_rcs[0], (double)t_wait);
+        atomicAdd(&sc->ph_rcs[1], (double)t_pts);
+        atomicAdd(&sc->ph_rcs[2], (double)t_prod);
+        atomicAdd(&sc->ph_rcs[3], (double)ngr);
     }
 }
 
@@ -365,7 +390,7 @@ static cudaError_t form_rcs_T(ba_problem *p, double lambda, size_t smem, long lo
     const int grid = (int)std::min<int64_t>(p->ngroups, (int64_t)ctas_per_sm * n_sm);
     k_form_rcs<T><<<grid, FORM_THREADS, smem, p->st>>>(p->grp, (int)p->ngroups, p->items, p->contrib, p->trk_ptr,
                                                       (const T *)p->J, lambda, (T *)p->part, (T *)p->Linv, (T *)p->lp,
-                                                      p->sc, p->fp32 ? 1 : 0, p->obs_max, limit);
+                                                      p->sc, p->fp32 ? 1 : 0, p->obs_max, limit, p->opt.profile >= 2 ? 1 : 0);
     return cudaGetLastError();
 }
 
