@@ -258,6 +258,36 @@ def test_lm_huber_fp32(B):
     assert abs(F - Fr) <= 1e-5 * Fr, (F, Fr)
 
 
+def test_blocks_scene_huber_outliers_parity(B):
+    """The large workload's features at a reduced size: overlapping aerial blocks,
+    tracks of 2 + Geom (mean 6, max 40), 1% outlier observations, Huber (2 px), FP32.
+    The RCS block by block and three LM iterations against the FP64 oracle."""
+    s = scenes.blocks_scene(n_blocks_x=2, n_blocks_y=2, block_side=8, n_pts=6000, seed=3101)
+    assert s.n_obs / s.n_pts > 4.5
+    g = _gpu(B, s, precision=B.BA_FP32, robust=B.BA_LOSS_HUBER, huber_delta=2.0, pcg_rel_tol=1e-6)
+    lam0, _, _ = g.lm_state()
+    g.linearize()
+    g.form_rcs(lam0)
+    row_ptr, col, val, b = g.rcs()
+    pb = _oracle(s, delta=2.0, tol=1e-6)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    _, A, bref = pb.rcs(e, Jc, Jp, lam0)
+    assert np.array_equal(row_ptr, A.row_ptr) and np.array_equal(col, A.col)
+    assert block_errors(row_ptr, col, val, A.val).max() <= 1e-4
+    bref = bref.reshape(-1, 6)
+    assert np.linalg.norm(b - bref) <= 1e-4 * np.linalg.norm(bref)
+    g.set_state(s.cams0, s.pts0, lam0, 2.0)
+    st = O.LMState(s.cams0.copy(), s.pts0.copy())
+    for _ in range(3):
+        info = g.lm_step()
+        st, ref, _ = pb.step(st)
+        if ref.predicted > 1e-6 * ref.cost_before:
+            assert info["accepted"] == int(ref.accepted)
+    _, _, F = g.lm_state()
+    Fr = pb.cost(st.cams, st.pts)
+    assert abs(F - Fr) <= 1e-5 * Fr, (F, Fr)
+
+
 def test_state_errors(B):
     s = scenes.ring_scene(n_cams=6, n_pts=50, seed=56)
     g = _gpu(B, s)
