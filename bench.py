@@ -451,7 +451,8 @@ def run_kernel_case(args):
         n_l, ms = kt["pcg_loop"]
         out.update(pcg_iters=iters, pcg_variant=args.pcg_variant or "auto",
                    us_per_iteration=round(1e3 * ms / max(sum(iters), 1), 2),
-                   split_phase_us=[round(x, 2) for x in g.stats()["pcg_phase_us"]])
+                   split_phase_us=[round(x, 2) for x in g.stats()["pcg_phase_us"]],
+                   split_work_imbalance=round(g.stats()["pcg_work_imbalance"], 3))
     print(json.dumps(out))
     g.close()
 

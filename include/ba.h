@@ -112,6 +112,8 @@ typedef struct {
     double rcs_phase_us[3];  /* profile >= 2: RCS formation per point group, mean over the
                                 groups formed so far, in us: wait for the group's copy,
                                 per-point work (V_k, Cholesky, P, e^), products and write-out */
+    double pcg_work_imbalance; /* profile >= 2: last split CG solve, the busiest CTA's
+                                passes + combine time over the mean CTA's (1 = balanced) */
 } ba_stats;
 
 /* Fills *o with the defaults listed above. */

@@ -78,7 +78,7 @@ class ba_stats(ctypes.Structure):
                 ("nnzb", ctypes.c_int64), ("n_groups", ctypes.c_int64), ("n_partials", ctypes.c_int64),
                 ("n_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("pcg_phase_us", ctypes.c_double * 3),
-                ("rcs_phase_us", ctypes.c_double * 3)]
+                ("rcs_phase_us", ctypes.c_double * 3), ("pcg_work_imbalance", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p

@@ -604,8 +604,13 @@ static ba_status run_pcg_split(ba_problem *p, const void *rhs, double tol, int m
     CK(p, launch_pcg_split(p));
     ba_status s = sync_scalars(p);
     if (s) return s;
-    if (p->opt.profile >= 2)
+    if (p->opt.profile >= 2) {
         for (int k = 0; k < 4; ++k) p->ph_sum[k] += p->sc_host->ph[k];
+        // busiest CTA's work per iteration, over the mean CTA's (load balance)
+        const double its = p->sc_host->iters > 0 ? p->sc_host->iters : 1;
+        const double mean_work = (p->sc_host->ph[0] + p->sc_host->ph[1]) / (p->sc_host->ph[3] > 0 ? p->sc_host->ph[3] : 1);
+        p->ph_imbalance = mean_work > 0 ? (double)p->sc_host->ph_work_max / its / mean_work : 0.0;
+    }
     if (p->sc_host->err == BA_ERR_TIMEOUT) {
         p->dead = true;
         return fail(BA_ERR_TIMEOUT, "PCG grid all-reduce timed out");
@@ -969,6 +974,7 @@ ba_status ba_get_stats(const ba_problem *p, ba_stats *o) {
     for (int k = 0; k < 3; ++k) o->pcg_phase_us[k] = p->ph_sum[3] > 0 ? p->ph_sum[k] / p->ph_sum[3] / 1e3 : 0.0;
     for (int k = 0; k < 3; ++k)
         o->rcs_phase_us[k] = p->sc_host->ph_rcs[3] > 0 ? p->sc_host->ph_rcs[k] / p->sc_host->ph_rcs[3] / 1e3 : 0.0;
+    o->pcg_work_imbalance = p->ph_imbalance;
     return BA_OK;
 }
 

@@ -53,6 +53,7 @@ struct DevScalars {
     int prof_on;   // split CG: time its phases (profile >= 2)
     double ph[4];  // split CG phase ns summed over CTAs and iterations; ph[3] = CTA iterations
     double ph_rcs[4];  // RCS formation phase ns summed over groups (profile >= 2); [3] = groups
+    unsigned long long ph_work_max;  // split CG: largest per-CTA total of passes + combine ns, one solve
 };
 constexpr int N_COUNTERS = 16;
 constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
@@ -193,6 +194,7 @@ struct ba_problem {
     int split_slot_floats = 0;
     size_t split_smem = 0;
     double ph_sum[4] = {};  // split CG phase totals over solves (profile >= 2)
+    double ph_imbalance = 0.0;  // last split solve: busiest CTA's work / mean CTA's
     bool minv_learned = false;  // Minv holds the learned M^-1 (else block-Jacobi)
     float2 *xs = nullptr;  // x64 split in FP32 pairs (refinement residual of FP32 problems)
     unsigned *ar_bar = nullptr;  // arrival counters of the split CG's all-reduce (one per line)

@@ -573,6 +573,7 @@ __global__ void __launch_bounds__(256) k_split_init(int n, const float *__restri
         sc->done = max_iters <= 0 ? 1 : 0;
         sc->prof_on = prof;
         for (int k = 0; k < 4; ++k) sc->ph[k] = 0.0;
+        sc->ph_work_max = 0ull;
     }
 }
 
@@ -911,6 +912,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
                     atomicAdd(&sc->ph[1], (double)t_comb);
                     atomicAdd(&sc->ph[2], (double)t_red);
                     atomicAdd(&sc->ph[3], (double)it);
+                    atomicMax(&sc->ph_work_max, t_pass + t_comb);
                 }
             }
             leave();
