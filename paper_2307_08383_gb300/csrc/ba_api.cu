@@ -135,6 +135,11 @@ static void free_all(ba_problem *p) {
     p->pending.clear();
     for (auto e : p->ev_pool) cudaEventDestroy(e);
     p->ev_pool.clear();
+    for (auto &e : p->step_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
     if (p->sc_host) cudaFreeHost(p->sc_host);
     p->sc_host = nullptr;
 }
@@ -599,25 +604,6 @@ static bool split_cg(ba_problem *p) {
     return p->sv.f32 && p->opt.pcg_variant != BA_PCG_STANDARD && split_available(p);
 }
 
-static ba_status run_pcg_split(ba_problem *p, const void *rhs, double tol, int max_iters, int *iters) {
-    CK(p, launch_split_init(p, (const float *)rhs, tol, max_iters));
-    CK(p, launch_pcg_split(p));
-    ba_status s = sync_scalars(p);
-    if (s) return s;
-    if (p->opt.profile >= 2) {
-        for (int k = 0; k < 4; ++k) p->ph_sum[k] += p->sc_host->ph[k];
-        // busiest CTA's work per iteration, over the mean CTA's (load balance)
-        const double its = p->sc_host->iters > 0 ? p->sc_host->iters : 1;
-        const double mean_work = (p->sc_host->ph[0] + p->sc_host->ph[1]) / (p->sc_host->ph[3] > 0 ? p->sc_host->ph[3] : 1);
-        p->ph_imbalance = mean_work > 0 ? (double)p->sc_host->ph_work_max / its / mean_work : 0.0;
-    }
-    if (p->sc_host->err == BA_ERR_TIMEOUT) {
-        p->dead = true;
-        return fail(BA_ERR_TIMEOUT, "PCG grid all-reduce timed out");
-    }
-    *iters = p->sc_host->iters;
-    return BA_OK;
-}
 
 static ba_status solve_once_view(ba_problem *p, ba_step_info *info);
 
@@ -667,32 +653,53 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
         // reduction still missing (half of tol / rho, rho = |r|/|b| now) when
         // that is looser, so a last sweep that needs a factor of a few takes
         // a few iterations rather than a full inner solve.
+        // One host synchronisation per sweep: the first sweep always runs (r = b;
+        // a zero b stops its PCG at once), and a sweep's PCG, accumulation and
+        // residual are queued together and read back once.
         CK(p, launch_resid64(p, false));  // r64 = b, x64 implicit 0
-        if ((s = sync_scalars(p))) return s;
         bool first = true;
         for (int o = 0; o < p->opt.refine_max; ++o) {
-            if (p->sc_host->rr64 <= tol * tol * p->sc_host->bb64) { converged = true; break; }
-            if (p->sc_host->bb64 == 0.0) { converged = true; break; }
+            if (!first) {
+                if (p->sc_host->rr64 <= tol * tol * p->sc_host->bb64) { converged = true; break; }
+                if (p->sc_host->bb64 == 0.0) { converged = true; break; }
+            }
             CK(p, launch_refine_rhs(p, p->sv.pv[1]));  // r buffer doubles as the rhs (copied by init)
-            const double rho = std::sqrt(p->sc_host->rr64 / p->sc_host->bb64);
+            const double rho = first ? 1.0 : std::sqrt(p->sc_host->rr64 / p->sc_host->bb64);
             const double inner = std::min(0.5, std::max(p->opt.inner_rel_tol, 0.5 * tol / rho));
-            int it = 0;
-            if ((s = split ? run_pcg_split(p, p->sv.pv[1], inner, max_iters, &it)
-                           : run_pcg(p, p->sv.pv[1], inner, max_iters, &it)))
-                return s;
-            if ((s = check_err_flag(p))) return s;
-            total += it;
-            ++refine;
+            if (split) {
+                CK(p, launch_split_init(p, (const float *)p->sv.pv[1], inner, max_iters));
+                CK(p, launch_pcg_split(p));
+            } else {
+                CK(p, launch_pcg_init(p, p->sv.pv[1], inner, max_iters));
+                CK(p, launch_pcg_loop(p));
+            }
             CK(p, split ? launch_accumulate_split(p, first) : launch_accumulate_solution(p, first));
             first = false;
             CK(p, launch_resid64(p, true));
             if ((s = sync_scalars(p))) return s;
+            if (split && p->opt.profile >= 2) {
+                for (int k = 0; k < 4; ++k) p->ph_sum[k] += p->sc_host->ph[k];
+                // busiest CTA's work per iteration, over the mean CTA's (load balance)
+                const double its = p->sc_host->iters > 0 ? p->sc_host->iters : 1;
+                const double cta_its = p->sc_host->ph[3] > 0 ? p->sc_host->ph[3] : 1;
+                const double mean_work = (p->sc_host->ph[0] + p->sc_host->ph[1]) / cta_its;
+                p->ph_imbalance = mean_work > 0 ? (double)p->sc_host->ph_work_max / its / mean_work : 0.0;
+            }
+            if (p->sc_host->err == BA_ERR_TIMEOUT) {
+                p->dead = true;
+                return fail(BA_ERR_TIMEOUT, "PCG grid wait timed out");
+            }
+            if ((s = check_err_flag(p))) return s;
+            total += p->sc_host->iters;
+            ++refine;
         }
-        if (first) CK(p, cudaMemsetAsync(p->x64, 0, p->n * 6 * 8, p->st));
         if (!converged) converged = p->sc_host->rr64 <= tol * tol * p->sc_host->bb64;
+        CK(p, launch_solution_to_step(p));
     }
-    CK(p, launch_solution_to_step(p));
-    if ((s = sync_scalars(p))) return s;
+    if (!p->sv.f32) {
+        CK(p, launch_solution_to_step(p));
+        if ((s = sync_scalars(p))) return s;
+    }
     const double bb = p->sc_host->bb64;
     p->last_true_rel = bb > 0 ? std::sqrt(p->sc_host->rr64 / bb) : 0.0;
     // a learned M^-1 is judged by the true residual, not PCG's recurrence
@@ -755,12 +762,9 @@ ba_status ba_lm_step(ba_problem *p, ba_step_info *info) {
     if (p->rcs_only) return fail(BA_ERR_STATE, "ba_lm_step: the problem holds an RCS only");
     ba_step_info loc;
     std::memset(&loc, 0, sizeof(loc));
-    cudaEvent_t ev[6];
-    for (auto &x : ev) CK(p, cudaEventCreate(&x));
-    struct EvGuard {
-        cudaEvent_t *e;
-        ~EvGuard() { for (int k = 0; k < 6; ++k) cudaEventDestroy(e[k]); }
-    } guard{ev};
+    if (!p->step_ev[0])
+        for (auto &x : p->step_ev) CK(p, cudaEventCreate(&x));
+    cudaEvent_t *ev = p->step_ev;
     ba_status s;
     CK(p, cudaEventRecord(ev[0], p->st));
     if ((s = ensure_cost(p))) return s;

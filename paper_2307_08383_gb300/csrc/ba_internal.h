@@ -171,6 +171,7 @@ struct ba_problem {
     int64_t klaunch[ba::K_COUNT] = {};
     double kms[ba::K_COUNT] = {};
     int64_t launches = 0;  // every kernel launched on behalf of this problem
+    cudaEvent_t step_ev[6] = {};  // phase boundaries of ba_lm_step (ba_step_info.ms)
 
     // solve view and FP32 shadows (FP64 problems solved in mixed precision)
     ba::SolverView sv;
