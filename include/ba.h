@@ -93,7 +93,8 @@ typedef struct {
     double rcs_rel_resid;    /* true ||b - S dx_c|| / ||b|| in FP64 */
     int64_t n_cheirality;    /* observations with z_cam <= 1e-6 at the trial point */
     int64_t n_v_fp64;        /* points whose 3x3 V was factored in FP64 (FP32 mode) */
-    float ms[8];             /* linearize, form_rcs, solve, back_subst, eval, total, -, - */
+    float ms[8];             /* linearize, form_rcs, solve, trial cameras, back-substitution with
+                                the trial evaluation (one pass over the points), total, -, - */
 } ba_step_info;
 
 typedef struct {

@@ -45,8 +45,8 @@ ba_status set_error(ba_status s, const char *msg) { return fail(s, msg); }
 const char *kernel_name(int k) {
     static const char *names[K_COUNT] = {"prepare_state", "linearize", "cost",    "form_rcs",
                                          "rcs_reduce",    "rcs_diag",  "pcg_init", "pcg_loop",
-                                         "resid64",       "back_substitute", "update", "eval",
-                                         "demote",        "split_prepare"};
+                                         "resid64",       "back_substitute", "trial_cameras",
+                                         "demote",        "split_prepare", "step_points"};
     return (k >= 0 && k < K_COUNT) ? names[k] : nullptr;
 }
 
@@ -780,12 +780,10 @@ ba_status ba_lm_step(ba_problem *p, ba_step_info *info) {
     s = ba_solve_rcs(p, &loc);
     if (s != BA_OK && s != BA_ERR_NO_CONVERGENCE) return s;
     CK(p, cudaEventRecord(ev[3], p->st));
-    CK(p, launch_back_substitute(p));
-    p->backsub = true;
+    CK(p, launch_trial_cameras(p));
     CK(p, cudaEventRecord(ev[4], p->st));
-    CK(p, launch_apply_update(p));
-    CK(p, launch_prepare_state(p, p->trial));
-    CK(p, launch_eval(p));
+    CK(p, launch_step_points(p));  // Eq. 5 + trial point + trial cost and model, one pass
+    p->backsub = true;
     CK(p, cudaEventRecord(ev[5], p->st));
     if ((s = sync_scalars(p))) return s;
     if ((s = check_err_flag(p))) return s;

@@ -60,7 +60,7 @@ constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
 
 enum KernelId {
     K_PREPARE = 0, K_LINEARIZE, K_COST, K_FORM_RCS, K_RCS_REDUCE, K_RCS_DIAG,
-    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_EVAL, K_DEMOTE, K_SPLIT_PREP, K_COUNT
+    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_DEMOTE, K_SPLIT_PREP, K_STEP_POINTS, K_COUNT
 };
 const char *kernel_name(int k);
 
@@ -232,8 +232,10 @@ cudaError_t launch_resid64(ba_problem *p, bool from_x64);
 cudaError_t launch_solution_to_step(ba_problem *p);
 cudaError_t launch_refine_rhs(ba_problem *p, void *rhs_T);
 cudaError_t launch_back_substitute(ba_problem *p);
-cudaError_t launch_apply_update(ba_problem *p);
-cudaError_t launch_eval(ba_problem *p);
+// LM step tail: trial cameras, then the fused point pass (Eq. 5, trial points,
+// trial cost and model decrease)
+cudaError_t launch_trial_cameras(ba_problem *p);
+cudaError_t launch_step_points(ba_problem *p);
 cudaError_t launch_block_jacobi(ba_problem *p);               // Minv from the diagonal blocks of S
 cudaError_t launch_demote(ba_problem *p);                     // S32, Minv32 from the FP64 S, Minv
 // split-preconditioned FP32 CG: G, H and S^ = G^T S G from the problem's S

@@ -215,48 +215,96 @@ __global__ void k_update_cams(int n, const double *__restrict__ cams, const T *_
     }
 }
 
-template <typename T>
-__global__ void k_update_pts(int64_t P, const double *__restrict__ pts, const T *__restrict__ dxp, double *__restrict__ out) {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < 3 * P; x += (int64_t)gridDim.x * blockDim.x)
-        out[x] = pts[x] + (double)dxp[x];
+
+// X_cam of camera i and a point given by value (FP64; FP32 as hi + lo parts).
+__device__ __forceinline__ void cam_point_v(const double *camc, int i, const double *X, const float *, double *Xc) {
+    const double *c = camc + 12 * i;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Xc[r] = c[3 * r] * X[0] + c[3 * r + 1] * X[1] + c[3 * r + 2] * X[2] + c[9 + r];
+}
+__device__ __forceinline__ void cam_point_v(const float *camc, int i, const double *, const float *hl, float *Xc) {
+    const float4 *c4 = reinterpret_cast<const float4 *>(camc + 16 * i);
+    const float4 a = c4[0], b = c4[1], c = c4[2], d = c4[3];
+    const float R[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x};
+    const float Chi[3] = {c.y, c.z, c.w}, Clo[3] = {d.x, d.y, d.z};
+    float D[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) D[r] = (hl[r] - Chi[r]) + (hl[3 + r] - Clo[r]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) Xc[r] = R[3 * r] * D[0] + R[3 * r + 1] * D[1] + R[3 * r + 2] * D[2];
 }
 
-// --------------------------------------------------------------------------
-// trial evaluation: F(x (+) dx) and the model decrease
-// 1/2 (||e||^2 - ||e + J dx||^2) = -1/2 sum_a (J_a dx)^T (2 e_a + J_a dx)
-// (weighted e and J under the Huber loss), both summed in FP64
-// --------------------------------------------------------------------------
+// The LM step's point pass, one thread per point: the back-substitution of
+// Eq. 5 (dx_p = V^-1 (l_p - sum_a J_p,a^T J_c,a dx_c), V^-1 = L^-T L^-1), the
+// trial point x_p + dx_p (FP64, and its FP32 hi + lo split), and, for the
+// point's observations, the trial cost F(x (+) dx) and the model decrease
+// -1/2 sum_a (J_a dx)^T (2 e_a + J_a dx) (weighted e, J under Huber), summed in
+// FP64.  The thread reads each of its observation rows twice, the second time
+// from cache: one DRAM pass over the stored linearization instead of two.
+// (A warp-cooperative variant over batches of whole points, with a segmented
+// scan, measured slower: each batch chains more dependent loads.)  The trial
+// cameras (cache included) are formed before.
 template <typename T>
-__global__ void __launch_bounds__(256) k_eval(int64_t m, const int *__restrict__ obs_cam, const int *__restrict__ obs_pt,
-                                              const T *__restrict__ uv, const T *__restrict__ camc,
-                                              const double *__restrict__ pts, const float *__restrict__ pts_hl,
-                                              const T *__restrict__ J, const T *__restrict__ dxc,
-                                              const T *__restrict__ dxp, Intr in, int huber, double delta,
-                                              DevScalars *sc, double *red, unsigned *ctr) {
+__global__ void __launch_bounds__(256) k_step_points(int64_t P, const int *__restrict__ trk_ptr,
+                                                     const int *__restrict__ obs_cam, const T *__restrict__ uv,
+                                                     const T *__restrict__ J, const T *__restrict__ dxc,
+                                                     const T *__restrict__ Linv, const T *__restrict__ lp,
+                                                     const double *__restrict__ pts, const T *__restrict__ camc_trial,
+                                                     Intr in, int huber, double delta, T *__restrict__ dxp,
+                                                     double *__restrict__ pts_trial, float *__restrict__ hl_trial,
+                                                     DevScalars *sc, double *red, unsigned *ctr) {
     RunSum<T> f, mdl;
     int ncheir = 0;
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
-        const int i = obs_cam[a], k = obs_pt[a];
-        T Xc[3], R[9];
-        cam_point(camc, pts, pts_hl, i, k, Xc, R);
-        const T iz = T(1) / Xc[2];
-        const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
-        const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
-        f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
-        ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
-        T j[JW];
-        load_jrow(J + a * JW, j);
-        T dc[6], dp[3];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+        const int a0 = __ldg(trk_ptr + k), a1 = __ldg(trk_ptr + k + 1);
+        T s0 = lp[3 * k], s1 = lp[3 * k + 1], s2 = lp[3 * k + 2];
+        for (int a = a0; a < a1; ++a) {
+            T j[JW];
+            load_jrow(J + (int64_t)a * JW, j);
+            const T *dc = dxc + 6 * __ldg(obs_cam + a);
+            T t0 = T(0), t1 = T(0);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) dc[c] = dxc[6 * i + c];
+            for (int c = 0; c < 6; ++c) { t0 += j[c] * dc[c]; t1 += j[6 + c] * dc[c]; }
+            s0 -= j[12] * t0 + j[15] * t1;
+            s1 -= j[13] * t0 + j[16] * t1;
+            s2 -= j[14] * t0 + j[17] * t1;
+        }
+        const T *mL = Linv + 6 * k;  // m00 m10 m11 m20 m21 m22
+        const T u0 = mL[0] * s0, u1 = mL[1] * s0 + mL[2] * s1, u2 = mL[3] * s0 + mL[4] * s1 + mL[5] * s2;
+        const T dp[3] = {mL[0] * u0 + mL[1] * u1 + mL[3] * u2, mL[2] * u1 + mL[4] * u2, mL[5] * u2};
+        double Xt[3];
+        float hl[6];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dp[c] = dxp[3 * (int64_t)k + c];
-        T jd0 = T(0), jd1 = T(0);
+        for (int d = 0; d < 3; ++d) {
+            dxp[3 * k + d] = dp[d];
+            Xt[d] = pts[3 * k + d] + (double)dp[d];
+            pts_trial[3 * k + d] = Xt[d];
+            hl[d] = (float)Xt[d];
+            hl[3 + d] = (float)(Xt[d] - (double)hl[d]);
+            if (hl_trial) {
+                hl_trial[6 * k + d] = hl[d];
+                hl_trial[6 * k + 3 + d] = hl[3 + d];
+            }
+        }
+        for (int a = a0; a < a1; ++a) {
+            const int i = __ldg(obs_cam + a);
+            T Xc[3];
+            cam_point_v(camc_trial, i, Xt, hl, Xc);
+            const T iz = T(1) / Xc[2];
+            const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * (int64_t)a];
+            const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * (int64_t)a + 1];
+            f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
+            ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
+            T j[JW];
+            load_jrow(J + (int64_t)a * JW, j);
+            const T *dc = dxc + 6 * i;
+            T jd0 = T(0), jd1 = T(0);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) { jd0 += j[c] * dc[c]; jd1 += j[6 + c] * dc[c]; }
+            for (int c = 0; c < 6; ++c) { jd0 += j[c] * dc[c]; jd1 += j[6 + c] * dc[c]; }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) { jd0 += j[12 + c] * dp[c]; jd1 += j[15 + c] * dp[c]; }
-        mdl.add(-(jd0 * (T(2) * j[18] + jd0) + jd1 * (T(2) * j[19] + jd1)));
+            for (int c = 0; c < 3; ++c) { jd0 += j[12 + c] * dp[c]; jd1 += j[15 + c] * dp[c]; }
+            mdl.add(-(jd0 * (T(2) * j[18] + jd0) + jd1 * (T(2) * j[19] + jd1)));
+        }
     }
     double v[3] = {f.get(), mdl.get(), (double)ncheir};
     grid_sum<3>(v, red, ctr, [&](double *t) {
@@ -377,41 +425,43 @@ cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_update(ba_problem *p) {
+
+// trial cameras and their cache (the point pass forms the trial points)
+cudaError_t launch_trial_cameras(ba_problem *p) {
     cudaEvent_t ev;
     ktimer_begin(p, K_UPDATE, &ev);
     const int nb = (p->n + 127) / 128;
-    const int gp = grid_for(3 * p->P, 256, GRID_CAP);
     if (p->fp32) {
         k_update_cams<float><<<nb, 128, 0, p->st>>>(p->n, p->cur.cams, (const float *)p->dxc, p->trial.cams);
-        k_update_pts<float><<<gp, 256, 0, p->st>>>(p->P, p->cur.pts, (const float *)p->dxp, p->trial.pts);
+        k_prepare_cams32<<<nb, 128, 0, p->st>>>(p->n, p->trial.cams, (float *)p->trial.camc);
     } else {
         k_update_cams<double><<<nb, 128, 0, p->st>>>(p->n, p->cur.cams, (const double *)p->dxc, p->trial.cams);
-        k_update_pts<double><<<gp, 256, 0, p->st>>>(p->P, p->cur.pts, (const double *)p->dxp, p->trial.pts);
+        k_prepare_cams64<<<nb, 128, 0, p->st>>>(p->n, p->trial.cams, (double *)p->trial.camc);
     }
     ktimer_end(p, K_UPDATE, ev);
     p->launches += 2;
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval(ba_problem *p) {
+cudaError_t launch_step_points(ba_problem *p) {
     cudaEvent_t ev;
-    ktimer_begin(p, K_EVAL, &ev);
-    const int g = grid_for(p->m, 256, GRID_CAP);
+    ktimer_begin(p, K_STEP_POINTS, &ev);
+    const int g = grid_for(p->P, 256, GRID_CAP);
     const int hub = p->opt.robust == BA_LOSS_HUBER;
     if (p->fp32)
-        k_eval<float><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv32, (const float *)p->trial.camc,
-                                            p->trial.pts, p->trial.pts_hl, (const float *)p->J, (const float *)p->dxc,
-                                            (const float *)p->dxp, intr_of(p), hub, p->opt.huber_delta, p->sc,
-                                            p->red, p->counters + 1);
+        k_step_points<float><<<g, 256, 0, p->st>>>(
+            p->P, p->trk_ptr, p->obs_cam, p->uv32, (const float *)p->J, (const float *)p->dxc,
+            (const float *)p->Linv, (const float *)p->lp, p->cur.pts, (const float *)p->trial.camc, intr_of(p), hub,
+            p->opt.huber_delta, (float *)p->dxp, p->trial.pts, p->trial.pts_hl, p->sc, p->red, p->counters + 1);
     else
-        k_eval<double><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv64, (const double *)p->trial.camc,
-                                             p->trial.pts, nullptr, (const double *)p->J, (const double *)p->dxc,
-                                             (const double *)p->dxp, intr_of(p), hub, p->opt.huber_delta, p->sc,
-                                             p->red, p->counters + 1);
-    ktimer_end(p, K_EVAL, ev);
+        k_step_points<double><<<g, 256, 0, p->st>>>(
+            p->P, p->trk_ptr, p->obs_cam, p->uv64, (const double *)p->J, (const double *)p->dxc,
+            (const double *)p->Linv, (const double *)p->lp, p->cur.pts, (const double *)p->trial.camc, intr_of(p),
+            hub, p->opt.huber_delta, (double *)p->dxp, p->trial.pts, nullptr, p->sc, p->red, p->counters + 1);
+    ktimer_end(p, K_STEP_POINTS, ev);
     p->launches += 1;
     return cudaGetLastError();
 }
+
 
 }  // namespace ba
