@@ -12,6 +12,7 @@
 // subtraction of two large world coordinates loses nothing before the FP32
 // rotation.
 #include "device_util.cuh"
+#include "tma_util.cuh"
 
 namespace ba {
 
@@ -216,6 +217,24 @@ __global__ void k_update_cams(int n, const double *__restrict__ cams, const T *_
 }
 
 
+// One staged observation row (JW values, 16-byte aligned) from shared memory.
+__device__ __forceinline__ void load_jrow_s(const float *s, float (&v)[JW]) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(s);
+#pragma unroll
+    for (int q = 0; q < JW / 4; ++q) {
+        const float4 t = s4[q];
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_jrow_s(const double *s, double (&v)[JW]) {
+    const double2 *s2 = reinterpret_cast<const double2 *>(s);
+#pragma unroll
+    for (int q = 0; q < JW / 2; ++q) {
+        const double2 t = s2[q];
+        v[2 * q] = t.x; v[2 * q + 1] = t.y;
+    }
+}
+
 // X_cam of camera i and a point given by value (FP64; FP32 as hi + lo parts).
 __device__ __forceinline__ void cam_point_v(const double *camc, int i, const double *X, const float *, double *Xc) {
     const double *c = camc + 12 * i;
@@ -234,77 +253,155 @@ __device__ __forceinline__ void cam_point_v(const float *camc, int i, const doub
     for (int r = 0; r < 3; ++r) Xc[r] = R[3 * r] * D[0] + R[3 * r + 1] * D[1] + R[3 * r + 2] * D[2];
 }
 
-// The LM step's point pass, one thread per point: the back-substitution of
-// Eq. 5 (dx_p = V^-1 (l_p - sum_a J_p,a^T J_c,a dx_c), V^-1 = L^-T L^-1), the
-// trial point x_p + dx_p (FP64, and its FP32 hi + lo split), and, for the
-// point's observations, the trial cost F(x (+) dx) and the model decrease
-// -1/2 sum_a (J_a dx)^T (2 e_a + J_a dx) (weighted e, J under Huber), summed in
-// FP64.  The thread reads each of its observation rows twice, the second time
-// from cache: one DRAM pass over the stored linearization instead of two.
-// (A warp-cooperative variant over batches of whole points, with a segmented
-// scan, measured slower: each batch chains more dependent loads.)  The trial
-// cameras (cache included) are formed before.
+// The LM step's point pass: the back-substitution of Eq. 5
+// (dx_p = V^-1 (l_p - sum_a J_p,a^T J_c,a dx_c), V^-1 = L^-T L^-1), the trial
+// point x_p + dx_p (FP64, and its FP32 hi + lo split), and for every
+// observation the trial cost F(x (+) dx) and the model decrease
+// -1/2 sum_a (J_a dx)^T (2 e_a + J_a dx) (weighted e, J under Huber), summed
+// in FP64.  It runs over the RCS formation's point groups (whole tracks,
+// <= obs_max observations, contiguous rows): a persistent CTA copies a
+// group's rows into shared memory with one bulk copy (double-buffered, the
+// next group's copy in flight), a thread per point solves Eq. 5 from shared
+// memory and keeps dx_p and the trial point there, then a thread per
+// observation evaluates it from shared memory.  The stored linearization is
+// read from DRAM once, in whole contiguous ranges, at any problem size (a
+// thread per point re-reading its rows from cache, and a warp-cooperative
+// variant over batches of points, both measured slower).  The trial cameras
+// (cache included) are formed before.
 template <typename T>
-__global__ void __launch_bounds__(256) k_step_points(int64_t P, const int *__restrict__ trk_ptr,
-                                                     const int *__restrict__ obs_cam, const T *__restrict__ uv,
+__global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict__ grp, int ngroups,
+                                                     const int *__restrict__ trk_ptr, const int *__restrict__ obs_cam,
+                                                     const int *__restrict__ obs_pt, const T *__restrict__ uv,
                                                      const T *__restrict__ J, const T *__restrict__ dxc,
                                                      const T *__restrict__ Linv, const T *__restrict__ lp,
                                                      const double *__restrict__ pts, const T *__restrict__ camc_trial,
                                                      Intr in, int huber, double delta, T *__restrict__ dxp,
                                                      double *__restrict__ pts_trial, float *__restrict__ hl_trial,
-                                                     DevScalars *sc, double *red, unsigned *ctr) {
+                                                     DevScalars *sc, double *red, unsigned *ctr, int obs_max,
+                                                     long long limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ GroupDesc sdesc[2];
+    __shared__ int s_ok;
+    const size_t buf_bytes = (size_t)obs_max * JW * sizeof(T);
+    // per point of the current group: dx_p (3 T), trial point (3 double), its split (6 float);
+    // per observation: J_p^T J_c dx_c (3 T), J_c dx_c (2 T), the camera
+    T *s_dp = reinterpret_cast<T *>(smem_raw + 2 * buf_bytes);
+    double *s_xt = reinterpret_cast<double *>(smem_raw + 2 * buf_bytes + (size_t)obs_max / 2 * 3 * sizeof(T));
+    float *s_hl = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s_xt) + (size_t)obs_max / 2 * 3 * 8);
+    T *s_c3 = reinterpret_cast<T *>(s_hl + (size_t)obs_max / 2 * 6);
+    T *s_jc = s_c3 + (size_t)obs_max * 3;
+    int *s_cam = reinterpret_cast<int *>(s_jc + (size_t)obs_max * 2);
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    auto issue = [&](int gi, int b) {
+        const GroupDesc d = grp[gi];
+        sdesc[b] = d;
+        const uint32_t jb = (uint32_t)d.nobs * JW * (uint32_t)sizeof(T);
+        fence_proxy_async();
+        mbar_expect_tx(&mbar[b], jb);
+        bulk_g2s(smem_raw + b * buf_bytes, J + (int64_t)d.obs_begin * JW, jb, &mbar[b]);
+    };
     RunSum<T> f, mdl;
     int ncheir = 0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-        const int a0 = __ldg(trk_ptr + k), a1 = __ldg(trk_ptr + k + 1);
-        T s0 = lp[3 * k], s1 = lp[3 * k + 1], s2 = lp[3 * k + 2];
-        for (int a = a0; a < a1; ++a) {
+    const T dl = (T)delta;
+    uint32_t parity = 0u, pending = 0u;
+    int gi = blockIdx.x;
+    if (threadIdx.x == 0 && gi < ngroups) issue(gi, 0);
+    if (gi < ngroups) pending |= 1u;
+    for (int k = 0; gi < ngroups; gi += gridDim.x, ++k) {
+        const int bsel = k & 1;
+        const int gn = gi + gridDim.x;
+        if (gn < ngroups) {
+            if (threadIdx.x == 0) issue(gn, bsel ^ 1);
+            pending |= 1u << (bsel ^ 1);
+        }
+        if (threadIdx.x == 0) s_ok = mbar_wait(&mbar[bsel], (parity >> bsel) & 1u, limit) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok) {
+            // give up: flag it, let the copies still in flight land (bounded), leave
+            if (threadIdx.x == 0) {
+                atomicExch(&sc->err, (int)BA_ERR_TIMEOUT);
+                mbar_wait(&mbar[bsel], (parity >> bsel) & 1u, limit);
+                if ((pending >> (bsel ^ 1)) & 1u) mbar_wait(&mbar[bsel ^ 1], (parity >> (bsel ^ 1)) & 1u, limit);
+            }
+            return;
+        }
+        parity ^= 1u << bsel;
+        pending &= ~(1u << bsel);
+        const GroupDesc g = sdesc[bsel];
+        const T *so = reinterpret_cast<const T *>(smem_raw + bsel * buf_bytes);
+        // per observation: J_c dx_c and its image J_p^T J_c dx_c under J_p
+        for (int al = threadIdx.x; al < g.nobs; al += blockDim.x) {
+            const int i = __ldg(obs_cam + g.obs_begin + al);
+            const T *dc = dxc + 6 * i;
             T j[JW];
-            load_jrow(J + (int64_t)a * JW, j);
-            const T *dc = dxc + 6 * __ldg(obs_cam + a);
+            load_jrow_s(so + al * JW, j);
             T t0 = T(0), t1 = T(0);
 #pragma unroll
             for (int c = 0; c < 6; ++c) { t0 += j[c] * dc[c]; t1 += j[6 + c] * dc[c]; }
-            s0 -= j[12] * t0 + j[15] * t1;
-            s1 -= j[13] * t0 + j[16] * t1;
-            s2 -= j[14] * t0 + j[17] * t1;
-        }
-        const T *mL = Linv + 6 * k;  // m00 m10 m11 m20 m21 m22
-        const T u0 = mL[0] * s0, u1 = mL[1] * s0 + mL[2] * s1, u2 = mL[3] * s0 + mL[4] * s1 + mL[5] * s2;
-        const T dp[3] = {mL[0] * u0 + mL[1] * u1 + mL[3] * u2, mL[2] * u1 + mL[4] * u2, mL[5] * u2};
-        double Xt[3];
-        float hl[6];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            dxp[3 * k + d] = dp[d];
-            Xt[d] = pts[3 * k + d] + (double)dp[d];
-            pts_trial[3 * k + d] = Xt[d];
-            hl[d] = (float)Xt[d];
-            hl[3 + d] = (float)(Xt[d] - (double)hl[d]);
-            if (hl_trial) {
-                hl_trial[6 * k + d] = hl[d];
-                hl_trial[6 * k + 3 + d] = hl[3 + d];
+            for (int d = 0; d < 3; ++d) s_c3[3 * al + d] = j[12 + d] * t0 + j[15 + d] * t1;
+            s_jc[2 * al] = t0;
+            s_jc[2 * al + 1] = t1;
+            s_cam[al] = i;
+        }
+        __syncthreads();
+        // Eq. 5 per point: dx_p = L^-T L^-1 (l_p - sum over the track)
+        for (int pl = threadIdx.x; pl < g.npts; pl += blockDim.x) {
+            const int64_t kp = (int64_t)g.pt_begin + pl;
+            const int a0 = __ldg(trk_ptr + kp) - g.obs_begin, a1 = __ldg(trk_ptr + kp + 1) - g.obs_begin;
+            T s0 = lp[3 * kp], s1 = lp[3 * kp + 1], s2 = lp[3 * kp + 2];
+            for (int a = a0; a < a1; ++a) {
+                s0 -= s_c3[3 * a];
+                s1 -= s_c3[3 * a + 1];
+                s2 -= s_c3[3 * a + 2];
+            }
+            const T *mL = Linv + 6 * kp;  // m00 m10 m11 m20 m21 m22
+            const T u0 = mL[0] * s0, u1 = mL[1] * s0 + mL[2] * s1, u2 = mL[3] * s0 + mL[4] * s1 + mL[5] * s2;
+            const T dp[3] = {mL[0] * u0 + mL[1] * u1 + mL[3] * u2, mL[2] * u1 + mL[4] * u2, mL[5] * u2};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double x = pts[3 * kp + d] + (double)dp[d];
+                const float h = (float)x, l = (float)(x - (double)h);
+                dxp[3 * kp + d] = dp[d];
+                pts_trial[3 * kp + d] = x;
+                if (hl_trial) {
+                    hl_trial[6 * kp + d] = h;
+                    hl_trial[6 * kp + 3 + d] = l;
+                }
+                s_dp[3 * pl + d] = dp[d];
+                s_xt[3 * pl + d] = x;
+                s_hl[6 * pl + d] = h;
+                s_hl[6 * pl + 3 + d] = l;
             }
         }
-        for (int a = a0; a < a1; ++a) {
-            const int i = __ldg(obs_cam + a);
+        __syncthreads();
+        // the trial cost and the model decrease, one thread per observation
+        for (int al = threadIdx.x; al < g.nobs; al += blockDim.x) {
+            const int64_t a = (int64_t)g.obs_begin + al;
+            const int i = s_cam[al], pl = __ldg(obs_pt + a) - g.pt_begin;
             T Xc[3];
-            cam_point_v(camc_trial, i, Xt, hl, Xc);
+            cam_point_v(camc_trial, i, s_xt + 3 * pl, s_hl + 6 * pl, Xc);
             const T iz = T(1) / Xc[2];
-            const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * (int64_t)a];
-            const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * (int64_t)a + 1];
-            f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
+            const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
+            const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
+            f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, dl));
             ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
-            T j[JW];
-            load_jrow(J + (int64_t)a * JW, j);
-            const T *dc = dxc + 6 * i;
-            T jd0 = T(0), jd1 = T(0);
+            const T *jr = so + al * JW;
+            T jd0 = s_jc[2 * al], jd1 = s_jc[2 * al + 1];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) { jd0 += j[c] * dc[c]; jd1 += j[6 + c] * dc[c]; }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) { jd0 += j[12 + c] * dp[c]; jd1 += j[15 + c] * dp[c]; }
-            mdl.add(-(jd0 * (T(2) * j[18] + jd0) + jd1 * (T(2) * j[19] + jd1)));
+            for (int c = 0; c < 3; ++c) {
+                jd0 += jr[12 + c] * s_dp[3 * pl + c];
+                jd1 += jr[15 + c] * s_dp[3 * pl + c];
+            }
+            mdl.add(-(jd0 * (T(2) * jr[18] + jd0) + jd1 * (T(2) * jr[19] + jd1)));
         }
+        __syncthreads();  // buffer and point area free for the next group
     }
     double v[3] = {f.get(), mdl.get(), (double)ncheir};
     grid_sum<3>(v, red, ctr, [&](double *t) {
@@ -443,24 +540,44 @@ cudaError_t launch_trial_cameras(ba_problem *p) {
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t step_groups_T(ba_problem *p, long long limit) {
+    static int ctas_per_sm = -1, n_sm = 0;
+    const size_t smem = 2 * (size_t)p->obs_max * JW * sizeof(T) +
+                        (size_t)p->obs_max / 2 * (3 * sizeof(T) + 3 * sizeof(double) + 6 * sizeof(float)) +
+                        (size_t)p->obs_max * (5 * sizeof(T) + sizeof(int));
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_step_groups<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    if (ctas_per_sm < 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_step_groups<T>, 256, smem)) !=
+            cudaSuccess)
+            return e;
+        if (ctas_per_sm < 1) ctas_per_sm = 1;
+    }
+    const int grid = (int)std::min<int64_t>(p->ngroups, (int64_t)ctas_per_sm * n_sm);
+    const int hub = p->opt.robust == BA_LOSS_HUBER;
+    k_step_groups<T><<<grid, 256, smem, p->st>>>(
+        p->grp, (int)p->ngroups, p->trk_ptr, p->obs_cam, p->obs_pt, (const T *)(p->fp32 ? (const void *)p->uv32
+                                                                                        : (const void *)p->uv64),
+        (const T *)p->J, (const T *)p->dxc, (const T *)p->Linv, (const T *)p->lp, p->cur.pts,
+        (const T *)p->trial.camc, intr_of(p), hub, p->opt.huber_delta, (T *)p->dxp, p->trial.pts,
+        p->fp32 ? p->trial.pts_hl : nullptr, p->sc, p->red, p->counters + 1, p->obs_max, limit);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step_points(ba_problem *p) {
     cudaEvent_t ev;
     ktimer_begin(p, K_STEP_POINTS, &ev);
-    const int g = grid_for(p->P, 256, GRID_CAP);
-    const int hub = p->opt.robust == BA_LOSS_HUBER;
-    if (p->fp32)
-        k_step_points<float><<<g, 256, 0, p->st>>>(
-            p->P, p->trk_ptr, p->obs_cam, p->uv32, (const float *)p->J, (const float *)p->dxc,
-            (const float *)p->Linv, (const float *)p->lp, p->cur.pts, (const float *)p->trial.camc, intr_of(p), hub,
-            p->opt.huber_delta, (float *)p->dxp, p->trial.pts, p->trial.pts_hl, p->sc, p->red, p->counters + 1);
-    else
-        k_step_points<double><<<g, 256, 0, p->st>>>(
-            p->P, p->trk_ptr, p->obs_cam, p->uv64, (const double *)p->J, (const double *)p->dxc,
-            (const double *)p->Linv, (const double *)p->lp, p->cur.pts, (const double *)p->trial.camc, intr_of(p),
-            hub, p->opt.huber_delta, (double *)p->dxp, p->trial.pts, nullptr, p->sc, p->red, p->counters + 1);
+    const long long limit = 4000000000LL;  // ~2 s of SM clock per copy wait
+    const cudaError_t e = p->fp32 ? step_groups_T<float>(p, limit) : step_groups_T<double>(p, limit);
     ktimer_end(p, K_STEP_POINTS, ev);
     p->launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 

@@ -215,12 +215,12 @@ def _nearest_tracks(rng, cam_xy, pts_xy, L, chunk=1 << 20):
 def aerial_scene(n_along=100, n_across=50, n_pts=1_000_000, along_m=40.0, across_m=70.0,
                  height=100.0, track_mean=5.0, track_max=20, seed=2001, sigma_px=1.0,
                  rot_sd=0.01, t_sd=0.05, pt_sd=0.1, yaw_sd=0.02, outlier_frac=0.0,
-                 origin=(0.0, 0.0), name="aerial") -> Scene:
+                 origin=(0.0, 0.0), name="aerial", track_min=2) -> Scene:
     """Nadir cameras on an n_along x n_across flight grid over sinusoidal terrain.
 
     Default: 50 x 100 = 5,000 cameras at 100 m (100 m footprint at f = 1000 px),
     40 m along track (60% forward overlap), 70 m across (30% side overlap),
-    1M points uniform in xy, track length L = 2 + Geometric (mean 5, max 20),
+    1M points uniform in xy, track length L = track_min + Geometric (mean 5, min 2, max 20),
     the L cameras being the nearest camera centres in xy (image bounds are not
     enforced: tracks of 20 do not fit a 60/30 overlap).
     """
@@ -234,7 +234,7 @@ def aerial_scene(n_along=100, n_across=50, n_pts=1_000_000, along_m=40.0, across
     x = rng.uniform(cx.min(), cx.max(), n_pts)
     y = rng.uniform(cy.min(), cy.max(), n_pts)
     pts = np.stack([x, y, _terrain(x, y)], 1)
-    L = _geom_track(rng, n_pts, track_mean, 2, track_max)
+    L = _geom_track(rng, n_pts, track_mean, track_min, track_max)
     obs_cam, obs_pt = _nearest_tracks(rng, centers[:, :2], pts[:, :2], L)
     return _finish(name, Rw2c, centers, pts, obs_cam, obs_pt, rng, sigma_px, rot_sd, t_sd, pt_sd,
                    outlier_frac=outlier_frac,
@@ -313,3 +313,12 @@ def shuffled(scene: Scene, seed: int = 0) -> Scene:
     p = rng.permutation(scene.n_obs)
     return dataclasses.replace(scene, obs_cam=scene.obs_cam[p], obs_pt=scene.obs_pt[p],
                                obs_uv=scene.obs_uv[p])
+
+
+def capacity_scene(seed=5001, n_along=500, n_across=400, n_pts=40_000_000) -> Scene:
+    """The capacity workload: 200,000 nadir cameras on a 400 x 500 flight grid,
+    40M points, tracks L = 5 + Geometric (parameter 6.5, redrawn above 9) of
+    the nearest cameras: a realised mean of about 6.1, so about 243M
+    observations, and about 33 co-visible cameras per camera."""
+    return aerial_scene(n_along=n_along, n_across=n_across, n_pts=n_pts, track_mean=6.5, track_max=9,
+                        track_min=5, seed=seed, name="capacity")
