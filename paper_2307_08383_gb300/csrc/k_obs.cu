@@ -260,8 +260,9 @@ __device__ __forceinline__ void cam_point_v(const float *camc, int i, const doub
 // -1/2 sum_a (J_a dx)^T (2 e_a + J_a dx) (weighted e, J under Huber), summed
 // in FP64.  It runs over the RCS formation's point groups (whole tracks,
 // <= obs_max observations, contiguous rows): a persistent CTA copies a
-// group's rows into shared memory with one bulk copy (double-buffered, the
-// next group's copy in flight), a thread per point solves Eq. 5 from shared
+// group's rows into shared memory with one bulk copy (one buffer, so that
+// three CTAs fit on an SM), a thread per observation forms J_c dx_c and
+// J_p^T J_c dx_c, a thread per point solves Eq. 5 from shared
 // memory and keeps dx_p and the trial point there, then a thread per
 // observation evaluates it from shared memory.  The stored linearization is
 // read from DRAM once, in whole contiguous ranges, at any problem size (a
@@ -280,61 +281,54 @@ __global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict
                                                      DevScalars *sc, double *red, unsigned *ctr, int obs_max,
                                                      long long limit) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ GroupDesc sdesc[2];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ GroupDesc sdesc;
     __shared__ int s_ok;
+    // one row buffer (more CTAs per SM rather than a second buffer); per point
+    // of the current group dx_p (3 T), its trial split (6 float) and, FP64
+    // only, the trial point (3 double); per observation J_p^T J_c dx_c (3 T),
+    // J_c dx_c (2 T) and the camera
     const size_t buf_bytes = (size_t)obs_max * JW * sizeof(T);
-    // per point of the current group: dx_p (3 T), trial point (3 double), its split (6 float);
-    // per observation: J_p^T J_c dx_c (3 T), J_c dx_c (2 T), the camera
-    T *s_dp = reinterpret_cast<T *>(smem_raw + 2 * buf_bytes);
-    double *s_xt = reinterpret_cast<double *>(smem_raw + 2 * buf_bytes + (size_t)obs_max / 2 * 3 * sizeof(T));
-    float *s_hl = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s_xt) + (size_t)obs_max / 2 * 3 * 8);
-    T *s_c3 = reinterpret_cast<T *>(s_hl + (size_t)obs_max / 2 * 6);
+    const size_t np = (size_t)obs_max / 2;
+    T *s_dp = reinterpret_cast<T *>(smem_raw + buf_bytes);
+    float *s_hl = reinterpret_cast<float *>(s_dp + np * 3);
+    double *s_xt = reinterpret_cast<double *>(smem_raw + buf_bytes + np * (3 * sizeof(T) + 6 * sizeof(float)));
+    T *s_c3 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s_xt) + (sizeof(T) == 8 ? np * 24 : 0));
     T *s_jc = s_c3 + (size_t)obs_max * 3;
     int *s_cam = reinterpret_cast<int *>(s_jc + (size_t)obs_max * 2);
     if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        mbar_init(&mbar, 1);
         fence_proxy_async();
     }
     __syncthreads();
-    auto issue = [&](int gi, int b) {
+    auto issue = [&](int gi) {
         const GroupDesc d = grp[gi];
-        sdesc[b] = d;
+        sdesc = d;
         const uint32_t jb = (uint32_t)d.nobs * JW * (uint32_t)sizeof(T);
         fence_proxy_async();
-        mbar_expect_tx(&mbar[b], jb);
-        bulk_g2s(smem_raw + b * buf_bytes, J + (int64_t)d.obs_begin * JW, jb, &mbar[b]);
+        mbar_expect_tx(&mbar, jb);
+        bulk_g2s(smem_raw, J + (int64_t)d.obs_begin * JW, jb, &mbar);
     };
     RunSum<T> f, mdl;
     int ncheir = 0;
     const T dl = (T)delta;
-    uint32_t parity = 0u, pending = 0u;
+    uint32_t parity = 0u;
     int gi = blockIdx.x;
-    if (threadIdx.x == 0 && gi < ngroups) issue(gi, 0);
-    if (gi < ngroups) pending |= 1u;
-    for (int k = 0; gi < ngroups; gi += gridDim.x, ++k) {
-        const int bsel = k & 1;
-        const int gn = gi + gridDim.x;
-        if (gn < ngroups) {
-            if (threadIdx.x == 0) issue(gn, bsel ^ 1);
-            pending |= 1u << (bsel ^ 1);
-        }
-        if (threadIdx.x == 0) s_ok = mbar_wait(&mbar[bsel], (parity >> bsel) & 1u, limit) ? 1 : 0;
+    if (threadIdx.x == 0 && gi < ngroups) issue(gi);
+    for (; gi < ngroups; gi += gridDim.x) {
+        if (threadIdx.x == 0) s_ok = mbar_wait(&mbar, parity, limit) ? 1 : 0;
         __syncthreads();
         if (!s_ok) {
-            // give up: flag it, let the copies still in flight land (bounded), leave
+            // give up: flag it, let the copy still in flight land (bounded), leave
             if (threadIdx.x == 0) {
                 atomicExch(&sc->err, (int)BA_ERR_TIMEOUT);
-                mbar_wait(&mbar[bsel], (parity >> bsel) & 1u, limit);
-                if ((pending >> (bsel ^ 1)) & 1u) mbar_wait(&mbar[bsel ^ 1], (parity >> (bsel ^ 1)) & 1u, limit);
+                mbar_wait(&mbar, parity, limit);
             }
             return;
         }
-        parity ^= 1u << bsel;
-        pending &= ~(1u << bsel);
-        const GroupDesc g = sdesc[bsel];
-        const T *so = reinterpret_cast<const T *>(smem_raw + bsel * buf_bytes);
+        parity ^= 1u;
+        const GroupDesc g = sdesc;
+        const T *so = reinterpret_cast<const T *>(smem_raw);
         // per observation: J_c dx_c and its image J_p^T J_c dx_c under J_p
         for (int al = threadIdx.x; al < g.nobs; al += blockDim.x) {
             const int i = __ldg(obs_cam + g.obs_begin + al);
@@ -375,7 +369,7 @@ __global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict
                     hl_trial[6 * kp + 3 + d] = l;
                 }
                 s_dp[3 * pl + d] = dp[d];
-                s_xt[3 * pl + d] = x;
+                if (sizeof(T) == 8) s_xt[3 * pl + d] = x;
                 s_hl[6 * pl + d] = h;
                 s_hl[6 * pl + 3 + d] = l;
             }
@@ -402,6 +396,8 @@ __global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict
             mdl.add(-(jd0 * (T(2) * jr[18] + jd0) + jd1 * (T(2) * jr[19] + jd1)));
         }
         __syncthreads();  // buffer and point area free for the next group
+        const int gn = gi + gridDim.x;
+        if (threadIdx.x == 0 && gn < ngroups) issue(gn);
     }
     double v[3] = {f.get(), mdl.get(), (double)ncheir};
     grid_sum<3>(v, red, ctr, [&](double *t) {
@@ -543,8 +539,8 @@ cudaError_t launch_trial_cameras(ba_problem *p) {
 template <typename T>
 static cudaError_t step_groups_T(ba_problem *p, long long limit) {
     static int ctas_per_sm = -1, n_sm = 0;
-    const size_t smem = 2 * (size_t)p->obs_max * JW * sizeof(T) +
-                        (size_t)p->obs_max / 2 * (3 * sizeof(T) + 3 * sizeof(double) + 6 * sizeof(float)) +
+    const size_t smem = (size_t)p->obs_max * JW * sizeof(T) +
+                        (size_t)p->obs_max / 2 * (3 * sizeof(T) + 6 * sizeof(float) + (sizeof(T) == 8 ? 24 : 0)) +
                         (size_t)p->obs_max * (5 * sizeof(T) + sizeof(int));
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_step_groups<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
