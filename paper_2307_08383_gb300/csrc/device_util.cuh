@@ -310,18 +310,22 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
 // `gen` numbers this kernel's calls 0, 1, 2, ...  Each CTA stores its NV
 // partials (v, valid in warp 0 as block_sum leaves them) in half (gen & 1)
 // of `part` (2 * gridDim.x * AR_NV_MAX doubles), announces itself with a release
-// add, waits (bounded) until (gen + 1) * gridDim.x arrivals, and then adds
-// all partials itself in CTA order with a fixed lane order and shuffle tree,
-// so every CTA obtains the same bits without a broadcast round trip.  A half
-// is written again only two calls later, by a CTA that has passed call
-// gen + 1, which every CTA enters after reading the partials of call gen.
-// On return every thread holds the totals; false on timeout.
+// add and waits (bounded) until (gen + 1) * gridDim.x arrivals.  Then every
+// thread loads the partials of CTAs threadIdx.x, threadIdx.x + blockDim.x, ...
+// (its loads issued together: one L2 round trip) and a block sum joins them,
+// an order fixed by the launch shape, so every CTA obtains the same bits
+// without a broadcast round trip.  A half is written again only two calls
+// later, by a CTA that has passed call gen + 1, which every CTA enters after
+// reading the partials of call gen.  On return every thread holds the totals;
+// false on timeout.  The shared totals are rewritten by the next call only
+// after its first barrier, which every thread reaches after reading them.
 constexpr int AR_NV_MAX = 4;
 template <int NV>
 __device__ __forceinline__ bool grid_allreduce_sym(double (&v)[NV], double *part, unsigned gen, unsigned *bar,
                                                    int *err, long long limit_cycles) {
     static_assert(NV <= AR_NV_MAX, "too many values");
     __shared__ double s_tot[NV];
+    __shared__ double s_red[NV * 32];
     __shared__ int s_ok;
     double *half = part + (size_t)(gen & 1u) * gridDim.x * AR_NV_MAX;
     if (threadIdx.x == 0) {
@@ -340,27 +344,32 @@ __device__ __forceinline__ bool grid_allreduce_sym(double (&v)[NV], double *part
         }
         s_ok = ok;
     }
-    if (threadIdx.x < 32) {
-        __syncwarp();
-        const int lane = threadIdx.x;
-        double acc[NV];
+    __syncthreads();  // thread 0's acquire orders every thread's partial reads
+    const bool ok = s_ok != 0;
+    double acc[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-        if (s_ok)
-            for (unsigned b = lane; b < gridDim.x; b += 32)
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    if (ok) {
+        const unsigned b0 = threadIdx.x, b1 = threadIdx.x + blockDim.x;
+        double t0[NV], t1[NV];
 #pragma unroll
-                for (int k = 0; k < NV; ++k) acc[k] += __ldcg(half + b * AR_NV_MAX + k);
+        for (int k = 0; k < NV; ++k) {
+            t0[k] = b0 < gridDim.x ? __ldcg(half + b0 * AR_NV_MAX + k) : 0.0;
+            t1[k] = b1 < gridDim.x ? __ldcg(half + b1 * AR_NV_MAX + k) : 0.0;
+        }
 #pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = warp_sum(acc[k]);
-        if (lane == 0)
+        for (int k = 0; k < NV; ++k) acc[k] = t0[k] + t1[k];
+        for (unsigned b = threadIdx.x + 2 * blockDim.x; b < gridDim.x; b += blockDim.x)
 #pragma unroll
-            for (int k = 0; k < NV; ++k) s_tot[k] = acc[k];
+            for (int k = 0; k < NV; ++k) acc[k] += __ldcg(half + b * AR_NV_MAX + k);
     }
+    block_sum<NV>(acc, s_red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s_tot[k] = acc[k];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = s_tot[k];
-    const bool ok = s_ok != 0;
-    __syncthreads();
     return ok;
 }
 
@@ -430,13 +439,22 @@ __device__ __forceinline__ void block_sum_df(df32 (&v)[NV], float2 *sh) {
 // slots): every CTA adds all partials itself in CTA order.  Arrivals are
 // spread over AR_SUB counters, one per 128-byte line (CTA c announces itself
 // on counter c % AR_SUB), so the release adds of a large grid do not queue on
-// one address; lanes 0..AR_SUB-1 of warp 0 each poll one counter.  `bar`
-// holds AR_SUB * 32 words, zero at launch.  On return the totals are valid
-// in thread 0 only (as doubles, hi + lo); false on timeout.
+// one address; lanes 0..AR_SUB-1 of warp 0 each poll one counter.  Once all
+// have arrived, every thread of the CTA loads the partials of CTAs
+// threadIdx.x, threadIdx.x + blockDim.x, ... (all loads of a thread issued
+// before its adds, so the grid's partials cost one L2 round trip instead of
+// gridDim.x / 32 dependent ones), and a block sum joins them: a fixed order
+// for a given launch shape, so every CTA gets the same bits.  `bar` holds
+// AR_SUB * 32 words, zero at launch; `sh` holds NV * warps float2, `s_ok` is
+// shared.  Every thread of the CTA calls this (it holds __syncthreads); the
+// CTA's own partial is v as left by block_sum_df (valid in warp 0).  On return
+// the totals are valid in thread 0 only (as doubles, hi + lo); false on
+// timeout.
 constexpr int AR_SUB = 16;
 template <int NV>
 __device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, unsigned gen, unsigned *bar,
-                                                  int *err, long long limit_cycles, double (&tot)[NV]) {
+                                                  int *err, long long limit_cycles, double (&tot)[NV], float2 *sh,
+                                                  int *s_ok) {
     static_assert(NV <= AR_NV_MAX, "too many values");
     float2 *half = reinterpret_cast<float2 *>(part + (size_t)(gen & 1u) * gridDim.x * AR_NV_MAX);
     if (threadIdx.x == 0) {
@@ -444,7 +462,6 @@ __device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, u
         for (int k = 0; k < NV; ++k) __stcg(half + blockIdx.x * AR_NV_MAX + k, make_float2(v[k].hi, v[k].lo));
         red_add_release(bar + 32 * (blockIdx.x % AR_SUB), 1u);
     }
-    bool ok = true;
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         int lane_ok = 1;
@@ -460,25 +477,40 @@ __device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, u
                 }
             }
         }
-        ok = __all_sync(0xffffffffu, lane_ok) != 0;
-        __syncwarp();  // each lane's acquire orders the partial reads of every lane
-        if (!ok && lane == 0) atomicExch(err, (int)BA_ERR_TIMEOUT);
-        df32 acc[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = df32{0.f, 0.f};
-        if (ok)
-            for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
-#pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    const float2 t = __ldcg(half + b * AR_NV_MAX + k);
-                    acc[k] = df_add(acc[k], df32{t.x, t.y});
-                }
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            acc[k] = warp_sum_df(acc[k]);
-            tot[k] = (double)acc[k].hi + (double)acc[k].lo;
+        const bool ok = __all_sync(0xffffffffu, lane_ok) != 0;
+        if (lane == 0) {
+            *s_ok = ok ? 1 : 0;
+            if (!ok) atomicExch(err, (int)BA_ERR_TIMEOUT);
         }
     }
+    __syncthreads();  // the pollers' acquires order every thread's partial reads
+    const bool ok = *s_ok != 0;
+    df32 acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = df32{0.f, 0.f};
+    if (ok) {
+        const unsigned b0 = threadIdx.x, b1 = threadIdx.x + blockDim.x;
+        float2 t0[NV], t1[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            t0[k] = b0 < gridDim.x ? __ldcg(half + b0 * AR_NV_MAX + k) : make_float2(0.f, 0.f);
+            t1[k] = b1 < gridDim.x ? __ldcg(half + b1 * AR_NV_MAX + k) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            acc[k] = df_add(df32{t0[k].x, t0[k].y}, df32{t1[k].x, t1[k].y});
+        }
+        for (unsigned b = threadIdx.x + 2 * blockDim.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const float2 u = __ldcg(half + b * AR_NV_MAX + k);
+                acc[k] = df_add(acc[k], df32{u.x, u.y});
+            }
+    }
+    block_sum_df<NV>(acc, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] = (double)acc[k].hi + (double)acc[k].lo;
     return ok;
 }
 

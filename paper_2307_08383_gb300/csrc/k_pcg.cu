@@ -818,6 +818,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
     // FP64 rate is far below FP32: no other thread does FP64 arithmetic).
     __shared__ float2 sh_df[3 * SPLIT_WARPS];
     __shared__ int s_ctl;  // 0 go on, 1 stop, 2 not SPD, 3 timeout
+    __shared__ int s_arok;
     __shared__ float s_ab[2];
     double gamma = 0.0, delta = 0.0, rr = 0.0, rr0 = 0.0, gamma_prev = 0.0, ga_prev = 0.0;
     int it = 0;
@@ -890,7 +891,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
         df32 v[3] = {{gp.s, gp.c}, {dp.s, dp.c}, {rp.s, rp.c}};
         block_sum_df<3>(v, sh_df);
         double t[3];
-        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t);
+        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t, sh_df, &s_arok);
         if (threadIdx.x == 0) decide(ok2, t, true);
         __syncthreads();
     }
@@ -965,7 +966,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
         block_sum_df<3>(v, sh_df);
         if (prof) t2 = global_ns();
         double t[3];
-        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t);
+        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t, sh_df, &s_arok);
         if (threadIdx.x == 0) {
             if (prof) {
                 const unsigned long long t3 = global_ns();
