@@ -406,6 +406,33 @@ __device__ __forceinline__ df32 df_add(df32 a, df32 b) {
     const float hi = s + e;
     return {hi, e - (hi - s)};
 }
+// Products and quotients of double-floats (Dekker's two-product by FMA, one
+// Newton correction of the FP32 quotient): about 2^-44 relative, within the
+// FP32 exponent range.
+__device__ __forceinline__ df32 df_fast_norm(float s, float e) {
+    const float hi = s + e;
+    return {hi, e - (hi - s)};
+}
+__device__ __forceinline__ df32 df_sub(df32 a, df32 b) { return df_add(a, df32{-b.hi, -b.lo}); }
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+    const float p = a.hi * b.hi;
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return df_fast_norm(p, e);
+}
+__device__ __forceinline__ df32 df_mulf(df32 a, float b) {
+    const float p = a.hi * b;
+    const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+    return df_fast_norm(p, e);
+}
+__device__ __forceinline__ df32 df_div(df32 a, df32 b) {
+    const float q1 = a.hi / b.hi;
+    float r = __fmaf_rn(-q1, b.hi, a.hi);  // exact: a.hi - q1 b.hi
+    r = __fmaf_rn(-q1, b.lo, r + a.lo);
+    return df_fast_norm(q1, r / b.hi);
+}
+__device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
+
 __device__ __forceinline__ df32 warp_sum_df(df32 v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -448,12 +475,12 @@ __device__ __forceinline__ void block_sum_df(df32 (&v)[NV], float2 *sh) {
 // AR_SUB * 32 words, zero at launch; `sh` holds NV * warps float2, `s_ok` is
 // shared.  Every thread of the CTA calls this (it holds __syncthreads); the
 // CTA's own partial is v as left by block_sum_df (valid in warp 0).  On return
-// the totals are valid in thread 0 only (as doubles, hi + lo); false on
+// the totals are valid in thread 0 only (as double-floats); false on
 // timeout.
 constexpr int AR_SUB = 16;
 template <int NV>
 __device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, unsigned gen, unsigned *bar,
-                                                  int *err, long long limit_cycles, double (&tot)[NV], float2 *sh,
+                                                  int *err, long long limit_cycles, df32 (&tot)[NV], float2 *sh,
                                                   int *s_ok) {
     static_assert(NV <= AR_NV_MAX, "too many values");
     float2 *half = reinterpret_cast<float2 *>(part + (size_t)(gen & 1u) * gridDim.x * AR_NV_MAX);
@@ -510,7 +537,7 @@ __device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, u
     block_sum_df<NV>(acc, sh);
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] = (double)acc[k].hi + (double)acc[k].lo;
+        for (int k = 0; k < NV; ++k) tot[k] = acc[k];
     return ok;
 }
 

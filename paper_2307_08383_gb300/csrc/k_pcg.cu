@@ -583,15 +583,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// a / b (b > 0) in FP32 for any FP64 magnitudes: both are scaled by the same
-// power of two, taken from b's exponent, before the FP32 division.
-__device__ __forceinline__ float ratio32(double a, double b) {
-    int e = (int)((__double_as_longlong(b) >> 52) & 0x7FF) - 1023;
-    e = e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
-    const double sc = __longlong_as_double((long long)(1023 - e) << 52);  // 2^-e
-    return (float)(a * sc) / (float)(b * sc);
-}
-
 // The new residual of a camera from the previous iteration's vectors: the row
 // owner and every row that gathers it evaluate exactly these two FMAs.
 __device__ __forceinline__ float next_r(float r, float w, float s, float a, float b) {
@@ -813,27 +804,31 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
         re0 = __ldg(tw_ptr + rb + lr0 + 1);
     }
     unsigned gen = 0;
-    // The recurrence's FP64 scalars live in thread 0, which decides alpha,
-    // beta and the stop after each all-reduce and publishes them here (GB300's
-    // FP64 rate is far below FP32: no other thread does FP64 arithmetic).
+    // The recurrence's scalars live in thread 0, which decides alpha, beta and
+    // the stop after each all-reduce and publishes them here.  They are
+    // double-floats (the all-reduce's totals as they come): GB300's FP64 pipe
+    // is slow enough that an FP64 recurrence on this critical path cost more
+    // than a microsecond per iteration; FP64 is used once, for the threshold.
     __shared__ float2 sh_df[3 * SPLIT_WARPS];
     __shared__ int s_ctl;  // 0 go on, 1 stop, 2 not SPD, 3 timeout
     __shared__ int s_arok;
     __shared__ float s_ab[2];
-    double gamma = 0.0, delta = 0.0, rr = 0.0, rr0 = 0.0, gamma_prev = 0.0, ga_prev = 0.0;
+    df32 gamma{0.f, 0.f}, delta{0.f, 0.f}, rr{0.f, 0.f}, rr0{0.f, 0.f}, gamma_prev{0.f, 0.f}, ga_prev{0.f, 0.f};
+    float thr = 0.f;  // tol^2 r0^T r0: the stop threshold on r^T r
     int it = 0;
     const double tol2 = threadIdx.x == 0 ? sc->tol2 : 0.0;
     const int max_iters = threadIdx.x == 0 ? sc->max_iters : 0;
-    // alpha = gamma / (delta - gamma^2 / (gamma_prev alpha_prev)): the
-    // difference (p^T S^ p, prone to cancellation) in FP64 with one division;
-    // alpha and beta, applied in FP32, by FP32 divisions
-    auto decide = [&](bool ok, const double(&t)[3], bool first) {
+    // alpha = gamma / (delta - gamma (gamma / (gamma_prev alpha_prev))): the
+    // difference (p^T S^ p, prone to cancellation) in double-float; alpha and
+    // beta, applied in FP32, as FP32 quotients of the leading parts
+    auto decide = [&](bool ok, const df32(&t)[3], bool first) {
         if (!ok) {
             s_ctl = 3;
             return;
         }
         if (first) {
             rr0 = t[2];
+            thr = (float)(tol2 * df_to_double(rr0));
         } else {
             gamma_prev = gamma;
             ++it;
@@ -841,15 +836,15 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
         gamma = t[0];
         delta = t[1];
         rr = t[2];
-        if (rr <= tol2 * rr0 || it >= max_iters) {
+        if (rr.hi <= thr || it >= max_iters) {
             s_ctl = 1;
             return;
         }
-        const double den = it == 0 ? delta : delta - gamma * gamma / ga_prev;
-        const float alpha = den > 0.0 ? ratio32(gamma, den) : 0.f;
-        const float beta = it == 0 ? 0.f : ratio32(gamma, gamma_prev);
-        ga_prev = gamma * (double)alpha;
-        if (!(den > 0.0) || !(alpha > 0.f) || !(alpha < 1e30f)) {  // p^T S^ p <= 0 or not finite
+        const df32 den = it == 0 ? delta : df_sub(delta, df_mul(gamma, df_div(gamma, ga_prev)));
+        const float alpha = den.hi > 0.f ? gamma.hi / den.hi : 0.f;
+        const float beta = it == 0 ? 0.f : gamma.hi / gamma_prev.hi;
+        ga_prev = df_mulf(gamma, alpha);
+        if (!(den.hi > 0.f) || !(alpha > 0.f) || !(alpha < 1e30f)) {  // p^T S^ p <= 0 or not finite
             s_ctl = 2;
             return;
         }
@@ -890,7 +885,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
         }
         df32 v[3] = {{gp.s, gp.c}, {dp.s, dp.c}, {rp.s, rp.c}};
         block_sum_df<3>(v, sh_df);
-        double t[3];
+        df32 t[3];
         const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t, sh_df, &s_arok);
         if (threadIdx.x == 0) decide(ok2, t, true);
         __syncthreads();
@@ -903,9 +898,9 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
                 if (blockIdx.x == 0 && ctl != 3) {
                     if (ctl == 2) sc->err = (int)BA_ERR_NOT_SPD;
                     sc->iters = it;
-                    sc->rr = rr;
-                    sc->rr0 = rr0;
-                    sc->rz = gamma;
+                    sc->rr = df_to_double(rr);
+                    sc->rr0 = df_to_double(rr0);
+                    sc->rz = df_to_double(gamma);
                     sc->done = 1;
                 }
                 if (prof) {
@@ -965,7 +960,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
         df32 v[3] = {{gp.s, gp.c}, {dp.s, dp.c}, {rp.s, rp.c}};
         block_sum_df<3>(v, sh_df);
         if (prof) t2 = global_ns();
-        double t[3];
+        df32 t[3];
         const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t, sh_df, &s_arok);
         if (threadIdx.x == 0) {
             if (prof) {
