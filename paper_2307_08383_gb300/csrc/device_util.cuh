@@ -474,14 +474,16 @@ __device__ __forceinline__ void block_sum_df(df32 (&v)[NV], float2 *sh) {
 // for a given launch shape, so every CTA gets the same bits.  `bar` holds
 // AR_SUB * 32 words, zero at launch; `sh` holds NV * warps float2, `s_ok` is
 // shared.  Every thread of the CTA calls this (it holds __syncthreads); the
-// CTA's own partial is v as left by block_sum_df (valid in warp 0).  On return
-// the totals are valid in thread 0 only (as double-floats); false on
-// timeout.
+// CTA's own partial is v as left by block_sum_df (valid in warp 0).  Once
+// every CTA has arrived, every thread runs after_wait() (what the grid wrote
+// before arriving is visible to it) right after issuing its partial reads;
+// meant for asynchronous copies that overlap the rest.  On return the
+// totals are valid in thread 0 only (as double-floats); false on timeout.
 constexpr int AR_SUB = 16;
-template <int NV>
+template <int NV, class F>
 __device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, unsigned gen, unsigned *bar,
                                                   int *err, long long limit_cycles, df32 (&tot)[NV], float2 *sh,
-                                                  int *s_ok) {
+                                                  int *s_ok, F &&after_wait) {
     static_assert(NV <= AR_NV_MAX, "too many values");
     float2 *half = reinterpret_cast<float2 *>(part + (size_t)(gen & 1u) * gridDim.x * AR_NV_MAX);
     if (threadIdx.x == 0) {
@@ -523,6 +525,7 @@ __device__ __forceinline__ bool grid_allreduce_df(df32 (&v)[NV], double *part, u
             t0[k] = b0 < gridDim.x ? __ldcg(half + b0 * AR_NV_MAX + k) : make_float2(0.f, 0.f);
             t1[k] = b1 < gridDim.x ? __ldcg(half + b1 * AR_NV_MAX + k) : make_float2(0.f, 0.f);
         }
+        after_wait();  // issued behind the partial reads, overlapping their use
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             acc[k] = df_add(df32{t0[k].x, t0[k].y}, df32{t1[k].x, t1[k].y});

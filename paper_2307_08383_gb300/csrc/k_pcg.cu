@@ -596,7 +596,11 @@ __device__ __forceinline__ float next_r(float r, float w, float s, float a, floa
 // hundred at the benchmark size) are gathered once per iteration from the
 // previous iteration's records, each transformed once into the vector the
 // SpMV applies, x_j = r_j - alpha (w_j + beta s_j), and kept in shared
-// memory.  A pass's 32 S^ blocks (4.6 KB, contiguous in entry order) and the
+// memory.  The gather of iteration k + 1 is issued (16-byte asynchronous
+// copies of the 80-byte records into the halo area, transformed there in
+// place) as soon as the all-reduce that ends iteration k has seen every CTA
+// arrive, so its L2 round trip overlaps the partial reads, the block sum and
+// the scalar update.  A pass's 32 S^ blocks (4.6 KB, contiguous in entry order) and the
 // entries' packed (local row, halo index) arrive by 1-D bulk copies into one
 // of the warp's two buffers; since S^ does not change during the solve, each
 // refill fetches the warp's pass two positions ahead, wrapping into the next
@@ -609,7 +613,7 @@ constexpr int SPLIT_WARPS = 9;
 constexpr int PASS_S_BYTES = 32 * BW * 4;                        // 4608
 constexpr int PASS_BYTES = PASS_S_BYTES + 32 * 4;                // + packed metadata
 constexpr int SPLIT_STAGE_BYTES = SPLIT_WARPS * 2 * PASS_BYTES;  // 75776
-constexpr int HX = 8;                                            // floats per halo vector
+constexpr int HX = 20;  // floats per halo camera: its fetched record, then x_j written over r_j
 
 struct SplitPipe {
     float *stage;    // [warp][2][32 * 36 floats + 32 u32]
@@ -725,15 +729,28 @@ __device__ __forceinline__ float split_combine(int lr, int c, int rs, int rend, 
 // Halo gather: for each halo camera the vector the SpMV applies (x = r for
 // the prologue, else next_r of its record), and for the CTA's own rows the
 // old r, w, s (own[lr][0..17]).
-__device__ __forceinline__ void split_halo(const int *__restrict__ halo_col, int hb, int H, int ob, int R,
-                                           const float *rec, bool first, float a, float b, float *hx, float *own) {
+__device__ __forceinline__ void split_halo_fetch(const int *__restrict__ halo_col, int hb, int H, int hj0,
+                                                 const float *rec, float *hx) {
     for (int h = threadIdx.x; h < H; h += blockDim.x) {
-        const int j = __ldg(halo_col + hb + h);
+        const int j = h == (int)threadIdx.x ? hj0 : __ldg(halo_col + hb + h);
         const float4 *q = reinterpret_cast<const float4 *>(rec + (int64_t)SREC * j);
+        float4 *d = reinterpret_cast<float4 *>(hx + HX * h);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) cp_async16(d + k, q + k);
+    }
+}
+// Each thread transforms, in place, the records it fetched (so no barrier is
+// needed between the copies and this); own rows keep their whole record.
+__device__ __forceinline__ void split_halo_apply(int H, int ob, int R, bool first, float a, float b, float *hx,
+                                                 float *own) {
+    static_assert(HX == SREC, "the halo area holds whole records");
+    cp_async_wait_all();
+    for (int h = threadIdx.x; h < H; h += blockDim.x) {
+        const float4 *q = reinterpret_cast<const float4 *>(hx + HX * h);
         float t[20];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            const float4 v = __ldcg(q + k);
+            const float4 v = q[k];
             t[4 * k] = v.x; t[4 * k + 1] = v.y; t[4 * k + 2] = v.z; t[4 * k + 3] = v.w;
         }
         float x[6];
@@ -778,9 +795,10 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
     const int hb = __ldg(halo_ptr + blockIdx.x), NH = __ldg(halo_ptr + blockIdx.x + 1) - hb;
     const int ob = __ldg(own_base + blockIdx.x);
     const int R = re - rb, P = (ee - eb + 31) >> 5, wid = threadIdx.x >> 5;
-    // dynamic shared memory: copy buffers | slots + row sums | halo vectors | own records
+    // dynamic shared memory: copy buffers | slots + row sums | halo | own records
     float *slot = sdyn + SPLIT_STAGE_BYTES / 4, *rowacc = slot + 12 * P;
     float *hx = slot + slot_floats, *own = hx + HX * NH;
+    const int hj0 = (int)threadIdx.x < NH ? __ldg(halo_col + hb + threadIdx.x) : 0;
     SplitPipe pp{sdyn, mbar, Sh, tw_meta + __ldg(meta_off + blockIdx.x), eb, ee,
                  wid < P ? (P - 1 - wid) / SPLIT_WARPS + 1 : 0, 0u};
     if (threadIdx.x < 2 * SPLIT_WARPS) mbar_init(&mbar[threadIdx.x], 1);
@@ -854,13 +872,15 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
     };
     auto leave = [&]() {
         if (has0) x[6 * (int64_t)(rb + lr0) + c0] = x0;
+        cp_async_wait_all();
         split_drain(pp, limit_cycles);
     };
     // phase timing (thread 0 of each CTA, profile >= 2): passes, combine, all-reduce
     const bool prof = sc->prof_on != 0 && threadIdx.x == 0;
     unsigned long long t_pass = 0, t_comb = 0, t_red = 0, t0 = 0, t1 = 0, t2 = 0;
     {  // prologue: w_0 = S^ r_0 and the dot products of iteration 0
-        split_halo(halo_col, hb, NH, ob, R, rec0, true, 0.f, 0.f, hx, own);
+        split_halo_fetch(halo_col, hb, NH, hj0, rec0, hx);
+        split_halo_apply(NH, ob, R, true, 0.f, 0.f, hx, own);
         __syncthreads();
         const bool ok = __syncthreads_and(split_passes(pp, rb, tw_ptr, hx, slot, rowacc, &sc->err, limit_cycles));
         if (!ok) {
@@ -886,7 +906,8 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
         df32 v[3] = {{gp.s, gp.c}, {dp.s, dp.c}, {rp.s, rp.c}};
         block_sum_df<3>(v, sh_df);
         df32 t[3];
-        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t, sh_df, &s_arok);
+        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t, sh_df, &s_arok,
+                                              [&]() { split_halo_fetch(halo_col, hb, NH, hj0, rec0, hx); });
         if (threadIdx.x == 0) decide(ok2, t, true);
         __syncthreads();
     }
@@ -915,10 +936,9 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
             return;
         }
         const float a = s_ab[0], b = s_ab[1];
-        const float *rc = par ? rec1 : rec0;
         float *rn = par ? rec0 : rec1;
         if (prof) t0 = global_ns();
-        split_halo(halo_col, hb, NH, ob, R, rc, false, a, b, hx, own);
+        split_halo_apply(NH, ob, R, false, a, b, hx, own);
         __syncthreads();
         const bool ok = __syncthreads_and(split_passes(pp, rb, tw_ptr, hx, slot, rowacc, &sc->err, limit_cycles));
         if (!ok) {
@@ -961,7 +981,8 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
         block_sum_df<3>(v, sh_df);
         if (prof) t2 = global_ns();
         df32 t[3];
-        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t, sh_df, &s_arok);
+        const bool ok2 = grid_allreduce_df<3>(v, red, gen++, bar, &sc->err, limit_cycles, t, sh_df, &s_arok,
+                                              [&]() { split_halo_fetch(halo_col, hb, NH, hj0, rn, hx); });
         if (threadIdx.x == 0) {
             if (prof) {
                 const unsigned long long t3 = global_ns();
@@ -1238,6 +1259,9 @@ static cudaError_t split_partition(ba_problem *p) {
     constexpr int SMEM_MAX = 200 * 1024, ROW_COST = 8;
     if ((e = cudaFuncSetAttribute(k_pcg_split, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX)) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_pcg_split, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+        return e;
     auto unavailable = [&]() {
         p->split_grid = -1;
         return cudaSuccess;
@@ -1282,7 +1306,8 @@ static cudaError_t split_partition(ba_problem *p) {
             Rmax = std::max(Rmax, R);
             slot_floats = std::max(slot_floats, (int)(12 * P + 6 * R + 3) & ~3);
         }
-        smem = SPLIT_STAGE_BYTES + ((size_t)slot_floats + (size_t)HX * Hmax + 20 * (size_t)Rmax) * sizeof(float);
+        smem = SPLIT_STAGE_BYTES +
+               ((size_t)slot_floats + (size_t)HX * Hmax + 20 * (size_t)Rmax) * sizeof(float);
         if (smem > (size_t)SMEM_MAX || Hmax > 0xFFFF || Rmax > 0xFFFE) return unavailable();
     }
     // the occupancy at the final shared-memory size must keep the grid resident
