@@ -111,8 +111,10 @@ typedef struct {
                                 iterations of all solves so far, in us: SpMV passes (to the
                                 CTA barrier), row combine and update, grid all-reduce */
     double rcs_phase_us[3];  /* profile >= 2: RCS formation per point group, mean over the
-                                groups formed so far, in us: wait for the group's copy,
-                                per-point work (V_k, Cholesky, P, e^), products and write-out */
+                                groups formed so far, in us, as the CTA's last thread sees
+                                them: wait at the group's barrier, products and write-out,
+                                then the next group's copy wait and per-point work (V_k,
+                                Cholesky, P, e^) */
     double pcg_work_imbalance; /* profile >= 2: last split CG solve, the busiest CTA's
                                 passes + combine time over the mean CTA's (1 = balanced) */
 } ba_stats;

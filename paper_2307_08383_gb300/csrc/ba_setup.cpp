@@ -100,6 +100,69 @@ void build_twosided(HostSetup &hs, int32_t n) {
 
 }
 
+// A work item of the RCS formation: products [cbeg, cbeg + cnt) of the
+// group's product list, all of local block blk (ordinal in the group's order).
+struct WorkItem {
+    int32_t blk, cbeg, cnt;
+};
+
+// Orders the products inside each work item for the shared-memory banks.
+// The product loop of the RCS formation reads, per product, the a- and
+// b-rows of two observations with 16-byte loads; rows are 80 bytes apart,
+// so row r starts in 16-byte bank group (5 r) mod 8, and one such load of a
+// quarter-warp (items 8m .. 8m + 7 of a group, one per lane) costs as many
+// wavefronts as the largest number of distinct rows sharing a bank group.
+// The order of a work item's products is free (they are summed), so at each
+// step every lane takes, from its remaining products, the one that adds the
+// fewest same-group rows to the step's a- and b-loads (diagonal items load
+// only the a-row).  Deterministic: ties keep the stored (point) order.
+void order_items_for_banks(uint32_t *cl, const WorkItem *its, int32_t nit, const std::vector<char> &is_diag,
+                           const std::vector<int32_t> &ord) {
+    std::vector<uint32_t> rem[8];
+    int32_t rowsA[8][8], nA[8], rowsB[8][8], nB[8];
+    auto seen = [](const int32_t *rows, int32_t n, int32_t r) {
+        for (int32_t q = 0; q < n; ++q)
+            if (rows[q] == r) return true;
+        return false;
+    };
+    for (int32_t m0 = 0; m0 < nit; m0 += 8) {
+        const int32_t m1 = std::min(nit, m0 + 8);
+        int32_t T = 0;
+        for (int32_t t = m0; t < m1; ++t) {
+            rem[t - m0].assign(cl + its[t].cbeg, cl + its[t].cbeg + its[t].cnt);
+            T = std::max(T, its[t].cnt);
+        }
+        for (int32_t step = 0; step < T; ++step) {
+            std::fill(nA, nA + 8, 0);
+            std::fill(nB, nB + 8, 0);
+            for (int32_t t = m0; t < m1; ++t) {
+                std::vector<uint32_t> &rl = rem[t - m0];
+                if (rl.empty()) continue;
+                const bool dg = is_diag[ord[its[t].blk]] != 0;
+                size_t best = 0;
+                int32_t best_cost = INT32_MAX;
+                for (size_t q = 0; q < rl.size() && best_cost > 0; ++q) {
+                    const int32_t ra = (int32_t)(rl[q] & 0xffffu), rb = (int32_t)(rl[q] >> 16);
+                    const int32_t ca = (5 * ra) & 7, cb = (5 * rb) & 7;
+                    int32_t cost = seen(rowsA[ca], nA[ca], ra) ? 0 : nA[ca];
+                    if (!dg) cost += seen(rowsB[cb], nB[cb], rb) ? 0 : nB[cb];
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        best = q;
+                    }
+                }
+                const uint32_t u = rl[best];
+                rl.erase(rl.begin() + (std::ptrdiff_t)best);
+                cl[its[t].cbeg + step] = u;
+                const int32_t ra = (int32_t)(u & 0xffffu), rb = (int32_t)(u >> 16);
+                const int32_t ca = (5 * ra) & 7, cb = (5 * rb) & 7;
+                if (!seen(rowsA[ca], nA[ca], ra)) rowsA[ca][nA[ca]++] = ra;
+                if (!dg && !seen(rowsB[cb], nB[cb], rb)) rowsB[cb][nB[cb]++] = rb;
+            }
+        }
+    }
+}
+
 ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam,
                          const int64_t *obs_pt, const double *pts, int obs_max, bool pattern_only,
                          HostSetup &hs, std::string &err) {
@@ -228,8 +291,7 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
         std::vector<int32_t> fill(start.begin(), start.end() - 1);
         for (auto &c : g_c) hs.contrib[g.c_begin + fill[pos[c.first]]++] = c.second;  // stable: point order
         // work items of <= ITEM_MAX products, sizes balanced within a block
-        struct It { int32_t blk, cbeg, cnt; };
-        std::vector<It> its;
+        std::vector<WorkItem> its;
         for (int32_t r = 0; r < nlb; ++r) {
             const int32_t c = cnt[ord[r]];
             const int32_t k = (c + ITEM_MAX - 1) / ITEM_MAX;
@@ -240,8 +302,9 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
                 off += sz;
             }
         }
-        // runs: consecutive items of one block inside one warp of 32
         const int32_t nit = (int32_t)its.size();
+        order_items_for_banks(hs.contrib.data() + g.c_begin, its.data(), nit, is_diag, ord);
+        // runs: consecutive items of one block inside one warp of 32
         int32_t npart = 0;
         for (int32_t q = 0; q < nit;) {
             int32_t e = q + 1;
