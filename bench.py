@@ -311,13 +311,13 @@ def run_ours(args):
 
 # Versions of the two kernels whose DRAM traffic was captured with ncu; the
 # captured bytes are reported only while the kernel is the one measured.
-PCG_KERNEL_VERSION = "pcg_split-halo-v2"
-RCS_KERNEL_VERSION = "form_rcs-v3"
+PCG_KERNEL_VERSION = "pcg_split-prefetch-v3"
+RCS_KERNEL_VERSION = "form_rcs-v4"
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum, profiles/pcg_split_aerial5k.md
-    "pcg_split": {"version": "pcg_split-halo-v2", "workload": "aerial5k", "bytes_per_unit": 1_157_700},
+    "pcg_split": {"version": "pcg_split-prefetch-v3", "workload": "aerial5k", "bytes_per_unit": 1_157_682},
     # profiles/form_rcs_aerial.md
-    "form_rcs": {"version": "form_rcs-v3", "workload": "aerial5k", "bytes_per_unit": 784_956_672},
+    "form_rcs": {"version": "form_rcs-v4", "workload": "aerial5k", "bytes_per_unit": 785_134_592},
 }
 
 
