@@ -285,6 +285,7 @@ def run_ours(args):
            "share_of_timed_kernels": round(tot / total_timed, 3) if total_timed else None}
     kernels = {nm: {"launches": v[0], "ms": round(v[1], 3)} for nm, v in ktimes.items() if v[0]}
     cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload, s.n_obs)
+    formats = None if args.no_formats else formats_bench(B, torch, g, st1, esz, peaks, peak_kind, stream)
     g.close()
     solver = None if args.no_solver else solver_bench(B, torch)
     acc = sum(i["accepted"] for i in infos)
@@ -299,7 +300,7 @@ def run_ours(args):
         "lm": {"accepted": acc, "pcg_iters": [i["pcg_iters"] for i in infos],
                "cost": [infos[0]["cost_before"], infos[-1]["cost_after"]],
                "rcs_rel_resid_max": max(i["rcs_rel_resid"] for i in infos)},
-        "kernels_ms": kernels, "solver": solver, "impl": "ours",
+        "kernels_ms": kernels, "solver": solver, "spmv_formats": formats, "impl": "ours",
         "setup": {"problem_create_s": round(t_create, 2), "device_bytes": int(st1["device_bytes"]),
                   "preconditioner": "learned (packaged weights), block-Jacobi fallback" if net else "block-Jacobi",
                   "used_fallback": [i["used_fallback"] for i in infos]},
@@ -319,6 +320,48 @@ NCU_TRAFFIC = {
     # profiles/form_rcs_aerial.md
     "form_rcs": {"version": "form_rcs-v4", "workload": "aerial5k", "bytes_per_unit": 785_134_592},
 }
+
+
+def formats_bench(B, torch, g, st, esz, peaks, peak_kind, stream, repeats=7):
+    """y = S x with the current RCS in each storage format of Sec. 4 (the
+    library's BSMC, block CSR of the full symmetric matrix, scalar CSR), one
+    launch per format through ba_rcs_spmv, L2 flushed before each launch (a
+    256 MB write), CUDA events on the problem's stream, median of repeats.
+    Bytes: the format's arrays read once plus x and y (6n values each)."""
+    import statistics
+    n = st["n_cams"]
+    # an accepted LM step drops the RCS: form the one of the final state
+    g.linearize()
+    g.form_rcs(g.lm_state()[0])
+    dt = torch.float32 if esz == 4 else torch.float64
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(6 * n, dtype=dt, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, fmt in (("bsmc", B.BA_FMT_BSMC), ("bsr_full", B.BA_FMT_BSR_FULL), ("csr", B.BA_FMT_CSR)):
+        nbytes = g.rcs_spmv(fmt, x, y)  # builds the format's arrays (untimed)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(repeats):
+            flush.zero_()
+            e0.record(stream)
+            g.rcs_spmv(fmt, x, y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        us = 1e3 * statistics.median(ts)
+        moved = nbytes + 2 * 6 * n * esz
+        res[name] = {"us": round(us, 2), "format_bytes": int(nbytes), "bytes_per_spmv": int(moved),
+                     "achieved_gbs": round(moved / us / 1e3, 1),
+                     "frac_hbm": round(moved / us / 1e3 / peaks["hbm_gbs"], 4)}
+    return {"what": "y = S x per RCS storage format (Sec. 4, Table 1, Eqs. 8-10)", "l2": "flushed before each launch",
+            "peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind, "formats": res,
+            "bytes_csr_over_bsmc": round(res["csr"]["format_bytes"] / res["bsmc"]["format_bytes"], 3),
+            "time_csr_over_bsmc": round(res["csr"]["us"] / res["bsmc"]["us"], 3),
+            "time_bsr_full_over_bsmc": round(res["bsr_full"]["us"] / res["bsmc"]["us"], 3)}
 
 
 def pcg_bytes_per_iteration(st, esz=4):
@@ -490,6 +533,7 @@ def main():
     ap.add_argument("--pcg-tol", type=float, default=None, help="kernel case: PCG relative tolerance")
     ap.add_argument("--pcg-variant", default=None, choices=["standard", "split"], help="kernel case: PCG variant")
     ap.add_argument("--group-obs", type=int, default=0, help="kernel case: observations per point group")
+    ap.add_argument("--no-formats", action="store_true", help="skip the RCS storage-format SpMV comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solver", action="store_true", help="skip the PCG time-to-1e-8 comparison")

@@ -215,6 +215,35 @@ ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs,
                               const int32_t *obs_cam, const int64_t *obs_pt, int32_t *row_ptr,
                               int32_t *col, int64_t *nnzb);
 
+/* ---- Storage formats of the RCS (Sec. 4, Table 1, Eqs. 8-10) -------------
+ * y = S x with the problem's current RCS held in one of three formats, each
+ * with its own GPU kernel, so that the paper's storage comparison can be
+ * measured (Table 1 lists the operations a format must serve; Eqs. 8-10 give
+ * the bytes of scalar CSR and of BSMC):
+ *   BA_FMT_BSMC      the library's storage: upper-triangle 6x6 blocks, the
+ *                    full diagonal block first in every row (Fig. 4); the
+ *                    product applies each off-diagonal block twice, as S_ij x_j
+ *                    and as S_ij^T x_i (a warp per block row over its two-sided
+ *                    entry list: no atomics, deterministic);
+ *   BA_FMT_BSR_FULL  block CSR of the whole symmetric matrix: both triangles
+ *                    stored as row-major 6x6 blocks, a column index per block,
+ *                    n + 1 row starts;
+ *   BA_FMT_CSR       scalar CSR of the whole matrix (Eq. 8): a value and a
+ *                    column index per element of every non-zero block, 6n + 1
+ *                    row starts.
+ * All three sum each row's blocks in the same order.  x and y are DEVICE
+ * arrays of 6n values in the problem's precision (double for BA_FP64
+ * problems, float for BA_FP32), owned by the caller, not overlapping; the
+ * product is queued on the problem's stream (no synchronisation).  The full
+ * formats are built on the device from the current S on the first call after
+ * each RCS is formed (ba_form_rcs, ba_lm_step, ba_problem_create_rcs) and are
+ * owned by the problem.  bytes_out (host, may be NULL) receives the format's
+ * array bytes: values + column indices + row starts.  Errors:
+ * BA_ERR_INVALID_ARG (bad format or NULL array), BA_ERR_STATE (no RCS
+ * formed), BA_ERR_OOM, BA_ERR_CUDA. */
+typedef enum { BA_FMT_BSMC = 0, BA_FMT_BSR_FULL = 1, BA_FMT_CSR = 2 } ba_rcs_format;
+ba_status ba_rcs_spmv(ba_problem *p, int32_t format, const void *x, void *y, int64_t *bytes_out);
+
 /* ---- Learned block-Jacobi correction (not in the paper) ------------------
  * The paper preconditions PCG with the block diagonal of the RCS (Sec. 3.2).
  * A small network corrects each block's inverse while keeping it SPD:

@@ -31,6 +31,7 @@ BA_ERR_INTERNAL = 9
 BA_FP64 = 0
 BA_FP32 = 1
 BA_PCG_AUTO, BA_PCG_STANDARD, BA_PCG_SPLIT = 0, 1, 2
+BA_FMT_BSMC, BA_FMT_BSR_FULL, BA_FMT_CSR = 0, 1, 2
 BA_LOSS_PLAIN = 0
 BA_LOSS_HUBER = 1
 BA_PC_BLOCK_JACOBI = 0
@@ -103,6 +104,7 @@ SIGNATURES = [
     ("ba_get_points", _S, [_P, _D]),
     ("ba_get_rcs", _S, [_P, _I64, _I32, _I32, _D, _D]),
     ("ba_get_step", _S, [_P, _D, _D]),
+    ("ba_rcs_spmv", _S, [_P, ctypes.c_int32, _P, _P, _I64]),
     ("ba_get_linearization", _S, [_P, _D, _D, _D]),
     ("ba_set_state", _S, [_P, _D, _D, ctypes.c_double, ctypes.c_double]),
     ("ba_get_lm_state", _S, [_P, _D, _D, _D]),
@@ -263,6 +265,15 @@ def ba_get_rcs(h, n):
     return row_ptr, col, val, b
 
 
+def ba_rcs_spmv(h, fmt, x_ptr, y_ptr):
+    """y = S x with the RCS in format fmt (BA_FMT_*); x_ptr, y_ptr are device
+    addresses (ints) of 6n values in the problem's precision; queued on the
+    problem's stream.  Returns the format's array bytes."""
+    nb = ctypes.c_int64()
+    _check(lib().ba_rcs_spmv(h, int(fmt), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), ctypes.byref(nb)))
+    return nb.value
+
+
 def ba_get_step(h, n, P):
     dxc = np.empty((n, 6))
     dxp = np.empty((P, 3))
@@ -404,6 +415,12 @@ class Problem:
 
     def rcs(self):
         return ba_get_rcs(self.h, self.n)
+
+    def rcs_spmv(self, fmt, x, y):
+        """y = S x (torch CUDA tensors of 6n values, float64 for FP64
+        problems, float32 for FP32) with the RCS in format fmt; returns the
+        format's array bytes."""
+        return ba_rcs_spmv(self.h, fmt, x.data_ptr(), y.data_ptr())
 
     def step(self):
         return ba_get_step(self.h, self.n, self.P)

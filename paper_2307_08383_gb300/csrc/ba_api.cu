@@ -505,6 +505,7 @@ ba_status ba_problem_create_rcs(const ba_options *opt, int32_t n, int64_t nnzb, 
     }
     default_view(p);
     p->rcs_formed = true;
+    ++p->rcs_gen;
     p->lambda = 0.0;
     if (sync_scalars(p) == BA_OK && p->sc_host->err == BA_ERR_NOT_SPD) {
         free_all(p);
@@ -569,6 +570,7 @@ ba_status ba_form_rcs(ba_problem *p, double lambda) {
     CK(p, launch_form_rcs(p, lambda));
     p->minv_learned = false;
     p->rcs_formed = true;
+    ++p->rcs_gen;
     p->rcs_lambda = lambda;
     p->solved = p->backsub = false;
     return BA_OK;
@@ -775,6 +777,7 @@ ba_status ba_lm_step(ba_problem *p, ba_step_info *info) {
     CK(p, launch_form_rcs(p, p->lambda));
     p->minv_learned = false;
     p->rcs_formed = true;
+    ++p->rcs_gen;
     p->rcs_lambda = p->lambda;
     CK(p, cudaEventRecord(ev[2], p->st));
     s = ba_solve_rcs(p, &loc);
@@ -880,6 +883,26 @@ ba_status ba_get_rcs(const ba_problem *p, int64_t *nnzb, int32_t *row_ptr, int32
         if ((s = fetch(q, p->b, p->n * 6, tmp))) return s;
         std::memcpy(b, tmp.data(), tmp.size() * 8);
     }
+    return BA_OK;
+}
+
+ba_status ba_rcs_spmv(ba_problem *p, int32_t format, const void *x, void *y, int64_t *bytes_out) {
+    LIVE(p);
+    if (format < BA_FMT_BSMC || format > BA_FMT_CSR) return fail(BA_ERR_INVALID_ARG, "unknown RCS format");
+    if (!x || !y) return fail(BA_ERR_INVALID_ARG, "null vector");
+    if (!p->rcs_formed) return fail(BA_ERR_STATE, "no RCS formed yet");
+    if (format == BA_FMT_CSR && (2 * p->nnzb - p->n) * (int64_t)BW >= (int64_t)INT32_MAX)
+        return fail(BA_ERR_INVALID_ARG, "scalar CSR of this RCS needs 64-bit row starts");
+    if (format != BA_FMT_BSMC) {
+        const cudaError_t e = launch_rcs_format_build(p, format);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return fail(BA_ERR_OOM, "ba_rcs_spmv: no device memory for the format's arrays");
+        }
+        CK(p, e);
+    }
+    CK(p, launch_rcs_spmv(p, format, x, y));
+    if (bytes_out) *bytes_out = rcs_format_bytes(p, format);
     return BA_OK;
 }
 

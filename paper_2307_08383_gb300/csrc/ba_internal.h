@@ -86,6 +86,7 @@ struct HostSetup {
     std::vector<int32_t> pptr;       // nnzb + 1: partials of each global block
     std::vector<int32_t> plist;
     int64_t n_pairs = 0;
+    int32_t max_nobs = 0, max_nc = 0;  // largest group: observations, products
 };
 
 // Column index and two-sided SpMV entry lists from hs.row_ptr / hs.col.
@@ -142,6 +143,12 @@ struct ba_problem {
     int32_t *tw_ptr = nullptr;
     int2 *tw_ent = nullptr;
     void *S = nullptr, *b = nullptr, *Minv = nullptr;
+    // S's generation (bumped whenever an RCS is formed or loaded) and the
+    // full-block and scalar CSR copies of S for ba_rcs_spmv, with the
+    // generation each was built from
+    uint64_t rcs_gen = 0, fmt_gen[3] = {~0ull, ~0ull, ~0ull};
+    void *fmt_bsr_val = nullptr, *fmt_csr_val = nullptr;
+    int32_t *fmt_bsr_col = nullptr, *fmt_csr_ptr = nullptr, *fmt_csr_col = nullptr;
     ba::GroupDesc *grp = nullptr;
     ba::ItemDesc *items = nullptr;
     uint32_t *contrib = nullptr;
@@ -248,6 +255,10 @@ cudaError_t launch_pcg_split(ba_problem *p);
 cudaError_t launch_accumulate_split(ba_problem *p, bool first);
 // y = S x for one FP32 vector (learned-preconditioner probes)
 cudaError_t launch_spmv_f32(ba_problem *p, const float *x, float *y);
+// RCS storage formats (k_formats.cu)
+cudaError_t launch_rcs_format_build(ba_problem *p, int format);
+cudaError_t launch_rcs_spmv(ba_problem *p, int format, const void *x, void *y);
+int64_t rcs_format_bytes(const ba_problem *p, int format);
 // learned preconditioner: M^-1 of the last formed RCS from the attached net
 // (the block-Jacobi M^-1 is saved first); restore the block-Jacobi M^-1
 ba_status gnn_apply(ba_problem *p);

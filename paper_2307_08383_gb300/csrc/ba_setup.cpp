@@ -257,6 +257,8 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
     hs.lb_gblk.clear();
     hs.contrib.clear();
     hs.n_pairs = 0;
+    hs.max_nobs = 0;
+    hs.max_nc = 0;
     GroupDesc g{};
     int32_t gid = 0;
     auto close_group = [&]() {
@@ -322,6 +324,8 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
             q = e;
         }
         g.nitems = nit;
+        hs.max_nobs = std::max(hs.max_nobs, g.nobs);
+        hs.max_nc = std::max(hs.max_nc, g.nc);
         hs.groups.push_back(g);
         g_gblk.clear();
         g_c.clear();

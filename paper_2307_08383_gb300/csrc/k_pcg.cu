@@ -28,46 +28,6 @@
 
 namespace ba {
 
-// One 6x6 block (16-byte aligned) into registers, read-only path.
-template <typename TS, typename TV>
-__device__ __forceinline__ void load_block(const TS *__restrict__ Sb, TV (&v)[36]) {
-    if constexpr (sizeof(TS) == 4) {
-        const float4 *s4 = reinterpret_cast<const float4 *>(Sb);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float4 t = __ldg(s4 + q);
-            v[4 * q] = (TV)t.x; v[4 * q + 1] = (TV)t.y; v[4 * q + 2] = (TV)t.z; v[4 * q + 3] = (TV)t.w;
-        }
-    } else {
-        const double2 *s2 = reinterpret_cast<const double2 *>(Sb);
-#pragma unroll
-        for (int q = 0; q < 18; ++q) {
-            const double2 t = __ldg(s2 + q);
-            v[2 * q] = (TV)t.x; v[2 * q + 1] = (TV)t.y;
-        }
-    }
-}
-
-// Six entries of a camera vector (24 B for FP32, 8-byte aligned; 48 B for FP64).
-__device__ __forceinline__ void load6(const float *p, float (&v)[6]) {
-    const float2 *p2 = reinterpret_cast<const float2 *>(p);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float2 t = __ldcg(p2 + k);
-        v[2 * k] = t.x;
-        v[2 * k + 1] = t.y;
-    }
-}
-__device__ __forceinline__ void load6(const double *p, double (&v)[6]) {
-    const double2 *p2 = reinterpret_cast<const double2 *>(p);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const double2 t = __ldcg(p2 + k);
-        v[2 * k] = t.x;
-        v[2 * k + 1] = t.y;
-    }
-}
-
 template <typename TV, bool PCG>
 __device__ __forceinline__ void gather_x(const TV *__restrict__ xz, const TV *__restrict__ dold, TV beta, int j,
                                          TV (&x)[6]) {
@@ -77,21 +37,6 @@ __device__ __forceinline__ void gather_x(const TV *__restrict__ xz, const TV *__
         load6(dold + 6 * j, d);
 #pragma unroll
         for (int c = 0; c < 6; ++c) x[c] += beta * d[c];
-    }
-}
-
-template <typename TV>
-__device__ __forceinline__ void block_apply(const TV (&Sv)[36], const TV (&x)[6], bool transposed, TV (&acc)[6]) {
-    if (!transposed) {
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) acc[r] += Sv[6 * r + c] * x[c];
-    } else {
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-#pragma unroll
-            for (int r = 0; r < 6; ++r) acc[c] += Sv[6 * r + c] * x[r];
     }
 }
 

@@ -247,6 +247,8 @@ __device__ __forceinline__ void rcs_products(const GroupDesc &g, const T *so, co
     }
 }
 
+__host__ __device__ constexpr size_t form_round128(size_t b) { return (b + 127) & ~(size_t)127; }
+
 template <typename T>
 __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__restrict__ grp, int ngroups,
                                                            const ItemDesc *__restrict__ items,
@@ -254,12 +256,14 @@ __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__re
                                                            const int *__restrict__ trk_ptr, const T *__restrict__ J,
                                                            double lambda, T *__restrict__ part, T *__restrict__ Linv_out,
                                                            T *__restrict__ lp_out, DevScalars *sc, int fp64_v,
-                                                           int obs_max, long long limit, int prof) {
+                                                           int o_cap, int c_cap, long long limit, int prof) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ GroupDesc sdesc[2];
-    const size_t jbytes_max = (size_t)obs_max * JW * sizeof(T);
-    const size_t buf_bytes = jbytes_max + (size_t)C_MAX * sizeof(uint32_t);
+    // a staging buffer: rows of up to o_cap observations, then c_cap products
+    // (the largest group's), each part starting on a 128-byte boundary
+    const size_t jbytes_max = form_round128((size_t)o_cap * JW * sizeof(T));
+    const size_t buf_bytes = form_round128(jbytes_max + (size_t)c_cap * sizeof(uint32_t));
     if (threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -424,13 +428,18 @@ static inline int grid_for(int64_t work, int threads, int cap) {
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
+static int form_o_cap(const ba_problem *p) { return std::max(1, p->hs.max_nobs); }
+static int form_c_cap(const ba_problem *p) { return std::max(4, (p->hs.max_nc + 3) & ~3); }
+
 template <typename T>
 static cudaError_t form_rcs_T(ba_problem *p, double lambda, size_t smem, long long limit) {
     static int ctas_per_sm = -1, n_sm = 0;
+    static size_t smem_seen = 0;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_form_rcs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    if (ctas_per_sm < 0) {
+    if (ctas_per_sm < 0 || smem != smem_seen) {
+        smem_seen = smem;
         int dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -442,7 +451,8 @@ static cudaError_t form_rcs_T(ba_problem *p, double lambda, size_t smem, long lo
     const int grid = (int)std::min<int64_t>(p->ngroups, (int64_t)ctas_per_sm * n_sm);
     k_form_rcs<T><<<grid, FORM_THREADS, smem, p->st>>>(p->grp, (int)p->ngroups, p->items, p->contrib, p->trk_ptr,
                                                       (const T *)p->J, lambda, (T *)p->part, (T *)p->Linv, (T *)p->lp,
-                                                      p->sc, p->fp32 ? 1 : 0, p->obs_max, limit, p->opt.profile >= 2 ? 1 : 0);
+                                                      p->sc, p->fp32 ? 1 : 0, form_o_cap(p), form_c_cap(p), limit,
+                                                      p->opt.profile >= 2 ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -459,7 +469,8 @@ cudaError_t launch_block_jacobi(ba_problem *p) {
 cudaError_t launch_form_rcs(ba_problem *p, double lambda) {
     cudaError_t err;
     cudaEvent_t ev;
-    const size_t smem = 2 * ((size_t)p->obs_max * JW * p->esz + (size_t)C_MAX * sizeof(uint32_t));
+    const size_t smem =
+        2 * form_round128(form_round128((size_t)form_o_cap(p) * JW * p->esz) + (size_t)form_c_cap(p) * sizeof(uint32_t));
     const long long limit = 4000000000LL;  // ~2 s of SM clock per copy wait
     ktimer_begin(p, K_FORM_RCS, &ev);
     if (p->fp32)

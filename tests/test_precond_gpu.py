@@ -18,11 +18,14 @@ def env():
     from paper_2307_08383_gb300.build import build
     build()
     import paper_2307_08383_gb300 as B
+    # the system is the oracle's RCS (initial state, lambda = 1e-3), held by
+    # the GPU in FP32
     s = scenes.aerial_small(n_along=12, n_across=8, pts_per_cam=80, seed=81)
-    g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, precision=B.BA_FP32, pcg_rel_tol=1e-6)
-    g.linearize()
-    g.form_rcs(1e-3)
-    row_ptr, col, val, b = g.rcs()
+    pb = O.Problem(s.n_cams, s.n_pts, s.obs_cam, s.obs_pt, s.obs_uv)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    _, A, b = pb.rcs(e, Jc, Jp, 1e-3)
+    row_ptr, col, val, b = A.row_ptr, A.col, A.val, np.asarray(b)
+    g = B.Problem.from_rcs(row_ptr, col, val, b, precision=B.BA_FP32, pcg_rel_tol=1e-6)
     diag, src, dst, w = N.graph_from_bsmc(row_ptr, col, val)
     return torch, B, g, (row_ptr, col, val, b), (diag, src, dst, w)
 
@@ -59,10 +62,8 @@ def test_zero_output_layer_is_block_jacobi(env):
     rel = np.linalg.norm((minv - ref).reshape(len(diag), -1), axis=1) / np.linalg.norm(ref.reshape(len(diag), -1), axis=1)
     assert rel.max() <= 1e-4
     # PCG with the attached untrained net takes block-Jacobi's iterations
-    g.form_rcs(1e-3)
     i_bj, _ = g.solve_rcs()
     B.ba_set_precond_net(g, net)
-    g.form_rcs(1e-3)
     i_nn, _ = g.solve_rcs()
     B.ba_set_precond_net(g, None)
     assert abs(i_nn["pcg_iters"] - i_bj["pcg_iters"]) <= 1 and i_nn["used_fallback"] == 0

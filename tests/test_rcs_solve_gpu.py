@@ -17,11 +17,12 @@ def sys64():
     from paper_2307_08383_gb300.build import build
     build()
     import paper_2307_08383_gb300 as B
+    # the system comes from the oracle (Eq. 4 at the initial state, lambda = 1e-3)
     s = scenes.aerial_small(n_along=16, n_across=10, pts_per_cam=100, seed=91)
-    g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, precision=B.BA_FP64)
-    g.linearize()
-    g.form_rcs(1e-3)
-    return B, g.rcs()
+    pb = O.Problem(s.n_cams, s.n_pts, s.obs_cam, s.obs_pt, s.obs_uv)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    _, A, b = pb.rcs(e, Jc, Jp, 1e-3)
+    return B, (A.row_ptr, A.col, A.val, np.asarray(b))
 
 
 def test_rcs_problem_fp64_matches_oracle_pcg(sys64):
