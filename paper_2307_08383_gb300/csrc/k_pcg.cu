@@ -1201,7 +1201,7 @@ static cudaError_t split_partition(ba_problem *p) {
     int dev = 0, n_sm = 0, bps = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    constexpr int SMEM_MAX = 200 * 1024, ROW_COST = 8;
+    constexpr int SMEM_MAX = 226 * 1024, ROW_COST = 8;  // 227 KB per CTA less the static part
     if ((e = cudaFuncSetAttribute(k_pcg_split, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_pcg_split, cudaFuncAttributePreferredSharedMemoryCarveout,
