@@ -21,6 +21,8 @@
 // (precomputed CSR) then forms S, adds lambda clamp(diag U) on the diagonal,
 // and inverts the diagonal blocks for the preconditioner.
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "device_util.cuh"
 #include "tma_util.cuh"
@@ -358,16 +360,44 @@ __global__ void __launch_bounds__(FORM_THREADS) k_form_rcs(const GroupDesc *__re
     }
 }
 
-// K3: S[block][e] = sum of the block's partials (fixed order), one thread per value.
+// K3: S[block] = sum of the block's partials in list order (fixed), a thread
+// per 16-byte chunk of the block (9 for FP32, 18 for FP64): the chunks of a
+// partial are read by consecutive threads, and each thread keeps four
+// partials' loads in flight before adding them in order.  (Writing each
+// partial straight to a block-ordered slot in RCS formation made this
+// reduction contiguous but cost the formation more than it saved here.)
+__device__ __forceinline__ void add16(float4 &s, const float4 v) {
+    s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+}
+__device__ __forceinline__ void add16(double2 &s, const double2 v) {
+    s.x += v.x; s.y += v.y;
+}
 template <typename T>
-__global__ void __launch_bounds__(256) k_rcs_reduce(int64_t nval, const int *__restrict__ pptr, const int *__restrict__ plist,
+__global__ void __launch_bounds__(256) k_rcs_reduce(int64_t nblk, const int *__restrict__ pptr, const int *__restrict__ plist,
                                                     const T *__restrict__ part, T *__restrict__ S) {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nval; x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t blk = x / BW;
-        const int e = (int)(x - blk * BW);
-        T s = T(0);
-        for (int q = pptr[blk]; q < pptr[blk + 1]; ++q) s += part[(int64_t)plist[q] * BW + e];
-        S[x] = s;
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    constexpr int NCH = BW * (int)sizeof(T) / 16;
+    const V *pv = reinterpret_cast<const V *>(part);
+    V *sv = reinterpret_cast<V *>(S);
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nblk * NCH; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = x / NCH;
+        const int c = (int)(x - blk * NCH);
+        const int q1 = __ldg(pptr + blk + 1);
+        int q = __ldg(pptr + blk);
+        V s;
+        std::memset(&s, 0, sizeof(V));
+        for (; q + 4 <= q1; q += 4) {
+            const int i0 = __ldg(plist + q), i1 = __ldg(plist + q + 1), i2 = __ldg(plist + q + 2),
+                      i3 = __ldg(plist + q + 3);
+            const V v0 = pv[(int64_t)i0 * NCH + c], v1 = pv[(int64_t)i1 * NCH + c], v2 = pv[(int64_t)i2 * NCH + c],
+                    v3 = pv[(int64_t)i3 * NCH + c];
+            add16(s, v0);
+            add16(s, v1);
+            add16(s, v2);
+            add16(s, v3);
+        }
+        for (; q < q1; ++q) add16(s, pv[(int64_t)__ldg(plist + q) * NCH + c]);
+        sv[x] = s;
     }
 }
 
@@ -480,13 +510,13 @@ cudaError_t launch_form_rcs(ba_problem *p, double lambda) {
     ktimer_end(p, K_FORM_RCS, ev);
     p->launches += 1;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    const int64_t nval = p->nnzb * BW;
     ktimer_begin(p, K_RCS_REDUCE, &ev);
-    const int g = grid_for(nval, 256, 152 * 16);
+    const int g = grid_for(p->nnzb * (int64_t)(BW * p->esz / 16), 256, 152 * 16);
     if (p->fp32)
-        k_rcs_reduce<float><<<g, 256, 0, p->st>>>(nval, p->pptr, p->plist, (const float *)p->part, (float *)p->S);
+        k_rcs_reduce<float><<<g, 256, 0, p->st>>>(p->nnzb, p->pptr, p->plist, (const float *)p->part, (float *)p->S);
     else
-        k_rcs_reduce<double><<<g, 256, 0, p->st>>>(nval, p->pptr, p->plist, (const double *)p->part, (double *)p->S);
+        k_rcs_reduce<double><<<g, 256, 0, p->st>>>(p->nnzb, p->pptr, p->plist, (const double *)p->part,
+                                                   (double *)p->S);
     ktimer_end(p, K_RCS_REDUCE, ev);
     p->launches += 1;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
