@@ -269,8 +269,11 @@ __device__ __forceinline__ void cam_point_v(const float *camc, int i, const doub
 // thread per point re-reading its rows from cache, and a warp-cooperative
 // variant over batches of points, both measured slower).  The trial cameras
 // (cache included) are formed before.
+constexpr int STEP_THREADS = 256;
+constexpr int STEP_OBS_PER_THREAD = (OBS_MAX_LIMIT + STEP_THREADS - 1) / STEP_THREADS;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict__ grp, int ngroups,
+__global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *__restrict__ grp, int ngroups,
                                                      const int *__restrict__ trk_ptr, const int *__restrict__ obs_cam,
                                                      const int *__restrict__ obs_pt, const T *__restrict__ uv,
                                                      const T *__restrict__ J, const T *__restrict__ dxc,
@@ -287,12 +290,16 @@ __global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict
     // one row buffer (more CTAs per SM rather than a second buffer); per point
     // of the current group dx_p (3 T), its trial split (6 float) and, FP64
     // only, the trial point (3 double); per observation J_p^T J_c dx_c (3 T),
-    // J_c dx_c (2 T) and the camera
+    // J_c dx_c (2 T) and the camera.  Each thread keeps J_p and e of its own
+    // observations (at most STEP_OBS_PER_THREAD) in registers from the first
+    // pass to the trial evaluation, so the row buffer is free for the next
+    // group's copy after the first pass.
     const size_t buf_bytes = (size_t)obs_max * JW * sizeof(T);
     const size_t np = (size_t)obs_max / 2;
-    T *s_dp = reinterpret_cast<T *>(smem_raw + buf_bytes);
+    unsigned char *aux = smem_raw + buf_bytes;
+    T *s_dp = reinterpret_cast<T *>(aux);
     float *s_hl = reinterpret_cast<float *>(s_dp + np * 3);
-    double *s_xt = reinterpret_cast<double *>(smem_raw + buf_bytes + np * (3 * sizeof(T) + 6 * sizeof(float)));
+    double *s_xt = reinterpret_cast<double *>(aux + np * (3 * sizeof(T) + 6 * sizeof(float)));
     T *s_c3 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s_xt) + (sizeof(T) == 8 ? np * 24 : 0));
     T *s_jc = s_c3 + (size_t)obs_max * 3;
     int *s_cam = reinterpret_cast<int *>(s_jc + (size_t)obs_max * 2);
@@ -330,7 +337,11 @@ __global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict
         const GroupDesc g = sdesc;
         const T *so = reinterpret_cast<const T *>(smem_raw);
         // per observation: J_c dx_c and its image J_p^T J_c dx_c under J_p
-        for (int al = threadIdx.x; al < g.nobs; al += blockDim.x) {
+        T pe[STEP_OBS_PER_THREAD][8];
+#pragma unroll
+        for (int k = 0; k < STEP_OBS_PER_THREAD; ++k) {
+            const int al = threadIdx.x + k * STEP_THREADS;
+            if (al >= g.nobs) break;
             const int i = __ldg(obs_cam + g.obs_begin + al);
             const T *dc = dxc + 6 * i;
             T j[JW];
@@ -343,8 +354,13 @@ __global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict
             s_jc[2 * al] = t0;
             s_jc[2 * al + 1] = t1;
             s_cam[al] = i;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) pe[k][q] = j[12 + q];
         }
         __syncthreads();
+        // the rows are no longer read: the next group's copy overlaps the rest
+        const int gn = gi + gridDim.x;
+        if (threadIdx.x == 0 && gn < ngroups) issue(gn);
         // Eq. 5 per point: dx_p = L^-T L^-1 (l_p - sum over the track)
         for (int pl = threadIdx.x; pl < g.npts; pl += blockDim.x) {
             const int64_t kp = (int64_t)g.pt_begin + pl;
@@ -376,7 +392,10 @@ __global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict
         }
         __syncthreads();
         // the trial cost and the model decrease, one thread per observation
-        for (int al = threadIdx.x; al < g.nobs; al += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < STEP_OBS_PER_THREAD; ++k) {
+            const int al = threadIdx.x + k * STEP_THREADS;
+            if (al >= g.nobs) break;
             const int64_t a = (int64_t)g.obs_begin + al;
             const int i = s_cam[al], pl = __ldg(obs_pt + a) - g.pt_begin;
             T Xc[3];
@@ -386,18 +405,17 @@ __global__ void __launch_bounds__(256) k_step_groups(const GroupDesc *__restrict
             const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
             f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, dl));
             ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
-            const T *jr = so + al * JW;
+            const T *jr = pe[k];  // J_p (2 x 3), e
             T jd0 = s_jc[2 * al], jd1 = s_jc[2 * al + 1];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                jd0 += jr[12 + c] * s_dp[3 * pl + c];
-                jd1 += jr[15 + c] * s_dp[3 * pl + c];
+                jd0 += jr[c] * s_dp[3 * pl + c];
+                jd1 += jr[3 + c] * s_dp[3 * pl + c];
             }
-            mdl.add(-(jd0 * (T(2) * jr[18] + jd0) + jd1 * (T(2) * jr[19] + jd1)));
+            mdl.add(-(jd0 * (T(2) * jr[6] + jd0) + jd1 * (T(2) * jr[7] + jd1)));
         }
-        __syncthreads();  // buffer and point area free for the next group
-        const int gn = gi + gridDim.x;
-        if (threadIdx.x == 0 && gn < ngroups) issue(gn);
+        // the per-point and per-observation areas are rewritten only after the
+        // barrier that follows the next group's copy wait
     }
     double v[3] = {f.get(), mdl.get(), (double)ncheir};
     grid_sum<3>(v, red, ctr, [&](double *t) {
@@ -539,6 +557,7 @@ cudaError_t launch_trial_cameras(ba_problem *p) {
 template <typename T>
 static cudaError_t step_groups_T(ba_problem *p, long long limit) {
     static int ctas_per_sm = -1, n_sm = 0;
+    static size_t smem_seen = 0;
     const size_t smem = (size_t)p->obs_max * JW * sizeof(T) +
                         (size_t)p->obs_max / 2 * (3 * sizeof(T) + 6 * sizeof(float) + (sizeof(T) == 8 ? 24 : 0)) +
                         (size_t)p->obs_max * (5 * sizeof(T) + sizeof(int));
@@ -546,18 +565,19 @@ static cudaError_t step_groups_T(ba_problem *p, long long limit) {
     if ((e = cudaFuncSetAttribute(k_step_groups<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
-    if (ctas_per_sm < 0) {
+    if (ctas_per_sm < 0 || smem != smem_seen) {
+        smem_seen = smem;
         int dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_step_groups<T>, 256, smem)) !=
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_step_groups<T>, STEP_THREADS, smem)) !=
             cudaSuccess)
             return e;
         if (ctas_per_sm < 1) ctas_per_sm = 1;
     }
     const int grid = (int)std::min<int64_t>(p->ngroups, (int64_t)ctas_per_sm * n_sm);
     const int hub = p->opt.robust == BA_LOSS_HUBER;
-    k_step_groups<T><<<grid, 256, smem, p->st>>>(
+    k_step_groups<T><<<grid, STEP_THREADS, smem, p->st>>>(
         p->grp, (int)p->ngroups, p->trk_ptr, p->obs_cam, p->obs_pt, (const T *)(p->fp32 ? (const void *)p->uv32
                                                                                         : (const void *)p->uv64),
         (const T *)p->J, (const T *)p->dxc, (const T *)p->Linv, (const T *)p->lp, p->cur.pts,
