@@ -17,6 +17,8 @@ matrix compression for super large scale datasets"):
 * Sec. 4 (Fig. 4, Eq. 9): BSMC storage - upper-triangle non-zero blocks,
   per-block column ids, per-row start, diagonal block first in each row.
 * Sec. 6.2 (Fig. 13): the BSMC matrix-vector product.
+* Sec. 3.1 (after Eq. 5) and Sec. 5: the points may instead be triangulated
+  from the camera poses; the method is not given (a reading below).
 
 Readings of what the paper leaves open (each one is listed in the design doc):
 
@@ -32,7 +34,11 @@ Readings of what the paper leaves open (each one is listed in the design doc):
   on reject lambda *= nu, nu *= 2);
 * robust loss (not in the paper): Huber on the squared norm s = ||e||^2,
   rho(s) = s for s <= delta^2 else 2 delta sqrt(s) - delta^2, applied by
-  scaling e and J with sqrt(rho'(s)) (first-order IRLS).
+  scaling e and J with sqrt(rho'(s)) (first-order IRLS);
+* triangulation: per point, the linear least-squares intersection of its
+  observations (each gives two equations linear in X from the pinhole model
+  with the depth multiplied out), then Gauss-Newton steps on the point's
+  plain reprojection error.
 """
 from __future__ import annotations
 
@@ -456,6 +462,42 @@ class Problem:
 def rms_px(cams, pts, obs_cam, obs_pt, obs_uv, intr):
     e, _ = residuals(cams, pts, obs_cam, obs_pt, obs_uv, intr)
     return float(np.sqrt(np.sum(e * e) / len(e)))
+
+
+# ----------------------------------------------------------------------------
+# triangulation from the camera poses (Sec. 3.1 after Eq. 5; Sec. 5)
+# ----------------------------------------------------------------------------
+
+def triangulation_rows(cam, uv, intr: Intrinsics):
+    """The two equations a X = r of one observation, linear in the point X:
+    with X_cam = R X + t, u - cx = f x/z and v - cy = f y/z, multiplying out z
+    gives ((u - cx) R_3 - f R_1) . X = f t_1 - (u - cx) t_3 and the same with
+    (v, cy, R_2, t_2)."""
+    R = rodrigues(cam[:3])
+    t = cam[3:]
+    du, dv = uv[0] - intr.cx, uv[1] - intr.cy
+    A = np.stack([du * R[2] - intr.f * R[0], dv * R[2] - intr.f * R[1]])
+    r = np.array([intr.f * t[0] - du * t[2], intr.f * t[1] - dv * t[2]])
+    return A, r
+
+
+def triangulate(cams, obs_cam, obs_pt, obs_uv, intr: Intrinsics, P: int, gn_iters: int = 3):
+    """Every point from the cameras: the least-squares solution of its stacked
+    linear equations (numpy lstsq), then gn_iters Gauss-Newton steps
+    (J_p^T J_p) dX = -J_p^T e on its reprojection error."""
+    obs_cam = np.asarray(obs_cam, dtype=np.int64)
+    out = np.zeros((P, 3))
+    for k, tr in enumerate(tracks(obs_pt, P)):
+        rows = [triangulation_rows(cams[obs_cam[a]], obs_uv[a], intr) for a in tr]
+        A = np.concatenate([r[0] for r in rows])
+        r = np.concatenate([r[1] for r in rows])
+        X = np.linalg.lstsq(A, r, rcond=None)[0]
+        for _ in range(gn_iters):
+            e, _, Jp = jacobians(cams, X[None, :], obs_cam[tr], np.zeros(len(tr), dtype=np.int64), obs_uv[tr], intr)
+            Jp = Jp.reshape(-1, 3)
+            X = X + np.linalg.solve(Jp.T @ Jp, -Jp.T @ e.reshape(-1))
+        out[k] = X
+    return out
 
 
 # ----------------------------------------------------------------------------

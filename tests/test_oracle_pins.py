@@ -393,3 +393,60 @@ def test_bsmc_and_csr_byte_counts():
     for a in (1e-3, 1e-4):
         for nn in (10_000, 200_000):
             assert 1.4 < O.csr_bsmc_ratio(a, nn, 11) < 3.0
+
+
+# ------------------------------------------------ triangulation (Sec. 3.1 after Eq. 5)
+
+def test_triangulation_rows_hold_for_exact_observations():
+    """Each observation's two linear equations are satisfied by the true point
+    (pixels synthesised by scipy's rotation, not the oracle's Rodrigues)."""
+    rng = np.random.default_rng(3)
+    intr = O.Intrinsics()
+    for _ in range(20):
+        w = rng.normal(0, 0.5, 3)
+        t = rng.normal(0, 5, 3)
+        X = rng.normal(0, 3, 3)
+        R = Rotation.from_rotvec(w).as_matrix()
+        Xc = R @ X + t
+        Xc[2] = abs(Xc[2]) + 5.0
+        t = Xc - R @ X  # a point in front of the camera
+        uv = np.array([intr.f * Xc[0] / Xc[2] + intr.cx, intr.f * Xc[1] / Xc[2] + intr.cy])
+        A, r = O.triangulation_rows(np.concatenate([w, t]), uv, intr)
+        np.testing.assert_allclose(A @ X, r, rtol=0, atol=1e-9 * np.abs(r).max())
+    # hand case: camera at the origin looking down +z, point (1, 2, 10):
+    # u = 1000 * 0.1 + 500 = 600, v = 700; rows (-1000, 0, 100) and (0, -1000, 200), rhs 0
+    A, r = O.triangulation_rows(np.zeros(6), np.array([600.0, 700.0]), intr)
+    np.testing.assert_allclose(A, [[-1000.0, 0.0, 100.0], [0.0, -1000.0, 200.0]])
+    np.testing.assert_allclose(r, [0.0, 0.0])
+
+
+@pytest.mark.parametrize("gn", [0, 3])
+def test_triangulation_recovers_noise_free_points(gn):
+    s = scenes.aerial_small(n_along=6, n_across=4, pts_per_cam=30, seed=77, sigma_px=0.0)
+    X = O.triangulate(s.cams_gt, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics(), s.n_pts, gn_iters=gn)
+    assert np.abs(X - s.pts_gt).max() <= 1e-9 * np.abs(s.pts_gt).max()
+
+
+def test_triangulation_is_the_least_squares_optimum():
+    """Noisy pixels: after Gauss-Newton every point is a stationary point of
+    its reprojection error (J_p^T e = 0), and an independent optimiser
+    (scipy least_squares, started elsewhere) finds the same points."""
+    from scipy.optimize import least_squares
+    s = scenes.aerial_small(n_along=6, n_across=4, pts_per_cam=30, seed=78, sigma_px=1.0)
+    intr = O.Intrinsics()
+    X = O.triangulate(s.cams_gt, s.obs_cam, s.obs_pt, s.obs_uv, intr, s.n_pts, gn_iters=5)
+    tr = O.tracks(s.obs_pt, s.n_pts)
+    for k in range(0, s.n_pts, 37):
+        a = tr[k]
+        sub = np.zeros(len(a), dtype=np.int64)
+        e, _, Jp = O.jacobians(s.cams_gt, X[k][None, :], s.obs_cam[a], sub, s.obs_uv[a], intr)
+        g = np.einsum("mij,mi->j", Jp, e)
+        assert np.linalg.norm(g) <= 1e-8 * np.linalg.norm(Jp) * max(np.linalg.norm(e), 1e-3)
+
+        def res(p):
+            R = Rotation.from_rotvec(s.cams_gt[s.obs_cam[a], :3]).as_matrix()
+            Xc = np.einsum("mij,j->mi", R, p) + s.cams_gt[s.obs_cam[a], 3:]
+            return (np.stack([intr.f * Xc[:, 0] / Xc[:, 2] + intr.cx,
+                              intr.f * Xc[:, 1] / Xc[:, 2] + intr.cy], 1) - s.obs_uv[a]).reshape(-1)
+        ref = least_squares(res, s.pts_gt[k] + 0.5, xtol=1e-14, ftol=1e-14, gtol=1e-14).x
+        assert np.abs(ref - X[k]).max() <= 1e-6, (k, ref, X[k])
