@@ -286,6 +286,7 @@ def run_ours(args):
     kernels = {nm: {"launches": v[0], "ms": round(v[1], 3)} for nm, v in ktimes.items() if v[0]}
     cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload, s.n_obs)
     formats = None if args.no_formats else formats_bench(B, torch, g, st1, esz, peaks, peak_kind, stream)
+    tri = triangulation_bench(g, st1, ktimes)
     g.close()
     solver = None if args.no_solver else solver_bench(B, torch)
     acc = sum(i["accepted"] for i in infos)
@@ -300,7 +301,7 @@ def run_ours(args):
         "lm": {"accepted": acc, "pcg_iters": [i["pcg_iters"] for i in infos],
                "cost": [infos[0]["cost_before"], infos[-1]["cost_after"]],
                "rcs_rel_resid_max": max(i["rcs_rel_resid"] for i in infos)},
-        "kernels_ms": kernels, "solver": solver, "spmv_formats": formats, "impl": "ours",
+        "kernels_ms": kernels, "solver": solver, "spmv_formats": formats, "triangulation": tri, "impl": "ours",
         "setup": {"problem_create_s": round(t_create, 2), "device_bytes": int(st1["device_bytes"]),
                   "preconditioner": "learned (packaged weights), block-Jacobi fallback" if net else "block-Jacobi",
                   "used_fallback": [i["used_fallback"] for i in infos]},
@@ -362,6 +363,23 @@ def formats_bench(B, torch, g, st, esz, peaks, peak_kind, stream, repeats=7):
             "bytes_csr_over_bsmc": round(res["csr"]["format_bytes"] / res["bsmc"]["format_bytes"], 3),
             "time_csr_over_bsmc": round(res["csr"]["us"] / res["bsmc"]["us"], 3),
             "time_bsr_full_over_bsmc": round(res["bsr_full"]["us"] / res["bsmc"]["us"], 3)}
+
+
+def triangulation_bench(g, st, ktimes, gn_iters=3, repeats=3):
+    """Every point re-triangulated from the final cameras (ba_triangulate:
+    linear solve + Gauss-Newton, FP64), after the timed LM steps, timed by the
+    library's CUDA events; beside it the point pass of the LM step (Eq. 5
+    back-substitution with the trial evaluation) from the timed steps."""
+    g.reset_kernel_times()
+    fails = []
+    for _ in range(repeats):
+        fails.append(g.triangulate(gn_iters)[0])
+    n, ms = g.kernel_times()["triangulate"]
+    avg = ms / max(n, 1)
+    sp = ktimes.get("step_points", (0, 0.0))
+    return {"gn_iters": gn_iters, "ms": round(avg, 4), "points_per_s": round(st["n_pts"] / (avg / 1e3)),
+            "points_unchanged": fails[-1],
+            "lm_point_pass_ms": round(sp[1] / sp[0], 4) if sp[0] else None}
 
 
 def pcg_bytes_per_iteration(st, esz=4):

@@ -182,6 +182,22 @@ ba_status ba_get_points(const ba_problem *p, double *out_pts);
 ba_status ba_get_rcs(const ba_problem *p, int64_t *nnzb, int32_t *row_ptr, int32_t *col,
                      double *val, double *b);
 
+/* Triangulation of every point from the current cameras, the alternative to
+ * the back-substitution of Eq. 5 that Sec. 3.1 (after Eq. 5) and Sec. 5 name
+ * without giving the method.  Per point, in FP64: the least-squares solution
+ * of the two equations each observation gives, linear in the point X (the
+ * pinhole model with the depth multiplied out:
+ * ((u - cx) R_3 - fx R_1) . X = fx t_1 - (u - cx) t_3 and likewise for v),
+ * through its 3x3 normal equations, then gn_iters (0..50) Gauss-Newton steps
+ * on the point's plain reprojection error.  The points of the current state
+ * are replaced (cameras unchanged; the linearization and RCS are dropped, as
+ * by ba_set_state).  A point whose 3x3 system is not positive definite, or
+ * whose result is not finite, keeps its value; n_failed_out (may be NULL)
+ * receives their number.  cost_out (may be NULL) receives the cost at the
+ * new state.  Errors: BA_ERR_INVALID_ARG, BA_ERR_STATE (RCS-only problem),
+ * BA_ERR_CUDA. */
+ba_status ba_triangulate(ba_problem *p, int32_t gn_iters, int64_t *n_failed_out, double *cost_out);
+
 /* The last step: dxc[n x 6], dxp[n_pts x 3] (caller's point order). */
 ba_status ba_get_step(const ba_problem *p, double *dxc, double *dxp);
 

@@ -105,6 +105,7 @@ SIGNATURES = [
     ("ba_get_rcs", _S, [_P, _I64, _I32, _I32, _D, _D]),
     ("ba_get_step", _S, [_P, _D, _D]),
     ("ba_rcs_spmv", _S, [_P, ctypes.c_int32, _P, _P, _I64]),
+    ("ba_triangulate", _S, [_P, ctypes.c_int32, _I64, _D]),
     ("ba_get_linearization", _S, [_P, _D, _D, _D]),
     ("ba_set_state", _S, [_P, _D, _D, ctypes.c_double, ctypes.c_double]),
     ("ba_get_lm_state", _S, [_P, _D, _D, _D]),
@@ -274,6 +275,15 @@ def ba_rcs_spmv(h, fmt, x_ptr, y_ptr):
     return nb.value
 
 
+def ba_triangulate(h, gn_iters=3):
+    """Re-triangulates every point from the current cameras; returns
+    (points left unchanged, cost at the new state)."""
+    nf = ctypes.c_int64()
+    cost = ctypes.c_double()
+    _check(lib().ba_triangulate(h, int(gn_iters), ctypes.byref(nf), ctypes.byref(cost)))
+    return nf.value, cost.value
+
+
 def ba_get_step(h, n, P):
     dxc = np.empty((n, 6))
     dxp = np.empty((P, 3))
@@ -415,6 +425,11 @@ class Problem:
 
     def rcs(self):
         return ba_get_rcs(self.h, self.n)
+
+    def triangulate(self, gn_iters=3):
+        """Points re-triangulated from the current cameras (linear, then
+        Gauss-Newton); returns (points left unchanged, new cost)."""
+        return ba_triangulate(self.h, gn_iters)
 
     def rcs_spmv(self, fmt, x, y):
         """y = S x (torch CUDA tensors of 6n values, float64 for FP64

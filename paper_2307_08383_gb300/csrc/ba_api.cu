@@ -46,7 +46,8 @@ const char *kernel_name(int k) {
     static const char *names[K_COUNT] = {"prepare_state", "linearize", "cost",    "form_rcs",
                                          "rcs_reduce",    "rcs_diag",  "pcg_init", "pcg_loop",
                                          "resid64",       "back_substitute", "trial_cameras",
-                                         "demote",        "split_prepare", "step_points"};
+                                         "demote",        "split_prepare", "step_points",
+                                         "triangulate"};
     return (k >= 0 && k < K_COUNT) ? names[k] : nullptr;
 }
 
@@ -903,6 +904,24 @@ ba_status ba_rcs_spmv(ba_problem *p, int32_t format, const void *x, void *y, int
     }
     CK(p, launch_rcs_spmv(p, format, x, y));
     if (bytes_out) *bytes_out = rcs_format_bytes(p, format);
+    return BA_OK;
+}
+
+ba_status ba_triangulate(ba_problem *p, int32_t gn_iters, int64_t *n_failed_out, double *cost_out) {
+    LIVE(p);
+    if (p->rcs_only) return fail(BA_ERR_STATE, "ba_triangulate: the problem holds an RCS only");
+    if (gn_iters < 0 || gn_iters > 50) return fail(BA_ERR_INVALID_ARG, "gn_iters must be in [0, 50]");
+    CK(p, launch_triangulate(p, gn_iters));
+    CK(p, launch_prepare_state(p, p->cur));
+    p->have_F = false;
+    p->linearized = p->rcs_formed = p->solved = p->backsub = false;
+    ba_status s = sync_scalars(p);
+    if (s) return s;
+    if (n_failed_out) *n_failed_out = (int64_t)p->sc_host->n_tri_fail;
+    if (cost_out) {
+        if ((s = ensure_cost(p))) return s;
+        *cost_out = p->F;
+    }
     return BA_OK;
 }
 

@@ -49,6 +49,7 @@ struct DevScalars {
     double rz, pAp, rr, rr0, alpha, beta, tol2;
     double rr64, bb64;
     unsigned long long n_cheir, n_cheir_trial, n_v64;
+    unsigned long long n_tri_fail;  // points triangulation left unchanged (last ba_triangulate)
     int iters, done, max_iters, err;
     int prof_on;   // split CG: time its phases (profile >= 2)
     double ph[4];  // split CG phase ns summed over CTAs and iterations; ph[3] = CTA iterations
@@ -60,7 +61,8 @@ constexpr int RED_SLOTS = 4096 * 4;  // per-CTA partial sums
 
 enum KernelId {
     K_PREPARE = 0, K_LINEARIZE, K_COST, K_FORM_RCS, K_RCS_REDUCE, K_RCS_DIAG,
-    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_DEMOTE, K_SPLIT_PREP, K_STEP_POINTS, K_COUNT
+    K_PCG_INIT, K_PCG_LOOP, K_RESID64, K_BACKSUB, K_UPDATE, K_DEMOTE, K_SPLIT_PREP, K_STEP_POINTS, K_TRIANGULATE,
+    K_COUNT
 };
 const char *kernel_name(int k);
 
@@ -149,6 +151,7 @@ struct ba_problem {
     uint64_t rcs_gen = 0, fmt_gen[3] = {~0ull, ~0ull, ~0ull};
     void *fmt_bsr_val = nullptr, *fmt_csr_val = nullptr;
     int32_t *fmt_bsr_col = nullptr, *fmt_csr_ptr = nullptr, *fmt_csr_col = nullptr;
+    double *tri_cam64 = nullptr;  // n x 12 FP64 [R | t] for the triangulation
     ba::GroupDesc *grp = nullptr;
     ba::ItemDesc *items = nullptr;
     uint32_t *contrib = nullptr;
@@ -255,6 +258,8 @@ cudaError_t launch_pcg_split(ba_problem *p);
 cudaError_t launch_accumulate_split(ba_problem *p, bool first);
 // y = S x for one FP32 vector (learned-preconditioner probes)
 cudaError_t launch_spmv_f32(ba_problem *p, const float *x, float *y);
+// every point re-triangulated from the current cameras (k_obs.cu)
+cudaError_t launch_triangulate(ba_problem *p, int gn_iters);
 // RCS storage formats (k_formats.cu)
 cudaError_t launch_rcs_format_build(ba_problem *p, int format);
 cudaError_t launch_rcs_spmv(ba_problem *p, int format, const void *x, void *y);

@@ -425,6 +425,91 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *_
     });
 }
 
+// Triangulation of the points from the camera poses, the alternative the
+// paper gives to the back-substitution of Eq. 5 (Sec. 3.1; Sec. 5): a thread
+// per point, in FP64.  Each observation gives two equations linear in the
+// point X (the pinhole model with the depth multiplied out):
+//   ((u - cx) R_3 - fx R_1) . X = fx t_1 - (u - cx) t_3,
+//   ((v - cy) R_3 - fy R_2) . X = fy t_2 - (v - cy) t_3;
+// their normal equations are solved by a 3x3 Cholesky factorisation, then
+// gn_iters Gauss-Newton steps (J_p^T J_p) dX = -J_p^T e refine X on the
+// reprojection error.  A point whose 3x3 matrix is not positive definite, or
+// whose result is not finite, keeps its value and is counted.
+__device__ __forceinline__ bool chol3_solve(const double (&N)[6], const double (&h)[3], double (&x)[3]) {
+    // N = [n00 n01 n02; . n11 n12; . . n22] packed as (00, 01, 02, 11, 12, 22)
+    if (!(N[0] > 0.0)) return false;
+    const double l00 = sqrt(N[0]), l10 = N[1] / l00, l20 = N[2] / l00;
+    const double d1 = N[3] - l10 * l10;
+    if (!(d1 > 0.0)) return false;
+    const double l11 = sqrt(d1), l21 = (N[4] - l20 * l10) / l11;
+    const double d2 = N[5] - l20 * l20 - l21 * l21;
+    if (!(d2 > 0.0)) return false;
+    const double l22 = sqrt(d2);
+    const double y0 = h[0] / l00, y1 = (h[1] - l10 * y0) / l11, y2 = (h[2] - l20 * y0 - l21 * y1) / l22;
+    x[2] = y2 / l22;
+    x[1] = (y1 - l21 * x[2]) / l11;
+    x[0] = (y0 - l10 * x[1] - l20 * x[2]) / l00;
+    return true;
+}
+__device__ __forceinline__ void sym3_add(double (&N)[6], double (&h)[3], const double (&a)[3], double r) {
+    N[0] += a[0] * a[0]; N[1] += a[0] * a[1]; N[2] += a[0] * a[2];
+    N[3] += a[1] * a[1]; N[4] += a[1] * a[2]; N[5] += a[2] * a[2];
+    h[0] += a[0] * r; h[1] += a[1] * r; h[2] += a[2] * r;
+}
+__global__ void __launch_bounds__(256) k_triangulate(int64_t P, const int *__restrict__ trk_ptr,
+                                                     const int *__restrict__ obs_cam, const double *__restrict__ uv,
+                                                     const double *__restrict__ cam64, Intr in, int gn_iters,
+                                                     double *__restrict__ pts, unsigned long long *nfail) {
+    unsigned long long bad = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+        const int a0 = __ldg(trk_ptr + k), a1 = __ldg(trk_ptr + k + 1);
+        double N[6] = {0, 0, 0, 0, 0, 0}, h[3] = {0, 0, 0}, X[3];
+        for (int a = a0; a < a1; ++a) {
+            const double *c = cam64 + 12 * (int64_t)__ldg(obs_cam + a);
+            const double du = uv[2 * (int64_t)a] - in.cx, dv = uv[2 * (int64_t)a + 1] - in.cy;
+            const double r0[3] = {du * c[6] - in.fx * c[0], du * c[7] - in.fx * c[1], du * c[8] - in.fx * c[2]};
+            const double r1[3] = {dv * c[6] - in.fy * c[3], dv * c[7] - in.fy * c[4], dv * c[8] - in.fy * c[5]};
+            sym3_add(N, h, r0, in.fx * c[9] - du * c[11]);
+            sym3_add(N, h, r1, in.fy * c[10] - dv * c[11]);
+        }
+        bool ok = chol3_solve(N, h, X);
+        for (int it = 0; ok && it < gn_iters; ++it) {
+            double M[6] = {0, 0, 0, 0, 0, 0}, g[3] = {0, 0, 0}, dX[3];
+            for (int a = a0; a < a1; ++a) {
+                const double *c = cam64 + 12 * (int64_t)__ldg(obs_cam + a);
+                const double x = c[0] * X[0] + c[1] * X[1] + c[2] * X[2] + c[9];
+                const double y = c[3] * X[0] + c[4] * X[1] + c[5] * X[2] + c[10];
+                const double z = c[6] * X[0] + c[7] * X[1] + c[8] * X[2] + c[11];
+                const double iz = 1.0 / z;
+                const double e0 = in.fx * x * iz + in.cx - uv[2 * (int64_t)a];
+                const double e1 = in.fy * y * iz + in.cy - uv[2 * (int64_t)a + 1];
+                // J_p = d(pi)/d(X_cam) R: rows fx/z (R_1 - x/z R_3), fy/z (R_2 - y/z R_3)
+                const double j0[3] = {in.fx * iz * (c[0] - x * iz * c[6]), in.fx * iz * (c[1] - x * iz * c[7]),
+                                      in.fx * iz * (c[2] - x * iz * c[8])};
+                const double j1[3] = {in.fy * iz * (c[3] - y * iz * c[6]), in.fy * iz * (c[4] - y * iz * c[7]),
+                                      in.fy * iz * (c[5] - y * iz * c[8])};
+                sym3_add(M, g, j0, -e0);
+                sym3_add(M, g, j1, -e1);
+            }
+            ok = chol3_solve(M, g, dX);
+            if (ok) {
+                X[0] += dX[0];
+                X[1] += dX[1];
+                X[2] += dX[2];
+            }
+        }
+        ok = ok && isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2]);
+        if (ok) {
+            pts[3 * k] = X[0];
+            pts[3 * k + 1] = X[1];
+            pts[3 * k + 2] = X[2];
+        } else {
+            ++bad;
+        }
+    }
+    if (bad) atomicAdd(nfail, bad);
+}
+
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
@@ -583,6 +668,27 @@ static cudaError_t step_groups_T(ba_problem *p, long long limit) {
         (const T *)p->J, (const T *)p->dxc, (const T *)p->Linv, (const T *)p->lp, p->cur.pts,
         (const T *)p->trial.camc, intr_of(p), hub, p->opt.huber_delta, (T *)p->dxp, p->trial.pts,
         p->fp32 ? p->trial.pts_hl : nullptr, p->sc, p->red, p->counters + 1, p->obs_max, limit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_triangulate(ba_problem *p, int gn_iters) {
+    cudaError_t e;
+    if (!p->tri_cam64) {
+        void *d = nullptr;
+        if ((e = cudaMalloc(&d, (size_t)p->n * 12 * sizeof(double))) != cudaSuccess) return e;
+        p->allocs.push_back(d);
+        p->dev_bytes += (size_t)p->n * 12 * sizeof(double);
+        p->tri_cam64 = (double *)d;
+    }
+    cudaEvent_t ev;
+    ktimer_begin(p, K_TRIANGULATE, &ev);
+    k_prepare_cams64<<<(p->n + 127) / 128, 128, 0, p->st>>>(p->n, p->cur.cams, p->tri_cam64);
+    if ((e = cudaMemsetAsync(&p->sc->n_tri_fail, 0, sizeof(unsigned long long), p->st)) != cudaSuccess) return e;
+    k_triangulate<<<grid_for(p->P, 256, GRID_CAP), 256, 0, p->st>>>(p->P, p->trk_ptr, p->obs_cam, p->uv64,
+                                                                    p->tri_cam64, intr_of(p), gn_iters, p->cur.pts,
+                                                                    &p->sc->n_tri_fail);
+    ktimer_end(p, K_TRIANGULATE, ev);
+    p->launches += 2;
     return cudaGetLastError();
 }
 
