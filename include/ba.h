@@ -184,12 +184,14 @@ ba_status ba_get_rcs(const ba_problem *p, int64_t *nnzb, int32_t *row_ptr, int32
 
 /* Triangulation of every point from the current cameras, the alternative to
  * the back-substitution of Eq. 5 that Sec. 3.1 (after Eq. 5) and Sec. 5 name
- * without giving the method.  Per point, in FP64: the least-squares solution
- * of the two equations each observation gives, linear in the point X (the
- * pinhole model with the depth multiplied out:
+ * without giving the method.  Per point: the least-squares solution of the
+ * two equations each observation gives, linear in the point X (the pinhole
+ * model with the depth multiplied out:
  * ((u - cx) R_3 - fx R_1) . X = fx t_1 - (u - cx) t_3 and likewise for v),
  * through its 3x3 normal equations, then gn_iters (0..50) Gauss-Newton steps
- * on the point's plain reprojection error.  The points of the current state
+ * on the point's plain reprojection error.  FP64 problems compute in FP64;
+ * FP32 problems in FP32, for the offset from the current point (camera-point
+ * vectors from the FP32 state caches), added to it in FP64.  The points of the current state
  * are replaced (cameras unchanged; the linearization and RCS are dropped, as
  * by ba_set_state).  A point whose 3x3 system is not positive definite, or
  * whose result is not finite, keeps its value; n_failed_out (may be NULL)

@@ -510,6 +510,89 @@ __global__ void __launch_bounds__(256) k_triangulate(int64_t P, const int *__res
     if (bad) atomicAdd(nfail, bad);
 }
 
+// The same for FP32 problems on the FP32 pipe, centred on each point's
+// current value X0: with X = X0 + d, observation a's equations read
+//   ((u - cx) R_3 - fx R_1) . d = fx x0 - (u - cx) z0   (and likewise for v),
+// (x0, y0, z0) = R X0 + t formed from the FP32 camera and point caches as
+// R ((X0_hi - C_hi) + (X0_lo - C_lo)), exact to the camera-point distance
+// rather than the world offset; Gauss-Newton on d; X = X0 + d in FP64.
+__device__ __forceinline__ bool chol3_solve(const float (&N)[6], const float (&h)[3], float (&x)[3]) {
+    if (!(N[0] > 0.f)) return false;
+    const float l00 = sqrtf(N[0]), l10 = N[1] / l00, l20 = N[2] / l00;
+    const float d1 = N[3] - l10 * l10;
+    if (!(d1 > 0.f)) return false;
+    const float l11 = sqrtf(d1), l21 = (N[4] - l20 * l10) / l11;
+    const float d2 = N[5] - l20 * l20 - l21 * l21;
+    if (!(d2 > 0.f)) return false;
+    const float l22 = sqrtf(d2);
+    const float y0 = h[0] / l00, y1 = (h[1] - l10 * y0) / l11, y2 = (h[2] - l20 * y0 - l21 * y1) / l22;
+    x[2] = y2 / l22;
+    x[1] = (y1 - l21 * x[2]) / l11;
+    x[0] = (y0 - l10 * x[1] - l20 * x[2]) / l00;
+    return true;
+}
+__device__ __forceinline__ void sym3_add(float (&N)[6], float (&h)[3], const float (&a)[3], float r) {
+    N[0] += a[0] * a[0]; N[1] += a[0] * a[1]; N[2] += a[0] * a[2];
+    N[3] += a[1] * a[1]; N[4] += a[1] * a[2]; N[5] += a[2] * a[2];
+    h[0] += a[0] * r; h[1] += a[1] * r; h[2] += a[2] * r;
+}
+__global__ void __launch_bounds__(256) k_triangulate32(int64_t P, const int *__restrict__ trk_ptr,
+                                                       const int *__restrict__ obs_cam, const float *__restrict__ uv,
+                                                       const float *__restrict__ camc, const float *__restrict__ hl,
+                                                       Intr in, int gn_iters, double *__restrict__ pts,
+                                                       unsigned long long *nfail) {
+    const float fx = (float)in.fx, fy = (float)in.fy, cx = (float)in.cx, cy = (float)in.cy;
+    unsigned long long bad = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+        const int a0 = __ldg(trk_ptr + k), a1 = __ldg(trk_ptr + k + 1);
+        float N[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f}, d[3];
+        for (int a = a0; a < a1; ++a) {
+            float Xc[3], R[9];
+            cam_point(camc, nullptr, hl, __ldg(obs_cam + a), (int)k, Xc, R);
+            const float du = uv[2 * (int64_t)a] - cx, dv = uv[2 * (int64_t)a + 1] - cy;
+            const float r0[3] = {du * R[6] - fx * R[0], du * R[7] - fx * R[1], du * R[8] - fx * R[2]};
+            const float r1[3] = {dv * R[6] - fy * R[3], dv * R[7] - fy * R[4], dv * R[8] - fy * R[5]};
+            sym3_add(N, h, r0, fx * Xc[0] - du * Xc[2]);
+            sym3_add(N, h, r1, fy * Xc[1] - dv * Xc[2]);
+        }
+        bool ok = chol3_solve(N, h, d);
+        for (int it = 0; ok && it < gn_iters; ++it) {
+            float M[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f}, dd[3];
+            for (int a = a0; a < a1; ++a) {
+                float Xc[3], R[9];
+                cam_point(camc, nullptr, hl, __ldg(obs_cam + a), (int)k, Xc, R);
+                const float x = Xc[0] + R[0] * d[0] + R[1] * d[1] + R[2] * d[2];
+                const float y = Xc[1] + R[3] * d[0] + R[4] * d[1] + R[5] * d[2];
+                const float z = Xc[2] + R[6] * d[0] + R[7] * d[1] + R[8] * d[2];
+                const float iz = 1.f / z;
+                const float e0 = fx * x * iz + cx - uv[2 * (int64_t)a];
+                const float e1 = fy * y * iz + cy - uv[2 * (int64_t)a + 1];
+                const float j0[3] = {fx * iz * (R[0] - x * iz * R[6]), fx * iz * (R[1] - x * iz * R[7]),
+                                     fx * iz * (R[2] - x * iz * R[8])};
+                const float j1[3] = {fy * iz * (R[3] - y * iz * R[6]), fy * iz * (R[4] - y * iz * R[7]),
+                                     fy * iz * (R[5] - y * iz * R[8])};
+                sym3_add(M, g, j0, -e0);
+                sym3_add(M, g, j1, -e1);
+            }
+            ok = chol3_solve(M, g, dd);
+            if (ok) {
+                d[0] += dd[0];
+                d[1] += dd[1];
+                d[2] += dd[2];
+            }
+        }
+        ok = ok && isfinite(d[0]) && isfinite(d[1]) && isfinite(d[2]);
+        if (ok) {
+            pts[3 * k] += (double)d[0];
+            pts[3 * k + 1] += (double)d[1];
+            pts[3 * k + 2] += (double)d[2];
+        } else {
+            ++bad;
+        }
+    }
+    if (bad) atomicAdd(nfail, bad);
+}
+
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
@@ -673,6 +756,19 @@ static cudaError_t step_groups_T(ba_problem *p, long long limit) {
 
 cudaError_t launch_triangulate(ba_problem *p, int gn_iters) {
     cudaError_t e;
+    cudaEvent_t ev;
+    if (p->fp32) {
+        // the FP32 caches of the current state are up to date (every state
+        // change refreshes them)
+        ktimer_begin(p, K_TRIANGULATE, &ev);
+        if ((e = cudaMemsetAsync(&p->sc->n_tri_fail, 0, sizeof(unsigned long long), p->st)) != cudaSuccess) return e;
+        k_triangulate32<<<grid_for(p->P, 256, GRID_CAP), 256, 0, p->st>>>(
+            p->P, p->trk_ptr, p->obs_cam, p->uv32, (const float *)p->cur.camc, p->cur.pts_hl, intr_of(p), gn_iters,
+            p->cur.pts, &p->sc->n_tri_fail);
+        ktimer_end(p, K_TRIANGULATE, ev);
+        p->launches += 1;
+        return cudaGetLastError();
+    }
     if (!p->tri_cam64) {
         void *d = nullptr;
         if ((e = cudaMalloc(&d, (size_t)p->n * 12 * sizeof(double))) != cudaSuccess) return e;
@@ -680,7 +776,6 @@ cudaError_t launch_triangulate(ba_problem *p, int gn_iters) {
         p->dev_bytes += (size_t)p->n * 12 * sizeof(double);
         p->tri_cam64 = (double *)d;
     }
-    cudaEvent_t ev;
     ktimer_begin(p, K_TRIANGULATE, &ev);
     k_prepare_cams64<<<(p->n + 127) / 128, 128, 0, p->st>>>(p->n, p->cur.cams, p->tri_cam64);
     if ((e = cudaMemsetAsync(&p->sc->n_tri_fail, 0, sizeof(unsigned long long), p->st)) != cudaSuccess) return e;

@@ -1,12 +1,14 @@
 """GPU parity of the triangulation of the points from the camera poses (the
 alternative to the back-substitution of Eq. 5, Sec. 3.1 and Sec. 5) against
 the oracle: ba_triangulate (linear equations through their 3x3 normal
-matrix, then Gauss-Newton, FP64 on the GPU) vs the oracle's least-squares
-solution and Gauss-Newton steps.
+matrix, then Gauss-Newton; FP64 for FP64 problems, FP32 centred on the
+current points for FP32 problems) vs the oracle's least-squares solution and
+Gauss-Newton steps.
 
-Tolerances: points within 1e-7 m of the oracle's (the two reach the same
-reprojection optimum; scene extent ~200 m), 1e-8 relative on noise-free
-data against the ground truth; the reported cost within 1e-9 (FP64
+Tolerances: points within 1e-7 m (FP64) or 2e-4 m (FP32: camera-point
+vectors to ~1e-7 relative at ~100 m) of the oracle's (the two reach the
+same reprojection optimum; scene extent ~200 m), 1e-8 relative on
+noise-free data against the ground truth (FP64); the reported cost within 1e-9 (FP64
 problems) or 1e-3 (FP32 problems: FP32 camera caches) relative of the
 oracle's cost at the oracle's points.
 """
@@ -38,7 +40,7 @@ def test_triangulation_matches_oracle(B, prec):
     X = g.points()
     ref = O.triangulate(s.cams_gt, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics(), s.n_pts, gn_iters=3)
     assert nfail == 0
-    assert np.abs(X - ref).max() <= 1e-7, np.abs(X - ref).max()
+    assert np.abs(X - ref).max() <= (1e-7 if prec == "fp64" else 2e-4), np.abs(X - ref).max()
     F_ref = O.cost(s.cams_gt, ref, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics())
     tol = 1e-9 if prec == "fp64" else 1e-3  # the FP32 cost is formed from FP32 camera caches
     assert abs(cost - F_ref) <= tol * F_ref, (cost, F_ref)
