@@ -249,7 +249,16 @@ ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs,
  *   BA_FMT_CSR       scalar CSR of the whole matrix (Eq. 8): a value and a
  *                    column index per element of every non-zero block, 6n + 1
  *                    row starts.
- * All three sum each row's blocks in the same order.  x and y are DEVICE
+ *   BA_FMT_IMPLICIT  no stored S (the aggregation-free next step the paper
+ *                    states, Sec. 8): the product from the stored linearization,
+ *                    S x = U x + lambda clamp(diag U) x - W V^-1 W^T x with the
+ *                    per-point factors of V of the last ba_form_rcs (same
+ *                    lambda); a thread per point forms V^-1 W^T x, a warp per
+ *                    camera sums its observations; needs a linearized problem
+ *                    (not an RCS-only one).  bytes_out: what one product reads
+ *                    instead of S (J rows, the factors, a work vector, the
+ *                    camera-major index).
+ * The three stored formats sum each row's blocks in the same order.  x and y are DEVICE
  * arrays of 6n values in the problem's precision (double for BA_FP64
  * problems, float for BA_FP32), owned by the caller, not overlapping; the
  * product is queued on the problem's stream (no synchronisation).  The full
@@ -259,7 +268,7 @@ ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs,
  * array bytes: values + column indices + row starts.  Errors:
  * BA_ERR_INVALID_ARG (bad format or NULL array), BA_ERR_STATE (no RCS
  * formed), BA_ERR_OOM, BA_ERR_CUDA. */
-typedef enum { BA_FMT_BSMC = 0, BA_FMT_BSR_FULL = 1, BA_FMT_CSR = 2 } ba_rcs_format;
+typedef enum { BA_FMT_BSMC = 0, BA_FMT_BSR_FULL = 1, BA_FMT_CSR = 2, BA_FMT_IMPLICIT = 3 } ba_rcs_format;
 ba_status ba_rcs_spmv(ba_problem *p, int32_t format, const void *x, void *y, int64_t *bytes_out);
 
 /* ---- Learned block-Jacobi correction (not in the paper) ------------------

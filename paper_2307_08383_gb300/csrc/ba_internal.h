@@ -152,6 +152,10 @@ struct ba_problem {
     void *fmt_bsr_val = nullptr, *fmt_csr_val = nullptr;
     int32_t *fmt_bsr_col = nullptr, *fmt_csr_ptr = nullptr, *fmt_csr_col = nullptr;
     double *tri_cam64 = nullptr;  // n x 12 FP64 [R | t] for the triangulation
+    // implicit S x (ba_rcs_spmv BA_FMT_IMPLICIT): camera-major observation
+    // index and the per-observation work vector
+    int32_t *imp_cam_ptr = nullptr, *imp_cam_obs = nullptr;
+    void *imp_w = nullptr;
     ba::GroupDesc *grp = nullptr;
     ba::ItemDesc *items = nullptr;
     uint32_t *contrib = nullptr;

@@ -14,6 +14,8 @@
 // (the entry order of row i: its stored blocks, then the transposed blocks
 // of its column), so all three products sum each row's terms in the same
 // block order.
+#include <vector>
+
 #include "device_util.cuh"
 
 namespace ba {
@@ -147,6 +149,89 @@ __global__ void __launch_bounds__(256) k_spmv_csr(int rows, const int *__restric
     }
 }
 
+// Implicit (matrix-free) y = S x from the stored linearization, without the
+// aggregated RCS (the next step the paper states for its cluster design):
+//   y_i = (U_i + lambda clamp(diag U_i)) x_i
+//         - sum_{a in cam i} J_c,a^T J_p,a V_k^-1 sum_{b in track k} J_p,b^T J_c,b x_cam(b)
+// Phase A, a thread per point k: s_a = J_c,a x_cam(a) for its observations,
+// t_k = sum_a J_p,a^T s_a, u_k = V_k^-1 t_k = L^-T L^-1 t_k (the per-point
+// factor of the last RCS formation, same lambda), w_a = s_a - J_p,a u_k.
+// Phase B, a warp per camera over its observations (camera-major index):
+// y_i = sum_a J_c,a^T w_a + lambda clamp(diag U_i) x_i, with diag U_i =
+// sum_a diag(J_c,a^T J_c,a) formed in the same pass.  Fixed orders: the
+// result is deterministic.
+template <typename T>
+__global__ void __launch_bounds__(256) k_implicit_points(int64_t P, const int *__restrict__ trk_ptr,
+                                                         const int *__restrict__ obs_cam, const T *__restrict__ J,
+                                                         const T *__restrict__ Linv, const T *__restrict__ x,
+                                                         T *__restrict__ w) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+        const int a0 = __ldg(trk_ptr + k), a1 = __ldg(trk_ptr + k + 1);
+        T t0 = T(0), t1 = T(0), t2 = T(0);
+        for (int a = a0; a < a1; ++a) {
+            T r[JW], xc[6];
+            load_jrow(J + (int64_t)a * JW, r);
+            load6(x + 6 * (int64_t)__ldg(obs_cam + a), xc);
+            T s0 = T(0), s1 = T(0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                s0 += r[c] * xc[c];
+                s1 += r[6 + c] * xc[c];
+            }
+            t0 += r[12] * s0 + r[15] * s1;
+            t1 += r[13] * s0 + r[16] * s1;
+            t2 += r[14] * s0 + r[17] * s1;
+            w[2 * (int64_t)a] = s0;
+            w[2 * (int64_t)a + 1] = s1;
+        }
+        const T *m = Linv + 6 * k;  // L^-1 lower: m00 m10 m11 m20 m21 m22
+        const T v0 = m[0] * t0, v1 = m[1] * t0 + m[2] * t1, v2 = m[3] * t0 + m[4] * t1 + m[5] * t2;
+        const T u0 = m[0] * v0 + m[1] * v1 + m[3] * v2, u1 = m[2] * v1 + m[4] * v2, u2 = m[5] * v2;
+        for (int a = a0; a < a1; ++a) {
+            const T *r = J + (int64_t)a * JW;
+            w[2 * (int64_t)a] -= r[12] * u0 + r[13] * u1 + r[14] * u2;
+            w[2 * (int64_t)a + 1] -= r[15] * u0 + r[16] * u1 + r[17] * u2;
+        }
+    }
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_implicit_cams(int n, const int *__restrict__ cam_ptr,
+                                                       const int *__restrict__ cam_obs, const T *__restrict__ J,
+                                                       const T *__restrict__ w, const T *__restrict__ x, double lambda,
+                                                       T *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    for (int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < n; i += nw) {
+        T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, dg[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        for (int q = __ldg(cam_ptr + i) + lane; q < __ldg(cam_ptr + i + 1); q += 32) {
+            const int64_t a = __ldg(cam_obs + q);
+            T r[JW];
+            load_jrow(J + a * JW, r);
+            const T w0 = w[2 * a], w1 = w[2 * a + 1];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                acc[c] += r[c] * w0 + r[6 + c] * w1;
+                dg[c] += r[c] * r[c] + r[6 + c] * r[6 + c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            acc[c] = warp_sum(acc[c]);
+            dg[c] = warp_sum(dg[c]);
+        }
+        if (lane < 6) {
+            T a = acc[0], d = dg[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c)
+                if (lane == c) {
+                    a = acc[c];
+                    d = dg[c];
+                }
+            y[6 * (int64_t)i + lane] = a + (T)lambda * clampT(d) * x[6 * (int64_t)i + lane];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -177,6 +262,29 @@ cudaError_t launch_rcs_format_build(ba_problem *p, int format) {
         }
         return r;
     };
+    if (format == BA_FMT_IMPLICIT) {
+        // the camera-major observation index (once per problem: the pattern is
+        // fixed) and the per-observation work vector
+        if (!p->imp_cam_ptr) {
+            const int64_t m = p->m;
+            std::vector<int32_t> oc(m), ptr(n + 1, 0), idx(m);
+            if ((e = cudaMemcpy(oc.data(), p->obs_cam, m * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return e;
+            for (int64_t a = 0; a < m; ++a) ptr[oc[a] + 1]++;
+            for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+            std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+            for (int64_t a = 0; a < m; ++a) idx[fill[oc[a]]++] = (int32_t)a;
+            if ((e = alloc((void **)&p->imp_cam_ptr, (size_t)(n + 1) * sizeof(int32_t))) != cudaSuccess) return e;
+            if ((e = alloc((void **)&p->imp_cam_obs, (size_t)m * sizeof(int32_t))) != cudaSuccess) return e;
+            if ((e = cudaMemcpy(p->imp_cam_ptr, ptr.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return e;
+            if ((e = cudaMemcpy(p->imp_cam_obs, idx.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return e;
+        }
+        return alloc(&p->imp_w, (size_t)p->m * 2 * p->esz);
+    }
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((E * BW + 255) / 256, 152 * 16));
     // the full BSR (also the source of the CSR)
     if (p->fmt_gen[BA_FMT_BSR_FULL] != p->rcs_gen) {
@@ -211,6 +319,15 @@ cudaError_t launch_rcs_format_build(ba_problem *p, int format) {
 template <typename T>
 static void spmv_format_T(ba_problem *p, int format, const T *x, T *y) {
     const int n = p->n;
+    if (format == BA_FMT_IMPLICIT) {
+        static int res_pts = 0, res_cams = 0;
+        k_implicit_points<T><<<fmt_grid((const void *)k_implicit_points<T>, (p->P + 31) / 32, res_pts), 256, 0,
+                                p->st>>>(p->P, p->trk_ptr, p->obs_cam, (const T *)p->J, (const T *)p->Linv, x,
+                                         (T *)p->imp_w);
+        k_implicit_cams<T><<<fmt_grid((const void *)k_implicit_cams<T>, n, res_cams), 256, 0, p->st>>>(
+            n, p->imp_cam_ptr, p->imp_cam_obs, (const T *)p->J, (const T *)p->imp_w, x, p->rcs_lambda, y);
+        return;
+    }
     static int res[3] = {0, 0, 0};  // resident CTAs per kernel (per precision: this template)
     if (format == BA_FMT_BSMC)
         k_spmv_blocks<T, true><<<fmt_grid((const void *)k_spmv_blocks<T, true>, n, res[0]), 256, 0, p->st>>>(
@@ -228,12 +345,18 @@ cudaError_t launch_rcs_spmv(ba_problem *p, int format, const void *x, void *y) {
         spmv_format_T<float>(p, format, (const float *)x, (float *)y);
     else
         spmv_format_T<double>(p, format, (const double *)x, (double *)y);
-    p->launches += 1;
+    p->launches += format == BA_FMT_IMPLICIT ? 2 : 1;
     return cudaGetLastError();
 }
 
 int64_t rcs_format_bytes(const ba_problem *p, int format) {
     const int64_t n = p->n, E = (2 * p->nnzb - p->n), nnzb = p->nnzb;
+    // implicit: what one product reads instead of S - the stored J rows (twice
+    // the J_c part), L^-1 per point, the work vector (written and read) and
+    // the camera-major index
+    if (format == BA_FMT_IMPLICIT)
+        return p->m * (int64_t)(JW + 12) * p->esz + p->P * 6 * (int64_t)p->esz + p->m * 2 * 2 * (int64_t)p->esz +
+               (p->m + n + 1) * 4;
     if (format == BA_FMT_BSMC) return nnzb * BW * p->esz + nnzb * 4 + (n + 1) * 4;
     if (format == BA_FMT_BSR_FULL) return E * BW * p->esz + E * 4 + (n + 1) * 4;
     return E * BW * (p->esz + 4) + (6 * n + 1) * 4;

@@ -1,7 +1,8 @@
 """GPU parity of y = S x in the three RCS storage formats (Sec. 4, Table 1,
-Eqs. 8-10): the library's BSMC, block CSR of the full symmetric matrix and
-scalar CSR, each through its own kernel via ba_rcs_spmv, against the oracle's
-product with the oracle's own S.
+Eqs. 8-10): the library's BSMC, block CSR of the full symmetric matrix,
+scalar CSR and the implicit product from the stored linearization (no S),
+each through its own kernels via ba_rcs_spmv, against the oracle's product
+with the oracle's own S.
 
 Tolerances: per component, relative to the row's |S||x| (the oracle's
 product of absolute values): 1e-10 in FP64 mode, 2e-4 in FP32 mode (both
@@ -45,7 +46,8 @@ def _products(B, g, x, dtype):
     import torch
     xt = torch.tensor(x, dtype=dtype, device="cuda")
     out, nbytes = {}, {}
-    for name, fmt in (("bsmc", B.BA_FMT_BSMC), ("bsr", B.BA_FMT_BSR_FULL), ("csr", B.BA_FMT_CSR)):
+    for name, fmt in (("bsmc", B.BA_FMT_BSMC), ("bsr", B.BA_FMT_BSR_FULL), ("csr", B.BA_FMT_CSR),
+                      ("implicit", B.BA_FMT_IMPLICIT)):
         yt = torch.full_like(xt, float("nan"))
         nbytes[name] = g.rcs_spmv(fmt, xt, yt)
         torch.cuda.synchronize()
@@ -76,6 +78,8 @@ def test_formats_match_oracle_product(B, scene, prec, tol, tol_csr):
         assert err.max() <= tol, (name, err.max())
     assert np.array_equal(out["bsmc"], out["bsr"])
     assert (np.abs(out["csr"] - out["bsmc"]) / mag).max() <= tol_csr
+    # the implicit product forms U x - W V^-1 W^T x without S: other rounding
+    assert (np.abs(out["implicit"] - out["bsmc"]) / mag).max() <= (1e-12 if fp64 else 5e-5)
 
     # bytes of each format's arrays, against the memory model of Sec. 4.1
     nnzb = len(A.col)
@@ -84,6 +88,8 @@ def test_formats_match_oracle_product(B, scene, prec, tol, tol_csr):
     assert nbytes["bsmc"] == nnzb * 36 * esz + nnzb * 4 + (n + 1) * 4
     assert nbytes["bsr"] == E * 36 * esz + E * 4 + (n + 1) * 4
     assert nbytes["csr"] == E * 36 * (esz + 4) + (6 * n + 1) * 4
+    m, P = s.n_obs, s.n_pts
+    assert nbytes["implicit"] == m * (20 + 12) * esz + P * 6 * esz + m * 4 * esz + (m + n + 1) * 4
     alpha = E / n ** 2                    # block density of the full matrix, as in Eq. 8
     # Eq. 8 (scalar CSR) counts n c row starts; the built array has one more
     assert nbytes["csr"] == pytest.approx(O.csr_bytes(alpha, n, 6, val_bytes=esz) + 4, rel=1e-12)
@@ -107,7 +113,7 @@ def test_formats_follow_a_new_rcs(B, scene):
     second, _ = _products(B, g, x, torch.float64)
     y_ref = O.bsmc_spmv(A, x)
     mag = O.bsmc_spmv(O.BSMC(A.row_ptr, A.col, np.abs(A.val)), np.abs(x))
-    for name in ("bsmc", "bsr", "csr"):
+    for name in ("bsmc", "bsr", "csr", "implicit"):
         assert not np.allclose(second[name], first[name])
         assert (np.abs(second[name] - y_ref) / mag).max() <= 1e-10, name
     # an accepted LM step moves the state (and drops the RCS); the next one
@@ -121,6 +127,7 @@ def test_formats_follow_a_new_rcs(B, scene):
     third, _ = _products(B, g, x, torch.float64)
     assert np.array_equal(third["bsmc"], third["bsr"])
     assert not np.array_equal(third["bsr"], second["bsr"])
+    assert not np.array_equal(third["implicit"], second["implicit"])
 
 
 def test_format_argument_and_state_errors(B, scene):
@@ -140,3 +147,10 @@ def test_format_argument_and_state_errors(B, scene):
     with pytest.raises(B.BAError) as ei:
         B.ba_rcs_spmv(g.h, B.BA_FMT_CSR, 0, y.data_ptr())
     assert ei.value.status == B.BA_ERR_INVALID_ARG
+    # an RCS-only problem has no linearization for the implicit product
+    row_ptr, col, val, b = g.rcs()
+    r = B.Problem.from_rcs(row_ptr, col, val, b, precision=B.BA_FP64)
+    r.rcs_spmv(B.BA_FMT_BSMC, x, y)
+    with pytest.raises(B.BAError) as ei:
+        r.rcs_spmv(B.BA_FMT_IMPLICIT, x, y)
+    assert ei.value.status == B.BA_ERR_STATE
