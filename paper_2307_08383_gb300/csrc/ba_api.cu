@@ -6,6 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <tuple>
+#include <mutex>
+#include <map>
 #include <string>
 
 #include "ba_internal.h"
@@ -41,6 +44,26 @@ static ba_status fail(ba_status s, const std::string &m) {
 namespace ba {
 
 ba_status set_error(ba_status s, const char *msg) { return fail(s, msg); }
+
+cudaError_t occupancy(const void *kernel, int threads, size_t smem, int *per_sm, int *n_sm) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, std::pair<int, int>> cache;
+    int dev = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    const auto key = std::make_tuple(dev, kernel, threads, smem);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        int sms = 0, ps = 0;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kernel, threads, smem)) != cudaSuccess) return e;
+        it = cache.emplace(key, std::make_pair(ps, sms)).first;
+    }
+    *per_sm = it->second.first;
+    *n_sm = it->second.second;
+    return cudaSuccess;
+}
 
 const char *kernel_name(int k) {
     static const char *names[K_COUNT] = {"prepare_state", "linearize", "cost",    "form_rcs",

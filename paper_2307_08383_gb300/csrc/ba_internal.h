@@ -264,6 +264,10 @@ cudaError_t launch_accumulate_split(ba_problem *p, bool first);
 cudaError_t launch_spmv_f32(ba_problem *p, const float *x, float *y);
 // every point re-triangulated from the current cameras (k_obs.cu)
 cudaError_t launch_triangulate(ba_problem *p, int gn_iters);
+// Resident CTAs of a kernel on the current device at a block size and dynamic
+// shared-memory size: *per_sm and *n_sm (the SM count).  Computed once per
+// (device, kernel, threads, smem) and cached under a lock.
+cudaError_t occupancy(const void *kernel, int threads, size_t smem, int *per_sm, int *n_sm);
 // RCS storage formats (k_formats.cu)
 cudaError_t launch_rcs_format_build(ba_problem *p, int format);
 cudaError_t launch_rcs_spmv(ba_problem *p, int format, const void *x, void *y);

@@ -237,14 +237,10 @@ __global__ void __launch_bounds__(256) k_implicit_cams(int n, const int *__restr
 // ---------------------------------------------------------------------------
 // One wave: at most the CTAs that fit on the GPU at once (the loops stride
 // over the rest), so no partial second wave.
-static int fmt_grid(const void *kern, int64_t warps, int &resident) {
-    if (!resident) {
-        int dev = 0, n_sm = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess)
-            return 1;
-        resident = std::max(1, per_sm) * n_sm;
-    }
+static int fmt_grid(const void *kern, int64_t warps) {
+    int per_sm = 0, n_sm = 0;
+    if (occupancy(kern, 256, 0, &per_sm, &n_sm) != cudaSuccess) return 1;
+    const int64_t resident = (int64_t)std::max(1, per_sm) * n_sm;
     const int64_t ctas = (warps * 32 + 255) / 256;
     return (int)std::max<int64_t>(1, std::min<int64_t>(ctas, resident));
 }
@@ -320,23 +316,21 @@ template <typename T>
 static void spmv_format_T(ba_problem *p, int format, const T *x, T *y) {
     const int n = p->n;
     if (format == BA_FMT_IMPLICIT) {
-        static int res_pts = 0, res_cams = 0;
-        k_implicit_points<T><<<fmt_grid((const void *)k_implicit_points<T>, (p->P + 31) / 32, res_pts), 256, 0,
+        k_implicit_points<T><<<fmt_grid((const void *)k_implicit_points<T>, (p->P + 31) / 32), 256, 0,
                                 p->st>>>(p->P, p->trk_ptr, p->obs_cam, (const T *)p->J, (const T *)p->Linv, x,
                                          (T *)p->imp_w);
-        k_implicit_cams<T><<<fmt_grid((const void *)k_implicit_cams<T>, n, res_cams), 256, 0, p->st>>>(
+        k_implicit_cams<T><<<fmt_grid((const void *)k_implicit_cams<T>, n), 256, 0, p->st>>>(
             n, p->imp_cam_ptr, p->imp_cam_obs, (const T *)p->J, (const T *)p->imp_w, x, p->rcs_lambda, y);
         return;
     }
-    static int res[3] = {0, 0, 0};  // resident CTAs per kernel (per precision: this template)
     if (format == BA_FMT_BSMC)
-        k_spmv_blocks<T, true><<<fmt_grid((const void *)k_spmv_blocks<T, true>, n, res[0]), 256, 0, p->st>>>(
+        k_spmv_blocks<T, true><<<fmt_grid((const void *)k_spmv_blocks<T, true>, n), 256, 0, p->st>>>(
             n, p->tw_ptr, p->tw_ent, nullptr, (const T *)p->S, x, y);
     else if (format == BA_FMT_BSR_FULL)
-        k_spmv_blocks<T, false><<<fmt_grid((const void *)k_spmv_blocks<T, false>, n, res[1]), 256, 0, p->st>>>(
+        k_spmv_blocks<T, false><<<fmt_grid((const void *)k_spmv_blocks<T, false>, n), 256, 0, p->st>>>(
             n, p->tw_ptr, nullptr, p->fmt_bsr_col, (const T *)p->fmt_bsr_val, x, y);
     else
-        k_spmv_csr<T><<<fmt_grid((const void *)k_spmv_csr<T>, 6 * (int64_t)n, res[2]), 256, 0, p->st>>>(
+        k_spmv_csr<T><<<fmt_grid((const void *)k_spmv_csr<T>, 6 * (int64_t)n), 256, 0, p->st>>>(
             6 * n, p->fmt_csr_ptr, p->fmt_csr_col, (const T *)p->fmt_csr_val, x, y);
 }
 

@@ -2,6 +2,9 @@
 // standalone GEMM entry point.
 #include <algorithm>
 
+#include <map>
+#include <mutex>
+#include <set>
 #include "tc_gemm.cuh"
 
 namespace ba {
@@ -13,13 +16,21 @@ cudaError_t tc_gemm(cudaStream_t st, tc::View<TA> A, tc::View<TB> B, int M, int 
                     int64_t c_cs, bool accumulate, int *err) {
     if (M <= 0 || K <= 0) return cudaSuccess;
     if (N <= 0 || N > tc::kMaxN || (N % 32) != 0) return cudaErrorInvalidValue;
-    static bool attr = false;
+    // the kernel's shared-memory attribute, once per device (kernel
+    // attributes belong to the device's context)
+    static std::mutex attr_mu;
+    static std::set<int> attr_set;
     cudaError_t e;
-    if (!attr) {
-        if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tc::kSmemBytes)) != cudaSuccess)
-            return e;
-        attr = true;
+    {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lock(attr_mu);
+        if (!attr_set.count(dev)) {
+            if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          tc::kSmemBytes)) != cudaSuccess)
+                return e;
+            attr_set.insert(dev);
+        }
     }
     const int kchunk = tc::kMaxK;
     const int ksplit = (K + kchunk - 1) / kchunk;
@@ -431,11 +442,17 @@ extern "C" ba_status ba_tc_gemm(int32_t M, int32_t N, int32_t K, const float *A,
     if (M < 0 || K < 0 || N <= 0 || N > 128 || N % 32 != 0)
         return set_error(BA_ERR_INVALID_ARG, "ba_tc_gemm: need M, K >= 0 and N in {32, 64, 96, 128}");
     if ((M > 0 && K > 0) && (!A || !B || !C)) return set_error(BA_ERR_INVALID_ARG, "ba_tc_gemm: null pointer");
-    static int *s_err = nullptr;
+    // without a caller's error word, one per device (kept for the process)
+    static std::mutex err_mu;
+    static std::map<int, int *> err_words;
     int *err = err_dev;
     if (!err) {
-        if (!s_err && cudaMalloc(&s_err, sizeof(int)) != cudaSuccess) return set_error(BA_ERR_CUDA, "cudaMalloc");
-        err = s_err;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return set_error(BA_ERR_CUDA, "cudaGetDevice");
+        std::lock_guard<std::mutex> lock(err_mu);
+        int *&w = err_words[dev];
+        if (!w && cudaMalloc(&w, sizeof(int)) != cudaSuccess) return set_error(BA_ERR_CUDA, "cudaMalloc");
+        err = w;
     }
     tc::View<float> va{A, a_rs, a_cs, M, K};
     tc::View<float> vb{B, b_rs, b_cs, K, N};

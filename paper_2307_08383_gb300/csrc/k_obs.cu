@@ -724,8 +724,6 @@ cudaError_t launch_trial_cameras(ba_problem *p) {
 
 template <typename T>
 static cudaError_t step_groups_T(ba_problem *p, long long limit) {
-    static int ctas_per_sm = -1, n_sm = 0;
-    static size_t smem_seen = 0;
     const size_t smem = (size_t)p->obs_max * JW * sizeof(T) +
                         (size_t)p->obs_max / 2 * (3 * sizeof(T) + 6 * sizeof(float) + (sizeof(T) == 8 ? 24 : 0)) +
                         (size_t)p->obs_max * (5 * sizeof(T) + sizeof(int));
@@ -733,17 +731,10 @@ static cudaError_t step_groups_T(ba_problem *p, long long limit) {
     if ((e = cudaFuncSetAttribute(k_step_groups<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
-    if (ctas_per_sm < 0 || smem != smem_seen) {
-        smem_seen = smem;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_step_groups<T>, STEP_THREADS, smem)) !=
-            cudaSuccess)
-            return e;
-        if (ctas_per_sm < 1) ctas_per_sm = 1;
-    }
-    const int grid = (int)std::min<int64_t>(p->ngroups, (int64_t)ctas_per_sm * n_sm);
+    int ctas_per_sm = 0, n_sm = 0;
+    if ((e = occupancy((const void *)k_step_groups<T>, STEP_THREADS, smem, &ctas_per_sm, &n_sm)) != cudaSuccess)
+        return e;
+    const int grid = (int)std::min<int64_t>(p->ngroups, (int64_t)std::max(1, ctas_per_sm) * n_sm);
     const int hub = p->opt.robust == BA_LOSS_HUBER;
     k_step_groups<T><<<grid, STEP_THREADS, smem, p->st>>>(
         p->grp, (int)p->ngroups, p->trk_ptr, p->obs_cam, p->obs_pt, (const T *)(p->fp32 ? (const void *)p->uv32

@@ -986,17 +986,11 @@ cudaError_t launch_pcg_init(ba_problem *p, const void *rhs, double tol, int max_
 
 template <typename T>
 static cudaError_t pcg_loop_T(ba_problem *p) {
-    static int blocks_per_sm = -1, n_sm = 0;
+    int blocks_per_sm = 0, n_sm = 0;
     cudaError_t e;
-    if (blocks_per_sm < 0) {
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pcg_persist<T>, 256, 0)) != cudaSuccess)
-            return e;
-        if (blocks_per_sm > 2) blocks_per_sm = 2;
-        if (blocks_per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    }
+    if ((e = occupancy((const void *)k_pcg_persist<T>, 256, 0, &blocks_per_sm, &n_sm)) != cudaSuccess) return e;
+    if (blocks_per_sm > 2) blocks_per_sm = 2;
+    if (blocks_per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     // enough warps for one block row each, at most what is co-resident
     int64_t want = ((int64_t)p->n * 32 + 255) / 256;
     int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)blocks_per_sm * n_sm);

@@ -463,21 +463,12 @@ static int form_c_cap(const ba_problem *p) { return std::max(4, (p->hs.max_nc + 
 
 template <typename T>
 static cudaError_t form_rcs_T(ba_problem *p, double lambda, size_t smem, long long limit) {
-    static int ctas_per_sm = -1, n_sm = 0;
-    static size_t smem_seen = 0;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_form_rcs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    if (ctas_per_sm < 0 || smem != smem_seen) {
-        smem_seen = smem;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_per_sm, k_form_rcs<T>, FORM_THREADS, smem)) !=
-            cudaSuccess)
-            return e;
-        if (ctas_per_sm < 1) ctas_per_sm = 1;
-    }
+    int ctas_per_sm = 0, n_sm = 0;
+    if ((e = occupancy((const void *)k_form_rcs<T>, FORM_THREADS, smem, &ctas_per_sm, &n_sm)) != cudaSuccess) return e;
+    ctas_per_sm = std::max(1, ctas_per_sm);
     const int grid = (int)std::min<int64_t>(p->ngroups, (int64_t)ctas_per_sm * n_sm);
     k_form_rcs<T><<<grid, FORM_THREADS, smem, p->st>>>(p->grp, (int)p->ngroups, p->items, p->contrib, p->trk_ptr,
                                                       (const T *)p->J, lambda, (T *)p->part, (T *)p->Linv, (T *)p->lp,
