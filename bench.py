@@ -46,6 +46,16 @@ def load_peaks():
         return dict(PEAKS_FALLBACK), "fallback"
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of a per-rank float over all ranks (a job takes as long as
+    its slowest rank); the value itself without a process group."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_scene(workload: str, rank: int = 0):
     import scenes
     if workload == "aerial5k":
@@ -210,10 +220,7 @@ def run_ours(args):
     st1 = g.stats()
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     ktimes = g.kernel_times()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda")
     value = world * args.steps / (ms_max / 1e3)
 
     # ---- end-to-end through the C ABI with host buffers
@@ -237,10 +244,7 @@ def run_ours(args):
             lam, nu, _ = g.lm_state()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        td = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(td, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / float(td.item()), "unit": "LM iters/s",
+        e2e = {"value": world * args.steps / max_over_ranks(dt, dist, "cuda"), "unit": "LM iters/s",
                "h2d_bytes_per_step": int(hc.nbytes + hp.nbytes),
                "d2h_bytes_per_step": int(hc.nbytes + hp.nbytes + 8)}
 
