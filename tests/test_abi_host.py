@@ -120,6 +120,8 @@ def test_memory_cap_is_checked_before_allocation(B):
 def test_null_problem_calls_fail_cleanly(B):
     assert B.lib().ba_linearize(None, None) == B.BA_ERR_INVALID_ARG
     assert B.lib().ba_lm_step(None, None) == B.BA_ERR_INVALID_ARG
+    assert B.lib().ba_rcs_spmv(None, B.BA_FMT_BSMC, None, None, None) == B.BA_ERR_INVALID_ARG
+    assert B.lib().ba_triangulate(None, 3, None, None) == B.BA_ERR_INVALID_ARG
     B.lib().ba_problem_destroy(None)
 
 
