@@ -17,7 +17,12 @@
  * (J^T J + lambda D^T D) dx = -J^T e, by the Schur complement: the reduced
  * camera system (RCS) of Eq. 4 is formed point by point (Sec. 5), stored as
  * BSMC (Sec. 4), solved by block-Jacobi PCG (Sec. 3.2, Eqs. 6-7), and the
- * points are back-substituted by Eq. 5.
+ * points are back-substituted by Eq. 5.  Beside that path: the points can be
+ * re-triangulated from the poses instead (ba_triangulate), the RCS product can
+ * be run in other storage formats, or without a stored RCS, for the paper's
+ * storage comparison (ba_rcs_spmv), a given BSMC system can be solved alone
+ * (ba_problem_create_rcs, ba_pcg_solve_static), and a learned correction of
+ * the block-Jacobi preconditioner can be attached (ba_precond_net_*).
  */
 #ifndef BA_H
 #define BA_H
