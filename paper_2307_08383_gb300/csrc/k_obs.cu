@@ -748,11 +748,11 @@ static cudaError_t step_groups_T(ba_problem *p, long long limit) {
 cudaError_t launch_triangulate(ba_problem *p, int gn_iters) {
     cudaError_t e;
     cudaEvent_t ev;
+    if ((e = cudaMemsetAsync(&p->sc->n_tri_fail, 0, sizeof(unsigned long long), p->st)) != cudaSuccess) return e;
     if (p->fp32) {
         // the FP32 caches of the current state are up to date (every state
         // change refreshes them)
         ktimer_begin(p, K_TRIANGULATE, &ev);
-        if ((e = cudaMemsetAsync(&p->sc->n_tri_fail, 0, sizeof(unsigned long long), p->st)) != cudaSuccess) return e;
         k_triangulate32<<<grid_for(p->P, 256, GRID_CAP), 256, 0, p->st>>>(
             p->P, p->trk_ptr, p->obs_cam, p->uv32, (const float *)p->cur.camc, p->cur.pts_hl, intr_of(p), gn_iters,
             p->cur.pts, &p->sc->n_tri_fail);
@@ -769,7 +769,6 @@ cudaError_t launch_triangulate(ba_problem *p, int gn_iters) {
     }
     ktimer_begin(p, K_TRIANGULATE, &ev);
     k_prepare_cams64<<<(p->n + 127) / 128, 128, 0, p->st>>>(p->n, p->cur.cams, p->tri_cam64);
-    if ((e = cudaMemsetAsync(&p->sc->n_tri_fail, 0, sizeof(unsigned long long), p->st)) != cudaSuccess) return e;
     k_triangulate<<<grid_for(p->P, 256, GRID_CAP), 256, 0, p->st>>>(p->P, p->trk_ptr, p->obs_cam, p->uv64,
                                                                     p->tri_cam64, intr_of(p), gn_iters, p->cur.pts,
                                                                     &p->sc->n_tri_fail);
