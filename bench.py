@@ -512,7 +512,8 @@ def run_kernel_case(args):
     if args.pcg_tol:
         opts.update(pcg_rel_tol=args.pcg_tol, inner_rel_tol=args.pcg_tol, refine_max=1)
     if args.pcg_variant:
-        opts["pcg_variant"] = {"standard": B.BA_PCG_STANDARD, "split": B.BA_PCG_SPLIT}[args.pcg_variant]
+        opts["pcg_variant"] = {"standard": B.BA_PCG_STANDARD, "split": B.BA_PCG_SPLIT,
+                               "implicit": B.BA_PCG_IMPLICIT}[args.pcg_variant]
     if args.group_obs:
         opts["group_max_obs"] = args.group_obs
     g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, profile=2, **opts)
@@ -557,7 +558,7 @@ def main():
     ap.add_argument("--kernel-case", default=None, choices=["form_rcs", "pcg"],
                     help="profiling driver: run one kernel family a few times on the workload and exit")
     ap.add_argument("--pcg-tol", type=float, default=None, help="kernel case: PCG relative tolerance")
-    ap.add_argument("--pcg-variant", default=None, choices=["standard", "split"], help="kernel case: PCG variant")
+    ap.add_argument("--pcg-variant", default=None, choices=["standard", "split", "implicit"], help="kernel case: PCG variant")
     ap.add_argument("--group-obs", type=int, default=0, help="kernel case: observations per point group")
     ap.add_argument("--no-formats", action="store_true", help="skip the RCS storage-format SpMV comparison")
     ap.add_argument("--no-e2e", action="store_true")

@@ -52,7 +52,7 @@ typedef enum {
 enum { BA_FP64 = 0, BA_FP32 = 1 };            /* ba_options.precision */
 enum { BA_LOSS_PLAIN = 0, BA_LOSS_HUBER = 1 }; /* ba_options.robust */
 enum { BA_PC_BLOCK_JACOBI = 0, BA_PC_LEARNED = 1 };
-enum { BA_PCG_AUTO = 0, BA_PCG_STANDARD = 1, BA_PCG_SPLIT = 2 }; /* ba_options.pcg_variant */
+enum { BA_PCG_AUTO = 0, BA_PCG_STANDARD = 1, BA_PCG_SPLIT = 2, BA_PCG_IMPLICIT = 3 }; /* ba_options.pcg_variant */
 
 typedef struct {
     int32_t precision;       /* BA_FP64: everything in FP64.  BA_FP32: Jacobians,
@@ -81,7 +81,14 @@ typedef struct {
                                 split system G^T S G (M^-1 = G G^T per camera; the same
                                 iterates as block-Jacobi PCG in exact arithmetic) with one
                                 grid-wide reduction per iteration; BA_PCG_STANDARD runs the
-                                Sec. 3.2 recurrence as written.  FP64 solves always run it. */
+                                Sec. 3.2 recurrence as written.  FP64 solves always run it.
+                                BA_PCG_IMPLICIT (any precision) runs the Sec. 3.2 recurrence
+                                with S d applied from the stored linearization as
+                                U d + lambda clamp(diag U) d - W V^-1 W^T d (the implicit
+                                operator of ba_rcs_spmv; S is still formed for M^-1 and
+                                the FP64 residual); the solve runs in the problem's
+                                precision (solve_precision is ignored); refused by
+                                ba_problem_create_rcs (no linearization). */
 } ba_options;
 
 typedef struct {

@@ -260,7 +260,7 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     if (o.robust != BA_LOSS_PLAIN && o.robust != BA_LOSS_HUBER) return fail(BA_ERR_INVALID_ARG, "robust must be BA_LOSS_PLAIN or BA_LOSS_HUBER");
     if (o.robust == BA_LOSS_HUBER && !(o.huber_delta > 0)) return fail(BA_ERR_INVALID_ARG, "huber_delta must be > 0");
     if (!(o.lambda0 >= 0) || !(o.pcg_rel_tol > 0) || !(o.inner_rel_tol > 0) || o.pcg_max_iters < 0 || o.refine_max < 1 ||
-        o.pcg_variant < BA_PCG_AUTO || o.pcg_variant > BA_PCG_SPLIT)
+        o.pcg_variant < BA_PCG_AUTO || o.pcg_variant > BA_PCG_IMPLICIT)
         return fail(BA_ERR_INVALID_ARG, "bad solver option");
     if (!(o.fx > 0) || !(o.fy > 0) || !std::isfinite(o.cx) || !std::isfinite(o.cy))
         return fail(BA_ERR_INVALID_ARG, "bad intrinsics");
@@ -600,9 +600,12 @@ ba_status ba_form_rcs(ba_problem *p, double lambda) {
     return BA_OK;
 }
 
+// The implicit variant: the PCG product from the stored linearization
+static bool implicit_cg(const ba_problem *p) { return p->opt.pcg_variant == BA_PCG_IMPLICIT; }
+
 static ba_status run_pcg(ba_problem *p, const void *rhs, double tol, int max_iters, int *iters) {
     CK(p, launch_pcg_init(p, rhs, tol, max_iters));
-    CK(p, launch_pcg_loop(p));
+    CK(p, implicit_cg(p) ? launch_pcg_implicit(p) : launch_pcg_loop(p));
     ba_status s = sync_scalars(p);
     if (s) return s;
     if (p->sc_host->err == BA_ERR_TIMEOUT) {
@@ -627,7 +630,8 @@ static ba_status ensure_shadows(ba_problem *p, bool matrix) {
 // FP32 solves run the split CG unless the standard recurrence is asked for
 // or the problem is too large for the balanced SpMV's shared memory
 static bool split_cg(ba_problem *p) {
-    return p->sv.f32 && p->opt.pcg_variant != BA_PCG_STANDARD && split_available(p);
+    return p->sv.f32 && (p->opt.pcg_variant == BA_PCG_AUTO || p->opt.pcg_variant == BA_PCG_SPLIT) &&
+           split_available(p);
 }
 
 
@@ -639,7 +643,8 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info);
 // demoted copy of S and M^-1 - and refines with the FP64 residual b - S x of
 // the FP64 system; the FP32 copies are made inside the timed solve.
 static ba_status solve_once(ba_problem *p, ba_step_info *info) {
-    const bool mixed = !p->fp32 && p->opt.solve_precision == BA_FP32;
+    // the implicit operator reads J in the problem's precision: no FP32 inner solve
+    const bool mixed = !p->fp32 && p->opt.solve_precision == BA_FP32 && !implicit_cg(p);
     ba_status s;
     if (mixed) {
         const bool standard = p->opt.pcg_variant == BA_PCG_STANDARD || !split_available(p);
@@ -697,7 +702,7 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
                 CK(p, launch_pcg_split(p));
             } else {
                 CK(p, launch_pcg_init(p, p->sv.pv[1], inner, max_iters));
-                CK(p, launch_pcg_loop(p));
+                CK(p, implicit_cg(p) ? launch_pcg_implicit(p) : launch_pcg_loop(p));
             }
             CK(p, split ? launch_accumulate_split(p, first) : launch_accumulate_solution(p, first));
             first = false;

@@ -242,6 +242,7 @@ cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial);
 cudaError_t launch_form_rcs(ba_problem *p, double lambda);
 cudaError_t launch_pcg_init(ba_problem *p, const void *rhs_T, double tol, int max_iters);
 cudaError_t launch_pcg_loop(ba_problem *p);
+cudaError_t launch_pcg_implicit(ba_problem *p);  // the loop on the implicit operator (k_formats.cu)
 cudaError_t launch_resid64(ba_problem *p, bool from_x64);
 cudaError_t launch_solution_to_step(ba_problem *p);
 cudaError_t launch_refine_rhs(ba_problem *p, void *rhs_T);

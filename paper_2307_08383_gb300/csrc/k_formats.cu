@@ -160,18 +160,38 @@ __global__ void __launch_bounds__(256) k_spmv_csr(int rows, const int *__restric
 // y_i = sum_a J_c,a^T w_a + lambda clamp(diag U_i) x_i, with diag U_i =
 // sum_a diag(J_c,a^T J_c,a) formed in the same pass.  Fixed orders: the
 // result is deterministic.
+// The vector the product applies, camera j's six entries: a plain x, or the
+// PCG direction d = z + beta d_old formed on the fly.
 template <typename T>
-__global__ void __launch_bounds__(256) k_implicit_points(int64_t P, const int *__restrict__ trk_ptr,
-                                                         const int *__restrict__ obs_cam, const T *__restrict__ J,
-                                                         const T *__restrict__ Linv, const T *__restrict__ x,
-                                                         T *__restrict__ w) {
+struct PlainX {
+    const T *x;
+    __device__ __forceinline__ void operator()(int64_t j, T (&v)[6]) const { load6(x + 6 * j, v); }
+};
+template <typename T>
+struct PcgDir {
+    const T *z, *dold;
+    T beta;
+    __device__ __forceinline__ void operator()(int64_t j, T (&v)[6]) const {
+        T d[6];
+        load6(z + 6 * j, v);
+        load6(dold + 6 * j, d);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] += beta * d[c];
+    }
+};
+
+// Phase A over the grid's threads (one point each, strided).
+template <typename T, class GX>
+__device__ __forceinline__ void implicit_points(int64_t P, const int *__restrict__ trk_ptr,
+                                                const int *__restrict__ obs_cam, const T *__restrict__ J,
+                                                const T *__restrict__ Linv, GX gx, T *__restrict__ w) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
         const int a0 = __ldg(trk_ptr + k), a1 = __ldg(trk_ptr + k + 1);
         T t0 = T(0), t1 = T(0), t2 = T(0);
         for (int a = a0; a < a1; ++a) {
             T r[JW], xc[6];
             load_jrow(J + (int64_t)a * JW, r);
-            load6(x + 6 * (int64_t)__ldg(obs_cam + a), xc);
+            gx(__ldg(obs_cam + a), xc);
             T s0 = T(0), s1 = T(0);
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
@@ -194,11 +214,12 @@ __global__ void __launch_bounds__(256) k_implicit_points(int64_t P, const int *_
         }
     }
 }
-template <typename T>
-__global__ void __launch_bounds__(256) k_implicit_cams(int n, const int *__restrict__ cam_ptr,
-                                                       const int *__restrict__ cam_obs, const T *__restrict__ J,
-                                                       const T *__restrict__ w, const T *__restrict__ x, double lambda,
-                                                       T *__restrict__ y) {
+// Phase B over the grid's warps (one camera each, strided): out(i, c, y_ic,
+// x_ic) receives each component of y_i = (S x)_i with x_i's own entry.
+template <typename T, class GX, class OUT>
+__device__ __forceinline__ void implicit_cams(int n, const int *__restrict__ cam_ptr, const int *__restrict__ cam_obs,
+                                              const T *__restrict__ J, const T *__restrict__ w, GX gx, double lambda,
+                                              OUT out) {
     const int lane = threadIdx.x & 31;
     const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
     for (int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < n; i += nw) {
@@ -207,7 +228,7 @@ __global__ void __launch_bounds__(256) k_implicit_cams(int n, const int *__restr
             const int64_t a = __ldg(cam_obs + q);
             T r[JW];
             load_jrow(J + a * JW, r);
-            const T w0 = w[2 * a], w1 = w[2 * a + 1];
+            const T w0 = __ldcg(w + 2 * a), w1 = __ldcg(w + 2 * a + 1);
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 acc[c] += r[c] * w0 + r[6 + c] * w1;
@@ -219,16 +240,127 @@ __global__ void __launch_bounds__(256) k_implicit_cams(int n, const int *__restr
             acc[c] = warp_sum(acc[c]);
             dg[c] = warp_sum(dg[c]);
         }
+        T xi[6];
+        gx(i, xi);
         if (lane < 6) {
-            T a = acc[0], d = dg[0];
+            T a = acc[0], d = dg[0], xv = xi[0];
 #pragma unroll
             for (int c = 1; c < 6; ++c)
                 if (lane == c) {
                     a = acc[c];
                     d = dg[c];
+                    xv = xi[c];
                 }
-            y[6 * (int64_t)i + lane] = a + (T)lambda * clampT(d) * x[6 * (int64_t)i + lane];
+            out(i, lane, a + (T)lambda * clampT(d) * xv, xv);
         }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_implicit_points(int64_t P, const int *__restrict__ trk_ptr,
+                                                         const int *__restrict__ obs_cam, const T *__restrict__ J,
+                                                         const T *__restrict__ Linv, const T *__restrict__ x,
+                                                         T *__restrict__ w) {
+    implicit_points<T>(P, trk_ptr, obs_cam, J, Linv, PlainX<T>{x}, w);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_implicit_cams(int n, const int *__restrict__ cam_ptr,
+                                                       const int *__restrict__ cam_obs, const T *__restrict__ J,
+                                                       const T *__restrict__ w, const T *__restrict__ x, double lambda,
+                                                       T *__restrict__ y) {
+    implicit_cams<T>(n, cam_ptr, cam_obs, J, w, PlainX<T>{x}, lambda,
+                     [&](int i, int c, T v, T) { y[6 * (int64_t)i + c] = v; });
+}
+
+// Block-Jacobi PCG (the Sec. 3.2 recurrence, as k_pcg_persist runs it) with
+// the implicit product in place of the stored RCS: per iteration phase A, a
+// grid barrier, phase B (which also stores d_new and sums d^T S d), the
+// all-reduce of d^T S d, the update phase, the all-reduce of r^T z and r^T r.
+// The preconditioner, right-hand side and per-point factors are those of the
+// last RCS formation (same lambda).  Cooperative launch; bounded waits.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_implicit(int n, int64_t P, const int *__restrict__ trk_ptr,
+                                                      const int *__restrict__ obs_cam, const T *__restrict__ J,
+                                                      const T *__restrict__ Linv, const int *__restrict__ cam_ptr,
+                                                      const int *__restrict__ cam_obs, T *w, double lambda,
+                                                      const T *__restrict__ Minv, T *y, T *r0, T *r1, T *z, T *d0,
+                                                      T *d1, T *q, DevScalars *sc, double *red, unsigned *bar,
+                                                      long long limit_cycles) {
+    __shared__ double sh[40];
+    if (sc->done) return;
+    double rz = sc->rz;
+    const double rr0 = sc->rr0, tol2 = sc->tol2;
+    const int max_iters = sc->max_iters;
+    double beta = 0.0;
+    int it = 0;
+    unsigned gen = 0;
+    const int ne = 6 * n;
+    for (;;) {
+        const bool odd = it & 1;
+        T *dold = odd ? d1 : d0, *dnew = odd ? d0 : d1;
+        T *rc = odd ? r1 : r0, *rn = odd ? r0 : r1;
+        const PcgDir<T> dir{z, dold, (T)beta};
+        implicit_points<T>(P, trk_ptr, obs_cam, J, Linv, dir, w);
+        double bar1[1] = {0.0};
+        block_sum<1>(bar1, sh);
+        if (!grid_allreduce_sym<1>(bar1, red, gen++, bar, &sc->err, limit_cycles)) return;  // w complete
+        T pap_t = T(0);
+        implicit_cams<T>(n, cam_ptr, cam_obs, J, w, dir, lambda, [&](int i, int c, T v, T xv) {
+            q[6 * (int64_t)i + c] = v;
+            dnew[6 * (int64_t)i + c] = xv;
+            pap_t += xv * v;
+        });
+        double v1[1] = {(double)pap_t};
+        block_sum<1>(v1, sh);
+        if (!grid_allreduce_sym<1>(v1, red, gen++, bar, &sc->err, limit_cycles)) return;
+        const double pAp = v1[0];
+        if (!(pAp > 0.0)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                sc->err = (int)BA_ERR_NOT_SPD;
+                sc->done = 1;
+                sc->iters = it;
+            }
+            return;
+        }
+        const T alpha = (T)(rz / pAp);
+        T rz_p = T(0), rr_p = T(0);
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+            const int i = e / 6, a = e - 6 * i;
+            T ri[6], qi[6];
+            load6(rc + 6 * i, ri);
+            load6(q + 6 * i, qi);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) ri[c] -= alpha * qi[c];
+            const T *M = Minv + 36 * (int64_t)i + 6 * a;
+            T ze = T(0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) ze += __ldg(M + c) * ri[c];
+            T ra = ri[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c)
+                if (a == c) ra = ri[c];
+            y[e] += alpha * __ldcg(dnew + e);
+            rn[e] = ra;
+            z[e] = ze;
+            rz_p += ra * ze;
+            rr_p += ra * ra;
+        }
+        double v2[2] = {(double)rz_p, (double)rr_p};
+        block_sum<2>(v2, sh);
+        if (!grid_allreduce_sym<2>(v2, red, gen++, bar, &sc->err, limit_cycles)) return;
+        const double rz_new = v2[0], rr = v2[1];
+        ++it;
+        if (rr <= tol2 * rr0 || it >= max_iters) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                sc->iters = it;
+                sc->rr = rr;
+                sc->rz = rz_new;
+                sc->done = 1;
+            }
+            return;
+        }
+        beta = rz_new / rz;
+        rz = rz_new;
     }
 }
 
@@ -340,6 +472,48 @@ cudaError_t launch_rcs_spmv(ba_problem *p, int format, const void *x, void *y) {
     else
         spmv_format_T<double>(p, format, (const double *)x, (double *)y);
     p->launches += format == BA_FMT_IMPLICIT ? 2 : 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t pcg_implicit_T(ba_problem *p) {
+    int per_sm = 0, n_sm = 0;
+    cudaError_t e;
+    if ((e = occupancy((const void *)k_pcg_implicit<T>, 256, 0, &per_sm, &n_sm)) != cudaSuccess) return e;
+    // the products are gathers from the stored J: as many warps in flight as fit
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    // enough threads for a point each or a warp per camera, at most what is co-resident
+    const int64_t want = std::max<int64_t>((p->P + 255) / 256, ((int64_t)p->n * 32 + 255) / 256);
+    int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)per_sm * n_sm);
+    if ((e = cudaMemsetAsync(p->counters + 14, 0, 2 * sizeof(unsigned), p->st)) != cudaSuccess) return e;
+    int n = p->n;
+    int64_t P = p->P;
+    const int *trk = p->trk_ptr, *oc = p->obs_cam, *cp = p->imp_cam_ptr, *co = p->imp_cam_obs;
+    const T *J = (const T *)p->J, *Li = (const T *)p->Linv, *Mi = (const T *)p->sv.Minv;
+    T *w = (T *)p->imp_w;
+    double lambda = p->rcs_lambda;
+    T *y = (T *)p->sv.pv[0], *r = (T *)p->sv.pv[1], *z = (T *)p->sv.pv[2], *d0 = (T *)p->sv.pv[3], *d1 = (T *)p->sv.pv[4];
+    T *q = (T *)p->sv.pv[5], *r1 = (T *)p->sv.pv[6];
+    DevScalars *sc = p->sc;
+    double *red = p->red;
+    unsigned *bar = p->counters + 14;
+    long long limit = 4000000000LL;  // ~2 s of SM clock per barrier wait
+    void *args[] = {&n, &P, &trk, &oc, &J, &Li, &cp, &co, &w, &lambda, &Mi, &y, &r, &r1, &z, &d0, &d1, &q, &sc, &red, &bar, &limit};
+    return cudaLaunchCooperativeKernel((const void *)k_pcg_implicit<T>, dim3(grid), dim3(256), args, 0, p->st);
+}
+
+// The PCG loop on the implicit operator (state from launch_pcg_init); the
+// solve vectors must be in the problem's precision.
+cudaError_t launch_pcg_implicit(ba_problem *p) {
+    cudaError_t e = launch_rcs_format_build(p, BA_FMT_IMPLICIT);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t ev;
+    ktimer_begin(p, K_PCG_LOOP, &ev);
+    e = p->fp32 ? pcg_implicit_T<float>(p) : pcg_implicit_T<double>(p);
+    ktimer_end(p, K_PCG_LOOP, ev);
+    p->launches += 1;
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

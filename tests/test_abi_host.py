@@ -104,7 +104,7 @@ def test_create_rejects_bad_input_without_gpu(B, case):
     elif case == "bad_tol":
         kw["pcg_rel_tol"] = 0.0
     elif case == "bad_pcg_variant":
-        kw["pcg_variant"] = 3
+        kw["pcg_variant"] = 4
     with pytest.raises(B.BAError) as ei:
         _create(B, s, **kw)
     assert ei.value.status == want

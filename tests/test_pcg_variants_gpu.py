@@ -130,3 +130,66 @@ def test_split_with_a_learned_preconditioner(B, scene):
         its[name] = info["pcg_iters"]
     assert abs(its["standard"] - its["split"]) <= 2, its
     net.close()
+
+
+def test_implicit_fp64_follows_block_jacobi_pcg(B, scene, oracle_rcs):
+    """The implicit variant (S d from the stored J: U d + lambda clamp(diag U) d
+    - W V^-1 W^T d, Sec. 4's matrix-free alternative to storing S) in the
+    Sec. 3.2 recurrence: its iteration count equals the FP64 oracle's
+    block-Jacobi PCG on the oracle's own RCS, and its solution is the
+    oracle's iterate up to rounding."""
+    A, b = oracle_rcs
+    tol = 1e-3
+    info, conv, dxc, _ = _solve(B, scene, 1e-4, precision=B.BA_FP64, pcg_rel_tol=tol,
+                                pcg_variant=B.BA_PCG_IMPLICIT)
+    ref = O.pcg(A, b.reshape(-1), O.block_jacobi(A), tol)
+    assert conv
+    assert abs(info["pcg_iters"] - ref.iters) <= 1, (info["pcg_iters"], ref.iters)
+    assert np.linalg.norm(dxc.reshape(-1) - ref.y) <= 1e-6 * np.linalg.norm(ref.y)
+
+
+def test_implicit_matches_the_stored_operator(B, scene):
+    """FP64: the implicit and the stored-S recurrences take the same number of
+    iterations to a tight tolerance and agree to its level; an FP32 inner
+    solve asked for is ignored (the operator reads J in the problem's
+    precision), bit for bit; LM steps follow the same costs."""
+    a = _solve(B, scene, 1e-4, precision=B.BA_FP64, pcg_rel_tol=1e-10, pcg_variant=B.BA_PCG_STANDARD)
+    b = _solve(B, scene, 1e-4, precision=B.BA_FP64, pcg_rel_tol=1e-10, pcg_variant=B.BA_PCG_IMPLICIT)
+    c = _solve(B, scene, 1e-4, precision=B.BA_FP64, pcg_rel_tol=1e-10, pcg_variant=B.BA_PCG_IMPLICIT,
+               solve_precision=B.BA_FP32)
+    assert a[1] and b[1]
+    # two roundings of the same operator: over ~100 iterations to 1e-10 CG's
+    # finite-precision paths drift apart by a few iterations
+    it_a, it_b = a[0]["pcg_iters"], b[0]["pcg_iters"]
+    assert abs(it_a - it_b) <= 0.1 * it_a + 2, (it_a, it_b)
+    assert b[0]["rcs_rel_resid"] <= 1e-9
+    # both solve the same system to 1e-10: compare them through S
+    row_ptr, col, val, rhs = a[3]
+    dd = _host_residual(row_ptr, col, val, np.zeros_like(rhs), a[2].reshape(-1) - b[2].reshape(-1))
+    assert np.linalg.norm(dd) <= 3e-10 * np.linalg.norm(rhs)
+    assert np.array_equal(b[2], c[2]) and c[0]["refine_steps"] == 0
+    s = scene
+    costs = {}
+    for name, v in (("standard", B.BA_PCG_STANDARD), ("implicit", B.BA_PCG_IMPLICIT)):
+        g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, precision=B.BA_FP64, pcg_rel_tol=1e-6,
+                      pcg_variant=v)
+        costs[name] = [g.lm_step()["cost_after"] for _ in range(3)]
+        g.close()
+    assert np.allclose(costs["standard"], costs["implicit"], rtol=1e-8, atol=0), costs
+
+
+def test_implicit_fp32_reaches_a_tight_residual(B, scene):
+    """FP32: the implicit inner PCG inside the FP64 refinement reaches the
+    same true residual as the stored-S variants."""
+    info, conv, dxc, (row_ptr, col, val, b) = _solve(B, scene, 1e-4, precision=B.BA_FP32, pcg_rel_tol=1e-8,
+                                                     pcg_variant=B.BA_PCG_IMPLICIT)
+    r = _host_residual(row_ptr, col, val, b, dxc.reshape(-1).astype(np.float64))
+    assert conv and info["rcs_rel_resid"] <= 1e-8
+    assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(b)
+
+
+def test_implicit_needs_a_linearization(B, oracle_rcs):
+    A, b = oracle_rcs
+    with pytest.raises(B.BAError) as ei:
+        B.Problem.from_rcs(A.row_ptr, A.col, A.val, b, precision=B.BA_FP64, pcg_variant=B.BA_PCG_IMPLICIT)
+    assert ei.value.status == B.BA_ERR_INVALID_ARG
