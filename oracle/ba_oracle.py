@@ -331,17 +331,19 @@ class PCGResult:
 
 
 def pcg(A: BSMC, b: np.ndarray, Minv: np.ndarray, tol: float, max_iters: int | None = None,
-        spmv=None) -> PCGResult:
+        spmv=None, precond=None) -> PCGResult:
     """Preconditioned CG on R y = b with y_0 = 0:
         r_0 = b, d_0 = M^-1 r_0;
         repeat: alpha = r^T M^-1 r / d^T R d; y += alpha d; r -= alpha R d;
                 beta = r+^T M^-1 r+ / r^T M^-1 r; d = M^-1 r+ + beta d
-        until ||r_k|| / ||r_0|| <= tol (or max_iters iterations)."""
+        until ||r_k|| / ||r_0|| <= tol (or max_iters iterations).
+    ``spmv`` / ``precond`` replace the products with R and M^-1 (other
+    storage, other block sizes)."""
     n = A.n
     if max_iters is None:
         max_iters = max(1000, 6 * n)
     mv = spmv or (lambda v: bsmc_spmv(A, v))
-    apply_m = lambda v: np.einsum("nij,nj->ni", Minv, v.reshape(-1, 6)).reshape(-1)
+    apply_m = precond or (lambda v: np.einsum("nij,nj->ni", Minv, v.reshape(-1, 6)).reshape(-1))
     y = np.zeros_like(b)
     r = b.copy()
     r0 = np.linalg.norm(r)

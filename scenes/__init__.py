@@ -322,3 +322,59 @@ def capacity_scene(seed=5001, n_along=500, n_across=400, n_pts=40_000_000) -> Sc
     observations, and about 33 co-visible cameras per camera."""
     return aerial_scene(n_along=n_along, n_across=n_across, n_pts=n_pts, track_mean=6.5, track_max=9,
                         track_min=5, seed=seed, name="capacity")
+
+
+# ----------------------------------------------------------------------------
+# interior parameters and variable block sizes (inputs only)
+# ----------------------------------------------------------------------------
+
+def interiors0(n: int, seed: int = 0, f_sd=0.01, c_sd=2.0, k_sd=0.01) -> np.ndarray:
+    """Initial interiors [f, cx, cy, k1, k2] per camera, (n, 5): the pinhole the
+    observations were made with, perturbed (relative N(0, f_sd) on f,
+    N(0, c_sd) px on the principal point, N(0, k_sd) on k1 and k2)."""
+    rng = np.random.default_rng(seed)
+    k = np.empty((n, 5))
+    k[:, 0] = F_PX * (1.0 + rng.normal(0.0, f_sd, n))
+    k[:, 1] = C_PX + rng.normal(0.0, c_sd, n)
+    k[:, 2] = C_PX + rng.normal(0.0, c_sd, n)
+    k[:, 3] = rng.normal(0.0, k_sd, n)
+    k[:, 4] = rng.normal(0.0, k_sd, n)
+    return k
+
+
+def block_sizes(n: int, frac_self_cal: float, seed: int = 0) -> np.ndarray:
+    """Unknowns per camera: 11 (six exterior + five interior) for a random
+    fraction of self-calibrating cameras, 6 for the rest; int32 (n,)."""
+    rng = np.random.default_rng(seed)
+    return np.where(rng.random(n) < frac_self_cal, 11, 6).astype(np.int32)
+
+
+def random_block_spd(row_ptr, col, cdim, seed: int = 0, dtype=np.float64):
+    """Values for a symmetric positive definite matrix with the given upper
+    block pattern (diagonal block first in each row) and block sizes, in one
+    packed array (block k row-major, c_i x c_j): off-diagonal blocks N(0, 1);
+    each diagonal block G G^T / c + (1 + the sum of the Frobenius norms of its
+    row's and column's off-diagonal blocks) I, so that every diagonal block
+    dominates its block row (block Gershgorin) and the matrix is SPD.
+    Returns (values, block offsets (nnzb + 1,) int64)."""
+    rng = np.random.default_rng(seed)
+    n = len(cdim)
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    row = np.repeat(np.arange(n), np.diff(row_ptr))
+    size = cdim[row].astype(np.int64) * cdim[col].astype(np.int64)
+    boff = np.concatenate([[0], np.cumsum(size)])
+    val = rng.standard_normal(int(boff[-1]))
+    off = row != col
+    seg = np.repeat(np.arange(len(col)), size)
+    nrm = np.sqrt(np.bincount(seg, weights=val * val, minlength=len(col)))
+    dom = np.ones(n)
+    np.add.at(dom, row[off], nrm[off])
+    np.add.at(dom, col[off], nrm[off])
+    for i in range(n):
+        k = row_ptr[i]
+        c = int(cdim[i])
+        G = val[boff[k]:boff[k + 1]].reshape(c, c)
+        Dm = G @ G.T / c + dom[i] * np.eye(c)
+        val[boff[k]:boff[k + 1]] = Dm.reshape(-1)
+    return val.astype(dtype), boff
