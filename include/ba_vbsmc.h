@@ -1,0 +1,81 @@
+/* Variable-size BSMC: a reduced camera system whose cameras carry different
+ * numbers of unknowns, its product and its block-Jacobi PCG.
+ *
+ * Sec. 4 (Fig. 4): the RCS block (i, j) has c_i x c_j entries, c_i being the
+ * number of unknowns of camera i, and BSMC stores the non-zero upper blocks
+ * with their position and size; Sec. 4.1 takes c = 11 (six exterior and five
+ * interior unknowns per camera) for its memory model (Eqs. 8-10).  Cameras
+ * that hold their interiors fixed have c_i = 6, self-calibrating ones 11; the
+ * format accepts any 1 <= c_i <= BA_VB_CMAX.  The product is the two-sided
+ * upper-triangle product of Sec. 6.2 (Fig. 13); the solver is the PCG of
+ * Sec. 3.2 (Eqs. 6-7) with M = the diagonal blocks of S.
+ *
+ * Conventions as in ba.h: every call returns a ba_status, with the reason in
+ * ba_last_error(); input arrays are host arrays owned by the caller and
+ * copied by ba_vbsmc_create.  After BA_ERR_CUDA or BA_ERR_TIMEOUT the object
+ * only accepts ba_vbsmc_destroy (BA_ERR_STATE otherwise).  Calls on one object
+ * are not thread-safe.
+ */
+#ifndef BA_VBSMC_H
+#define BA_VBSMC_H
+
+#include "ba.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_vbsmc ba_vbsmc; /* opaque; owns its device memory */
+
+#define BA_VB_CMAX 16 /* largest number of unknowns per camera */
+
+/* A variable-size BSMC system S x = b.
+ *   opt       precision (BA_FP64, or BA_FP32: values, vectors and PCG in
+ *             FP32, reductions in FP64), cuda_stream, device_mem_cap; NULL =
+ *             defaults.  Other fields are ignored.
+ *   n         cameras (block rows), n >= 1;
+ *   cdim[n]   unknowns per camera, 1..BA_VB_CMAX; camera i's entries of x and
+ *             b are the c_i consecutive entries after those of cameras < i;
+ *   nnzb      stored (upper-triangle) blocks, n <= nnzb < 2^31;
+ *   row_ptr[n+1], col[nnzb]: block row i holds blocks row_ptr[i] ..
+ *             row_ptr[i+1]-1, the first being the diagonal (col = i), the
+ *             others with strictly increasing columns i < col < n;
+ *   val       the blocks in that order, block (i, j) as c_i x c_j row-major
+ *             doubles, packed without gaps (sum over blocks of c_i c_j);
+ *   b         sum c_i doubles.
+ * The block-Jacobi preconditioner (the inverse of every diagonal block, by an
+ * FP64 Cholesky factorisation on the device) is built here.
+ * Errors: BA_ERR_INVALID_ARG (sizes, pattern, options), BA_ERR_NONFINITE (a
+ * value or b), BA_ERR_NOT_SPD (a diagonal block), BA_ERR_OOM, BA_ERR_CUDA. */
+ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim, int64_t nnzb,
+                          const int32_t *row_ptr, const int32_t *col, const double *val,
+                          const double *b, ba_vbsmc **out);
+
+/* y = S x on the object's stream (asynchronous): x and y are device arrays of
+ * sum c_i values in the object's precision (double or float), not
+ * overlapping.  Errors: BA_ERR_INVALID_ARG (null), BA_ERR_STATE, BA_ERR_CUDA. */
+ba_status ba_vbsmc_spmv(ba_vbsmc *h, const void *x, void *y);
+
+/* Block-Jacobi PCG on S y = b from y = 0 until ||r_k|| / ||r_0|| <= tol or
+ * max_iters iterations (0: max(1000, 6 n)); one cooperative kernel.
+ * Synchronous.  x_out (host, sum c_i doubles) receives y, and may be NULL;
+ * iters, rel_resid (the recurrence's ||r_k|| / ||r_0||) and kernel_ms (the
+ * device time of the solve) may be NULL.  Errors: BA_ERR_INVALID_ARG (tol <=
+ * 0, max_iters < 0), BA_ERR_NOT_SPD (d^T S d <= 0), BA_ERR_NO_CONVERGENCE
+ * (max_iters reached; the outputs are still written), BA_ERR_TIMEOUT (a grid
+ * wait gave up), BA_ERR_STATE, BA_ERR_CUDA. */
+ba_status ba_vbsmc_solve(ba_vbsmc *h, double tol, int32_t max_iters, double *x_out, int32_t *iters,
+                         double *rel_resid, double *kernel_ms);
+
+/* Sizes: unknowns (sum c_i), and the bytes of the stored format: the block
+ * values, a column and a value offset per block (4 + 8 bytes: the three
+ * 4-byte ids per block of Eq. 9), n + 1 row starts and n block sizes. */
+ba_status ba_vbsmc_info(const ba_vbsmc *h, int64_t *n_unknowns, int64_t *storage_bytes);
+
+void ba_vbsmc_destroy(ba_vbsmc *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BA_VBSMC_H */

@@ -88,7 +88,7 @@ _I32 = ctypes.POINTER(ctypes.c_int32)
 _I64 = ctypes.POINTER(ctypes.c_int64)
 _S = ctypes.c_int  # ba_status
 
-# (name, restype, argtypes) of every C entry point in include/ba.h
+# (name, restype, argtypes) of every C entry point in include/*.h
 SIGNATURES = [
     ("ba_options_default", None, [ctypes.POINTER(ba_options)]),
     ("ba_problem_create", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _D, ctypes.c_int64, _D,
@@ -127,6 +127,12 @@ SIGNATURES = [
     ("ba_precond_net_forward", _S, [_P, _P, ctypes.POINTER(ctypes.c_float), _D]),
     ("ba_precond_net_train_step", _S, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), ctypes.c_uint64,
                                        ctypes.c_double, _D, ctypes.POINTER(ctypes.c_float)]),
+    ("ba_vbsmc_create", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _I32, ctypes.c_int64, _I32, _I32, _D, _D,
+                             ctypes.POINTER(_P)]),
+    ("ba_vbsmc_spmv", _S, [_P, _P, _P]),
+    ("ba_vbsmc_solve", _S, [_P, ctypes.c_double, ctypes.c_int32, _D, _I32, _D, _D]),
+    ("ba_vbsmc_info", _S, [_P, _I64, _I64]),
+    ("ba_vbsmc_destroy", None, [_P]),
     ("ba_tc_gemm", _S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int64, _P,
                         ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P, _P]),
 ]
@@ -563,3 +569,74 @@ def unpack_params(p):
 def pack_params(d):
     return np.concatenate([np.asarray(d[k], dtype=np.float32).reshape(-1) for k in ("W1", "b1", "W2", "b2", "Wo",
                                                                                       "bo")])
+
+
+BA_VB_CMAX = 16
+
+
+class VBSMC:
+    """A variable-size BSMC system (include/ba_vbsmc.h): cameras with c_i
+    unknowns each (6 exterior, 11 with five interiors), the upper blocks
+    packed row by row (block (i, j) row-major c_i x c_j), b of sum c_i."""
+
+    def __init__(self, cdim, row_ptr, col, val, b, stream="current", **opts):
+        if stream == "current":
+            stream = _default_stream()
+        self.opts = ba_options_default(cuda_stream=stream, **opts)
+        self.cdim = np.ascontiguousarray(cdim, dtype=np.int32)
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64).reshape(-1)
+        b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+        n = len(self.cdim)
+        if len(row_ptr) != n + 1:
+            raise BAError(BA_ERR_INVALID_ARG, "row_ptr must have n + 1 entries")
+        if len(b) != int(self.cdim.sum()):
+            raise BAError(BA_ERR_INVALID_ARG, "b must have sum(cdim) entries")
+        if len(row_ptr) and row_ptr[-1] == len(col) and len(col):
+            rows = np.repeat(np.arange(n), np.diff(row_ptr))
+            if rows.size == len(col) and np.all((col >= 0) & (col < n)):
+                need = int((self.cdim[rows].astype(np.int64) * self.cdim[col]).sum())
+                if len(val) != need:
+                    raise BAError(BA_ERR_INVALID_ARG, f"val must have {need} entries")
+        h = _P()
+        _check(lib().ba_vbsmc_create(ctypes.byref(self.opts), n, self.cdim.ctypes.data_as(_I32), len(col),
+                                     row_ptr.ctypes.data_as(_I32), col.ctypes.data_as(_I32), _dp(val), _dp(b),
+                                     ctypes.byref(h)))
+        self.h = h
+        self.n = n
+
+    def spmv(self, x, y):
+        """y = S x for torch device tensors of sum c_i values in the system's
+        precision; queued on the system's stream."""
+        _check(lib().ba_vbsmc_spmv(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr())))
+
+    def solve(self, tol, max_iters=0, allow=()):
+        """Block-Jacobi PCG from 0: returns (x, iterations, ||r|| / ||r0||,
+        device ms, status)."""
+        N, _ = self.info()
+        x = np.empty(N)
+        it = ctypes.c_int32()
+        rel = ctypes.c_double()
+        ms = ctypes.c_double()
+        st = _check(lib().ba_vbsmc_solve(self.h, float(tol), int(max_iters), _dp(x), ctypes.byref(it),
+                                         ctypes.byref(rel), ctypes.byref(ms)), allow)
+        return x, it.value, rel.value, ms.value, st
+
+    def info(self):
+        """(unknowns, bytes of the stored format)."""
+        N = ctypes.c_int64()
+        nb = ctypes.c_int64()
+        _check(lib().ba_vbsmc_info(self.h, ctypes.byref(N), ctypes.byref(nb)))
+        return N.value, nb.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ba_vbsmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

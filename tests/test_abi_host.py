@@ -1,4 +1,4 @@
-"""CPU-only tests of the C ABI: the library loads, exports what include/ba.h
+"""CPU-only tests of the C ABI: the library loads, exports what include/*.h
 declares, validates inputs before touching the GPU, and its host-side
 symbolic phase (BSMC pattern, Sec. 4) matches the oracle."""
 import os
@@ -23,7 +23,8 @@ def B():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "ba.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(ba_[a-z0-9_]+)\s*\(", src)))
 
@@ -149,4 +150,48 @@ def test_create_rcs_rejects_malformed_input_without_gpu(B, case):
     o = B.ba_options_default()
     with pytest.raises(B.BAError) as ei:
         B.ba_problem_create_rcs(o, row_ptr, col, val, b)
+    assert ei.value.status == want
+
+
+def _vb_valid():
+    cdim = np.array([6, 11, 2], dtype=np.int32)
+    row_ptr = np.array([0, 2, 4, 5], dtype=np.int32)
+    col = np.array([0, 2, 1, 2, 2], dtype=np.int32)
+    val, _ = scenes.random_block_spd(row_ptr, col, cdim, seed=1)
+    return dict(cdim=cdim, row_ptr=row_ptr, col=col, val=val, b=np.ones(int(cdim.sum())))
+
+
+@pytest.mark.parametrize("case", ["c_zero", "c_too_big", "no_diagonal", "unsorted", "col_range", "row_ptr_end",
+                                  "nan_val", "inf_b", "bad_precision"])
+def test_vbsmc_create_rejects_bad_input_without_gpu(B, case):
+    s = _vb_valid()
+    kw = {}
+    want = B.BA_ERR_INVALID_ARG
+    if case == "c_zero":
+        s["cdim"][2] = 0
+        s["val"] = s["val"][:36 + 11 * 11]       # blocks (0,0), (1,1) keep their sizes
+        s["b"] = s["b"][:17]
+    elif case == "c_too_big":
+        s["cdim"][1] = B.BA_VB_CMAX + 1
+        s["val"] = np.ones(36 + 12 + 17 * 17 + 17 * 2 + 4)
+        s["b"] = np.ones(6 + 17 + 2)
+    elif case == "no_diagonal":
+        s["col"][2], s["col"][3] = 2, 1          # row 1 starts with column 2
+    elif case == "unsorted":
+        s["row_ptr"] = np.array([0, 2, 3, 5], dtype=np.int32)
+        s["col"] = np.array([0, 2, 1, 2, 1], dtype=np.int32)
+    elif case == "col_range":
+        s["col"][1] = 3
+    elif case == "row_ptr_end":
+        s["row_ptr"][3] = 4
+    elif case == "nan_val":
+        s["val"][40] = np.nan
+        want = B.BA_ERR_NONFINITE
+    elif case == "inf_b":
+        s["b"][3] = np.inf
+        want = B.BA_ERR_NONFINITE
+    elif case == "bad_precision":
+        kw["precision"] = 3
+    with pytest.raises(B.BAError) as ei:
+        B.VBSMC(s["cdim"], s["row_ptr"], s["col"], s["val"], s["b"], stream=None, **kw)
     assert ei.value.status == want
