@@ -291,6 +291,7 @@ def run_ours(args):
     cpu = None if args.no_cpu_baseline else cpu_baseline(args.workload, s.n_obs)
     formats = None if args.no_formats else formats_bench(B, torch, g, st1, esz, peaks, peak_kind, stream)
     tri = triangulation_bench(g, st1, ktimes)
+    vbs = None if args.no_vbsmc else vbsmc_bench(B, torch, g, peaks, peak_kind, esz)
     g.close()
     solver = None if args.no_solver else solver_bench(B, torch)
     acc = sum(i["accepted"] for i in infos)
@@ -305,7 +306,8 @@ def run_ours(args):
         "lm": {"accepted": acc, "pcg_iters": [i["pcg_iters"] for i in infos],
                "cost": [infos[0]["cost_before"], infos[-1]["cost_after"]],
                "rcs_rel_resid_max": max(i["rcs_rel_resid"] for i in infos)},
-        "kernels_ms": kernels, "solver": solver, "spmv_formats": formats, "triangulation": tri, "impl": "ours",
+        "kernels_ms": kernels, "solver": solver, "spmv_formats": formats, "triangulation": tri, "vbsmc": vbs,
+        "impl": "ours",
         "setup": {"problem_create_s": round(t_create, 2), "device_bytes": int(st1["device_bytes"]),
                   "preconditioner": "learned (packaged weights), block-Jacobi fallback" if net else "block-Jacobi",
                   "used_fallback": [i["used_fallback"] for i in infos]},
@@ -371,6 +373,67 @@ def formats_bench(B, torch, g, st, esz, peaks, peak_kind, stream, repeats=7):
             "time_implicit_over_bsmc": round(res["implicit"]["us"] / res["bsmc"]["us"], 3),
             "note": "implicit: no stored S; its bytes are what one product reads instead (stored J rows, "
                     "per-point factors, a work vector, a camera-major index)"}
+
+
+def vbsmc_bench(B, torch, g, peaks, peak_kind, esz, c=11, tol=1e-10, repeats=7):
+    """The RCS pattern of the workload with c unknowns per camera (c = 11:
+    six exterior and five interior, Sec. 4.1) in variable-size BSMC
+    (ba_vbsmc_*): y = S x with L2 flushed before each launch (CUDA events on
+    the current stream, median of repeats), and a block-Jacobi PCG solve
+    timed by the library's CUDA events.  Values from a seeded SPD generator
+    (off-diagonal blocks N(0, 1), diagonal blocks dominant), so the iteration
+    count says nothing about BA conditioning; the times per product and per
+    iteration are what this measures.  Bytes: the stored format read once plus
+    x and y."""
+    import numpy as np
+
+    import scenes
+    g.linearize()
+    g.form_rcs(g.lm_state()[0])
+    row_ptr, col, _, _ = g.rcs()
+    n = len(row_ptr) - 1
+    cdim = np.full(n, c, dtype=np.int32)
+    val, _ = scenes.random_block_spd(row_ptr, col, cdim, seed=7)
+    b = np.random.default_rng(8).standard_normal(c * n)
+    prec = B.BA_FP32 if esz == 4 else B.BA_FP64
+    vb = B.VBSMC(cdim, row_ptr, col, val, b, precision=prec)
+    N, nbytes = vb.info()
+    dt = torch.float32 if esz == 4 else torch.float64
+    x = torch.randn(N, dtype=dt, device="cuda", generator=torch.Generator(device="cuda").manual_seed(9))
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    vb.spmv(x, y)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(repeats):
+        flush.zero_()
+        e0.record(stream)
+        vb.spmv(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    us = 1e3 * statistics.median(ts)
+    moved = nbytes + 2 * N * esz
+    # per iteration: the difference of a loose and a tight solve (the start
+    # phase and the launch cancel), medians of three
+    vb.solve(tol)  # warm-up
+    lo = [vb.solve(1e-1) for _ in range(3)]
+    hi = [vb.solve(tol) for _ in range(3)]
+    its = hi[-1][1]
+    d_it = max(its - lo[-1][1], 1)
+    us_it = 1e3 * (statistics.median([r[3] for r in hi]) - statistics.median([r[3] for r in lo])) / d_it
+    vb.close()
+    return {"what": "variable-size BSMC (Sec. 4: c_i x c_j blocks), c = %d on every camera" % c,
+            "cameras": n, "blocks": len(col), "unknowns": N, "storage_bytes": int(nbytes),
+            "spmv_us": round(us, 2), "bytes_per_spmv": int(moved), "achieved_gbs": round(moved / us / 1e3, 1),
+            "frac_hbm": round(moved / us / 1e3 / peaks["hbm_gbs"], 4), "peak_kind": peak_kind,
+            "l2": "flushed before each product",
+            "pcg": {"tol": tol, "iterations": its, "us_per_iteration": round(us_it, 2),
+                    "per_iteration": "(t(tol) - t(1e-1)) / (iterations(tol) - iterations(1e-1))",
+                    "values": "seeded SPD generator, diagonally dominant blocks"}}
 
 
 def triangulation_bench(g, st, ktimes, gn_iters=3, repeats=3):
@@ -561,6 +624,7 @@ def main():
     ap.add_argument("--pcg-variant", default=None, choices=["standard", "split", "implicit"], help="kernel case: PCG variant")
     ap.add_argument("--group-obs", type=int, default=0, help="kernel case: observations per point group")
     ap.add_argument("--no-formats", action="store_true", help="skip the RCS storage-format SpMV comparison")
+    ap.add_argument("--no-vbsmc", action="store_true", help="skip the variable-size BSMC (c = 11) measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solver", action="store_true", help="skip the PCG time-to-1e-8 comparison")

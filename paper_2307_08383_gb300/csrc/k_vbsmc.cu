@@ -8,8 +8,9 @@
 // block sizes cdim and vector offsets off (camera i's entries are
 // off[i] .. off[i] + c_i - 1).  The product runs from two-sided entry lists
 // built on the host: row i lists its stored blocks, then the blocks of its
-// column in the rows above it, flagged "transposed"; so every row is summed by
-// one warp with no atomics, in a fixed order.
+// column in the rows above it, flagged "transposed" (one 16-byte record per
+// entry); so every row is summed by one warp with no atomics, in a fixed
+// order.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -28,27 +29,38 @@ struct VbScalars {
 
 // Warp-per-row product: lane a + 16 h (a < 16 the output component, h the
 // parity of the entries it takes) sums S_ij x_j over its entries; the halves
-// are joined by one shuffle.  gx(idx) returns x at vector index idx; the lanes
-// a < c_i of half 0 call out(idx, (S x)_idx).
+// are joined by one shuffle.  Each two-sided entry is one 16-byte record
+// (value offset lo / hi, vector offset of j, c_j << 1 | transposed), and a
+// lane loads its whole block row (or column) and the c_j values of x with
+// independent predicated loads before the FMAs, so an entry costs two
+// dependent memory round trips, not one per column.  (Staging each block in
+// shared memory with coalesced loads first measured 1.9x slower: the copy,
+// the warp barrier and the shared reads chain per entry.)  gx(idx) returns x
+// at vector index idx; lanes a < c_i of half 0 call out(idx, (S x)_idx).
 template <typename T, class GX, class OUT>
 __device__ __forceinline__ void vb_row(int i, const int *__restrict__ cdim, const int *__restrict__ off,
-                                       const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
-                                       const int64_t *__restrict__ boff, const T *__restrict__ val, GX gx, OUT out) {
+                                       const int *__restrict__ tw_ptr, const int4 *__restrict__ tw_info,
+                                       const T *__restrict__ val, GX gx, OUT out) {
     const int lane = threadIdx.x & 31, a = lane & 15, h = lane >> 4;
     const int ci = __ldg(cdim + i);
     T acc = T(0);
     const int e1 = __ldg(tw_ptr + i + 1);
     for (int e = __ldg(tw_ptr + i) + h; e < e1; e += 2) {
-        const int2 en = __ldg(tw_ent + e);
-        const int j = en.y >> 1, tr = en.y & 1;
-        const int cj = __ldg(cdim + j), oj = __ldg(off + j);
-        const T *B = val + __ldg(boff + en.x);
-        if (a < ci) {
-            if (tr)
-                for (int c = 0; c < cj; ++c) acc += __ldg(B + c * ci + a) * gx(oj + c);
-            else
-                for (int c = 0; c < cj; ++c) acc += __ldg(B + a * cj + c) * gx(oj + c);
+        const int4 in = __ldg(tw_info + e);
+        const int64_t vo = (int64_t)(uint32_t)in.x | ((int64_t)in.y << 32);
+        const int oj = in.z, cj = in.w >> 1;
+        const T *B = val + vo;
+        // element (a, c) of this row's block: B[c * ci + a] if transposed, else B[a * cj + c]
+        const int stride = (in.w & 1) ? ci : 1, base = (in.w & 1) ? a : a * cj;
+        T bv[BA_VB_CMAX], xv[BA_VB_CMAX];
+#pragma unroll
+        for (int c = 0; c < BA_VB_CMAX; ++c) {
+            const bool on = c < cj && a < ci;
+            bv[c] = on ? __ldg(B + base + c * stride) : T(0);
+            xv[c] = c < cj ? gx(oj + c) : T(0);
         }
+#pragma unroll
+        for (int c = 0; c < BA_VB_CMAX; ++c) acc += bv[c] * xv[c];
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 16);
     if (h == 0 && a < ci) out(__ldg(off + i) + a, acc);
@@ -56,12 +68,11 @@ __device__ __forceinline__ void vb_row(int i, const int *__restrict__ cdim, cons
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_vb_spmv(int n, const int *__restrict__ cdim, const int *__restrict__ off,
-                                                 const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
-                                                 const int64_t *__restrict__ boff, const T *__restrict__ val,
-                                                 const T *__restrict__ x, T *__restrict__ y) {
+                                                 const int *__restrict__ tw_ptr, const int4 *__restrict__ tw_info,
+                                                 const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
     const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
     for (int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < n; i += nw)
-        vb_row<T>(i, cdim, off, tw_ptr, tw_ent, boff, val, [&](int idx) { return __ldg(x + idx); },
+        vb_row<T>(i, cdim, off, tw_ptr, tw_info, val, [&](int idx) { return __ldg(x + idx); },
                   [&](int idx, T v) { y[idx] = v; });
 }
 
@@ -135,8 +146,8 @@ __device__ __forceinline__ T vb_precond_entry(int i, int a, const int *__restric
 template <typename T>
 __global__ void __launch_bounds__(256) k_vb_pcg(int n, int N, const int *__restrict__ cdim, const int *__restrict__ off,
                                                 const int *__restrict__ ent_cam, const int *__restrict__ tw_ptr,
-                                                const int2 *__restrict__ tw_ent, const int64_t *__restrict__ boff,
-                                                const T *__restrict__ val, const int64_t *__restrict__ moff,
+                                                const int4 *__restrict__ tw_info, const T *__restrict__ val,
+                                                const int64_t *__restrict__ moff,
                                                 const T *__restrict__ Minv, const T *__restrict__ b, T *y, T *r0, T *r1,
                                                 T *z, T *d0, T *d1, T *q, VbScalars *sc, double *red, unsigned *bar,
                                                 long long limit_cycles) {
@@ -181,7 +192,7 @@ __global__ void __launch_bounds__(256) k_vb_pcg(int n, int N, const int *__restr
         auto dir = [&](int k) { return __ldcg(z + k) + bt * __ldcg(dold + k); };
         T pap_t = T(0);
         for (int i = tid >> 5; i < n; i += nw)
-            vb_row<T>(i, cdim, off, tw_ptr, tw_ent, boff, val, dir, [&](int idx, T v) {
+            vb_row<T>(i, cdim, off, tw_ptr, tw_info, val, dir, [&](int idx, T v) {
                 const T dv = dir(idx);
                 q[idx] = v;
                 dnew[idx] = dv;
@@ -242,7 +253,7 @@ struct ba_vbsmc {
     size_t esz = 8, dev_bytes = 0, cap = 0;
     cudaStream_t st = nullptr;
     int *cdim = nullptr, *off = nullptr, *row_ptr = nullptr, *col = nullptr, *ent_cam = nullptr, *tw_ptr = nullptr;
-    int2 *tw_ent = nullptr;
+    int4 *tw_info = nullptr;
     int64_t *boff = nullptr, *moff = nullptr;
     void *val = nullptr, *Minv = nullptr, *b = nullptr, *vec[7] = {};
     VbScalars *sc = nullptr;
@@ -290,7 +301,7 @@ cudaError_t vb_spmv_T(ba_vbsmc *h, const T *x, T *y) {
     if (e != cudaSuccess) return e;
     const int64_t want = ((int64_t)h->n * 32 + 255) / 256;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)std::max(per_sm, 1) * n_sm));
-    k_vb_spmv<T><<<grid, 256, 0, h->st>>>(h->n, h->cdim, h->off, h->tw_ptr, h->tw_ent, h->boff, (const T *)h->val, x, y);
+    k_vb_spmv<T><<<grid, 256, 0, h->st>>>(h->n, h->cdim, h->off, h->tw_ptr, h->tw_info, (const T *)h->val, x, y);
     return cudaGetLastError();
 }
 
@@ -306,8 +317,8 @@ cudaError_t vb_pcg_T(ba_vbsmc *h) {
     if ((e = cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->st)) != cudaSuccess) return e;
     int n = h->n, N = (int)h->N;
     const int *cd = h->cdim, *of = h->off, *ec = h->ent_cam, *twp = h->tw_ptr;
-    const int2 *twe = h->tw_ent;
-    const int64_t *bo = h->boff, *mo = h->moff;
+    const int4 *twi = h->tw_info;
+    const int64_t *mo = h->moff;
     const T *val = (const T *)h->val, *Mi = (const T *)h->Minv, *b = (const T *)h->b;
     T *y = (T *)h->vec[0], *r0 = (T *)h->vec[1], *r1 = (T *)h->vec[2], *z = (T *)h->vec[3], *d0 = (T *)h->vec[4],
       *d1 = (T *)h->vec[5], *q = (T *)h->vec[6];
@@ -315,7 +326,7 @@ cudaError_t vb_pcg_T(ba_vbsmc *h) {
     double *red = h->red;
     unsigned *bar = h->bar;
     long long limit = 4000000000LL;  // ~2 s of SM clock per grid wait
-    void *args[] = {&n, &N, &cd, &of, &ec, &twp, &twe, &bo, &val, &mo, &Mi, &b, &y, &r0, &r1, &z, &d0, &d1, &q,
+    void *args[] = {&n, &N, &cd, &of, &ec, &twp, &twi, &val, &mo, &Mi, &b, &y, &r0, &r1, &z, &d0, &d1, &q,
                     &sc, &red, &bar, &limit};
     return cudaLaunchCooperativeKernel((const void *)k_vb_pcg<T>, dim3(grid), dim3(256), args, 0, h->st);
 }
@@ -369,13 +380,18 @@ ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim,
         for (int32_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) tw_ptr[col[k] + 1] += 1;
     }
     for (int32_t i = 0; i < n; ++i) tw_ptr[i + 1] += tw_ptr[i];
-    std::vector<int2> tw_ent(tw_ptr[n]);
+    // two-sided entry records: value offset (lo, hi), vector offset of the
+    // other camera j, c_j << 1 | transposed
+    std::vector<int4> tw_info(tw_ptr[n]);
     {
+        auto rec = [&](int32_t k, int32_t j, int tr) {
+            return make_int4((int)(uint32_t)(boff[k] & 0xffffffffu), (int)(boff[k] >> 32), off[j], (cdim[j] << 1) | tr);
+        };
         std::vector<int32_t> fill(tw_ptr.begin(), tw_ptr.end() - 1);
         for (int32_t i = 0; i < n; ++i)
-            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) tw_ent[fill[i]++] = make_int2(k, col[k] << 1);
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) tw_info[fill[i]++] = rec(k, col[k], 0);
         for (int32_t i = 0; i < n; ++i)
-            for (int32_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) tw_ent[fill[col[k]]++] = make_int2(k, (i << 1) | 1);
+            for (int32_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) tw_info[fill[col[k]]++] = rec(k, i, 1);
     }
 
     ba_vbsmc *h = new ba_vbsmc();
@@ -407,7 +423,7 @@ ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim,
     VB_TRY(up((void **)&h->col, col, nnzb * sizeof(int32_t)));
     VB_TRY(up((void **)&h->ent_cam, ent_cam.data(), N * sizeof(int32_t)));
     VB_TRY(up((void **)&h->tw_ptr, tw_ptr.data(), (n + 1) * sizeof(int32_t)));
-    VB_TRY(up((void **)&h->tw_ent, tw_ent.data(), tw_ent.size() * sizeof(int2)));
+    VB_TRY(up((void **)&h->tw_info, tw_info.data(), tw_info.size() * sizeof(int4)));
     VB_TRY(up((void **)&h->boff, boff.data(), (nnzb + 1) * sizeof(int64_t)));
     VB_TRY(up((void **)&h->moff, moff.data(), (n + 1) * sizeof(int64_t)));
     VB_TRY(vb_alloc(h, &h->val, nval * h->esz));
