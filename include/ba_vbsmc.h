@@ -51,6 +51,40 @@ ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim,
                           const int32_t *row_ptr, const int32_t *col, const double *val,
                           const double *b, ba_vbsmc **out);
 
+/* The reduced camera system of a scene whose cameras carry interior
+ * parameters, formed on the device into a variable-size BSMC system.
+ *   cams[n_cams x 6]  exterior [omega, t] (X_cam = R(omega) X + t);
+ *   intr[n_cams x 5]  interiors [f, cx, cy, k1, k2]: with xh = x/z, yh = y/z,
+ *                     r2 = xh^2 + yh^2, d = 1 + k1 r2 + k2 r2^2, the projection
+ *                     is u = f d xh + cx, v = f d yh + cy;
+ *   cdim[n_cams]      6 (interiors held fixed) or 11 (the five interior
+ *                     unknowns follow the six exterior ones);
+ *   pts, obs_*        as for ba_problem_create (every point seen at least
+ *                     twice, no duplicate (camera, point) pairs);
+ *   lambda >= 0       LM damping: lambda times diag(J^T J) clamped to
+ *                     [1e-6, 1e32] on every unknown.
+ * Forms Eq. 1's e and J (two rows per observation: 11 camera columns, 3
+ * point columns), then Eq. 3-4 with c_i unknowns per camera: V_k, V_k^-1
+ * and l_p per point; per stored block (i, j) the sum over the points seen by
+ * both cameras of -W_ik V_k^-1 W_jk^T, plus U_i (damped) on the diagonal, and
+ * b_i = l_c,i - sum_k W_ik V_k^-1 l_p,k.  Arithmetic in FP64; stored in
+ * opt->precision.  No atomics: every block is summed by one warp from its
+ * own list of point pairs, in track order.  The pattern is that of
+ * ba_symbolic_pattern.  Then as ba_vbsmc_create (M^-1 built).
+ * Errors: BA_ERR_INVALID_ARG (sizes, indices, cdim, lambda), BA_ERR_NONFINITE
+ * (an input), BA_ERR_NOT_SPD (a V_k or a diagonal block), BA_ERR_OOM,
+ * BA_ERR_CUDA. */
+ba_status ba_vbsmc_create_interiors(const ba_options *opt, int32_t n_cams, const double *cams, const double *intr,
+                                    const int32_t *cdim, int64_t n_pts, const double *pts, int64_t n_obs,
+                                    const int32_t *obs_cam, const int64_t *obs_pt, const double *obs_uv,
+                                    double lambda, ba_vbsmc **out);
+
+/* Copies the system to host arrays (each may be NULL): row_ptr[n+1],
+ * col[nnzb], the packed block values (as ba_vbsmc_create takes them,
+ * upcast to double) and b.  Synchronous.  Errors: BA_ERR_INVALID_ARG,
+ * BA_ERR_STATE, BA_ERR_CUDA. */
+ba_status ba_vbsmc_get_system(const ba_vbsmc *h, int32_t *row_ptr, int32_t *col, double *val, double *b);
+
 /* y = S x on the object's stream (asynchronous): x and y are device arrays of
  * sum c_i values in the object's precision (double or float), not
  * overlapping.  Errors: BA_ERR_INVALID_ARG (null), BA_ERR_STATE, BA_ERR_CUDA. */
@@ -67,10 +101,11 @@ ba_status ba_vbsmc_spmv(ba_vbsmc *h, const void *x, void *y);
 ba_status ba_vbsmc_solve(ba_vbsmc *h, double tol, int32_t max_iters, double *x_out, int32_t *iters,
                          double *rel_resid, double *kernel_ms);
 
-/* Sizes: unknowns (sum c_i), and the bytes of the stored format: the block
- * values, a column and a value offset per block (4 + 8 bytes: the three
- * 4-byte ids per block of Eq. 9), n + 1 row starts and n block sizes. */
-ba_status ba_vbsmc_info(const ba_vbsmc *h, int64_t *n_unknowns, int64_t *storage_bytes);
+/* Sizes (each output may be NULL): unknowns (sum c_i), the bytes of the
+ * stored format - the block values, a column and a value offset per block
+ * (4 + 8 bytes: the three 4-byte ids per block of Eq. 9), n + 1 row starts
+ * and n block sizes - and the number of stored blocks. */
+ba_status ba_vbsmc_info(const ba_vbsmc *h, int64_t *n_unknowns, int64_t *storage_bytes, int64_t *n_blocks);
 
 void ba_vbsmc_destroy(ba_vbsmc *h);
 

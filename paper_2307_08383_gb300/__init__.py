@@ -129,9 +129,12 @@ SIGNATURES = [
                                        ctypes.c_double, _D, ctypes.POINTER(ctypes.c_float)]),
     ("ba_vbsmc_create", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _I32, ctypes.c_int64, _I32, _I32, _D, _D,
                              ctypes.POINTER(_P)]),
+    ("ba_vbsmc_create_interiors", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _D, _D, _I32, ctypes.c_int64, _D,
+                                       ctypes.c_int64, _I32, _I64, _D, ctypes.c_double, ctypes.POINTER(_P)]),
+    ("ba_vbsmc_get_system", _S, [_P, _I32, _I32, _D, _D]),
     ("ba_vbsmc_spmv", _S, [_P, _P, _P]),
     ("ba_vbsmc_solve", _S, [_P, ctypes.c_double, ctypes.c_int32, _D, _I32, _D, _D]),
-    ("ba_vbsmc_info", _S, [_P, _I64, _I64]),
+    ("ba_vbsmc_info", _S, [_P, _I64, _I64, _I64]),
     ("ba_vbsmc_destroy", None, [_P]),
     ("ba_tc_gemm", _S, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int64, _P,
                         ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _P, _P]),
@@ -606,6 +609,52 @@ class VBSMC:
         self.h = h
         self.n = n
 
+    @classmethod
+    def from_scene(cls, cams, intr, cdim, pts, obs_cam, obs_pt, obs_uv, lam, stream="current", **opts):
+        """The RCS of a scene whose cameras carry interiors [f, cx, cy, k1, k2]
+        (c_i = 6: held fixed, 11: estimated), formed on the device at damping
+        lam (ba_vbsmc_create_interiors)."""
+        if stream == "current":
+            stream = _default_stream()
+        self = cls.__new__(cls)
+        self.opts = ba_options_default(cuda_stream=stream, **opts)
+        n = len(cams)
+        self.cdim = np.ascontiguousarray(cdim, dtype=np.int32)
+        cams = _f64(cams, (n, 6))
+        intr = _f64(intr, (n, 5))
+        pts = np.ascontiguousarray(pts, dtype=np.float64)
+        P = len(pts)
+        pts = _f64(pts, (P, 3))
+        obs_cam = np.ascontiguousarray(obs_cam, dtype=np.int32)
+        obs_pt = np.ascontiguousarray(obs_pt, dtype=np.int64)
+        m = len(obs_cam)
+        obs_uv = _f64(obs_uv, (m, 2))
+        if len(self.cdim) != n or len(obs_pt) != m:
+            raise BAError(BA_ERR_INVALID_ARG, "array lengths disagree")
+        h = _P()
+        _check(lib().ba_vbsmc_create_interiors(ctypes.byref(self.opts), n, _dp(cams), _dp(intr),
+                                               self.cdim.ctypes.data_as(_I32), P, _dp(pts), m,
+                                               obs_cam.ctypes.data_as(_I32), obs_pt.ctypes.data_as(_I64),
+                                               _dp(obs_uv), float(lam), ctypes.byref(h)))
+        self.h = h
+        self.n = n
+        return self
+
+    def system(self):
+        """(row_ptr, col, packed block values, b) as host arrays (float64)."""
+        N = ctypes.c_int64()
+        nb = ctypes.c_int64()
+        _check(lib().ba_vbsmc_info(self.h, ctypes.byref(N), None, ctypes.byref(nb)))
+        row_ptr = np.empty(self.n + 1, dtype=np.int32)
+        col = np.empty(nb.value, dtype=np.int32)
+        _check(lib().ba_vbsmc_get_system(self.h, row_ptr.ctypes.data_as(_I32), col.ctypes.data_as(_I32), None, None))
+        rows = np.repeat(np.arange(self.n), np.diff(row_ptr))
+        nval = int((self.cdim[rows].astype(np.int64) * self.cdim[col]).sum())
+        val = np.empty(nval)
+        b = np.empty(N.value)
+        _check(lib().ba_vbsmc_get_system(self.h, None, None, _dp(val), _dp(b)))
+        return row_ptr, col, val, b
+
     def spmv(self, x, y):
         """y = S x for torch device tensors of sum c_i values in the system's
         precision; queued on the system's stream."""
@@ -627,7 +676,7 @@ class VBSMC:
         """(unknowns, bytes of the stored format)."""
         N = ctypes.c_int64()
         nb = ctypes.c_int64()
-        _check(lib().ba_vbsmc_info(self.h, ctypes.byref(N), ctypes.byref(nb)))
+        _check(lib().ba_vbsmc_info(self.h, ctypes.byref(N), ctypes.byref(nb), None))
         return N.value, nb.value
 
     def close(self):

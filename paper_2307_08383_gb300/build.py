@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libba.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["ba_api.cu", "k_obs.cu", "k_rcs.cu", "k_pcg.cu", "k_pcg_static.cu", "k_gnn.cu", "k_formats.cu",
-                "k_vbsmc.cu"]
+                "k_vbsmc.cu", "k_interiors.cu"]
 CXX_SOURCES = ["ba_setup.cpp"]
 
 

@@ -17,15 +17,10 @@
 #include <string>
 #include <vector>
 
-#include "ba_vbsmc.h"
 #include "device_util.cuh"
+#include "vbsmc_internal.h"
 
 namespace ba {
-
-struct VbScalars {
-    double rz, rr, rr0, tol2;
-    int iters, done, max_iters, err;
-};
 
 // Warp-per-row product: lane a + 16 h (a < 16 the output component, h the
 // parity of the entries it takes) sums S_ij x_j over its entries; the halves
@@ -246,26 +241,7 @@ __global__ void __launch_bounds__(256) k_vb_pcg(int n, int N, const int *__restr
 
 using namespace ba;
 
-struct ba_vbsmc {
-    int n = 0;
-    int64_t nnzb = 0, N = 0, nval = 0, nminv = 0;
-    bool fp32 = false, dead = false;
-    size_t esz = 8, dev_bytes = 0, cap = 0;
-    cudaStream_t st = nullptr;
-    int *cdim = nullptr, *off = nullptr, *row_ptr = nullptr, *col = nullptr, *ent_cam = nullptr, *tw_ptr = nullptr;
-    int4 *tw_info = nullptr;
-    int64_t *boff = nullptr, *moff = nullptr;
-    void *val = nullptr, *Minv = nullptr, *b = nullptr, *vec[7] = {};
-    VbScalars *sc = nullptr;
-    VbScalars host{};
-    double *red = nullptr;
-    unsigned *bar = nullptr;
-    int *err = nullptr;
-    std::vector<void *> allocs;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-};
-
-namespace {
+namespace ba {
 
 ba_status vb_alloc(ba_vbsmc *h, void **d, size_t bytes) {
     bytes = bytes < 16 ? 16 : bytes;
@@ -286,6 +262,10 @@ ba_status vb_cuda(ba_vbsmc *h, cudaError_t e, const char *what) {
     h->dead = true;
     return set_error(BA_ERR_CUDA, (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
 }
+
+}  // namespace ba
+
+namespace {
 
 template <typename T>
 ba_status vb_upload(ba_vbsmc *h, void *dst, const double *src, size_t cnt) {
@@ -333,24 +313,19 @@ cudaError_t vb_pcg_T(ba_vbsmc *h) {
 
 }  // namespace
 
-extern "C" {
+namespace ba {
 
-ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim, int64_t nnzb, const int32_t *row_ptr,
-                          const int32_t *col, const double *val, const double *b, ba_vbsmc **out) {
-    if (!out) return set_error(BA_ERR_INVALID_ARG, "null output pointer");
-    *out = nullptr;
-    ba_options o;
-    if (opt) o = *opt; else ba_options_default(&o);
+ba_status vb_check_pattern(const ba_options &o, int32_t n, const int32_t *cdim, int64_t nnzb, const int32_t *row_ptr,
+                           const int32_t *col, int64_t *N_out, int64_t *nval_out) {
     if (o.precision != BA_FP64 && o.precision != BA_FP32) return set_error(BA_ERR_INVALID_ARG, "bad precision");
     if (n <= 0 || n >= (1 << 30) || nnzb < n || nnzb >= (int64_t)INT32_MAX)
         return set_error(BA_ERR_INVALID_ARG, "need 0 < n < 2^30 and n <= nnzb < 2^31");
-    if (!cdim || !row_ptr || !col || !val || !b) return set_error(BA_ERR_INVALID_ARG, "null input array");
+    if (!cdim || !row_ptr || !col) return set_error(BA_ERR_INVALID_ARG, "null input array");
     if (row_ptr[0] != 0 || row_ptr[n] != nnzb) return set_error(BA_ERR_INVALID_ARG, "row_ptr must run from 0 to nnzb");
-    int64_t N = 0, nval = 0, nminv = 0;
+    int64_t N = 0, nval = 0;
     for (int32_t i = 0; i < n; ++i) {
         if (cdim[i] < 1 || cdim[i] > BA_VB_CMAX) return set_error(BA_ERR_INVALID_ARG, "block size out of 1..BA_VB_CMAX");
         N += cdim[i];
-        nminv += (int64_t)cdim[i] * cdim[i];
     }
     if (N >= (int64_t)INT32_MAX) return set_error(BA_ERR_INVALID_ARG, "too many unknowns");
     for (int32_t i = 0; i < n; ++i) {
@@ -361,11 +336,16 @@ ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim,
                 return set_error(BA_ERR_INVALID_ARG, "columns must increase within a row and stay below n");
         for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) nval += (int64_t)cdim[i] * cdim[col[k]];
     }
-    for (int64_t k = 0; k < nval; ++k)
-        if (!std::isfinite(val[k])) return set_error(BA_ERR_NONFINITE, "non-finite block value");
-    for (int64_t k = 0; k < N; ++k)
-        if (!std::isfinite(b[k])) return set_error(BA_ERR_NONFINITE, "non-finite b");
+    *N_out = N;
+    *nval_out = nval;
+    return BA_OK;
+}
 
+ba_status vb_build(const ba_options &o, int32_t n, const int32_t *cdim, int64_t nnzb, const int32_t *row_ptr,
+                   const int32_t *col, ba_vbsmc **out) {
+    int64_t N = 0, nval = 0, nminv = 0;
+    ba_status s = vb_check_pattern(o, n, cdim, nnzb, row_ptr, col, &N, &nval);
+    if (s) return s;
     // host-side layout: offsets, two-sided entry lists
     std::vector<int32_t> off(n + 1, 0), ent_cam(N), tw_ptr(n + 1, 0);
     std::vector<int64_t> boff(nnzb + 1, 0), moff(n + 1, 0);
@@ -375,6 +355,7 @@ ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim,
         for (int32_t a = 0; a < cdim[i]; ++a) ent_cam[off[i] + a] = i;
         for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) boff[k + 1] = boff[k] + (int64_t)cdim[i] * cdim[col[k]];
     }
+    nminv = moff[n];
     for (int32_t i = 0; i < n; ++i) {
         tw_ptr[i + 1] += row_ptr[i + 1] - row_ptr[i];
         for (int32_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) tw_ptr[col[k] + 1] += 1;
@@ -393,7 +374,6 @@ ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim,
         for (int32_t i = 0; i < n; ++i)
             for (int32_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) tw_info[fill[col[k]]++] = rec(k, i, 1);
     }
-
     ba_vbsmc *h = new ba_vbsmc();
     h->n = n;
     h->nnzb = nnzb;
@@ -404,63 +384,114 @@ ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim,
     h->esz = h->fp32 ? 4 : 8;
     h->st = (cudaStream_t)o.cuda_stream;
     h->cap = o.device_mem_cap;
-    ba_status s = BA_OK;
     auto up = [&](void **d, const void *src, size_t bytes) -> ba_status {
         ba_status r = vb_alloc(h, d, bytes);
         if (r) return r;
         return vb_cuda(h, cudaMemcpy(*d, src, bytes, cudaMemcpyHostToDevice), "upload");
     };
-#define VB_TRY(x)                \
-    do {                         \
-        if ((s = (x)) != BA_OK) { \
-            ba_vbsmc_destroy(h); \
-            return s;            \
-        }                        \
-    } while (0)
-    VB_TRY(up((void **)&h->cdim, cdim, n * sizeof(int32_t)));
-    VB_TRY(up((void **)&h->off, off.data(), (n + 1) * sizeof(int32_t)));
-    VB_TRY(up((void **)&h->row_ptr, row_ptr, (n + 1) * sizeof(int32_t)));
-    VB_TRY(up((void **)&h->col, col, nnzb * sizeof(int32_t)));
-    VB_TRY(up((void **)&h->ent_cam, ent_cam.data(), N * sizeof(int32_t)));
-    VB_TRY(up((void **)&h->tw_ptr, tw_ptr.data(), (n + 1) * sizeof(int32_t)));
-    VB_TRY(up((void **)&h->tw_info, tw_info.data(), tw_info.size() * sizeof(int4)));
-    VB_TRY(up((void **)&h->boff, boff.data(), (nnzb + 1) * sizeof(int64_t)));
-    VB_TRY(up((void **)&h->moff, moff.data(), (n + 1) * sizeof(int64_t)));
-    VB_TRY(vb_alloc(h, &h->val, nval * h->esz));
-    VB_TRY(vb_alloc(h, &h->b, N * h->esz));
-    VB_TRY(vb_alloc(h, &h->Minv, nminv * h->esz));
-    for (auto &v : h->vec) VB_TRY(vb_alloc(h, &v, N * h->esz));
-    VB_TRY(vb_alloc(h, (void **)&h->sc, sizeof(VbScalars)));
-    VB_TRY(vb_alloc(h, (void **)&h->red, (size_t)RED_SLOTS * sizeof(double)));
-    VB_TRY(vb_alloc(h, (void **)&h->bar, sizeof(unsigned)));
-    VB_TRY(vb_alloc(h, (void **)&h->err, sizeof(int)));
-    if (h->fp32) {
-        VB_TRY(vb_upload<float>(h, h->val, val, nval));
-        VB_TRY(vb_upload<float>(h, h->b, b, N));
-    } else {
-        VB_TRY(vb_upload<double>(h, h->val, val, nval));
-        VB_TRY(vb_upload<double>(h, h->b, b, N));
+    std::vector<int32_t> brow(nnzb);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) brow[k] = i;
+    if (!s) s = up((void **)&h->cdim, cdim, n * sizeof(int32_t));
+    if (!s) s = up((void **)&h->off, off.data(), (n + 1) * sizeof(int32_t));
+    if (!s) s = up((void **)&h->row_ptr, row_ptr, (n + 1) * sizeof(int32_t));
+    if (!s) s = up((void **)&h->col, col, nnzb * sizeof(int32_t));
+    if (!s) s = up((void **)&h->brow, brow.data(), nnzb * sizeof(int32_t));
+    if (!s) s = up((void **)&h->ent_cam, ent_cam.data(), N * sizeof(int32_t));
+    if (!s) s = up((void **)&h->tw_ptr, tw_ptr.data(), (n + 1) * sizeof(int32_t));
+    if (!s) s = up((void **)&h->tw_info, tw_info.data(), tw_info.size() * sizeof(int4));
+    if (!s) s = up((void **)&h->boff, boff.data(), (nnzb + 1) * sizeof(int64_t));
+    if (!s) s = up((void **)&h->moff, moff.data(), (n + 1) * sizeof(int64_t));
+    if (!s) s = vb_alloc(h, &h->val, nval * h->esz);
+    if (!s) s = vb_alloc(h, &h->b, N * h->esz);
+    if (!s) s = vb_alloc(h, &h->Minv, nminv * h->esz);
+    for (auto &v : h->vec)
+        if (!s) s = vb_alloc(h, &v, N * h->esz);
+    if (!s) s = vb_alloc(h, (void **)&h->sc, sizeof(VbScalars));
+    if (!s) s = vb_alloc(h, (void **)&h->red, (size_t)RED_SLOTS * sizeof(double));
+    if (!s) s = vb_alloc(h, (void **)&h->bar, sizeof(unsigned));
+    if (!s) s = vb_alloc(h, (void **)&h->err, sizeof(int));
+    if (!s) s = vb_cuda(h, cudaEventCreate(&h->ev[0]), "event");
+    if (!s) s = vb_cuda(h, cudaEventCreate(&h->ev[1]), "event");
+    if (s) {
+        ba_vbsmc_destroy(h);
+        return s;
     }
-    VB_TRY(vb_cuda(h, cudaEventCreate(&h->ev[0]), "event"));
-    VB_TRY(vb_cuda(h, cudaEventCreate(&h->ev[1]), "event"));
-    VB_TRY(vb_cuda(h, cudaMemsetAsync(h->err, 0, sizeof(int), h->st), "memset"));
-    const int g = (n + 127) / 128;
+    *out = h;
+    return BA_OK;
+}
+
+ba_status vb_finish(ba_vbsmc *h) {
+    ba_status s;
+    if ((s = vb_cuda(h, cudaMemsetAsync(h->err, 0, sizeof(int), h->st), "memset"))) return s;
+    const int g = (h->n + 127) / 128;
     if (h->fp32)
-        k_vb_minv<float><<<g, 128, 0, h->st>>>(n, h->cdim, h->row_ptr, h->boff, (const float *)h->val, h->moff,
+        k_vb_minv<float><<<g, 128, 0, h->st>>>(h->n, h->cdim, h->row_ptr, h->boff, (const float *)h->val, h->moff,
                                                (float *)h->Minv, h->err);
     else
-        k_vb_minv<double><<<g, 128, 0, h->st>>>(n, h->cdim, h->row_ptr, h->boff, (const double *)h->val, h->moff,
+        k_vb_minv<double><<<g, 128, 0, h->st>>>(h->n, h->cdim, h->row_ptr, h->boff, (const double *)h->val, h->moff,
                                                 (double *)h->Minv, h->err);
-    VB_TRY(vb_cuda(h, cudaGetLastError(), "k_vb_minv"));
+    if ((s = vb_cuda(h, cudaGetLastError(), "k_vb_minv"))) return s;
     int err = 0;
-    VB_TRY(vb_cuda(h, cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st), "read flag"));
-    VB_TRY(vb_cuda(h, cudaStreamSynchronize(h->st), "sync"));
-    if (err == BA_ERR_NOT_SPD) {
+    if ((s = vb_cuda(h, cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st), "read flag")))
+        return s;
+    if ((s = vb_cuda(h, cudaStreamSynchronize(h->st), "sync"))) return s;
+    if (err == BA_ERR_NOT_SPD) return set_error(BA_ERR_NOT_SPD, "a diagonal block is not positive definite");
+    return BA_OK;
+}
+
+}  // namespace ba
+
+extern "C" {
+
+ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim, int64_t nnzb, const int32_t *row_ptr,
+                          const int32_t *col, const double *val, const double *b, ba_vbsmc **out) {
+    if (!out) return set_error(BA_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    ba_options o;
+    if (opt) o = *opt; else ba_options_default(&o);
+    if (!val || !b) return set_error(BA_ERR_INVALID_ARG, "null input array");
+    int64_t N = 0, nval = 0;
+    ba_status s = vb_check_pattern(o, n, cdim, nnzb, row_ptr, col, &N, &nval);
+    if (s) return s;
+    for (int64_t k = 0; k < nval; ++k)
+        if (!std::isfinite(val[k])) return set_error(BA_ERR_NONFINITE, "non-finite block value");
+    for (int64_t k = 0; k < N; ++k)
+        if (!std::isfinite(b[k])) return set_error(BA_ERR_NONFINITE, "non-finite b");
+    ba_vbsmc *h = nullptr;
+    if ((s = vb_build(o, n, cdim, nnzb, row_ptr, col, &h))) return s;
+    s = h->fp32 ? vb_upload<float>(h, h->val, val, nval) : vb_upload<double>(h, h->val, val, nval);
+    if (!s) s = h->fp32 ? vb_upload<float>(h, h->b, b, N) : vb_upload<double>(h, h->b, b, N);
+    if (!s) s = vb_finish(h);
+    if (s) {
         ba_vbsmc_destroy(h);
-        return set_error(BA_ERR_NOT_SPD, "a diagonal block is not positive definite");
+        return s;
     }
-#undef VB_TRY
     *out = h;
+    return BA_OK;
+}
+
+ba_status ba_vbsmc_get_system(const ba_vbsmc *h, int32_t *row_ptr, int32_t *col, double *val, double *b) {
+    if (!h) return set_error(BA_ERR_INVALID_ARG, "null object");
+    if (h->dead) return set_error(BA_ERR_STATE, "the object is unusable after an earlier error");
+    ba_vbsmc *m = const_cast<ba_vbsmc *>(h);
+    ba_status s;
+    if (row_ptr && (s = vb_cuda(m, cudaMemcpy(row_ptr, h->row_ptr, (h->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost),
+                                "read row_ptr")))
+        return s;
+    if (col && (s = vb_cuda(m, cudaMemcpy(col, h->col, h->nnzb * sizeof(int32_t), cudaMemcpyDeviceToHost), "read col")))
+        return s;
+    auto rd = [&](double *dst, const void *src, int64_t cnt) -> ba_status {
+        std::vector<char> raw(cnt * h->esz);
+        ba_status r = vb_cuda(m, cudaMemcpy(raw.data(), src, raw.size(), cudaMemcpyDeviceToHost), "read values");
+        if (r) return r;
+        for (int64_t k = 0; k < cnt; ++k)
+            dst[k] = h->fp32 ? (double)reinterpret_cast<const float *>(raw.data())[k]
+                             : reinterpret_cast<const double *>(raw.data())[k];
+        return BA_OK;
+    };
+    if (val && (s = rd(val, h->val, h->nval))) return s;
+    if (b && (s = rd(b, h->b, h->N))) return s;
     return BA_OK;
 }
 
@@ -516,9 +547,10 @@ ba_status ba_vbsmc_solve(ba_vbsmc *h, double tol, int32_t max_iters, double *x_o
     return BA_OK;
 }
 
-ba_status ba_vbsmc_info(const ba_vbsmc *h, int64_t *n_unknowns, int64_t *storage_bytes) {
+ba_status ba_vbsmc_info(const ba_vbsmc *h, int64_t *n_unknowns, int64_t *storage_bytes, int64_t *n_blocks) {
     if (!h) return set_error(BA_ERR_INVALID_ARG, "null object");
     if (n_unknowns) *n_unknowns = h->N;
+    if (n_blocks) *n_blocks = h->nnzb;
     if (storage_bytes)
         *storage_bytes = h->nval * (int64_t)h->esz + h->nnzb * (4 + 8) + (int64_t)(h->n + 1) * 4 + (int64_t)h->n * 4;
     return BA_OK;

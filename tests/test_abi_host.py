@@ -195,3 +195,30 @@ def test_vbsmc_create_rejects_bad_input_without_gpu(B, case):
     with pytest.raises(B.BAError) as ei:
         B.VBSMC(s["cdim"], s["row_ptr"], s["col"], s["val"], s["b"], stream=None, **kw)
     assert ei.value.status == want
+
+
+@pytest.mark.parametrize("case", ["cdim_7", "neg_lambda", "nan_intr", "cam_range", "single_obs"])
+def test_vbsmc_interiors_rejects_bad_input_without_gpu(B, case):
+    s = _valid()
+    n = len(s["cams"])
+    intr = np.tile([1000.0, 500.0, 500.0, 0.0, 0.0], (n, 1))
+    cdim = np.full(n, 11, dtype=np.int32)
+    lam = 1e-3
+    want = B.BA_ERR_INVALID_ARG
+    if case == "cdim_7":
+        cdim[1] = 7
+    elif case == "neg_lambda":
+        lam = -1.0
+    elif case == "nan_intr":
+        intr[2, 3] = np.nan
+        want = B.BA_ERR_NONFINITE
+    elif case == "cam_range":
+        s["obs_cam"][0] = n
+    elif case == "single_obs":
+        s["obs_pt"] = np.append(s["obs_pt"], len(s["pts"]))
+        s["obs_cam"] = np.append(s["obs_cam"], 0).astype(np.int32)
+        s["obs_uv"] = np.vstack([s["obs_uv"], [1.0, 2.0]])
+        s["pts"] = np.vstack([s["pts"], [0.0, 0.0, 5.0]])
+    with pytest.raises(B.BAError) as ei:
+        B.VBSMC.from_scene(s["cams"], intr, cdim, s["pts"], s["obs_cam"], s["obs_pt"], s["obs_uv"], lam, stream=None)
+    assert ei.value.status == want

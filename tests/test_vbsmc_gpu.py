@@ -1,7 +1,8 @@
 """GPU parity of the variable-size BSMC (Sec. 4, Fig. 4: block (i, j) is
 c_i x c_j; c = 6 exterior or 11 with five interior unknowns, Sec. 4.1)
-against the oracle: the product (Sec. 6.2, Fig. 13) and the block-Jacobi PCG
-(Sec. 3.2) of ba_vbsmc_* on the oracle's RCS with interiors, and on seeded
+against the oracle: the RCS with interiors formed on the device (Eqs. 1, 3, 4),
+the product (Sec. 6.2, Fig. 13) and the block-Jacobi PCG (Sec. 3.2) of
+ba_vbsmc_* on the oracle's RCS with interiors, and on seeded
 SPD systems at the edge sizes (one camera, blocks of 1..16 unknowns, the
 5,000-camera aerial pattern with c = 11).
 
@@ -64,13 +65,48 @@ def _abs_product(A, x):
     return I.vbsmc_spmv(I.VBSMC(A.row_ptr, A.col, A.cdim, [np.abs(v) for v in A.val]), np.abs(x))
 
 
+_SCENE = dict(n_along=8, n_across=5, pts_per_cam=40, seed=4601)
+
+
 @pytest.fixture(scope="module", params=[0.0, 0.5, 1.0], ids=["c6", "mixed", "c11"])
-def interior_system(request):
-    s = scenes.aerial_small(n_along=8, n_across=5, pts_per_cam=40, seed=4601)
+def interior_case(request):
+    s = scenes.aerial_small(**_SCENE)
     intr = scenes.interiors0(s.n_cams, seed=4602)
     cdim = scenes.block_sizes(s.n_cams, request.param, seed=4603)
     A, b = I.scene_rcs_vb(s, intr, cdim, 1e-3)
-    return A, b
+    return s, intr, cdim, A, b
+
+
+@pytest.fixture(scope="module")
+def interior_system(interior_case):
+    return interior_case[3], interior_case[4]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_device_rcs_with_interiors_matches_oracle(B, interior_case, prec):
+    """ba_vbsmc_create_interiors (e, J with five interiors; Eq. 3-4 with c_i
+    unknowns, formed on the device) against the oracle's RCS of the same
+    scene: the same pattern; values and b within 1e-11 of the largest |S|
+    (FP64; the same sums in another order) plus, in FP32 storage, the
+    rounding of each entry (2^-24 relative); then the solve."""
+    s, intr, cdim, A, b = interior_case
+    fp64 = prec == "fp64"
+    g = B.VBSMC.from_scene(s.cams0, intr, cdim, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, 1e-3,
+                           precision=B.BA_FP64 if fp64 else B.BA_FP32)
+    row_ptr, col, val, bg = g.system()
+    assert np.array_equal(row_ptr, A.row_ptr) and np.array_equal(col, A.col)
+    ref = _packed(A)
+    scale = np.abs(ref).max()
+    rnd = 0.0 if fp64 else 1.01 * 2.0 ** -24
+    assert np.all(np.abs(val - ref) <= 1e-11 * scale + rnd * np.abs(ref)), np.abs(val - ref).max() / scale
+    bs = np.abs(b).max()
+    assert np.all(np.abs(bg - b) <= 1e-11 * bs + rnd * np.abs(b)), np.abs(bg - b).max() / bs
+    if fp64:
+        x, it, rel, _, _ = g.solve(1e-10)
+        y = I.vb_pcg(A, b, 1e-10)
+        assert abs(it - y.iters) <= 1
+        assert np.linalg.norm(x - y.y) <= 1e-7 * np.linalg.norm(y.y)
+    g.close()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
