@@ -20,7 +20,7 @@ matrix compression for super large scale datasets"):
 * Sec. 3.1 (after Eq. 5) and Sec. 5: the points may instead be triangulated
   from the camera poses; the method is not given (a reading below).
 
-Readings of what the paper leaves open (each one is listed in the design doc):
+Readings of what the paper leaves open:
 
 * camera model: pinhole, +z forward, focal f, principal point (cx, cy), no
   distortion; cameras are [omega(3), t(3)] with X_cam = R(omega) X + t;

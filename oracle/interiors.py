@@ -20,7 +20,7 @@ their interiors, so that the RCS has blocks of mixed sizes:
   height and width per block);
 * the PCG of Sec. 3.2 on it (``ba_oracle.pcg`` with these products).
 
-Readings of what the paper leaves open (each one is listed in the design doc):
+Readings of what the paper leaves open:
 
 * the five interiors are the focal length f, the principal point (cx, cy) and
   two radial distortion coefficients k1, k2 acting on the normalised image
