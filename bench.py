@@ -505,8 +505,9 @@ def solver_bench(B, torch, seed=200, repeats=5):
             "speedup_fp32_block_jacobi_vs_fp64": round(t64 / sum(res["fp32_block_jacobi"]["ms"]), 3)}
 
 
-def _oracle_steps(workload, n_steps, sample_cams):
-    """Times n_steps oracle LM iterations on a sample of the workload."""
+def _oracle_steps(workload, n_steps, sample_cams, phases=False):
+    """Times n_steps oracle LM iterations on a sample of the workload (and,
+    with phases, the phases of one more)."""
     import oracle as O
     import scenes
     if workload == "ring50":
@@ -523,17 +524,34 @@ def _oracle_steps(workload, n_steps, sample_cams):
         t0 = time.perf_counter()
         st, _, _ = pb.step(st)
         times.append(time.perf_counter() - t0)
-    return s, times
+    if not phases:
+        return s, times
+    # one more iteration's phases, each timed alone: linearize, RCS (Eq. 3-4),
+    # PCG, back-substitution (Eq. 5)
+    t = [time.perf_counter()]
+    e, Jc, Jp = pb.linearize(st.cams, st.pts)
+    t.append(time.perf_counter())
+    blk, A, b = pb.rcs(e, Jc, Jp, st.lam)
+    t.append(time.perf_counter())
+    res = pb.solve(A, b)
+    t.append(time.perf_counter())
+    O.back_substitute(blk, pb.obs_cam, pb.obs_pt, pb.P, res.y.reshape(-1, 6))
+    t.append(time.perf_counter())
+    names = ("linearize", "form_rcs", "pcg", "back_substitute")
+    return s, times, {k: t[q + 1] - t[q] for q, k in enumerate(names)}
 
 
 def cpu_baseline(workload, m_full):
-    s, times = _oracle_steps(workload, 3, (20, 10))
+    s, times, ph = _oracle_steps(workload, 3, (20, 10), phases=True)
     per_obs = sum(times) / len(times) / s.n_obs
     est = per_obs * m_full
     return {"value": round(1.0 / est, 6), "unit": "LM iters/s", "cores": 1, "kind": "oracle",
             "sample": f"3 FP64 oracle LM iterations on a {s.n_cams}-camera, {s.n_pts}-point, {s.n_obs}-observation "
                       f"sample of the same aerial layout ({sum(times):.1f} s), scaled to {m_full} observations "
-                      f"by time per observation"}
+                      f"by time per observation",
+            "phases_s_scaled": {k: round(v / s.n_obs * m_full, 3) for k, v in ph.items()},
+            "phases_note": "one further oracle iteration on the sample, each phase timed alone, scaled to the "
+                           "workload by time per observation (the PCG's iteration count is the sample's)"}
 
 
 def run_reference(args):
