@@ -16,7 +16,10 @@ Conventions shared with every consumer (the problem statement, Sec. 3.1):
 The observations are synthesised from ground truth with rotation matrices built
 by a look-at construction and converted to angle-axis with scipy, then Gaussian
 pixel noise is added; the initial values handed to the solver are perturbed
-ground truth.  Scene shapes follow the paper's workloads (aerial grids, tracks
+ground truth.  For cameras that also estimate interior parameters the module
+gives perturbed initial interiors and the number of unknowns per camera; for
+storage and solver measurements at sizes no reference can form, it gives
+seeded symmetric positive definite values for a block pattern.  Scene shapes follow the paper's workloads (aerial grids, tracks
 of a few cameras per point, N(0, sigma^2) px noise, Sec. 7.1).
 """
 from __future__ import annotations
