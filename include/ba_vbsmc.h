@@ -70,7 +70,10 @@ ba_status ba_vbsmc_create(const ba_options *opt, int32_t n, const int32_t *cdim,
  * b_i = l_c,i - sum_k W_ik V_k^-1 l_p,k.  Arithmetic in FP64; stored in
  * opt->precision.  No atomics: every block is summed by one warp from its
  * own list of point pairs, in track order.  The pattern is that of
- * ba_symbolic_pattern.  Then as ba_vbsmc_create (M^-1 built).
+ * ba_symbolic_pattern.  Then as ba_vbsmc_create (M^-1 built).  The
+ * formation's temporary device buffers (a 256-byte J row per observation,
+ * 96 bytes per point, 8 bytes per point pair) are freed before the call
+ * returns and are not counted against device_mem_cap.
  * Errors: BA_ERR_INVALID_ARG (sizes, indices, cdim, lambda), BA_ERR_NONFINITE
  * (an input), BA_ERR_NOT_SPD (a V_k or a diagonal block), BA_ERR_OOM,
  * BA_ERR_CUDA. */
