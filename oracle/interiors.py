@@ -18,7 +18,9 @@ their interiors, so that the RCS has blocks of mixed sizes:
 * BSMC with per-block sizes (Sec. 4, Fig. 4), its product (Sec. 6.2, Fig. 13),
   its block-Jacobi preconditioner (Sec. 3.2) and its bytes (Eq. 9 with a
   height and width per block);
-* the PCG of Sec. 3.2 on it (``ba_oracle.pcg`` with these products).
+* the PCG of Sec. 3.2 on it (``ba_oracle.pcg`` with these products);
+* interiors shared by the images of one physical camera: a block row of five
+  unknowns per physical camera beside the images' six-unknown rows.
 
 Readings of what the paper leaves open:
 
@@ -29,6 +31,8 @@ Readings of what the paper leaves open:
 * every camera has interiors of its own; a camera whose interiors are held
   fixed has c_i = 6 unknowns, a self-calibrating one c_i = 11, its five
   interior unknowns after the six exterior ones; interiors update additively;
+  where several images share a physical camera, its interiors are one block of
+  five unknowns of their own (``rcs_shared``);
 * damping, as for six unknowns: lambda times diag(J^T J) clamped to
   [1e-6, 1e32], on every unknown.
 """
@@ -259,3 +263,76 @@ def scene_rcs_vb(scene, intr, cdim, lam):
     oc, op, uv = scene.obs_cam[order], scene.obs_pt[order], scene.obs_uv[order]
     e, Jc, Jp = jacobians_intr(scene.cams0, intr, scene.pts0, oc, op, uv)
     return rcs_vb(e, Jc, Jp, oc, op, cdim, scene.n_pts, lam)
+
+
+# ----------------------------------------------------------------------------
+# interiors shared by the images of one physical camera
+# ----------------------------------------------------------------------------
+
+def rcs_shared(e, Jc, Jp, obs_cam, obs_pt, phys, K, P, lam):
+    """The RCS when the images of a physical camera share one set of
+    interiors: images 0..n-1 keep their six exterior unknowns (block size 6),
+    and physical camera q becomes block n + q with the five interior unknowns
+    (block size 5), coupled to every image phys maps to it.
+
+    Per observation a of image i, the exterior columns of J_c go to block i
+    and the interior columns to block n + phys[i].  Eq. 3 per block:
+    U = sum J_s^T J_t over the slots s, t of each observation (which couples
+    image i and its physical camera even without a point), damped on the
+    diagonal; l_c = -sum J_s^T e.  Eq. 4 per point k: with W_beta the sum of
+    J_s^T J_p over the point's slots in block beta, S(beta, gamma) -=
+    W_beta V_k^-1 W_gamma^T and b_beta -= W_beta V_k^-1 l_p,k for the blocks
+    beta <= gamma the point touches.  Observations must be sorted by
+    (point, camera).  Returns (VBSMC, b)."""
+    n = len(phys)
+    cdim = np.array([N_EXT] * n + [N_INT] * K, dtype=np.int32)
+
+    def slots(a):
+        i = obs_cam[a]
+        return ((i, Jc[a][:, :N_EXT]), (n + phys[i], Jc[a][:, N_EXT:C_MAX]))
+
+    S = {}
+    lc = [np.zeros(c) for c in cdim]
+    V = np.zeros((P, 3, 3))
+    lp = np.zeros((P, 3))
+    for a in range(len(e)):
+        sl = slots(a)
+        for (bs, Js) in sl:
+            lc[bs] -= Js.T @ e[a]
+            for (bt, Jt) in sl:
+                if bs <= bt:
+                    S.setdefault((bs, bt), np.zeros((cdim[bs], cdim[bt])))
+                    S[(bs, bt)] = S[(bs, bt)] + Js.T @ Jt
+        k = obs_pt[a]
+        V[k] += Jp[a].T @ Jp[a]
+        lp[k] -= Jp[a].T @ e[a]
+    for beta in range(n + K):
+        D = S[(beta, beta)]
+        S[(beta, beta)] = D + lam * np.diag(_damp(np.diag(D)))
+    for k in range(P):
+        V[k] = V[k] + lam * np.diag(_damp(np.diag(V[k])))
+    b = [x.copy() for x in lc]
+    for k, tr in enumerate(tracks(obs_pt, P)):
+        Vinv = np.linalg.inv(V[k])
+        W = {}
+        for a in tr:
+            for (bs, Js) in slots(a):
+                W[bs] = W.get(bs, np.zeros((cdim[bs], 3))) + Js.T @ Jp[a]
+        for beta, Wb in W.items():
+            b[beta] = b[beta] - Wb @ Vinv @ lp[k]
+            for gamma, Wg in W.items():
+                if beta <= gamma:
+                    S.setdefault((beta, gamma), np.zeros((cdim[beta], cdim[gamma])))
+                    S[(beta, gamma)] = S[(beta, gamma)] - Wb @ Vinv @ Wg.T
+    return vbsmc_from_blocks(S, cdim), np.concatenate(b)
+
+
+def scene_rcs_shared(scene, intr_phys, phys, lam):
+    """The shared-interior RCS of a scene at its initial state: ``intr_phys``
+    (K, 5) are the physical cameras' interiors, ``phys`` (n,) maps each image
+    to its physical camera."""
+    order = sort_observations(scene.obs_cam, scene.obs_pt)
+    oc, op, uv = scene.obs_cam[order], scene.obs_pt[order], scene.obs_uv[order]
+    phys = np.asarray(phys)
+    e, Jc, Jp = jacobians_intr(scene.cams0, intr_phys[phys], scene.pts0, oc, op, uv)
+    return rcs_shared(e, Jc, Jp, oc, op, phys, len(intr_phys), scene.n_pts, lam)

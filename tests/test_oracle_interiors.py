@@ -188,3 +188,88 @@ def test_variable_bsmc_bytes():
     U = I.VBSMC(rp, col, np.full(n, 11), [np.zeros((11, 11))] * len(col))
     alpha = (2 * len(col) - n) / n ** 2
     assert I.vbsmc_bytes(U) == pytest.approx(O.bsmc_bytes(alpha, n, 11), rel=1e-12)
+
+
+# ------------------------------------------------ interiors shared by the images of a physical camera
+
+def _retract_shared(cams, intr_phys, pts, dx, phys):
+    """Camera-frame pose update per image, additive interiors per physical
+    camera (every image of it moves with them), additive points."""
+    n, K = len(cams), len(intr_phys)
+    dxc = dx[:6 * n].reshape(n, 6)
+    dR = Rotation.from_rotvec(dxc[:, :3])
+    R = dR * Rotation.from_rotvec(cams[:, :3])
+    c2 = np.concatenate([R.as_rotvec(), dR.apply(cams[:, 3:]) + dxc[:, 3:]], 1)
+    k2 = intr_phys + dx[6 * n:6 * n + 5 * K].reshape(K, 5)
+    return c2, k2[phys], pts + dx[6 * n + 5 * K:].reshape(-1, 3)
+
+
+def _dense_j_shared(e, Jc, Jp, oc, op, phys, K, P):
+    n = len(phys)
+    J = np.zeros((2 * len(e), 6 * n + 5 * K + 3 * P))
+    for a in range(len(e)):
+        i, k = oc[a], op[a]
+        J[2 * a:2 * a + 2, 6 * i:6 * i + 6] = Jc[a][:, :6]
+        J[2 * a:2 * a + 2, 6 * n + 5 * phys[i]:6 * n + 5 * phys[i] + 5] = Jc[a][:, 6:11]
+        J[2 * a:2 * a + 2, 6 * n + 5 * K + 3 * k:6 * n + 5 * K + 3 * k + 3] = Jp[a]
+    return J, 6 * n + 5 * K
+
+
+@pytest.mark.parametrize("seed,phys,lam", [(41, [0, 0, 1, 1, 0, 1], 1e-3), (42, [2, 0, 1, 2, 0, 1], 0.1),
+                                           (43, [0, 0, 0, 0, 0, 0], 1e-4)])
+def test_shared_interiors_rcs_equals_dense_schur(seed, phys, lam):
+    s = scenes.tiny_scene(n_cams=6, n_pts=40, seed=seed, sigma_px=2.0)
+    phys = np.array(phys)
+    K = phys.max() + 1
+    intr = scenes.interiors0(K, seed=seed, k_sd=0.05)
+    A, b = I.scene_rcs_shared(s, intr, phys, lam)
+    assert list(A.cdim) == [6] * s.n_cams + [5] * K
+    oc, op, uv = _sorted(s)
+    e, Jc, Jp = I.jacobians_intr(s.cams0, intr[phys], s.pts0, oc, op, uv)
+    J, c = _dense_j_shared(e, Jc, Jp, oc, op, phys, K, s.n_pts)
+    Sd, bd = _dense_schur(J, e.reshape(-1), c, lam)
+    D = I.vbsmc_to_dense(A)
+    assert np.abs(D - Sd).max() <= 1e-12 * np.abs(Sd).max()
+    assert np.abs(b - bd).max() <= 1e-12 * np.abs(bd).max()
+    r = I.vb_pcg(A, b, 1e-12)
+    y = np.linalg.solve(D, b)
+    assert np.linalg.norm(r.y - y) <= 1e-7 * np.linalg.norm(y)
+
+
+def test_shared_interiors_rcs_equals_dense_schur_of_fd_jacobian():
+    """Independent of the analytic Jacobian: shared interiors moved together."""
+    s = scenes.tiny_scene(n_cams=4, n_pts=15, seed=44, sigma_px=2.0)
+    phys = np.array([0, 1, 0, 1])
+    intr = scenes.interiors0(2, seed=44, k_sd=0.05)
+    lam = 1e-2
+    oc, op, uv = _sorted(s)
+    N = 6 * s.n_cams + 5 * 2 + 3 * s.n_pts
+    h = 1e-6
+    Jfd = np.zeros((2 * len(oc), N))
+    for k in range(N):
+        d = np.zeros(N)
+        d[k] = h
+        cp, kp, pp = _retract_shared(s.cams0, intr, s.pts0, d, phys)
+        cm, km, pm = _retract_shared(s.cams0, intr, s.pts0, -d, phys)
+        Jfd[:, k] = ((_project(cp, kp, pp, oc, op) - _project(cm, km, pm, oc, op)) / (2 * h)).reshape(-1)
+    e = (_project(s.cams0, intr[phys], s.pts0, oc, op) - uv).reshape(-1)
+    Sd, bd = _dense_schur(Jfd, e, 6 * s.n_cams + 10, lam)
+    A, b = I.scene_rcs_shared(s, intr, phys, lam)
+    assert np.abs(I.vbsmc_to_dense(A) - Sd).max() <= 1e-6 * np.abs(Sd).max()
+    assert np.abs(b - bd).max() <= 1e-6 * np.abs(bd).max()
+
+
+def test_one_physical_camera_per_image_is_the_per_image_rcs():
+    """With a physical camera per image the shared layout is the c_i = 11
+    layout with its unknowns reordered (exteriors first, then interiors)."""
+    s = scenes.tiny_scene(n_cams=5, n_pts=30, seed=45, sigma_px=1.0)
+    n = s.n_cams
+    intr = scenes.interiors0(n, seed=45, k_sd=0.05)
+    A, b = I.scene_rcs_shared(s, intr, np.arange(n), 1e-3)
+    A11, b11 = I.scene_rcs_vb(s, intr, np.full(n, 11), 1e-3)
+    perm = np.concatenate([np.arange(11 * i, 11 * i + 6) for i in range(n)] +
+                          [np.arange(11 * i + 6, 11 * i + 11) for i in range(n)])
+    D11 = I.vbsmc_to_dense(A11)
+    D = I.vbsmc_to_dense(A)
+    assert np.abs(D - D11[np.ix_(perm, perm)]).max() <= 1e-12 * np.abs(D11).max()
+    assert np.abs(b - b11[perm]).max() <= 1e-12 * np.abs(b11).max()
