@@ -259,3 +259,28 @@ def test_aerial_pattern_with_interiors(B):
             assert rel <= 1e-8
             assert np.linalg.norm(b - I.vbsmc_spmv(A, y)) <= 2e-8 * np.linalg.norm(b)
         g.close()
+
+
+def test_shared_interior_system(B):
+    """Interiors shared by the images of a physical camera (three physical
+    cameras over 40 images): image rows of 6 unknowns and physical-camera
+    rows of 5, the latter coupled to every image they serve.  The oracle's
+    system through ba_vbsmc_create: the product against the oracle's, and a
+    solve whose true residual the oracle's product checks."""
+    import torch
+    s = scenes.aerial_small(n_along=8, n_across=5, pts_per_cam=40, seed=4620)
+    phys = np.arange(s.n_cams) % 3
+    intr = scenes.interiors0(3, seed=4621)
+    A, b = I.scene_rcs_shared(s, intr, phys, 1e-3)
+    g = B.VBSMC(A.cdim, A.row_ptr, A.col, _packed(A), b, precision=B.BA_FP64)
+    x = np.random.default_rng(4622).standard_normal(len(b))
+    xt = torch.tensor(x, device="cuda")
+    yt = torch.empty_like(xt)
+    g.spmv(xt, yt)
+    torch.cuda.synchronize()
+    err = np.abs(yt.cpu().numpy() - I.vbsmc_spmv(A, x)) / _abs_product(A, x)
+    assert err.max() <= 1e-12
+    y, it, rel, _, _ = g.solve(1e-8)
+    assert rel <= 1e-8
+    assert np.linalg.norm(b - I.vbsmc_spmv(A, y)) <= 1e-6 * np.linalg.norm(b)
+    g.close()
