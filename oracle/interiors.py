@@ -20,7 +20,9 @@ their interiors, so that the RCS has blocks of mixed sizes:
   height and width per block);
 * the PCG of Sec. 3.2 on it (``ba_oracle.pcg`` with these products);
 * interiors shared by the images of one physical camera: a block row of five
-  unknowns per physical camera beside the images' six-unknown rows.
+  unknowns per physical camera beside the images' six-unknown rows;
+* the back-substitution of Eq. 5 and one LM iteration with interiors (the
+  gain ratio and damping schedule of ``ba_oracle.Problem.step``).
 
 Readings of what the paper leaves open:
 
@@ -42,7 +44,7 @@ import dataclasses
 
 import numpy as np
 
-from .ba_oracle import DAMP_MAX, DAMP_MIN, camera_points, hat, pcg, sort_observations, tracks
+from .ba_oracle import DAMP_MAX, DAMP_MIN, apply_update, camera_points, hat, pcg, sort_observations, tracks
 
 N_EXT = 6
 N_INT = 5
@@ -336,3 +338,72 @@ def scene_rcs_shared(scene, intr_phys, phys, lam):
     phys = np.asarray(phys)
     e, Jc, Jp = jacobians_intr(scene.cams0, intr_phys[phys], scene.pts0, oc, op, uv)
     return rcs_shared(e, Jc, Jp, oc, op, phys, len(intr_phys), scene.n_pts, lam)
+
+
+# ----------------------------------------------------------------------------
+# Eq. 5 and one LM iteration with per-camera interiors
+# ----------------------------------------------------------------------------
+
+def back_substitute_vb(e, Jc, Jp, obs_cam, obs_pt, cdim, P, lam, dxc):
+    """Eq. 5 with c_i unknowns per camera: V_k dx_p,k = l_p,k - sum_a
+    W_a^T dx_c,cam(a), W_a = J_c,a^T J_p,a over the camera's c_i columns.
+    ``dxc`` is one vector in camera order; returns (P, 3)."""
+    off = np.concatenate([[0], np.cumsum(cdim)])
+    V = np.zeros((P, 3, 3))
+    rhs = np.zeros((P, 3))
+    for a in range(len(e)):
+        i, k = obs_cam[a], obs_pt[a]
+        Ja = Jc[a][:, :cdim[i]]
+        V[k] += Jp[a].T @ Jp[a]
+        rhs[k] -= Jp[a].T @ e[a] + (Ja.T @ Jp[a]).T @ dxc[off[i]:off[i + 1]]
+    for k in range(P):
+        V[k] = V[k] + lam * np.diag(_damp(np.diag(V[k])))
+    return np.linalg.solve(V, rhs[..., None])[..., 0]
+
+
+@dataclasses.dataclass
+class LMStateVB:
+    cams: np.ndarray
+    intr: np.ndarray
+    pts: np.ndarray
+    lam: float = 1e-4
+    nu: float = 2.0
+
+
+def cost_intr(cams, intr, pts, obs_cam, obs_pt, obs_uv):
+    e = residuals_intr(cams, intr, pts, obs_cam, obs_pt, obs_uv)
+    return 0.5 * float(np.sum(e * e))
+
+
+def lm_step_vb(st: LMStateVB, obs_cam, obs_pt, obs_uv, cdim, P, tol=1e-10):
+    """One LM iteration with interiors: linearize, the variable-size RCS,
+    block-Jacobi PCG, Eq. 5, the update (the pose as in ``apply_update``,
+    interiors and points additively), the gain ratio against the model
+    decrease 1/2 (||e||^2 - ||e + J dx||^2) and Nielsen's damping rule.
+    Observations sorted by (point, camera).  Returns (new state, accepted,
+    cost before, cost after, (dxc, dxp))."""
+    cdim = np.asarray(cdim)
+    off = np.concatenate([[0], np.cumsum(cdim)])
+    F0 = cost_intr(st.cams, st.intr, st.pts, obs_cam, obs_pt, obs_uv)
+    e, Jc, Jp = jacobians_intr(st.cams, st.intr, st.pts, obs_cam, obs_pt, obs_uv)
+    A, b = rcs_vb(e, Jc, Jp, obs_cam, obs_pt, cdim, P, st.lam)
+    dxc = vb_pcg(A, b, tol).y
+    dxp = back_substitute_vb(e, Jc, Jp, obs_cam, obs_pt, cdim, P, st.lam, dxc)
+    n = len(cdim)
+    ext = np.stack([dxc[off[i]:off[i] + N_EXT] for i in range(n)])
+    cams1, pts1 = apply_update(st.cams, st.pts, ext, dxp)
+    intr1 = st.intr.copy()
+    for i in range(n):
+        if cdim[i] == C_MAX:
+            intr1[i] += dxc[off[i] + N_EXT:off[i + 1]]
+    F1 = cost_intr(cams1, intr1, pts1, obs_cam, obs_pt, obs_uv)
+    Jd = np.stack([Jc[a][:, :cdim[obs_cam[a]]] @ dxc[off[obs_cam[a]]:off[obs_cam[a] + 1]] for a in range(len(e))])
+    Jd = Jd + np.einsum("mij,mj->mi", Jp, dxp[obs_pt])
+    pred = 0.5 * float(np.sum(e * e) - np.sum((e + Jd) ** 2))
+    rho = (F0 - F1) / pred if pred > 0 else -np.inf
+    ok = bool(pred > 0 and rho > 1e-3 and np.isfinite(F1))
+    if ok:
+        new = LMStateVB(cams1, intr1, pts1, st.lam * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3), 2.0)
+    else:
+        new = LMStateVB(st.cams, st.intr, st.pts, st.lam * st.nu, st.nu * 2.0)
+    return new, ok, F0, (F1 if ok else F0), (dxc, dxp)

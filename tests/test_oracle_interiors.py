@@ -273,3 +273,49 @@ def test_one_physical_camera_per_image_is_the_per_image_rcs():
     D = I.vbsmc_to_dense(A)
     assert np.abs(D - D11[np.ix_(perm, perm)]).max() <= 1e-12 * np.abs(D11).max()
     assert np.abs(b - b11[perm]).max() <= 1e-12 * np.abs(b11).max()
+
+
+# ------------------------------------------------ Eq. 5 and the LM iteration with interiors
+
+def test_schur_step_equals_the_dense_normal_equations():
+    """The variable-size RCS, PCG and Eq. 5 give the solution of Eq. 1 built
+    densely (camera, interior and point unknowns together)."""
+    s = scenes.tiny_scene(n_cams=6, n_pts=40, seed=46, sigma_px=2.0)
+    intr = scenes.interiors0(s.n_cams, seed=46, k_sd=0.05)
+    cdim = np.array([11, 6, 11, 6, 11, 11])
+    lam = 1e-2
+    oc, op, uv = _sorted(s)
+    e, Jc, Jp = I.jacobians_intr(s.cams0, intr, s.pts0, oc, op, uv)
+    A, b = I.rcs_vb(e, Jc, Jp, oc, op, cdim, s.n_pts, lam)
+    dxc = I.vb_pcg(A, b, 1e-13).y
+    dxp = I.back_substitute_vb(e, Jc, Jp, oc, op, cdim, s.n_pts, lam, dxc)
+    J, c = _dense_j(e, Jc, Jp, oc, op, cdim, s.n_pts)
+    H = J.T @ J
+    H = H + lam * np.diag(np.clip(np.diag(H), 1e-6, 1e32))
+    dx = np.linalg.solve(H, -J.T @ e.reshape(-1))
+    assert np.linalg.norm(dxc - dx[:c]) <= 1e-8 * np.linalg.norm(dx[:c])
+    assert np.linalg.norm(dxp.reshape(-1) - dx[c:]) <= 1e-8 * np.linalg.norm(dx[c:])
+
+
+def test_lm_with_interiors_recovers_a_noise_free_scene():
+    """Noise-free observations made with the plain pinhole; poses, points and
+    the interiors of the self-calibrating cameras start perturbed.  Accepted
+    steps lower the cost, and LM drives it to rounding level."""
+    s = scenes.tiny_scene(n_cams=6, n_pts=60, seed=47, sigma_px=0.0, track=(3, 5))
+    n = s.n_cams
+    cdim = np.array([11, 6, 11, 6, 11, 6])
+    pin = np.tile([O.Intrinsics.f, O.Intrinsics.cx, O.Intrinsics.cy, 0.0, 0.0], (n, 1))
+    intr0 = pin.copy()
+    intr0[cdim == 11] = scenes.interiors0(n, seed=47, f_sd=0.002, c_sd=0.5, k_sd=0.002)[cdim == 11]
+    oc, op, uv = _sorted(s)
+    st = I.LMStateVB(s.cams0.copy(), intr0, s.pts0.copy())
+    F_start = I.cost_intr(st.cams, st.intr, st.pts, oc, op, uv)
+    last = F_start
+    for _ in range(30):
+        st, ok, F0, F1, _ = I.lm_step_vb(st, oc, op, uv, cdim, s.n_pts)
+        if ok:
+            assert F1 < F0
+        last = F1
+    assert last <= 1e-12 * F_start, (F_start, last)
+    # the fixed cameras kept the pinhole they were given
+    assert np.array_equal(st.intr[cdim == 6], pin[cdim == 6])
