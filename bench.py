@@ -13,7 +13,11 @@ timed steps are LM iterations 1..K from the initial state (the state is reset
 after the warm-up).  ``value`` is K / device time with all inputs resident in
 HBM; ``e2e`` is the same metric with each step's state copied in from host
 memory and the result copied back.  ``roofline`` is for the dominant kernel
-(RCS formation), from CUDA events the library records around each launch.
+(the PCG), ``rcs_assembly`` for the RCS formation, both from CUDA events the
+library records around each launch.  After the timed steps, untimed: the
+storage formats' products (``spmv_formats``), the variable-size BSMC at
+c = 11 (``vbsmc``), triangulation, the solver comparison (``solver``) and the
+oracle's rate and phase times on the host (``cpu_baseline``).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores (bounded
 samples of the same workload, scaled to the full observation count).
