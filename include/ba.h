@@ -23,6 +23,8 @@
  * storage comparison (ba_rcs_spmv), a given BSMC system can be solved alone
  * (ba_problem_create_rcs, ba_pcg_solve_static), and a learned correction of
  * the block-Jacobi preconditioner can be attached (ba_precond_net_*).
+ * Cameras that also carry interior parameters give RCS blocks of mixed sizes
+ * (Sec. 4): those systems are declared in ba_vbsmc.h.
  */
 #ifndef BA_H
 #define BA_H
