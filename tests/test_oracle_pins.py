@@ -450,3 +450,57 @@ def test_triangulation_is_the_least_squares_optimum():
                               intr.f * Xc[:, 1] / Xc[:, 2] + intr.cy], 1) - s.obs_uv[a]).reshape(-1)
         ref = least_squares(res, s.pts_gt[k] + 0.5, xtol=1e-14, ftol=1e-14, gtol=1e-14).x
         assert np.abs(ref - X[k]).max() <= 1e-6, (k, ref, X[k])
+
+
+# ----------------------------------------------------------------- sampled RCS blocks
+
+def test_sampled_rcs_blocks_equal_the_full_rcs():
+    """rcs_blocks_sampled (Eq. 4 on the sub-problem of the points that reach
+    the requested blocks) against the full block-assembled RCS, for every
+    stored block of a small aerial scene: the diagonal blocks (whose U_ii and
+    damping need every observation of camera i), the off-diagonal blocks and
+    b.  A sub-problem that dropped any point or observation a block depends
+    on changes that block."""
+    s = scenes.aerial_small(n_along=5, n_across=4, pts_per_cam=40, seed=2301)
+    lam = 3e-3
+    pb = _problem(s)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    _, A, b = pb.rcs(e, Jc, Jp, lam)
+    b = b.reshape(-1, 6)
+    pairs = [(i, int(A.col[k])) for i in range(A.n) for k in range(A.row_ptr[i], A.row_ptr[i + 1])]
+    scale = np.abs(A.val).max()
+    # one request per block, so that no block borrows points another request kept
+    for k, (i, j) in enumerate(pairs):
+        S_s, b_s = O.rcs_blocks_sampled(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics(), lam,
+                                        [(i, j)])
+        assert np.abs(S_s[(i, j)] - A.val[k]).max() <= 1e-12 * scale, (i, j)
+        if i == j:
+            assert np.abs(b_s[i] - b[i]).max() <= 1e-12 * np.abs(b).max(), i
+        else:
+            assert not b_s
+
+
+@pytest.mark.parametrize("delta", [None, 2.0])
+def test_sampled_rcs_blocks_equal_dense_schur(delta):
+    """The same function against the dense Schur complement of the dense
+    damped J^T J (Eq. 1, Eq. 4), for a handful of requested blocks at a time
+    (each request builds its own sub-problem)."""
+    s = scenes.tiny_scene(n_cams=6, n_pts=40, seed=17, sigma_px=3.0)
+    pb = _problem(s, delta=delta)
+    lam = 1e-2
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    m, n, P = len(e), s.n_cams, s.n_pts
+    J = np.zeros((2 * m, 6 * n + 3 * P))
+    for a in range(m):
+        i, k = pb.obs_cam[a], pb.obs_pt[a]
+        J[2 * a:2 * a + 2, 6 * i:6 * i + 6] = Jc[a]
+        J[2 * a:2 * a + 2, 6 * n + 3 * k:6 * n + 3 * k + 3] = Jp[a]
+    Sd, bd, _, _ = _dense_rcs(J, e.reshape(-1), n, lam)
+    for pairs in ([(0, 0)], [(1, 3)], [(2, 2), (2, 5), (4, 4)]):
+        S_s, b_s = O.rcs_blocks_sampled(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, O.Intrinsics(), lam,
+                                        pairs, delta=delta)
+        for (i, j) in pairs:
+            ref = Sd[6 * i:6 * i + 6, 6 * j:6 * j + 6]
+            assert np.abs(S_s[(i, j)] - ref).max() <= 1e-11 * np.abs(Sd).max(), (pairs, i, j)
+        for i, bi in b_s.items():
+            assert np.abs(bi - bd[6 * i:6 * i + 6]).max() <= 1e-11 * np.abs(bd).max()
