@@ -46,16 +46,31 @@ std::mutex g_mu;
 unsigned char *g_ptr[kMaxDevices] = {};
 
 // Block-Jacobi: M_i^-1 = inverse of the first (diagonal) block of row i.
-__global__ void k_static_minv(int n, const int *__restrict__ row_ptr, const float *__restrict__ val,
-                              float *__restrict__ Minv, StaticScalars *sc) {
+// Row i is checked first: its blocks lie in [0, nnzb), the first is the
+// diagonal block and the other columns ascend above i (the upper-triangle
+// layout).  A malformed row - for instance one of a matrix stored with both
+// triangles, which the two-sided product would count twice - sets
+// BA_ERR_INVALID_ARG; a diagonal block that is not SPD sets BA_ERR_NOT_SPD.
+// Either error stops the solve before its first iteration.
+__global__ void k_static_minv(int n, int64_t nnzb, const int *__restrict__ row_ptr, const int *__restrict__ col,
+                              const float *__restrict__ val, float *__restrict__ Minv, StaticScalars *sc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double A[36], Ai[36];
-    const float *d = val + (int64_t)row_ptr[i] * BW;
+    const int rs = row_ptr[i], re = row_ptr[i + 1];
+    bool ok = rs >= 0 && re > rs && (int64_t)re <= nnzb && (i + 1 < n || (int64_t)re == nnzb) && col[rs] == i;
+    for (int k = rs + 1; ok && k < re; ++k) ok = col[k] > col[k - 1] && col[k] < n;
+    if (!ok) {
+        atomicExch(&sc->err, (int)BA_ERR_INVALID_ARG);
+#pragma unroll
+        for (int q = 0; q < 36; ++q) Minv[36 * (int64_t)i + q] = 0.f;
+        return;
+    }
+    const float *d = val + (int64_t)rs * BW;
 #pragma unroll
     for (int q = 0; q < 36; ++q) A[q] = d[q];
     if (!spd_inverse6<double>(A, Ai)) {
-        atomicExch(&sc->err, (int)BA_ERR_NOT_SPD);
+        atomicCAS(&sc->err, 0, (int)BA_ERR_NOT_SPD);
 #pragma unroll
         for (int q = 0; q < 36; ++q) Ai[q] = 0.0;
     }
@@ -106,7 +121,8 @@ __global__ void k_static_init(int n, const float *__restrict__ b, float *x, floa
         sc->iters = 0;
         sc->tol2 = tol2;
         sc->max_iters = max_iters;
-        sc->done = (t[1] == 0.0 || max_iters <= 0) ? 1 : 0;
+        // a malformed row or an indefinite diagonal block ends the solve here
+        sc->done = (t[1] == 0.0 || max_iters <= 0 || sc->err != 0) ? 1 : 0;
     });
 }
 
@@ -264,7 +280,7 @@ extern "C" ba_status ba_pcg_solve_static(int32_t n, int64_t nnzb, const int32_t 
     if ((e = cudaMemsetAsync(ctr, 0, 64, st)) != cudaSuccess) return set_error(BA_ERR_CUDA, cudaGetErrorString(e));
     if ((e = cudaMemsetAsync(sc, 0, sizeof(StaticScalars), st)) != cudaSuccess)
         return set_error(BA_ERR_CUDA, cudaGetErrorString(e));
-    k_static_minv<<<(n + 127) / 128, 128, 0, st>>>(n, row_ptr, val, Minv, sc);
+    k_static_minv<<<(n + 127) / 128, 128, 0, st>>>(n, nnzb, row_ptr, col, val, Minv, sc);
     const int gv = (n + 255) / 256 < 152 * 4 ? (n + 255) / 256 : 152 * 4;
     const int gs = ((int64_t)n * 32 + 255) / 256 < 152 * 8 ? (int)(((int64_t)n * 32 + 255) / 256) : 152 * 8;
     k_static_init<<<gv, 256, 0, st>>>(n, b, x, r, z, d[0], q, Minv, sc, rel_tol * rel_tol, iters_cap, red, ctr + 0);
@@ -287,6 +303,10 @@ extern "C" ba_status ba_pcg_solve_static(int32_t n, int64_t nnzb, const int32_t 
     if (iters_out) *iters_out = hs.iters;
     const double rel = hs.rr0 > 0 ? sqrt(hs.rr / hs.rr0) : 0.0;
     if (rel_resid_out) *rel_resid_out = rel;
+    if (hs.err == BA_ERR_INVALID_ARG)
+        return set_error(BA_ERR_INVALID_ARG,
+                         "ba_pcg_solve_static: malformed BSMC pattern (row starts, diagonal block first, ascending "
+                         "upper-triangle columns)");
     if (hs.err == BA_ERR_NOT_SPD) return set_error(BA_ERR_NOT_SPD, "ba_pcg_solve_static: matrix is not positive definite");
     if (!(hs.rr <= hs.tol2 * hs.rr0)) return set_error(BA_ERR_NO_CONVERGENCE, "ba_pcg_solve_static: iteration cap reached");
     return BA_OK;
