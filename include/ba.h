@@ -46,7 +46,7 @@ typedef enum {
     BA_ERR_NONFINITE = 4,     /* NaN/Inf in an input or in a computed cost */
     BA_ERR_NOT_SPD = 5,       /* a V_k or an RCS diagonal block is not positive definite */
     BA_ERR_NO_CONVERGENCE = 6,/* PCG hit its iteration cap; the partial solution is kept */
-    BA_ERR_TIMEOUT = 7,       /* reserved: a bounded device wait gave up */
+    BA_ERR_TIMEOUT = 7,       /* a bounded device wait gave up; the problem is unusable after it */
     BA_ERR_STATE = 8,         /* call out of order, or problem unusable */
     BA_ERR_INTERNAL = 9       /* a device-side consistency check failed */
 } ba_status;
@@ -106,7 +106,8 @@ typedef struct {
     int32_t used_fallback;   /* reserved for a learned preconditioner */
     double rcs_rel_resid;    /* true ||b - S dx_c|| / ||b|| in FP64 */
     int64_t n_cheirality;    /* observations with z_cam <= 1e-6 at the trial point */
-    int64_t n_v_fp64;        /* points whose 3x3 V was factored in FP64 (FP32 mode) */
+    int64_t n_v_fp64;        /* FP32 mode: points whose 3x3 V was re-factored in FP64 in
+                                this step's RCS formation (kappa~ > 1e4) */
     float ms[8];             /* linearize, form_rcs, solve, trial cameras, back-substitution with
                                 the trial evaluation (one pass over the points), total, -, - */
 } ba_step_info;
@@ -131,6 +132,9 @@ typedef struct {
                                 Cholesky, P, e^) */
     double pcg_work_imbalance; /* profile >= 2: last split CG solve, the busiest CTA's
                                 passes + combine time over the mean CTA's (1 = balanced) */
+    int64_t n_v_fp64;        /* FP32 problems, last RCS formation: points whose damped 3x3
+                                V_k was re-factored in FP64 because its FP32 factor gave
+                                kappa~ = ||V||_F ||V^-1||_F > 1e4 */
 } ba_stats;
 
 /* Fills *o with the defaults listed above. */
@@ -232,6 +236,20 @@ ba_status ba_get_stats(const ba_problem *p, ba_stats *out);
  * the number of launches and their summed device time since the last reset. */
 ba_status ba_get_kernel_time(ba_problem *p, int32_t k, int64_t *launches, double *total_ms);
 ba_status ba_reset_kernel_times(ba_problem *p);
+
+/* Test hook for the bounded device waits (not part of the method).  Every
+ * grid-wide wait inside the library gives up after a limit of SM clock cycles
+ * (about 2 s), sets an error word the host reads, and leaves its kernel, so
+ * that a stalled wait ends as a status instead of a hung GPU.  This call arms
+ * the next PCG launch of p (the split CG of FP32 solves or the Sec. 3.2
+ * recurrence) to start its all-reduce arrival counters one arrival short of
+ * their targets and to wait at most limit_cycles (1 .. 4e9) cycles: the first
+ * all-reduce then runs out on every CTA, the kernel leaves after its copies
+ * in flight have landed, and the solve returns BA_ERR_TIMEOUT.  As after any
+ * BA_ERR_TIMEOUT, p is then unusable (later calls on it return BA_ERR_STATE;
+ * ba_problem_destroy still frees it) while the CUDA context and other
+ * problems are unaffected.  The arming is used up by that one launch. */
+ba_status ba_debug_arm_wait_timeout(ba_problem *p, int64_t limit_cycles);
 const char *ba_kernel_name(int32_t k); /* NULL past the last id */
 
 void ba_problem_destroy(ba_problem *p);
@@ -357,8 +375,15 @@ ba_status ba_tc_gemm(int32_t M, int32_t N, int32_t K, const float *A, int64_t a_
  * All pointers are DEVICE pointers owned by the caller: row_ptr[n+1],
  * col[nnzb] and val[nnzb x 36] are an FP32 BSMC matrix in the layout that
  * ba_get_rcs returns (upper-triangle 6x6 blocks, row-major, the full diagonal
- * block first in every row), b[n x 6] the right-hand side, x[n x 6] receives
- * the solution.  iters_out and rel_resid_out (host pointers, may be NULL)
+ * block first in every row, the other columns ascending above the row),
+ * b[n x 6] the right-hand side, x[n x 6] receives the solution.  Only the
+ * upper triangle may be stored: the product applies every off-diagonal block
+ * also as its transpose, so a matrix passed with both triangles would count
+ * them twice.  The pattern is checked on the device before the first
+ * iteration (row_ptr[n] == nnzb, the diagonal block first, ascending columns
+ * in [i, n)); a malformed one returns BA_ERR_INVALID_ARG, and a diagonal
+ * block that is not positive definite BA_ERR_NOT_SPD, both after zero
+ * iterations.  iters_out and rel_resid_out (host pointers, may be NULL)
  * receive the iteration count and the final ||r|| / ||r_0||.
  *
  * Scratch: one fixed array of about 2.2 MB in the library's device code,

@@ -79,7 +79,8 @@ class ba_stats(ctypes.Structure):
                 ("nnzb", ctypes.c_int64), ("n_groups", ctypes.c_int64), ("n_partials", ctypes.c_int64),
                 ("n_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("pcg_phase_us", ctypes.c_double * 3),
-                ("rcs_phase_us", ctypes.c_double * 3), ("pcg_work_imbalance", ctypes.c_double)]
+                ("rcs_phase_us", ctypes.c_double * 3), ("pcg_work_imbalance", ctypes.c_double),
+                ("n_v_fp64", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -112,6 +113,7 @@ SIGNATURES = [
     ("ba_get_stats", _S, [_P, ctypes.POINTER(ba_stats)]),
     ("ba_get_kernel_time", _S, [_P, ctypes.c_int32, _I64, _D]),
     ("ba_reset_kernel_times", _S, [_P]),
+    ("ba_debug_arm_wait_timeout", _S, [_P, ctypes.c_int64]),
     ("ba_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
     ("ba_problem_destroy", None, [_P]),
     ("ba_last_error", ctypes.c_char_p, []),
@@ -466,6 +468,11 @@ class Problem:
 
     def reset_kernel_times(self):
         ba_reset_kernel_times(self.h)
+
+    def arm_wait_timeout(self, limit_cycles):
+        """Test hook: the next PCG launch misses one arrival at its first
+        all-reduce and gives up after limit_cycles SM cycles (include/ba.h)."""
+        _check(lib().ba_debug_arm_wait_timeout(self.h, int(limit_cycles)))
 
 
 def ba_pcg_solve_static(n, nnzb, row_ptr, col, val, b, x, rel_tol, max_iters=0, stream=None):

@@ -1031,7 +1031,7 @@ ba_status ba_get_lm_state(const ba_problem *p, double *lambda, double *nu, doubl
 ba_status ba_get_stats(const ba_problem *p, ba_stats *o) {
     LIVE(p);
     if (!o) return fail(BA_ERR_INVALID_ARG, "null output");
-    if (p->opt.profile >= 2) {  // the device-side phase totals
+    {  // the device-side counters and phase totals
         ba_status s = sync_scalars(const_cast<ba_problem *>(p));
         if (s) return s;
     }
@@ -1049,6 +1049,15 @@ ba_status ba_get_stats(const ba_problem *p, ba_stats *o) {
     for (int k = 0; k < 3; ++k)
         o->rcs_phase_us[k] = p->sc_host->ph_rcs[3] > 0 ? p->sc_host->ph_rcs[k] / p->sc_host->ph_rcs[3] / 1e3 : 0.0;
     o->pcg_work_imbalance = p->ph_imbalance;
+    o->n_v_fp64 = p->rcs_only ? 0 : (int64_t)p->sc_host->n_v64;
+    return BA_OK;
+}
+
+ba_status ba_debug_arm_wait_timeout(ba_problem *p, int64_t limit_cycles) {
+    LIVE(p);
+    if (limit_cycles <= 0 || limit_cycles > 4000000000LL)
+        return fail(BA_ERR_INVALID_ARG, "ba_debug_arm_wait_timeout: limit_cycles must be in (0, 4e9]");
+    p->test_wait_limit = limit_cycles;
     return BA_OK;
 }
 

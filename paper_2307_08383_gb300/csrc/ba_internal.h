@@ -213,6 +213,10 @@ struct ba_problem {
     bool minv_learned = false;  // Minv holds the learned M^-1 (else block-Jacobi)
     float2 *xs = nullptr;  // x64 split in FP32 pairs (refinement residual of FP32 problems)
     unsigned *ar_bar = nullptr;  // arrival counters of the split CG's all-reduce (one per line)
+    // > 0: the next PCG launch (split or standard recurrence) starts its
+    // all-reduce counters one arrival short and waits at most this many SM
+    // cycles (ba_debug_arm_wait_timeout; a test of the timeout path)
+    long long test_wait_limit = 0;
 
     // caller-order point I/O on the device, allocated on first use: the
     // internal -> caller permutation, a P x 3 staging buffer, a flag word

@@ -994,7 +994,12 @@ static cudaError_t pcg_loop_T(ba_problem *p) {
     // enough warps for one block row each, at most what is co-resident
     int64_t want = ((int64_t)p->n * 32 + 255) / 256;
     int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)blocks_per_sm * n_sm);
-    if ((e = cudaMemsetAsync(p->counters + 14, 0, 2 * sizeof(unsigned), p->st)) != cudaSuccess) return e;
+    // armed test of the timeout path: the counter starts at -1 (one arrival short)
+    const long long test_limit = p->test_wait_limit;
+    p->test_wait_limit = 0;
+    if ((e = cudaMemsetAsync(p->counters + 14, test_limit > 0 ? 0xFF : 0, sizeof(unsigned), p->st)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(p->counters + 15, 0, sizeof(unsigned), p->st)) != cudaSuccess) return e;
     int n = p->n;
     const int *twp = p->tw_ptr;
     const int2 *twe = p->tw_ent;
@@ -1004,7 +1009,7 @@ static cudaError_t pcg_loop_T(ba_problem *p) {
     DevScalars *sc = p->sc;
     double *red = p->red;
     unsigned *bar = p->counters + 14;
-    long long limit = 4000000000LL;  // ~2 s of SM clock per barrier wait
+    long long limit = test_limit > 0 ? test_limit : 4000000000LL;  // ~2 s of SM clock per barrier wait
     void *args[] = {&n, &twp, &twe, &S, &Mi, &y, &r, &r1, &z, &d0, &d1, &q, &sc, &red, &bar, &limit};
     return cudaLaunchCooperativeKernel((const void *)k_pcg_persist<T>, dim3(grid), dim3(256), args, 0, p->st);
 }
@@ -1324,7 +1329,11 @@ cudaError_t launch_pcg_split(ba_problem *p) {
         p->dev_bytes += AR_SUB * 32 * sizeof(unsigned);
     }
     ktimer_begin(p, K_PCG_LOOP, &ev);
-    e = cudaMemsetAsync(p->ar_bar, 0, AR_SUB * 32 * sizeof(unsigned), p->st);
+    // armed test of the timeout path: every counter starts at -1, so each one
+    // ends a call one arrival short of its target and the wait runs out
+    const long long test_limit = p->test_wait_limit;
+    p->test_wait_limit = 0;
+    e = cudaMemsetAsync(p->ar_bar, test_limit > 0 ? 0xFF : 0, AR_SUB * 32 * sizeof(unsigned), p->st);
     if (e == cudaSuccess) {
         const int *cr = p->cta_rows, *twp = p->tw_ptr, *mo = p->meta_off, *hp = p->halo_ptr, *hc = p->halo_col,
                   *ob = p->own_base;
@@ -1337,7 +1346,7 @@ cudaError_t launch_pcg_split(ba_problem *p) {
         DevScalars *sc = p->sc;
         double *red = p->red;
         unsigned *bar = p->ar_bar;
-        long long limit = 4000000000LL;  // ~2 s of SM clock per wait
+        long long limit = test_limit > 0 ? test_limit : 4000000000LL;  // ~2 s of SM clock per wait
         void *args[] = {&cr, &twp, &meta, &mo, &hp, &hc, &ob, &sf, &Sh, &H, &x, &pp, &rec0, &rec1, &sc, &red, &bar,
                         &limit};
         e = cudaLaunchCooperativeKernel((const void *)k_pcg_split, dim3(p->split_grid), dim3(SPLIT_WARPS * 32), args,

@@ -493,6 +493,8 @@ cudaError_t launch_form_rcs(ba_problem *p, double lambda) {
     const size_t smem =
         2 * form_round128(form_round128((size_t)form_o_cap(p) * JW * p->esz) + (size_t)form_c_cap(p) * sizeof(uint32_t));
     const long long limit = 4000000000LL;  // ~2 s of SM clock per copy wait
+    // points re-factored in FP64 are counted per formation
+    if ((err = cudaMemsetAsync(&p->sc->n_v64, 0, sizeof(unsigned long long), p->st)) != cudaSuccess) return err;
     ktimer_begin(p, K_FORM_RCS, &ev);
     if (p->fp32)
         err = form_rcs_T<float>(p, lambda, smem, limit);

@@ -172,6 +172,42 @@ def ring_scene(n_cams=50, n_pts=2000, track=(3, 8), seed=1001, sigma_px=0.5,
                    meta={"seed": seed, "layout": "ring"})
 
 
+def short_baseline_scene(n_cams=12, n_pts=400, n_twins=3, baseline=0.05, twin_pts=60, seed=1201,
+                         sigma_px=0.5, radius=30.0, half=5.0) -> Scene:
+    """A ring scene plus ``n_twins`` twin cameras: each stands ``baseline`` m
+    beside a ring camera (along the ring's tangent, same orientation) and
+    shares ``twin_pts`` extra points with it alone.  Those points are seen
+    along two nearly parallel rays (about baseline / radius rad apart), so the
+    depth of each is poorly determined: the ill-conditioned 3x3 point blocks of
+    short-baseline image pairs.  Twin cameras are appended after the ring
+    cameras; ring camera 2 k + 1 has twin n_cams + k."""
+    base = ring_scene(n_cams=n_cams, n_pts=n_pts, seed=seed, sigma_px=0.0, radius=radius, half=half,
+                      name="short_baseline")
+    rng = np.random.default_rng(seed + 17)
+    phi = 2 * np.pi * np.arange(n_cams) / n_cams
+    centers = np.stack([radius * np.cos(phi), radius * np.sin(phi), np.zeros(n_cams)], 1)
+    Rw2c = _look_at(centers, np.zeros_like(centers), np.array([0.0, 0.0, 1.0]))
+    host = 2 * np.arange(n_twins) + 1
+    tangent = np.stack([-np.sin(phi[host]), np.cos(phi[host]), np.zeros(n_twins)], 1)
+    centers = np.concatenate([centers, centers[host] + baseline * tangent])
+    Rw2c = np.concatenate([Rw2c, Rw2c[host]])
+    pts, obs_cam, obs_pt = [base.pts_gt], [base.obs_cam], [base.obs_pt]
+    P = base.n_pts
+    for k in range(n_twins):
+        X = rng.uniform(-half, half, (twin_pts, 3))
+        pts.append(X)
+        ids = P + np.arange(twin_pts)
+        obs_cam += [np.full(twin_pts, host[k]), np.full(twin_pts, n_cams + k)]
+        obs_pt += [ids, ids]
+        P += twin_pts
+    pts = np.concatenate(pts)
+    obs_cam = np.concatenate(obs_cam)
+    obs_pt = np.concatenate(obs_pt)
+    return _finish("short_baseline", Rw2c, centers, pts, obs_cam, obs_pt, rng, sigma_px, 0.01, 0.05, 0.1,
+                   meta={"seed": seed, "layout": "ring + short-baseline twins", "baseline_m": baseline,
+                         "twin_of": {int(n_cams + k): int(host[k]) for k in range(n_twins)}})
+
+
 def tiny_scene(n_cams=5, n_pts=30, seed=7, sigma_px=0.5, track=(2, 4), **kw) -> Scene:
     """A few cameras and points, small enough for dense brute force."""
     return ring_scene(n_cams=n_cams, n_pts=n_pts, track=track, seed=seed, sigma_px=sigma_px,

@@ -3,7 +3,10 @@
 Tolerances (per-block relative Frobenius error of S, denominators guarded
 against cancellation by 1e-3 sqrt(||S_ii|| ||S_jj||)):
   FP64 mode <= 1e-10, FP32 mode <= 1e-4; the BSMC pattern is bit-exact;
-  LM: final cost within 1e-6 relative of the oracle after the same iterations.
+  LM: final cost within 1e-6 relative of the oracle after the same iterations,
+  in FP64 and in FP32 mode (FP32 runs measured on a GB300 stay within 5e-7:
+  near the minimum F is flat, so FP32 errors in the steps move it at second
+  order only).
 """
 import numpy as np
 import pytest
@@ -136,6 +139,43 @@ def test_rcs_parity(B, prec, tol, variant):
         assert st["n_groups"] > 20
 
 
+def test_ill_conditioned_points_refactor_in_fp64(B):
+    """Points seen along two nearly parallel rays (twin cameras 2 cm apart at
+    30 m, lambda = 1e-7) have damped 3x3 blocks V_k with kappa~ ~ 1e5-1e6.  In
+    FP32 mode those V_k are re-factored in FP64 (kappa~ > 1e4); the stats
+    counter shows it fired for them, and the blocks they form - the twin
+    cameras' diagonal blocks and each twin pair's off-diagonal block, made of
+    those points alone - match the FP64 oracle within the FP32 bar (1e-4).
+    An FP32 factor of V_k instead leaves a relative error of ~1e-3 per point
+    at these kappa~ (an FP32 emulation of the factor on the host measures a
+    median of 1.6e-3)."""
+    s = scenes.short_baseline_scene(baseline=0.02, seed=1201)
+    lam = 1e-7
+    g, (row_ptr, col, val, b), (A, bref) = _rcs_case(B, s, "fp32", lam)
+    assert np.array_equal(row_ptr, A.row_ptr) and np.array_equal(col, A.col)
+    # kappa~ of every damped V_k from the oracle's Jacobians
+    pb = _oracle(s)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    V = np.zeros((s.n_pts, 3, 3))
+    np.add.at(V, pb.obs_pt, np.einsum("mri,mrj->mij", Jp, Jp))
+    d = np.clip(np.einsum("kii->ki", V), 1e-6, 1e32)
+    V[:, [0, 1, 2], [0, 1, 2]] += lam * d
+    kap = np.linalg.norm(V, axis=(1, 2)) * np.linalg.norm(np.linalg.inv(V), axis=(1, 2))
+    n64 = g.stats()["n_v_fp64"]
+    assert (kap > 2e4).sum() <= n64 <= (kap > 5e3).sum(), (n64, (kap > 1e4).sum())
+    assert n64 >= 150  # the 3 x 60 twin points, give or take the threshold
+    errs = block_errors(row_ptr, col, val, A.val)
+    twin_blocks = []
+    for t, h in s.meta["twin_of"].items():
+        for (i, j) in ((h, h), (t, t), (min(h, t), max(h, t))):
+            twin_blocks.append(row_ptr[i] + int(np.searchsorted(col[row_ptr[i]:row_ptr[i + 1]], j)))
+    assert errs[twin_blocks].max() <= 1e-4, errs[twin_blocks]
+    assert errs.max() <= 1e-4, (errs.max(), np.argmax(errs))
+    # FP64 mode never takes the branch
+    g64, _, _ = _rcs_case(B, s, "fp64", lam)
+    assert g64.stats()["n_v_fp64"] == 0
+
+
 def test_rcs_is_deterministic(B):
     s = scenes.ring_scene(n_cams=16, n_pts=600, seed=44)
     g = _gpu(B, s, precision=B.BA_FP32)
@@ -254,7 +294,7 @@ def test_lm_fp32_aerial_against_fp64_oracle(B):
             assert info["accepted"] == int(ref.accepted)
     _, _, F = g.lm_state()
     Fr = pb.cost(st.cams, st.pts)
-    assert abs(F - Fr) <= 1e-5 * Fr, (F, Fr)
+    assert abs(F - Fr) <= 1e-6 * Fr, (F, Fr)
 
 
 def test_lm_huber_fp32(B):
@@ -267,7 +307,7 @@ def test_lm_huber_fp32(B):
         st, ref, _ = pb.step(st)
     _, _, F = g.lm_state()
     Fr = pb.cost(st.cams, st.pts)
-    assert abs(F - Fr) <= 1e-5 * Fr, (F, Fr)
+    assert abs(F - Fr) <= 1e-6 * Fr, (F, Fr)
 
 
 def test_blocks_scene_huber_outliers_parity(B):
@@ -297,7 +337,7 @@ def test_blocks_scene_huber_outliers_parity(B):
             assert info["accepted"] == int(ref.accepted)
     _, _, F = g.lm_state()
     Fr = pb.cost(st.cams, st.pts)
-    assert abs(F - Fr) <= 1e-5 * Fr, (F, Fr)
+    assert abs(F - Fr) <= 1e-6 * Fr, (F, Fr)
 
 
 def test_state_errors(B):

@@ -47,7 +47,9 @@ def test_forward_matches_oracle(env):
     x = N.node_features(diag, src, dst, w)
     o_ref, _ = N.forward(Wt, x, src, dst, w)
     scale = np.abs(o_ref).max()
-    assert np.abs(o - o_ref).max() <= 3e-2 * scale, np.abs(o - o_ref).max() / scale
+    # BF16 activations on the tensor cores against FP64 activations in the
+    # oracle: ~3e-3 of the output scale measured on a GB300
+    assert np.abs(o - o_ref).max() <= 1e-2 * scale, np.abs(o - o_ref).max() / scale
     m_ref, _, _ = N.precond_blocks(diag, o.astype(np.float64))  # same outputs -> M^-1 in FP32 vs FP64
     rel = np.linalg.norm((minv - m_ref).reshape(len(diag), -1), axis=1) / np.linalg.norm(m_ref.reshape(len(diag), -1), axis=1)
     assert rel.max() <= 1e-3
@@ -79,11 +81,11 @@ def test_loss_and_gradients_match_oracle(env):
     Up = N.apply_S_blocks(row_ptr, col, val, Wp)
     Sap = lambda Z: N.apply_S_blocks(row_ptr, col, val, Z)
     loss_ref, g_ref = N.loss_and_grad(Wt, diag, src, dst, w, Wp, Up, Sap)
-    assert abs(loss - loss_ref) <= 2e-2 * loss_ref, (loss, loss_ref)
+    assert abs(loss - loss_ref) <= 2e-3 * loss_ref, (loss, loss_ref)
     gd = B.unpack_params(grads)
     for name in ("Wo", "bo", "W2", "b2", "W1", "b1"):
         err = np.linalg.norm(gd[name] - g_ref[name]) / max(np.linalg.norm(g_ref[name]), 1e-30)
-        assert err <= 5e-2, (name, err)
+        assert err <= 3e-2, (name, err)  # measured up to ~9e-3 over four random nets
 
 
 def test_training_lowers_the_loss(env):
