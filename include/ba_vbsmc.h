@@ -82,6 +82,78 @@ ba_status ba_vbsmc_create_interiors(const ba_options *opt, int32_t n_cams, const
                                     const int32_t *obs_cam, const int64_t *obs_pt, const double *obs_uv,
                                     double lambda, ba_vbsmc **out);
 
+/* The reduced camera system when the images of one physical camera share
+ * its interiors: images 0 .. n_images-1 keep their six exterior unknowns
+ * (blocks of size 6), and physical camera q becomes block n_images + q with
+ * its five interior unknowns [f, cx, cy, k1, k2] (block size 5).  phys[i]
+ * (0 .. n_phys-1) names image i's physical camera, intr_phys[n_phys x 5] the
+ * physical cameras' interiors (camera model as for
+ * ba_vbsmc_create_interiors); cams, pts and the observations as there.
+ * Per observation of image i, the exterior columns of J_c belong to block i
+ * and the interior columns to block n_images + phys[i].  Eq. 3 per block:
+ * U = sum J_s^T J_t over the two column groups s, t of each observation
+ * (which couples image i to its physical camera), damped with lambda times
+ * its clamped diagonal on the diagonal blocks; l = -sum J_s^T e.  Eq. 4 per
+ * point k: W_beta = sum of J_s^T J_p over the point's observations with
+ * columns in block beta, S(beta, gamma) -= W_beta V_k^-1 W_gamma^T and
+ * b_beta -= W_beta V_k^-1 l_p,k.  The pattern is every diagonal block plus
+ * each (beta < gamma) that one point's observations reach.  Formed on the
+ * device in FP64 (one warp per block over its list of column-group pairs; no
+ * atomics), stored in opt->precision, M^-1 built as by ba_vbsmc_create.
+ * Temporary device buffers as for ba_vbsmc_create_interiors.  Errors:
+ * BA_ERR_INVALID_ARG (sizes, indices, phys, lambda), BA_ERR_NONFINITE,
+ * BA_ERR_NOT_SPD, BA_ERR_OOM, BA_ERR_CUDA. */
+ba_status ba_vbsmc_create_shared(const ba_options *opt, int32_t n_images, const double *cams, int32_t n_phys,
+                                 const double *intr_phys, const int32_t *phys, int64_t n_pts, const double *pts,
+                                 int64_t n_obs, const int32_t *obs_cam, const int64_t *obs_pt, const double *obs_uv,
+                                 double lambda, ba_vbsmc **out);
+
+/* ---- The LM iteration with interior parameters --------------------------
+ * An LM problem whose cameras carry interiors (camera model, cdim and
+ * observation rules as for ba_vbsmc_create_interiors): cameras with cdim 11
+ * estimate their five interiors, those with cdim 6 hold them fixed.  One
+ * ba_vbi_lm_step is the iteration of ba_lm_step with c_i unknowns per
+ * camera (Fig. 2; Eq. 1 by Eqs. 3-5): linearize (FP64 rows of e and J with
+ * 11 camera columns) if the state changed, form the variable-size RCS with
+ * lambda (Eq. 3-4, as ba_vbsmc_create_interiors), solve it by block-Jacobi
+ * PCG (Sec. 3.2; stop at pcg_rel_tol, cap pcg_max_iters or max(1000, 6n)),
+ * back-substitute the points (Eq. 5: dx_p = V^-1 (l_p - sum W^T dx_c)), move
+ * to the trial state (pose X_cam <- Exp(d_omega) X_cam + dt, interiors and
+ * points additively), evaluate its cost and the model decrease
+ * 1/2 (||e||^2 - ||e + J dx||^2) in FP64, and accept if the gain ratio
+ * exceeds 1e-3 (Nielsen's damping rule, lambda starting at opt->lambda0).
+ * On a rejection only lambda changes: the next step re-forms the RCS from
+ * the stored linearization.  opt->precision BA_FP32 stores the RCS and runs
+ * the PCG in FP32 (formation, Eq. 5 and the trial evaluation stay FP64);
+ * BA_FP64 runs everything in FP64.  Other options: lambda0, pcg_rel_tol,
+ * pcg_max_iters, cuda_stream, device_mem_cap.  ba_step_info: cost_before,
+ * cost_after, cost_trial, predicted, rho, lambda, accepted, pcg_iters,
+ * rcs_rel_resid (the PCG recurrence's ||r|| / ||r_0||), n_cheirality and
+ * ms[0..5] = linearize, RCS formation with M^-1, PCG, Eq. 5 and the trial
+ * cameras, trial evaluation, total.  States are in the caller's order
+ * (cams n x 6, intr n x 5, pts n_pts x 3).  After BA_ERR_CUDA or
+ * BA_ERR_TIMEOUT the problem only accepts ba_vbi_problem_destroy. */
+typedef struct ba_vbi_problem ba_vbi_problem;
+
+ba_status ba_vbi_problem_create(const ba_options *opt, int32_t n_cams, const double *cams, const double *intr,
+                                const int32_t *cdim, int64_t n_pts, const double *pts, int64_t n_obs,
+                                const int32_t *obs_cam, const int64_t *obs_pt, const double *obs_uv,
+                                ba_vbi_problem **out);
+ba_status ba_vbi_lm_step(ba_vbi_problem *p, ba_step_info *info);
+ba_status ba_vbi_get_state(const ba_vbi_problem *p, double *cams, double *intr, double *pts);
+ba_status ba_vbi_set_state(ba_vbi_problem *p, const double *cams, const double *intr, const double *pts,
+                           double lambda, double nu);
+/* lambda, nu and the cost F of the current state (computed if needed). */
+ba_status ba_vbi_get_lm_state(const ba_vbi_problem *p, double *lambda, double *nu, double *cost);
+/* The last step: dxc (sum c_i values, camera order, c_i per camera), dxp
+ * (n_pts x 3); BA_ERR_STATE before the first step. */
+ba_status ba_vbi_get_step(const ba_vbi_problem *p, double *dxc, double *dxp);
+/* The variable-size system of the last formation (owned by the problem; for
+ * ba_vbsmc_get_system / ba_vbsmc_spmv / ba_vbsmc_info). */
+const ba_vbsmc *ba_vbi_system(const ba_vbi_problem *p);
+ba_status ba_vbi_info(const ba_vbi_problem *p, int64_t *n_unknowns, int64_t *n_blocks, int64_t *device_bytes);
+void ba_vbi_problem_destroy(ba_vbi_problem *p);
+
 /* Copies the system to host arrays (each may be NULL): row_ptr[n+1],
  * col[nnzb], the packed block values (as ba_vbsmc_create takes them,
  * upcast to double) and b.  Synchronous.  Errors: BA_ERR_INVALID_ARG,

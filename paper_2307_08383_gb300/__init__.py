@@ -133,6 +133,19 @@ SIGNATURES = [
                              ctypes.POINTER(_P)]),
     ("ba_vbsmc_create_interiors", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _D, _D, _I32, ctypes.c_int64, _D,
                                        ctypes.c_int64, _I32, _I64, _D, ctypes.c_double, ctypes.POINTER(_P)]),
+    ("ba_vbsmc_create_shared", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _D, ctypes.c_int32, _D, _I32,
+                                    ctypes.c_int64, _D, ctypes.c_int64, _I32, _I64, _D, ctypes.c_double,
+                                    ctypes.POINTER(_P)]),
+    ("ba_vbi_problem_create", _S, [ctypes.POINTER(ba_options), ctypes.c_int32, _D, _D, _I32, ctypes.c_int64, _D,
+                                   ctypes.c_int64, _I32, _I64, _D, ctypes.POINTER(_P)]),
+    ("ba_vbi_lm_step", _S, [_P, ctypes.POINTER(ba_step_info)]),
+    ("ba_vbi_get_state", _S, [_P, _D, _D, _D]),
+    ("ba_vbi_set_state", _S, [_P, _D, _D, _D, ctypes.c_double, ctypes.c_double]),
+    ("ba_vbi_get_lm_state", _S, [_P, _D, _D, _D]),
+    ("ba_vbi_get_step", _S, [_P, _D, _D]),
+    ("ba_vbi_system", _P, [_P]),
+    ("ba_vbi_info", _S, [_P, _I64, _I64, _I64]),
+    ("ba_vbi_problem_destroy", None, [_P]),
     ("ba_vbsmc_get_system", _S, [_P, _I32, _I32, _D, _D]),
     ("ba_vbsmc_spmv", _S, [_P, _P, _P]),
     ("ba_vbsmc_solve", _S, [_P, ctypes.c_double, ctypes.c_int32, _D, _I32, _D, _D]),
@@ -647,6 +660,48 @@ class VBSMC:
         self.n = n
         return self
 
+    @classmethod
+    def from_shared(cls, cams, intr_phys, phys, pts, obs_cam, obs_pt, obs_uv, lam, stream="current", **opts):
+        """The RCS when the images of each physical camera share its interiors
+        [f, cx, cy, k1, k2]: n image blocks of six unknowns, then one block of
+        five per physical camera (ba_vbsmc_create_shared)."""
+        if stream == "current":
+            stream = _default_stream()
+        self = cls.__new__(cls)
+        self.opts = ba_options_default(cuda_stream=stream, **opts)
+        n = len(cams)
+        K = len(intr_phys)
+        cams = _f64(cams, (n, 6))
+        intr_phys = _f64(intr_phys, (K, 5))
+        phys = np.ascontiguousarray(phys, dtype=np.int32)
+        pts = np.ascontiguousarray(pts, dtype=np.float64)
+        P = len(pts)
+        pts = _f64(pts, (P, 3))
+        obs_cam = np.ascontiguousarray(obs_cam, dtype=np.int32)
+        obs_pt = np.ascontiguousarray(obs_pt, dtype=np.int64)
+        m = len(obs_cam)
+        obs_uv = _f64(obs_uv, (m, 2))
+        if len(phys) != n or len(obs_pt) != m:
+            raise BAError(BA_ERR_INVALID_ARG, "array lengths disagree")
+        self.cdim = np.array([6] * n + [5] * K, dtype=np.int32)
+        h = _P()
+        _check(lib().ba_vbsmc_create_shared(ctypes.byref(self.opts), n, _dp(cams), K, _dp(intr_phys),
+                                            phys.ctypes.data_as(_I32), P, _dp(pts), m, obs_cam.ctypes.data_as(_I32),
+                                            obs_pt.ctypes.data_as(_I64), _dp(obs_uv), float(lam), ctypes.byref(h)))
+        self.h = h
+        self.n = n + K
+        return self
+
+    @classmethod
+    def borrowed(cls, h, cdim):
+        """A view of a system owned by another object (not destroyed here)."""
+        self = cls.__new__(cls)
+        self.h = h
+        self.cdim = np.ascontiguousarray(cdim, dtype=np.int32)
+        self.n = len(self.cdim)
+        self._borrowed = True
+        return self
+
     def system(self):
         """(row_ptr, col, packed block values, b) as host arrays (float64)."""
         N = ctypes.c_int64()
@@ -688,7 +743,87 @@ class VBSMC:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().ba_vbsmc_destroy(self.h)
+            if not getattr(self, "_borrowed", False):
+                lib().ba_vbsmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class VBIProblem:
+    """An LM problem whose cameras carry interiors [f, cx, cy, k1, k2]
+    (cdim 11: estimated, 6: held fixed), on the device (include/ba_vbsmc.h,
+    ba_vbi_*).  States are in the caller's order."""
+
+    def __init__(self, cams, intr, cdim, pts, obs_cam, obs_pt, obs_uv, stream="current", **opts):
+        if stream == "current":
+            stream = _default_stream()
+        self.opts = ba_options_default(cuda_stream=stream, **opts)
+        n = len(cams)
+        self.cdim = np.ascontiguousarray(cdim, dtype=np.int32)
+        cams = _f64(cams, (n, 6))
+        intr = _f64(intr, (n, 5))
+        pts = np.ascontiguousarray(pts, dtype=np.float64)
+        P = len(pts)
+        pts = _f64(pts, (P, 3))
+        obs_cam = np.ascontiguousarray(obs_cam, dtype=np.int32)
+        obs_pt = np.ascontiguousarray(obs_pt, dtype=np.int64)
+        m = len(obs_cam)
+        obs_uv = _f64(obs_uv, (m, 2))
+        if len(self.cdim) != n or len(obs_pt) != m:
+            raise BAError(BA_ERR_INVALID_ARG, "array lengths disagree")
+        h = _P()
+        _check(lib().ba_vbi_problem_create(ctypes.byref(self.opts), n, _dp(cams), _dp(intr),
+                                           self.cdim.ctypes.data_as(_I32), P, _dp(pts), m,
+                                           obs_cam.ctypes.data_as(_I32), obs_pt.ctypes.data_as(_I64), _dp(obs_uv),
+                                           ctypes.byref(h)))
+        self.h, self.n, self.P = h, n, P
+
+    def lm_step(self):
+        info = ba_step_info()
+        _check(lib().ba_vbi_lm_step(self.h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def state(self):
+        """(cams n x 6, intr n x 5, pts P x 3)."""
+        c = np.empty((self.n, 6))
+        k = np.empty((self.n, 5))
+        x = np.empty((self.P, 3))
+        _check(lib().ba_vbi_get_state(self.h, _dp(c), _dp(k), _dp(x)))
+        return c, k, x
+
+    def set_state(self, cams, intr, pts, lam, nu):
+        _check(lib().ba_vbi_set_state(self.h, _dp(_f64(cams, (self.n, 6))), _dp(_f64(intr, (self.n, 5))),
+                                      _dp(_f64(pts, (self.P, 3))), float(lam), float(nu)))
+
+    def lm_state(self):
+        lam, nu, F = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().ba_vbi_get_lm_state(self.h, ctypes.byref(lam), ctypes.byref(nu), ctypes.byref(F)))
+        return lam.value, nu.value, F.value
+
+    def step(self):
+        """(dx_c as one vector of sum c_i values, dx_p P x 3) of the last step."""
+        dxc = np.empty(int(self.cdim.sum()))
+        dxp = np.empty((self.P, 3))
+        _check(lib().ba_vbi_get_step(self.h, _dp(dxc), _dp(dxp)))
+        return dxc, dxp
+
+    def system(self):
+        """The variable-size RCS of the last formation, as a borrowed VBSMC."""
+        return VBSMC.borrowed(lib().ba_vbi_system(self.h), self.cdim)
+
+    def info(self):
+        N, nb, by = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ba_vbi_info(self.h, ctypes.byref(N), ctypes.byref(nb), ctypes.byref(by)))
+        return {"unknowns": N.value, "blocks": nb.value, "device_bytes": by.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ba_vbi_problem_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
                                               const double *__restrict__ pts, const float *__restrict__ pts_hl,
                                               Intr in, int huber, double delta, DevScalars *sc, int trial,
                                               double *red, unsigned *ctr) {
-    RunSum<T> f;
+    RunSum<double> f;  // FP64 accumulation in both modes (each term is formed in T)
     int ncheir = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
         const int i = obs_cam[a], k = obs_pt[a];
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
         const T iz = T(1) / Xc[2];
         const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
         const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
-        f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
+        f.add((double)huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
         ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
     }
     double v[2] = {f.get(), (double)ncheir};
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *_
         mbar_expect_tx(&mbar, jb);
         bulk_g2s(smem_raw, J + (int64_t)d.obs_begin * JW, jb, &mbar);
     };
-    RunSum<T> f, mdl;
+    RunSum<double> f, mdl;  // FP64 accumulation of the gain ratio's sums (terms formed in T)
     int ncheir = 0;
     const T dl = (T)delta;
     uint32_t parity = 0u;
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *_
             const T iz = T(1) / Xc[2];
             const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
             const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
-            f.add(huber_rho<T>(e0 * e0 + e1 * e1, huber, dl));
+            f.add((double)huber_rho<T>(e0 * e0 + e1 * e1, huber, dl));
             ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
             const T *jr = pe[k];  // J_p (2 x 3), e
             T jd0 = s_jc[2 * al], jd1 = s_jc[2 * al + 1];
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *_
                 jd0 += jr[c] * s_dp[3 * pl + c];
                 jd1 += jr[3 + c] * s_dp[3 * pl + c];
             }
-            mdl.add(-(jd0 * (T(2) * jr[6] + jd0) + jd1 * (T(2) * jr[7] + jd1)));
+            mdl.add(-(double)(jd0 * (T(2) * jr[6] + jd0) + jd1 * (T(2) * jr[7] + jd1)));
         }
         // the per-point and per-observation areas are rewritten only after the
         // barrier that follows the next group's copy wait

@@ -61,6 +61,21 @@ def _fp32_tol(A):
     return np.repeat(1.5 * (t + 2) * 2.0 ** -24, np.diff(off))
 
 
+def vb_block_errors(row_ptr, col, cdim, val, A):
+    """Per-block relative Frobenius error of packed values against the oracle's
+    blocks, the denominator guarded against cancellation by
+    1e-3 sqrt(||S_ii|| ||S_jj||) (as for the six-unknown RCS)."""
+    got = _from_packed(row_ptr, col, cdim, val)
+    dn = np.array([np.linalg.norm(A.val[A.row_ptr[i]]) for i in range(A.n)])
+    errs = np.empty(len(col))
+    for i in range(A.n):
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            j = A.col[k]
+            den = max(np.linalg.norm(A.val[k]), 1e-3 * np.sqrt(dn[i] * dn[j]))
+            errs[k] = np.linalg.norm(got.val[k] - A.val[k]) / den
+    return errs
+
+
 def _abs_product(A, x):
     return I.vbsmc_spmv(I.VBSMC(A.row_ptr, A.col, A.cdim, [np.abs(v) for v in A.val]), np.abs(x))
 
@@ -86,9 +101,11 @@ def interior_system(interior_case):
 def test_device_rcs_with_interiors_matches_oracle(B, interior_case, prec):
     """ba_vbsmc_create_interiors (e, J with five interiors; Eq. 3-4 with c_i
     unknowns, formed on the device) against the oracle's RCS of the same
-    scene: the same pattern; values and b within 1e-11 of the largest |S|
-    (FP64; the same sums in another order) plus, in FP32 storage, the
-    rounding of each entry (2^-24 relative); then the solve."""
+    scene: the same pattern; FP64: values and b within 1e-11 of the largest
+    |S| (the same sums in another order); FP32 (Jacobians and formation in
+    FP32): the FP32 bar of the six-unknown RCS, 1e-4 per block (relative
+    Frobenius, guarded denominators) and 2e-3 of the largest |b|; then the
+    solve."""
     s, intr, cdim, A, b = interior_case
     fp64 = prec == "fp64"
     g = B.VBSMC.from_scene(s.cams0, intr, cdim, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, 1e-3,
@@ -97,10 +114,14 @@ def test_device_rcs_with_interiors_matches_oracle(B, interior_case, prec):
     assert np.array_equal(row_ptr, A.row_ptr) and np.array_equal(col, A.col)
     ref = _packed(A)
     scale = np.abs(ref).max()
-    rnd = 0.0 if fp64 else 1.01 * 2.0 ** -24
-    assert np.all(np.abs(val - ref) <= 1e-11 * scale + rnd * np.abs(ref)), np.abs(val - ref).max() / scale
     bs = np.abs(b).max()
-    assert np.all(np.abs(bg - b) <= 1e-11 * bs + rnd * np.abs(b)), np.abs(bg - b).max() / bs
+    if fp64:
+        assert np.all(np.abs(val - ref) <= 1e-11 * scale), np.abs(val - ref).max() / scale
+        assert np.all(np.abs(bg - b) <= 1e-11 * bs), np.abs(bg - b).max() / bs
+    else:
+        errs = vb_block_errors(row_ptr, col, cdim, val, A)
+        assert errs.max() <= 1e-4, errs.max()
+        assert np.abs(bg - b).max() <= 2e-3 * bs, np.abs(bg - b).max() / bs
     if fp64:
         x, it, rel, _, _ = g.solve(1e-10)
         y = I.vb_pcg(A, b, 1e-10)
