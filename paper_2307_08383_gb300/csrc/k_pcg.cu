@@ -536,9 +536,10 @@ __device__ __forceinline__ float next_r(float r, float w, float s, float a, floa
 
 // Balanced SpMV of the split CG with a shared-memory halo.  CTA c owns block
 // rows [rb, re) (chosen on the host for about equal work) and their entries
-// [eb, ee), cut into passes of 32 consecutive entries; warp w of the nine
-// takes passes w, w + 9, ...  The cameras the CTA's entries reference (its halo, about a
-// hundred at the benchmark size) are gathered once per iteration from the
+// [eb, ee), cut into passes of 32 consecutive entries; warp w of the
+// SPLIT_WARPS takes passes w, w + SPLIT_WARPS, ...  The cameras the CTA's
+// entries reference (its halo, a few hundred at the benchmark size, with one
+// CTA per SM) are gathered once per iteration from the
 // previous iteration's records, each transformed once into the vector the
 // SpMV applies, x_j = r_j - alpha (w_j + beta s_j), and kept in shared
 // memory.  The gather of iteration k + 1 is issued (16-byte asynchronous
@@ -547,17 +548,19 @@ __device__ __forceinline__ float next_r(float r, float w, float s, float a, floa
 // arrive, so its L2 round trip overlaps the partial reads, the block sum and
 // the scalar update.  A pass's 32 S^ blocks (4.6 KB, contiguous in entry order) and the
 // entries' packed (local row, halo index) arrive by 1-D bulk copies into one
-// of the warp's two buffers; since S^ does not change during the solve, each
-// refill fetches the warp's pass two positions ahead, wrapping into the next
-// iteration.  The pass loop thus reads shared memory only.  A segmented
+// of the warp's SPLIT_NBUF buffers; since S^ does not change during the
+// solve, each refill fetches the warp's pass SPLIT_NBUF positions ahead,
+// wrapping into the next iteration.  The pass loop thus reads shared memory only.  A segmented
 // shuffle scan over the pass (entries are sorted by row) leaves each row
 // segment's sum in its last lane, which stores it in a slot: (q, 0) if the
 // segment opens pass q, (q, 1) if it closes it, else the row's own slot.  The
 // sums depend only on the entry order: deterministic.
-constexpr int SPLIT_WARPS = 9;
+constexpr int SPLIT_WARPS = 16;
+constexpr int SPLIT_NBUF = 2;         // copy buffers (passes in flight) per warp
+constexpr int SPLIT_CTAS_PER_SM = 1;  // co-resident CTAs per SM the grid is sized for
 constexpr int PASS_S_BYTES = 32 * BW * 4;                        // 4608
 constexpr int PASS_BYTES = PASS_S_BYTES + 32 * 4;                // + packed metadata
-constexpr int SPLIT_STAGE_BYTES = SPLIT_WARPS * 2 * PASS_BYTES;  // 75776
+constexpr int SPLIT_STAGE_BYTES = SPLIT_WARPS * SPLIT_NBUF * PASS_BYTES;
 constexpr int HX = 20;  // floats per halo camera: its fetched record, then x_j written over r_j
 
 struct SplitPipe {
@@ -570,16 +573,16 @@ struct SplitPipe {
 };
 
 __device__ __forceinline__ float *pass_buf(const SplitPipe &pp, uint32_t s) {
-    return pp.stage + (size_t)(2 * (threadIdx.x >> 5) + (s & 1)) * (PASS_BYTES / 4);
+    return pp.stage + (size_t)(SPLIT_NBUF * (threadIdx.x >> 5) + s % SPLIT_NBUF) * (PASS_BYTES / 4);
 }
 
-// lane 0: refill buffer (s & 1) with the warp's pass number (s mod m)
+// lane 0: refill buffer (s mod NBUF) with the warp's pass number (s mod m)
 __device__ __forceinline__ void split_issue(const SplitPipe &pp, uint32_t s) {
     const int wid = threadIdx.x >> 5;
     const int q = wid + SPLIT_WARPS * (int)(s % (uint32_t)pp.m);
     const int cnt = min(32, pp.ee - pp.eb - 32 * q);
     const uint32_t sbytes = (uint32_t)cnt * BW * 4, mbytes = (uint32_t)((cnt + 3) & ~3) * 4;
-    uint64_t *bar = pp.mbar + 2 * wid + (s & 1);
+    uint64_t *bar = pp.mbar + SPLIT_NBUF * wid + s % SPLIT_NBUF;
     float *buf = pass_buf(pp, s);
     mbar_expect_tx(bar, sbytes + mbytes);
     bulk_g2s(buf, pp.Sh + (int64_t)(pp.eb + 32 * q) * BW, sbytes, bar);
@@ -590,7 +593,8 @@ __device__ __forceinline__ void split_issue(const SplitPipe &pp, uint32_t s) {
 __device__ __forceinline__ void split_drain(const SplitPipe &pp, long long limit) {
     if ((threadIdx.x & 31) != 0 || pp.m == 0) return;
     const int wid = threadIdx.x >> 5;
-    for (uint32_t s = pp.seq; s < pp.seq + 2; ++s) mbar_wait(pp.mbar + 2 * wid + (s & 1), (s >> 1) & 1u, limit);
+    for (uint32_t s = pp.seq; s < pp.seq + SPLIT_NBUF; ++s)
+        mbar_wait(pp.mbar + SPLIT_NBUF * wid + s % SPLIT_NBUF, (s / SPLIT_NBUF) & 1u, limit);
 }
 
 // One sweep of the warp's passes over the halo vectors hx.  False on an
@@ -604,9 +608,9 @@ __device__ __forceinline__ bool split_passes(SplitPipe &pp, int rb, const int *_
         const int q = wid + SPLIT_WARPS * k;
         const int t = eb + 32 * q + lane;
         const bool valid = t < ee;
-        const uint32_t b = pp.seq & 1;
+        const uint32_t b = pp.seq % SPLIT_NBUF;
         // every lane observes the copy's completion; the verdict is warp-uniform
-        if (!__all_sync(0xffffffffu, mbar_wait(pp.mbar + 2 * wid + b, (pp.seq >> 1) & 1u, limit))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(pp.mbar + SPLIT_NBUF * wid + b, (pp.seq / SPLIT_NBUF) & 1u, limit))) {
             if (lane == 0) atomicExch(err, (int)BA_ERR_TIMEOUT);
             return false;
         }
@@ -633,7 +637,7 @@ __device__ __forceinline__ bool split_passes(SplitPipe &pp, int rb, const int *_
             }
         }
         __syncwarp();
-        if (lane == 0) split_issue(pp, pp.seq + 2);  // this buffer is free again
+        if (lane == 0) split_issue(pp, pp.seq + SPLIT_NBUF);  // this buffer is free again
         ++pp.seq;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -723,7 +727,7 @@ __device__ __forceinline__ void split_halo_apply(int H, int ob, int R, bool firs
 // in registers across iterations).  The stop test uses the original
 // residual norm ||H r^|| (block-Jacobi: ||L r^||).  One grid all-reduce of
 // (gamma, delta, ||H r||^2) ends each phase.
-__global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__restrict__ cta_rows, const int *__restrict__ tw_ptr,
+__global__ void __launch_bounds__(SPLIT_WARPS * 32, SPLIT_CTAS_PER_SM) k_pcg_split(const int *__restrict__ cta_rows, const int *__restrict__ tw_ptr,
                                                       const uint32_t *__restrict__ tw_meta,
                                                       const int *__restrict__ meta_off,
                                                       const int *__restrict__ halo_ptr,
@@ -733,7 +737,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
                                                       float *x, float *p, float *rec0, float *rec1, DevScalars *sc,
                                                       double *red, unsigned *bar, long long limit_cycles) {
     extern __shared__ __align__(16) float sdyn[];
-    __shared__ uint64_t mbar[2 * SPLIT_WARPS];
+    __shared__ uint64_t mbar[SPLIT_NBUF * SPLIT_WARPS];
     if (sc->done) return;
     const int rb = __ldg(cta_rows + blockIdx.x), re = __ldg(cta_rows + blockIdx.x + 1);
     const int eb = __ldg(tw_ptr + rb), ee = __ldg(tw_ptr + re);
@@ -746,13 +750,11 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, 2) k_pcg_split(const int *__
     const int hj0 = (int)threadIdx.x < NH ? __ldg(halo_col + hb + threadIdx.x) : 0;
     SplitPipe pp{sdyn, mbar, Sh, tw_meta + __ldg(meta_off + blockIdx.x), eb, ee,
                  wid < P ? (P - 1 - wid) / SPLIT_WARPS + 1 : 0, 0u};
-    if (threadIdx.x < 2 * SPLIT_WARPS) mbar_init(&mbar[threadIdx.x], 1);
+    if (threadIdx.x < SPLIT_NBUF * SPLIT_WARPS) mbar_init(&mbar[threadIdx.x], 1);
     fence_proxy_async();
     __syncthreads();
-    if ((threadIdx.x & 31) == 0 && pp.m > 0) {
-        split_issue(pp, 0);
-        split_issue(pp, 1);
-    }
+    if ((threadIdx.x & 31) == 0 && pp.m > 0)
+        for (uint32_t q = 0; q < (uint32_t)SPLIT_NBUF; ++q) split_issue(pp, q);
     // this thread's first (row, component): p, x^, its row of H and the row's
     // entry range stay in registers
     const int u0 = threadIdx.x;
@@ -1215,7 +1217,7 @@ static cudaError_t split_partition(ba_problem *p) {
     int slot_floats = 0, G = 0;
     for (int attempt = 0; attempt < 4; ++attempt) {
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_pcg_split, SPLIT_WARPS * 32, smem)) != cudaSuccess) return e;
-        bps = std::min(bps, 2);
+        bps = std::min(bps, SPLIT_CTAS_PER_SM);
         if (bps < 1) return unavailable();
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * n_sm, (E + 255) / 256));
         if (g == G) break;
