@@ -331,7 +331,8 @@ def run_ours(args):
 # the stored figure no longer describes the kernel that runs, and the bench
 # line reports null instead.
 NCU_TRAFFIC = {
-    "pcg_split": {"source": "k_pcg.cu", "digest": None, "workload": "aerial5k", "bytes_per_unit": None},
+    "pcg_split": {"source": "k_pcg.cu", "digest": "a79cea617bb62c35", "workload": "aerial5k",
+                  "bytes_per_unit": (47_371_776 + 44_544) // 41},
     "form_rcs": {"source": "k_rcs.cu", "digest": None, "workload": "aerial5k", "bytes_per_unit": None},
 }
 
@@ -372,8 +373,8 @@ def formats_bench(B, torch, g, st, esz, peaks, peak_kind, stream, repeats=7):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     res = {}
-    for name, fmt in (("bsmc", B.BA_FMT_BSMC), ("bsr_full", B.BA_FMT_BSR_FULL), ("csr", B.BA_FMT_CSR),
-                      ("implicit", B.BA_FMT_IMPLICIT)):
+    for name, fmt in (("bsmc", B.BA_FMT_BSMC), ("bsmc_once", B.BA_FMT_BSMC_ONCE), ("bsr_full", B.BA_FMT_BSR_FULL),
+                      ("csr", B.BA_FMT_CSR), ("implicit", B.BA_FMT_IMPLICIT)):
         nbytes = g.rcs_spmv(fmt, x, y)  # builds the format's arrays (untimed)
         torch.cuda.synchronize()
         ts = []
@@ -790,6 +791,60 @@ def run_kernel_case(args):
     g.close()
 
 
+def run_spmv_case(args, repeats=5):
+    """A short driver for the storage-format products at a workload's RCS
+    pattern without the rest of its problem: the pattern of the workload's
+    observations (ba_symbolic_pattern, on the host), seeded SPD values
+    (off-diagonal blocks N(0, 1), dominant diagonal blocks), an RCS-only FP32
+    problem (ba_problem_create_rcs), then y = S x in BSMC, full block CSR and
+    scalar CSR, each after an L2 flush, timed with CUDA events (median of
+    repeats).  The device holds the system and the formats only (about 1.1 GB
+    at 50,000 cameras with BSMC alone, 3.5 GB with all three)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2307_08383_gb300 as B
+    import scenes
+    s = make_scene(args.workload)
+    row_ptr, col = B.ba_symbolic_pattern(s.n_cams, s.n_pts, s.obs_cam, s.obs_pt)
+    del s
+    n = len(row_ptr) - 1
+    val, _ = scenes.random_block_spd(row_ptr, col, np.full(n, 6, dtype=np.int32), seed=7)
+    b = np.random.default_rng(8).standard_normal(6 * n)
+    g = B.Problem.from_rcs(row_ptr, col, val.reshape(-1, 36), b, precision=B.BA_FP32)
+    del val
+    stream = torch.cuda.current_stream()
+    x = torch.randn(6 * n, dtype=torch.float32, device="cuda", generator=torch.Generator(device="cuda").manual_seed(9))
+    y = torch.empty_like(x)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    peaks, peak_kind = load_peaks()
+    fmts = [("bsmc", B.BA_FMT_BSMC), ("bsmc_once", B.BA_FMT_BSMC_ONCE)] + \
+        ([] if args.spmv_bsmc_only else [("bsr_full", B.BA_FMT_BSR_FULL), ("csr", B.BA_FMT_CSR)])
+    res = {}
+    for name, fmt in fmts:
+        nbytes = g.rcs_spmv(fmt, x, y)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(repeats):
+            flush.zero_()
+            e0.record(stream)
+            g.rcs_spmv(fmt, x, y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        us = 1e3 * statistics.median(ts)
+        moved = nbytes + 2 * 6 * n * 4
+        res[name] = {"us": round(us, 2), "format_bytes": int(nbytes), "achieved_gbs": round(moved / us / 1e3, 1),
+                     "frac_hbm": round(moved / us / 1e3 / peaks["hbm_gbs"], 4)}
+    print(json.dumps({"kernel_case": "spmv", "workload": args.workload, "n_cams": n, "nnzb": len(col),
+                      "peak_kind": peak_kind, "formats": res}))
+    g.close()
+
+
 def _aerial5k_obs():
     # observation count of the full aerial workload (seeded, deterministic)
     return make_scene("aerial5k").n_obs
@@ -803,9 +858,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="aerial5k",
                     choices=["aerial5k", "ring50", "aerial_small", "aerial2400", "blocks50k", "capacity"])
-    ap.add_argument("--kernel-case", default=None, choices=["form_rcs", "pcg"],
+    ap.add_argument("--kernel-case", default=None, choices=["form_rcs", "pcg", "spmv"],
                     help="profiling driver: run one kernel family a few times on the workload and exit")
     ap.add_argument("--pcg-tol", type=float, default=None, help="kernel case: PCG relative tolerance")
+    ap.add_argument("--spmv-bsmc-only", action="store_true", help="spmv kernel case: the BSMC product only")
     ap.add_argument("--pcg-variant", default=None, choices=["standard", "split", "implicit"], help="kernel case: PCG variant")
     ap.add_argument("--group-obs", type=int, default=0, help="kernel case: observations per point group")
     ap.add_argument("--no-formats", action="store_true", help="skip the RCS storage-format SpMV comparison")
@@ -817,7 +873,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.kernel_case:
+    if args.kernel_case == "spmv":
+        run_spmv_case(args)
+    elif args.kernel_case:
         run_kernel_case(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -290,7 +290,17 @@ ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs,
  *                    (not an RCS-only one).  bytes_out: what one product reads
  *                    instead of S (J rows, the factors, a work vector, the
  *                    camera-major index).
- * The three stored formats sum each row's blocks in the same order.  x and y are DEVICE
+ *   BA_FMT_BSMC_ONCE the library's BSMC read once: a warp per block row applies
+ *                    each stored block as S_ij x_j to its row and as S_ij^T x_i
+ *                    to row j, both added into y (L2-resident) with vector
+ *                    reductions, so no block is read twice (the two-sided
+ *                    product reads each off-diagonal block twice, and beyond L2
+ *                    moves that many bytes); the order of y's terms is not
+ *                    fixed, so results may differ in the last bits between
+ *                    runs.  Same arrays and bytes as BA_FMT_BSMC.  y (FP32:
+ *                    8-byte aligned, as any cudaMalloc'd array) is zeroed first
+ *                    on the stream, as part of the product.
+ * The three two-sided stored formats sum each row's blocks in the same order.  x and y are DEVICE
  * arrays of 6n values in the problem's precision (double for BA_FP64
  * problems, float for BA_FP32), owned by the caller, not overlapping; the
  * product is queued on the problem's stream (no synchronisation).  The full
@@ -300,7 +310,8 @@ ba_status ba_symbolic_pattern(int32_t n_cams, int64_t n_pts, int64_t n_obs,
  * array bytes: values + column indices + row starts.  Errors:
  * BA_ERR_INVALID_ARG (bad format or NULL array), BA_ERR_STATE (no RCS
  * formed), BA_ERR_OOM, BA_ERR_CUDA. */
-typedef enum { BA_FMT_BSMC = 0, BA_FMT_BSR_FULL = 1, BA_FMT_CSR = 2, BA_FMT_IMPLICIT = 3 } ba_rcs_format;
+typedef enum { BA_FMT_BSMC = 0, BA_FMT_BSR_FULL = 1, BA_FMT_CSR = 2, BA_FMT_IMPLICIT = 3,
+               BA_FMT_BSMC_ONCE = 4 } ba_rcs_format;
 ba_status ba_rcs_spmv(ba_problem *p, int32_t format, const void *x, void *y, int64_t *bytes_out);
 
 /* ---- Learned block-Jacobi correction (not in the paper) ------------------

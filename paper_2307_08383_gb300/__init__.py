@@ -31,7 +31,7 @@ BA_ERR_INTERNAL = 9
 BA_FP64 = 0
 BA_FP32 = 1
 BA_PCG_AUTO, BA_PCG_STANDARD, BA_PCG_SPLIT, BA_PCG_IMPLICIT = 0, 1, 2, 3
-BA_FMT_BSMC, BA_FMT_BSR_FULL, BA_FMT_CSR, BA_FMT_IMPLICIT = 0, 1, 2, 3
+BA_FMT_BSMC, BA_FMT_BSR_FULL, BA_FMT_CSR, BA_FMT_IMPLICIT, BA_FMT_BSMC_ONCE = 0, 1, 2, 3, 4
 BA_LOSS_PLAIN = 0
 BA_LOSS_HUBER = 1
 BA_PC_BLOCK_JACOBI = 0

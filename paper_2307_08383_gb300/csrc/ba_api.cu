@@ -917,14 +917,14 @@ ba_status ba_get_rcs(const ba_problem *p, int64_t *nnzb, int32_t *row_ptr, int32
 
 ba_status ba_rcs_spmv(ba_problem *p, int32_t format, const void *x, void *y, int64_t *bytes_out) {
     LIVE(p);
-    if (format < BA_FMT_BSMC || format > BA_FMT_IMPLICIT) return fail(BA_ERR_INVALID_ARG, "unknown RCS format");
+    if (format < BA_FMT_BSMC || format > BA_FMT_BSMC_ONCE) return fail(BA_ERR_INVALID_ARG, "unknown RCS format");
     if (format == BA_FMT_IMPLICIT && p->rcs_only)
         return fail(BA_ERR_STATE, "the implicit product needs the linearization (not an RCS-only problem)");
     if (!x || !y) return fail(BA_ERR_INVALID_ARG, "null vector");
     if (!p->rcs_formed) return fail(BA_ERR_STATE, "no RCS formed yet");
     if (format == BA_FMT_CSR && (2 * p->nnzb - p->n) * (int64_t)BW >= (int64_t)INT32_MAX)
         return fail(BA_ERR_INVALID_ARG, "scalar CSR of this RCS needs 64-bit row starts");
-    if (format != BA_FMT_BSMC) {
+    if (format != BA_FMT_BSMC && format != BA_FMT_BSMC_ONCE) {
         const cudaError_t e = launch_rcs_format_build(p, format);
         if (e == cudaErrorMemoryAllocation) {
             cudaGetLastError();

@@ -121,6 +121,90 @@ __global__ void __launch_bounds__(256) k_spmv_blocks(int n, const int *__restric
     }
 }
 
+// Vector reductions into an L2-resident result (sm_90 and later).
+__device__ __forceinline__ void red_add2(float *a, float u, float v) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(a), "f"(u), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add2(double *a, double u, double v) {
+    atomicAdd(a, u);
+    atomicAdd(a + 1, v);
+}
+
+// The transposed product S_ij^T x_i of a block added into y_j (6 values,
+// 8-byte aligned): two vector reductions, the 16-byte one on the aligned half.
+__device__ __forceinline__ void red_add4(float *a, float u0, float u1, float u2, float u3) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(u0), "f"(u1), "f"(u2), "f"(u3)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add6(float *yj, const float (&t)[6]) {
+    if ((reinterpret_cast<uintptr_t>(yj) & 15u) == 0) {
+        red_add4(yj, t[0], t[1], t[2], t[3]);
+        red_add2(yj + 4, t[4], t[5]);
+    } else {
+        red_add2(yj, t[0], t[1]);
+        red_add4(yj + 2, t[2], t[3], t[4], t[5]);
+    }
+}
+__device__ __forceinline__ void red_add6(double *yj, const double (&t)[6]) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) atomicAdd(yj + c, t[c]);
+}
+
+// y += S x over BSMC reading every stored block once: a warp per block row i
+// takes the row's stored blocks (i, j >= i; contiguous in memory) two at a
+// time per lane, adds S_ij x_j to its row sum and, for j > i, S_ij^T x_i
+// into y_j with vector reductions; the row sum joins y_i the same way (other
+// rows add to it concurrently).  y must be zero on entry and 16-byte
+// aligned.  The transposed product of Sec. 6.2 (Fig. 13) as the paper
+// describes it: each block read once and its two results added where they
+// belong.  The order in which y's terms are added is not fixed
+// (floating-point reductions), so results may differ from run to run in the
+// last bits.
+template <typename T>
+__global__ void __launch_bounds__(256) k_spmv_bsmc_once(int n, const int *__restrict__ row_ptr,
+                                                        const int *__restrict__ col, const T *__restrict__ val,
+                                                        const T *__restrict__ x, T *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    for (int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < n; i += nw) {
+        const int tb = __ldg(row_ptr + i), te = __ldg(row_ptr + i + 1);
+        T xi[6];
+        load6(x + 6 * (int64_t)i, xi);
+        T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        for (int t0 = tb + lane; t0 < te; t0 += 64) {
+            const int t1 = t0 + 32;
+            const bool has1 = t1 < te;
+            const int ja = __ldg(col + t0), jb = __ldg(col + (has1 ? t1 : t0));
+            T va[36], vb[36], xa[6], xb[6];
+            load_block<T, T>(val + (int64_t)t0 * BW, va);
+            load_block<T, T>(val + (int64_t)(has1 ? t1 : t0) * BW, vb);
+            load6(x + 6 * (int64_t)ja, xa);
+            load6(x + 6 * (int64_t)jb, xb);
+            block_apply<T>(va, xa, false, acc);
+            if (has1) block_apply<T>(vb, xb, false, acc);
+            if (ja != i) {
+                T tr[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                block_apply<T>(va, xi, true, tr);
+                red_add6(y + 6 * (int64_t)ja, tr);
+            }
+            if (has1 && jb != i) {
+                T tr[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                block_apply<T>(vb, xi, true, tr);
+                red_add6(y + 6 * (int64_t)jb, tr);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] = warp_sum(acc[c]);
+        if (lane < 6) {
+            T out = acc[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c)
+                if (lane == c) out = acc[c];
+            atomicAdd(y + 6 * (int64_t)i + lane, out);
+        }
+    }
+}
+
 // y = S x over scalar CSR, a warp per scalar row (the row's values and
 // column indices read coalesced), a shuffle sum per row.
 template <typename T>
@@ -369,9 +453,9 @@ __global__ void __launch_bounds__(256) k_pcg_implicit(int n, int64_t P, const in
 // ---------------------------------------------------------------------------
 // One wave: at most the CTAs that fit on the GPU at once (the loops stride
 // over the rest), so no partial second wave.
-static int fmt_grid(const void *kern, int64_t warps) {
+static int fmt_grid(const void *kern, int64_t warps, size_t smem = 0) {
     int per_sm = 0, n_sm = 0;
-    if (occupancy(kern, 256, 0, &per_sm, &n_sm) != cudaSuccess) return 1;
+    if (occupancy(kern, 256, smem, &per_sm, &n_sm) != cudaSuccess) return 1;
     const int64_t resident = (int64_t)std::max(1, per_sm) * n_sm;
     const int64_t ctas = (warps * 32 + 255) / 256;
     return (int)std::max<int64_t>(1, std::min<int64_t>(ctas, resident));
@@ -458,6 +542,11 @@ static void spmv_format_T(ba_problem *p, int format, const T *x, T *y) {
     if (format == BA_FMT_BSMC)
         k_spmv_blocks<T, true><<<fmt_grid((const void *)k_spmv_blocks<T, true>, n), 256, 0, p->st>>>(
             n, p->tw_ptr, p->tw_ent, nullptr, (const T *)p->S, x, y);
+    else if (format == BA_FMT_BSMC_ONCE) {
+        cudaMemsetAsync(y, 0, (size_t)6 * n * sizeof(T), p->st);
+        k_spmv_bsmc_once<T><<<fmt_grid((const void *)k_spmv_bsmc_once<T>, n), 256, 0, p->st>>>(
+            n, p->row_ptr, p->col, (const T *)p->S, x, y);
+    }
     else if (format == BA_FMT_BSR_FULL)
         k_spmv_blocks<T, false><<<fmt_grid((const void *)k_spmv_blocks<T, false>, n), 256, 0, p->st>>>(
             n, p->tw_ptr, nullptr, p->fmt_bsr_col, (const T *)p->fmt_bsr_val, x, y);
@@ -525,7 +614,7 @@ int64_t rcs_format_bytes(const ba_problem *p, int format) {
     if (format == BA_FMT_IMPLICIT)
         return p->m * (int64_t)(JW + 12) * p->esz + p->P * 6 * (int64_t)p->esz + p->m * 2 * 2 * (int64_t)p->esz +
                (p->m + n + 1) * 4;
-    if (format == BA_FMT_BSMC) return nnzb * BW * p->esz + nnzb * 4 + (n + 1) * 4;
+    if (format == BA_FMT_BSMC || format == BA_FMT_BSMC_ONCE) return nnzb * BW * p->esz + nnzb * 4 + (n + 1) * 4;
     if (format == BA_FMT_BSR_FULL) return E * BW * p->esz + E * 4 + (n + 1) * 4;
     return E * BW * (p->esz + 4) + (6 * n + 1) * 4;
 }

@@ -47,7 +47,7 @@ def _products(B, g, x, dtype):
     xt = torch.tensor(x, dtype=dtype, device="cuda")
     out, nbytes = {}, {}
     for name, fmt in (("bsmc", B.BA_FMT_BSMC), ("bsr", B.BA_FMT_BSR_FULL), ("csr", B.BA_FMT_CSR),
-                      ("implicit", B.BA_FMT_IMPLICIT)):
+                      ("implicit", B.BA_FMT_IMPLICIT), ("bsmc_once", B.BA_FMT_BSMC_ONCE)):
         yt = torch.full_like(xt, float("nan"))
         nbytes[name] = g.rcs_spmv(fmt, xt, yt)
         torch.cuda.synchronize()
@@ -80,12 +80,15 @@ def test_formats_match_oracle_product(B, scene, prec, tol, tol_csr):
     assert (np.abs(out["csr"] - out["bsmc"]) / mag).max() <= tol_csr
     # the implicit product forms U x - W V^-1 W^T x without S: other rounding
     assert (np.abs(out["implicit"] - out["bsmc"]) / mag).max() <= (1e-12 if fp64 else 5e-5)
+    # BSMC read once: the same products, added with reductions in no fixed order
+    assert (np.abs(out["bsmc_once"] - out["bsmc"]) / mag).max() <= (1e-13 if fp64 else 1e-5)
 
     # bytes of each format's arrays, against the memory model of Sec. 4.1
     nnzb = len(A.col)
     E = 2 * nnzb - n                      # non-zero blocks of the full matrix
     esz = 8 if fp64 else 4
     assert nbytes["bsmc"] == nnzb * 36 * esz + nnzb * 4 + (n + 1) * 4
+    assert nbytes["bsmc_once"] == nbytes["bsmc"]
     assert nbytes["bsr"] == E * 36 * esz + E * 4 + (n + 1) * 4
     assert nbytes["csr"] == E * 36 * (esz + 4) + (6 * n + 1) * 4
     m, P = s.n_obs, s.n_pts
