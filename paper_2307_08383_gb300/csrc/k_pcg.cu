@@ -104,6 +104,91 @@ __device__ __forceinline__ double spmv_rows(int n, const int *__restrict__ tw_pt
     return (double)pap;
 }
 
+// The same product reading every stored block once (FP32 solves of large
+// systems, where the second, transposed read of each off-diagonal block
+// would come from DRAM): a warp per block row i takes the row's stored
+// blocks (i, j >= i), lane l the blocks l, l + 32, ... two at a time; each
+// applies S_ij d_j to the row sum and, for j > i, S_ij^T d_i to q_j with
+// vector reductions; the row sum joins q_i the same way.  q must be zero on
+// entry.  d^T S d is summed per block as (2 for j > i, 1 for j = i)
+// d_i^T S_ij d_j, so it needs no complete q.  The order of q's terms is not
+// fixed (floating-point reductions).
+__device__ __forceinline__ void red_add2_f(float *a, float u, float v) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(a), "f"(u), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add4_f(float *a, float u0, float u1, float u2, float u3) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(u0), "f"(u1), "f"(u2), "f"(u3)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add6_f(float *qj, const float (&t)[6]) {
+    if ((reinterpret_cast<uintptr_t>(qj) & 15u) == 0) {
+        red_add4_f(qj, t[0], t[1], t[2], t[3]);
+        red_add2_f(qj + 4, t[4], t[5]);
+    } else {
+        red_add2_f(qj, t[0], t[1]);
+        red_add4_f(qj + 2, t[2], t[3], t[4], t[5]);
+    }
+}
+__device__ __forceinline__ double spmv_rows_once(int n, const int *__restrict__ row_ptr,
+                                                 const int *__restrict__ col, const float *__restrict__ S,
+                                                 const float *__restrict__ z, const float *__restrict__ dold,
+                                                 float *__restrict__ dnew, float *__restrict__ q, float beta) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    float pap = 0.f;
+    for (int i = warp; i < n; i += nw) {
+        float di[6];
+        gather_x<float, true>(z, dold, beta, i, di);
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            if (lane == c) dnew[6 * i + c] = di[c];
+        const int tb = __ldg(row_ptr + i), te = __ldg(row_ptr + i + 1);
+        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int t0 = tb + lane; t0 < te; t0 += 64) {
+            const int t1 = t0 + 32;
+            const bool has1 = t1 < te;
+            const int ja = __ldg(col + t0), jb = __ldg(col + (has1 ? t1 : t0));
+            float va[36], vb[36], xa[6], xb[6];
+            load_block<float, float>(S + (int64_t)t0 * BW, va);
+            load_block<float, float>(S + (int64_t)(has1 ? t1 : t0) * BW, vb);
+            gather_x<float, true>(z, dold, beta, ja, xa);
+            gather_x<float, true>(z, dold, beta, jb, xb);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !has1) break;
+                const float(&v)[36] = h ? vb : va;
+                const float(&xj)[6] = h ? xb : xa;
+                const int j = h ? jb : ja;
+                float yb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                block_apply<float>(v, xj, false, yb);
+                float dy = 0.f;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    acc[c] += yb[c];
+                    dy += di[c] * yb[c];
+                }
+                pap += j == i ? dy : 2.f * dy;
+                if (j != i) {
+                    float tr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    block_apply<float>(v, di, true, tr);
+                    red_add6_f(q + 6 * (int64_t)j, tr);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] = warp_sum(acc[c]);
+        if (lane < 6) {
+            float out = acc[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c)
+                if (lane == c) out = acc[c];
+            atomicAdd(q + 6 * (int64_t)i + lane, out);
+        }
+    }
+    return (double)pap;
+}
+
 // q = S x with FP64 accumulation, for the refinement residual.
 template <typename TS>
 __global__ void __launch_bounds__(256) k_spmv64(int n, const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
@@ -222,11 +307,15 @@ __global__ void __launch_bounds__(256) k_pcg_init(int n, const T *__restrict__ r
 // reads r_k (all six entries of a camera) and writes r_k+1.  The update runs one thread per vector entry
 // e = 6 i + a; each recomputes camera i's six new residual entries (reads
 // shared through L1) to form z_e = sum_c M^-1_i[a][c] r_i[c].
-template <typename T>
+// ONCE (FP32 only): the product reads each stored block once (spmv_rows_once)
+// into q, which is double-buffered by iteration parity: the update phase of
+// iteration k reads q_k and zeroes the buffer iteration k + 1 adds into.
+template <typename T, bool ONCE>
 __global__ void __launch_bounds__(256) k_pcg_persist(int n, const int *__restrict__ tw_ptr, const int2 *__restrict__ tw_ent,
+                                                     const int *__restrict__ row_ptr, const int *__restrict__ col,
                                                      const T *__restrict__ S, const T *__restrict__ Minv, T *y, T *r0,
-                                                     T *r1, T *z, T *d0, T *d1, T *q, DevScalars *sc, double *red,
-                                                     unsigned *bar, long long limit_cycles) {
+                                                     T *r1, T *z, T *d0, T *d1, T *q0, T *q1, DevScalars *sc,
+                                                     double *red, unsigned *bar, long long limit_cycles) {
     __shared__ double sh[40];
     if (sc->done) return;
     double rz = sc->rz;
@@ -240,8 +329,13 @@ __global__ void __launch_bounds__(256) k_pcg_persist(int n, const int *__restric
         const bool odd = it & 1;
         T *dold = odd ? d1 : d0, *dnew = odd ? d0 : d1;
         T *rc = odd ? r1 : r0, *rn = odd ? r0 : r1;
+        T *q = (ONCE && odd) ? q1 : q0, *qz = odd ? q0 : q1;
         // SpMV phase: d = z + beta d_old, q = S d, d^T S d
-        double v1[1] = {spmv_rows<T, T, true>(n, tw_ptr, tw_ent, S, z, dold, dnew, q, (T)beta)};
+        double v1[1];
+        if constexpr (ONCE)
+            v1[0] = spmv_rows_once(n, row_ptr, col, S, z, dold, dnew, q, (float)beta);
+        else
+            v1[0] = spmv_rows<T, T, true>(n, tw_ptr, tw_ent, S, z, dold, dnew, q, (T)beta);
         block_sum<1>(v1, sh);
         if (!grid_allreduce_sym<1>(v1, red, gen++, bar, &sc->err, limit_cycles)) return;
         const double pAp = v1[0];
@@ -274,6 +368,7 @@ __global__ void __launch_bounds__(256) k_pcg_persist(int n, const int *__restric
             y[e] += alpha * __ldcg(dnew + e);
             rn[e] = ra;
             z[e] = ze;
+            if (ONCE) qz[e] = T(0);  // the next product adds into it
             rz_p += ra * ze;
             rr_p += ra * ra;
         }
@@ -986,11 +1081,17 @@ cudaError_t launch_pcg_init(ba_problem *p, const void *rhs, double tol, int max_
     return cudaGetLastError();
 }
 
-template <typename T>
+// FP32 systems whose stored blocks exceed this many bytes run the product
+// that reads each block once (the second, transposed read of the two-sided
+// product would come from DRAM); smaller ones keep the deterministic
+// two-sided product, whose second read hits L2.
+constexpr int64_t ONCE_MIN_BYTES = 64ll << 20;
+
+template <typename T, bool ONCE>
 static cudaError_t pcg_loop_T(ba_problem *p) {
     int blocks_per_sm = 0, n_sm = 0;
     cudaError_t e;
-    if ((e = occupancy((const void *)k_pcg_persist<T>, 256, 0, &blocks_per_sm, &n_sm)) != cudaSuccess) return e;
+    if ((e = occupancy((const void *)k_pcg_persist<T, ONCE>, 256, 0, &blocks_per_sm, &n_sm)) != cudaSuccess) return e;
     if (blocks_per_sm > 2) blocks_per_sm = 2;
     if (blocks_per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     // enough warps for one block row each, at most what is co-resident
@@ -1003,23 +1104,25 @@ static cudaError_t pcg_loop_T(ba_problem *p) {
         return e;
     if ((e = cudaMemsetAsync(p->counters + 15, 0, sizeof(unsigned), p->st)) != cudaSuccess) return e;
     int n = p->n;
-    const int *twp = p->tw_ptr;
+    const int *twp = p->tw_ptr, *rp = p->row_ptr, *cl = p->col;
     const int2 *twe = p->tw_ent;
     const T *S = (const T *)p->sv.S, *Mi = (const T *)p->sv.Minv;
     T *y = (T *)p->sv.pv[0], *r = (T *)p->sv.pv[1], *z = (T *)p->sv.pv[2], *d0 = (T *)p->sv.pv[3], *d1 = (T *)p->sv.pv[4];
-    T *q = (T *)p->sv.pv[5], *r1 = (T *)p->sv.pv[6];
+    T *q = (T *)p->sv.pv[5], *r1 = (T *)p->sv.pv[6], *q1 = (T *)p->sv.pv[7];
     DevScalars *sc = p->sc;
     double *red = p->red;
     unsigned *bar = p->counters + 14;
     long long limit = test_limit > 0 ? test_limit : 4000000000LL;  // ~2 s of SM clock per barrier wait
-    void *args[] = {&n, &twp, &twe, &S, &Mi, &y, &r, &r1, &z, &d0, &d1, &q, &sc, &red, &bar, &limit};
-    return cudaLaunchCooperativeKernel((const void *)k_pcg_persist<T>, dim3(grid), dim3(256), args, 0, p->st);
+    void *args[] = {&n, &twp, &twe, &rp, &cl, &S, &Mi, &y, &r, &r1, &z, &d0, &d1, &q, &q1, &sc, &red, &bar, &limit};
+    return cudaLaunchCooperativeKernel((const void *)k_pcg_persist<T, ONCE>, dim3(grid), dim3(256), args, 0, p->st);
 }
 
 cudaError_t launch_pcg_loop(ba_problem *p) {
     cudaEvent_t ev;
     ktimer_begin(p, K_PCG_LOOP, &ev);
-    cudaError_t e = p->sv.f32 ? pcg_loop_T<float>(p) : pcg_loop_T<double>(p);
+    cudaError_t e = !p->sv.f32 ? pcg_loop_T<double, false>(p)
+                    : (p->nnzb * (int64_t)BW * 4 > ONCE_MIN_BYTES ? pcg_loop_T<float, true>(p)
+                                                                 : pcg_loop_T<float, false>(p));
     ktimer_end(p, K_PCG_LOOP, ev);
     p->launches += 1;
     if (e != cudaSuccess) return e;
