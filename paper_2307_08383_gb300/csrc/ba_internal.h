@@ -23,6 +23,7 @@ constexpr int LB_MAX = 2048;          // local blocks (sub-RCS blocks) per group
 constexpr int C_MAX = 4096;           // (obs, obs) products per group (staged in shared memory)
 constexpr int ITEM_MAX = 8;           // products per work item
 constexpr int FORM_THREADS = 256;
+constexpr int CAMC32_W = 32;          // floats per camera of the FP32 camera cache
 
 // A point group: a run of whole point tracks formed by one CTA (Sec. 6.1).
 struct GroupDesc {
@@ -104,7 +105,7 @@ ba_status symbolic_setup(int32_t n, int64_t P, int64_t m, const int32_t *obs_cam
 struct StateBuf {
     double *cams = nullptr;   // n x 6  [omega, t]
     double *pts = nullptr;    // P x 3  (internal point order)
-    void *camc = nullptr;     // FP64: n x 12 [R, t]; FP32: n x 16 [R, C_hi, C_lo, pad]
+    void *camc = nullptr;     // FP64: n x 12 [R, t]; FP32: n x 32 [R_hi, C_hi, C_lo, 0, R_lo, 0 x 7]
     float *pts_hl = nullptr;  // FP32 mode: P x 6 [X_hi, X_lo]
 };
 
@@ -202,6 +203,9 @@ struct ba_problem {
     // S^ = G^T S G in two-sided entry order (one block per entry), the vector
     // records; allocated on the first such solve
     float *Gs = nullptr, *Hs = nullptr, *Sh = nullptr, *srec = nullptr;
+    float *Shd = nullptr;            // diagonal blocks of S^ when they are not the identity (n x 36)
+    int32_t *tws_ptr = nullptr;      // two-sided entry lists without the diagonal block (n + 1) ...
+    int2 *tws_ent = nullptr;         // ... and their entries
     int32_t *cta_rows = nullptr;   // row range of each CTA of the balanced SpMV
     uint32_t *tw_meta = nullptr;   // per entry: local row | halo index << 16 (per-CTA aligned)
     int32_t *meta_off = nullptr, *halo_ptr = nullptr, *halo_col = nullptr, *own_base = nullptr;

@@ -10,7 +10,11 @@
 // FP32 mode keeps the state in FP64 and evaluates X_cam = R (X - C) with
 // X and the camera centre C = -R^T t split into FP32 hi + lo parts, so the
 // subtraction of two large world coordinates loses nothing before the FP32
-// rotation.
+// rotation.  The cost F (the LM's gain ratio compares F at two states) is
+// evaluated in double-float arithmetic from the same parts and the rotation's
+// lo parts, against the FP64 observations: near convergence an LM step
+// changes F by less than FP32 residuals resolve (~1e-8 of F at 1M points),
+// and the accept/reject decision must follow the step, not the rounding.
 #include "device_util.cuh"
 #include "tma_util.cuh"
 
@@ -35,6 +39,8 @@ __global__ void k_prepare_cams64(int n, const double *__restrict__ cams, double 
     for (int k = 0; k < 3; ++k) camc[12 * i + 9 + k] = cams[6 * i + 3 + k];
 }
 
+// FP32 camera cache, CAMC32_W floats per camera:
+// [R_hi (9), C_hi (3), C_lo (3), 0, R_lo (9), 0 (7)]
 __global__ void k_prepare_cams32(int n, const double *__restrict__ cams, float *__restrict__ camc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -42,9 +48,15 @@ __global__ void k_prepare_cams32(int n, const double *__restrict__ cams, float *
     quat_exp(cams + 6 * i, q);
     quat_to_R(q, R);
     const double *t = cams + 6 * i + 3;
-    float *o = camc + 16 * i;
+    float *o = camc + CAMC32_W * i;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) o[k] = (float)R[k];
+    for (int k = 0; k < 9; ++k) {
+        const float hi = (float)R[k];
+        o[k] = hi;
+        o[16 + k] = (float)(R[k] - (double)hi);
+    }
+#pragma unroll
+    for (int k = 25; k < CAMC32_W; ++k) o[k] = 0.f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double C = -(R[0 + d] * t[0] + R[3 + d] * t[1] + R[6 + d] * t[2]);
@@ -79,7 +91,7 @@ __device__ __forceinline__ void cam_point(const double *camc, const double *pts,
 }
 __device__ __forceinline__ void cam_point(const float *camc, const double *, const float *hl, int i, int k,
                                           float *Xc, float *R) {
-    const float4 *c4 = reinterpret_cast<const float4 *>(camc + 16 * i);
+    const float4 *c4 = reinterpret_cast<const float4 *>(camc + CAMC32_W * i);
     const float4 a = c4[0], b = c4[1], c = c4[2], d = c4[3];
     R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w; R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w; R[8] = c.x;
     const float Chi[3] = {c.y, c.z, c.w}, Clo[3] = {d.x, d.y, d.z};
@@ -95,6 +107,39 @@ template <typename T>
 __device__ __forceinline__ T huber_rho(T s, int on, T delta) {
     if (!on || s <= delta * delta) return s;
     return T(2) * delta * sqrt(s) - delta * delta;
+}
+
+// ||e||^2 of observation a (camera i, point given by its hi + lo parts) in
+// double-float arithmetic: X - C, the rotation with R = R_hi + R_lo, the two
+// quotients and the intrinsics each to ~2^-44 relative; e itself is then
+// formed and squared in FP64 against the FP64 observation.  behind: z <= 1e-6.
+__device__ __forceinline__ df32 df_of(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double sq_resid_df(const float *__restrict__ camc, int i, const float *hl, const Intr &in,
+                                              const double *__restrict__ uv64, int64_t a, bool &behind) {
+    const float4 *c4 = reinterpret_cast<const float4 *>(camc + CAMC32_W * i);
+    const float4 c0 = c4[0], c1 = c4[1], c2 = c4[2], c3 = c4[3], c5 = c4[4], c6 = c4[5], c7 = c4[6];
+    const float Rh[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
+    const float Rl[9] = {c5.x, c5.y, c5.z, c5.w, c6.x, c6.y, c6.z, c6.w, c7.x};
+    const float Ch[3] = {c2.y, c2.z, c2.w}, Cl[3] = {c3.x, c3.y, c3.z};
+    df32 D[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) D[r] = df_add(df32{hl[r], hl[3 + r]}, df32{-Ch[r], -Cl[r]});
+    df32 X[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        df32 acc = df_mul(df32{Rh[3 * r], Rl[3 * r]}, D[0]);
+        acc = df_add(acc, df_mul(df32{Rh[3 * r + 1], Rl[3 * r + 1]}, D[1]));
+        X[r] = df_add(acc, df_mul(df32{Rh[3 * r + 2], Rl[3 * r + 2]}, D[2]));
+    }
+    behind = X[2].hi <= 1e-6f;
+    const df32 u = df_add(df_mul(df_of(in.fx), df_div(X[0], X[2])), df_of(in.cx));
+    const df32 v = df_add(df_mul(df_of(in.fy), df_div(X[1], X[2])), df_of(in.cy));
+    const double e0 = ((double)u.hi - uv64[2 * a]) + (double)u.lo;
+    const double e1 = ((double)v.hi - uv64[2 * a + 1]) + (double)v.lo;
+    return e0 * e0 + e1 * e1;
 }
 
 // --------------------------------------------------------------------------
@@ -166,18 +211,25 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
                                               const T *__restrict__ uv, const T *__restrict__ camc,
                                               const double *__restrict__ pts, const float *__restrict__ pts_hl,
                                               Intr in, int huber, double delta, DevScalars *sc, int trial,
-                                              double *red, unsigned *ctr) {
-    RunSum<double> f;  // FP64 accumulation in both modes (each term is formed in T)
+                                              double *red, unsigned *ctr, const double *__restrict__ uv64) {
+    RunSum<double> f;  // FP64 accumulation (FP64 terms; double-float residuals in FP32 mode)
     int ncheir = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
         const int i = obs_cam[a], k = obs_pt[a];
-        T Xc[3], R[9];
-        cam_point(camc, pts, pts_hl, i, k, Xc, R);
-        const T iz = T(1) / Xc[2];
-        const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
-        const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
-        f.add((double)huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
-        ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
+        if constexpr (sizeof(T) == 4) {
+            bool behind;
+            const double s = sq_resid_df(camc, i, pts_hl + 6 * (int64_t)k, in, uv64, a, behind);
+            f.add(huber_rho<double>(s, huber, delta));
+            ncheir += behind ? 1 : 0;
+        } else {
+            T Xc[3], R[9];
+            cam_point(camc, pts, pts_hl, i, k, Xc, R);
+            const T iz = T(1) / Xc[2];
+            const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
+            const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
+            f.add((double)huber_rho<T>(e0 * e0 + e1 * e1, huber, (T)delta));
+            ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
+        }
     }
     double v[2] = {f.get(), (double)ncheir};
     grid_sum<2>(v, red, ctr, [&](double *t) {
@@ -242,7 +294,7 @@ __device__ __forceinline__ void cam_point_v(const double *camc, int i, const dou
     for (int r = 0; r < 3; ++r) Xc[r] = c[3 * r] * X[0] + c[3 * r + 1] * X[1] + c[3 * r + 2] * X[2] + c[9 + r];
 }
 __device__ __forceinline__ void cam_point_v(const float *camc, int i, const double *, const float *hl, float *Xc) {
-    const float4 *c4 = reinterpret_cast<const float4 *>(camc + 16 * i);
+    const float4 *c4 = reinterpret_cast<const float4 *>(camc + CAMC32_W * i);
     const float4 a = c4[0], b = c4[1], c = c4[2], d = c4[3];
     const float R[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x};
     const float Chi[3] = {c.y, c.z, c.w}, Clo[3] = {d.x, d.y, d.z};
@@ -282,7 +334,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *_
                                                      Intr in, int huber, double delta, T *__restrict__ dxp,
                                                      double *__restrict__ pts_trial, float *__restrict__ hl_trial,
                                                      DevScalars *sc, double *red, unsigned *ctr, int obs_max,
-                                                     long long limit) {
+                                                     long long limit, const double *__restrict__ uv64) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ GroupDesc sdesc;
@@ -398,13 +450,20 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *_
             if (al >= g.nobs) break;
             const int64_t a = (int64_t)g.obs_begin + al;
             const int i = s_cam[al], pl = __ldg(obs_pt + a) - g.pt_begin;
-            T Xc[3];
-            cam_point_v(camc_trial, i, s_xt + 3 * pl, s_hl + 6 * pl, Xc);
-            const T iz = T(1) / Xc[2];
-            const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
-            const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
-            f.add((double)huber_rho<T>(e0 * e0 + e1 * e1, huber, dl));
-            ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
+            if constexpr (sizeof(T) == 4) {
+                bool behind;
+                const double s = sq_resid_df(camc_trial, i, s_hl + 6 * pl, in, uv64, a, behind);
+                f.add(huber_rho<double>(s, huber, delta));
+                ncheir += behind ? 1 : 0;
+            } else {
+                T Xc[3];
+                cam_point_v(camc_trial, i, s_xt + 3 * pl, s_hl + 6 * pl, Xc);
+                const T iz = T(1) / Xc[2];
+                const T e0 = T(in.fx) * (Xc[0] * iz) + T(in.cx) - uv[2 * a];
+                const T e1 = T(in.fy) * (Xc[1] * iz) + T(in.cy) - uv[2 * a + 1];
+                f.add((double)huber_rho<T>(e0 * e0 + e1 * e1, huber, dl));
+                ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
+            }
             const T *jr = pe[k];  // J_p (2 x 3), e
             T jd0 = s_jc[2 * al], jd1 = s_jc[2 * al + 1];
 #pragma unroll
@@ -694,11 +753,11 @@ cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial) {
     if (p->fp32)
         k_cost<float><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv32, (const float *)s.camc, s.pts,
                                             s.pts_hl, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
-                                            p->red, p->counters + 0);
+                                            p->red, p->counters + 0, p->uv64);
     else
         k_cost<double><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv64, (const double *)s.camc, s.pts,
                                              nullptr, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
-                                             p->red, p->counters + 0);
+                                             p->red, p->counters + 0, p->uv64);
     ktimer_end(p, K_COST, ev);
     p->launches += 1;
     return cudaGetLastError();
@@ -741,7 +800,7 @@ static cudaError_t step_groups_T(ba_problem *p, long long limit) {
                                                                                         : (const void *)p->uv64),
         (const T *)p->J, (const T *)p->dxc, (const T *)p->Linv, (const T *)p->lp, p->cur.pts,
         (const T *)p->trial.camc, intr_of(p), hub, p->opt.huber_delta, (T *)p->dxp, p->trial.pts,
-        p->fp32 ? p->trial.pts_hl : nullptr, p->sc, p->red, p->counters + 1, p->obs_max, limit);
+        p->fp32 ? p->trial.pts_hl : nullptr, p->sc, p->red, p->counters + 1, p->obs_max, limit, p->uv64);
     return cudaGetLastError();
 }
 

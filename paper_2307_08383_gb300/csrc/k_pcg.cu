@@ -488,11 +488,13 @@ __device__ bool chol6_with_inverse(const double *A, double *L, double *Li) {
 // (H r^ gives back the residual of the original system):
 //   block-Jacobi (from_minv = 0): S_ii = L L^T, G = L^-T, H = L;
 //   a given M^-1 (from_minv = 1):  M^-1 = C C^T, G = C,   H = C^-T.
-// Stored row-major FP32, n x 36 each.
+// Stored row-major FP32, n x 36 each.  The diagonal block of S^ = G^T S G is
+// the identity for block-Jacobi (L^-1 L L^T L^-T); for a given M^-1 it is
+// G_i^T S_ii G_i, written to Shd (n x 36).
 template <typename T>
 __global__ void __launch_bounds__(128) k_split_factor(int n, const int *__restrict__ row_ptr, const T *__restrict__ S,
                                                       const T *__restrict__ Minv, int from_minv, float *__restrict__ G,
-                                                      float *__restrict__ H, DevScalars *sc) {
+                                                      float *__restrict__ H, float *__restrict__ Shd, DevScalars *sc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const T *src = from_minv ? Minv + 36 * (int64_t)i : S + (int64_t)__ldg(row_ptr + i) * BW;
@@ -515,14 +517,39 @@ __global__ void __launch_bounds__(128) k_split_factor(int n, const int *__restri
             g[6 * a + c] = (float)(from_minv ? low : lit);
             h[6 * a + c] = (float)(from_minv ? lit : low);
         }
+    if (from_minv) {
+        // S_ii G, then G^T (S_ii G), with G = L (lower) in FP64
+        const T *sd = S + (int64_t)__ldg(row_ptr + i) * BW;
+        double SG[36];
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                double v = 0.0;
+#pragma unroll
+                for (int k = c; k < 6; ++k) v += (double)sd[6 * a + k] * L[k * (k + 1) / 2 + c];
+                SG[6 * a + c] = v;
+            }
+        float *d = Shd + 36 * (int64_t)i;
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                double v = 0.0;
+#pragma unroll
+                for (int k = a; k < 6; ++k) v += L[k * (k + 1) / 2 + a] * SG[6 * k + c];
+                d[6 * a + c] = (float)v;
+            }
+    }
 }
 
-// S^ in two-sided entry order: entry t of block row i (column j = the
-// entry's y) gets S^_ij = G_i^T S_ij G_j, with S_ij the stored block or, for
-// the entries of column i, the transpose of the stored block (j, i).  Every
-// off-diagonal block is thus held twice, already transposed where needed, so
-// the entries of consecutive rows are one contiguous, 16-byte aligned range
-// that a bulk copy moves.  A warp per block row, a lane per entry.
+// S^ in two-sided entry order without the diagonal blocks (the split CG's
+// lists): entry t of block row i (column j = the entry's y) gets
+// S^_ij = G_i^T S_ij G_j, with S_ij the stored block or, for the entries of
+// column i, the transpose of the stored block (j, i).  Every off-diagonal
+// block is thus held twice, already transposed where needed, so the entries
+// of consecutive rows are one contiguous, 16-byte aligned range that a bulk
+// copy moves.  A warp per block row, a lane per entry.
 template <typename TS>
 __global__ void __launch_bounds__(128) k_split_scale(int n, const int *__restrict__ tw_ptr,
                                                      const int2 *__restrict__ tw_ent, const TS *__restrict__ S,
@@ -757,16 +784,30 @@ __device__ __forceinline__ bool split_passes(SplitPipe &pp, int rb, const int *_
     return true;
 }
 
-// Component c of (S^ x)_i for local row lr after split_passes and a
-// __syncthreads: the row's segment sums in pass order.
+// Component c of the off-diagonal part of (S^ x)_i for local row lr after
+// split_passes and a __syncthreads: the row's segment sums in pass order
+// (zero for a row without off-diagonal entries).
 __device__ __forceinline__ float split_combine(int lr, int c, int rs, int rend, int eb, int ee, const float *slot,
                                                const float *rowacc) {
     float w = 0.f;
+    if (rs >= rend) return w;
     for (int q = (rs - eb) >> 5; q <= (rend - 1 - eb) >> 5; ++q) {
         const int ps = eb + 32 * q, pe = min(ps + 32, ee);
         const float *src = rs <= ps ? slot + 12 * q : (rend >= pe ? slot + 12 * q + 6 : rowacc + 6 * lr);
         w += src[c];
     }
+    return w;
+}
+
+// Component c of S^_ii x_i: x_i itself for block-Jacobi (S^_ii = I), else
+// row c of the stored diagonal block times x_i.
+__device__ __forceinline__ float split_diag(int i, int c, const float *x6, const float *__restrict__ Shd,
+                                            int ident) {
+    if (ident) return x6[c];
+    const float *d = Shd + 36 * (int64_t)i + 6 * c;
+    float w = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w = __fmaf_rn(__ldg(d + k), x6[k], w);
     return w;
 }
 
@@ -829,6 +870,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, SPLIT_CTAS_PER_SM) k_pcg_spl
                                                       const int *__restrict__ halo_col,
                                                       const int *__restrict__ own_base, int slot_floats,
                                                       const float *__restrict__ Sh, const float *__restrict__ H,
+                                                      const float *__restrict__ Shd, int diag_ident,
                                                       float *x, float *p, float *rec0, float *rec1, DevScalars *sc,
                                                       double *red, unsigned *bar, long long limit_cycles) {
     extern __shared__ __align__(16) float sdyn[];
@@ -933,8 +975,8 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, SPLIT_CTAS_PER_SM) k_pcg_spl
         for (int u = threadIdx.x; u < 6 * R; u += blockDim.x) {
             const int lr = u / 6, c = u - 6 * lr, i = rb + lr;
             const int rs = u == u0 ? rs0 : __ldg(tw_ptr + i), rend = u == u0 ? re0 : __ldg(tw_ptr + i + 1);
-            const float wc = split_combine(lr, c, rs, rend, eb, ee, slot, rowacc);
             const float *r6 = hx + HX * (ob + lr);
+            const float wc = split_combine(lr, c, rs, rend, eb, ee, slot, rowacc) + split_diag(i, c, r6, Shd, diag_ident);
             rec0[(int64_t)SREC * i + 6 + c] = wc;
             float hr = 0.f;
 #pragma unroll
@@ -993,8 +1035,8 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32, SPLIT_CTAS_PER_SM) k_pcg_spl
             const int lr = u / 6, c = u - 6 * lr, i = rb + lr, e = 6 * i + c;
             const bool first = u == u0;
             const int rs = first ? rs0 : __ldg(tw_ptr + i), rend = first ? re0 : __ldg(tw_ptr + i + 1);
-            const float w_e = split_combine(lr, c, rs, rend, eb, ee, slot, rowacc);
             const float *rnew = hx + HX * (ob + lr);  // this row's new residual (all six components)
+            const float w_e = split_combine(lr, c, rs, rend, eb, ee, slot, rowacc) + split_diag(i, c, rnew, Shd, diag_ident);
             const float *o6 = own + 20 * lr;
             const float r_e = rnew[c], rold = o6[c], wold = o6[6 + c], sold = o6[12 + c];
             const float pval = __fmaf_rn(b, first ? p0 : __ldcg(p + e), rold);
@@ -1256,7 +1298,8 @@ static cudaError_t split_alloc(ba_problem *p) {
     };
     al(&p->Gs, (size_t)p->n * 36);
     al(&p->Hs, (size_t)p->n * 36);
-    const size_t E = (size_t)(2 * p->nnzb - p->n);
+    al(&p->Shd, (size_t)p->n * 36);
+    const size_t E = std::max<size_t>(1, (size_t)(2 * p->nnzb - 2 * p->n));  // entries without the diagonal
     al(&p->Sh, E * BW);
     al(&p->srec, (size_t)2 * SREC * p->n);
     return e;
@@ -1270,12 +1313,13 @@ cudaError_t launch_split_prepare(ba_problem *p, bool from_minv) {
     const int nb = (p->n + 127) / 128, ns = (int)(((int64_t)p->n * 32 + 127) / 128);
     if (p->fp32) {
         k_split_factor<float><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const float *)p->S, (const float *)p->Minv,
-                                                     from_minv ? 1 : 0, p->Gs, p->Hs, p->sc);
-        k_split_scale<float><<<ns, 128, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const float *)p->S, p->Gs, p->Sh);
+                                                     from_minv ? 1 : 0, p->Gs, p->Hs, p->Shd, p->sc);
+        k_split_scale<float><<<ns, 128, 0, p->st>>>(p->n, p->tws_ptr, p->tws_ent, (const float *)p->S, p->Gs, p->Sh);
     } else {
         k_split_factor<double><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const double *)p->S,
-                                                      (const double *)p->Minv, from_minv ? 1 : 0, p->Gs, p->Hs, p->sc);
-        k_split_scale<double><<<ns, 128, 0, p->st>>>(p->n, p->tw_ptr, p->tw_ent, (const double *)p->S, p->Gs, p->Sh);
+                                                      (const double *)p->Minv, from_minv ? 1 : 0, p->Gs, p->Hs,
+                                                      p->Shd, p->sc);
+        k_split_scale<double><<<ns, 128, 0, p->st>>>(p->n, p->tws_ptr, p->tws_ent, (const double *)p->S, p->Gs, p->Sh);
     }
     ktimer_end(p, K_SPLIT_PREP, ev);
     p->launches += 2;
@@ -1295,13 +1339,25 @@ static cudaError_t split_partition(ba_problem *p) {
     if (p->split_grid != 0) return cudaSuccess;
     cudaError_t e;
     const int n = p->n;
-    std::vector<int32_t> twp(n + 1);
-    if ((e = cudaMemcpy(twp.data(), p->tw_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    std::vector<int32_t> twp0(n + 1);
+    if ((e = cudaMemcpy(twp0.data(), p->tw_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return e;
+    std::vector<int2> twe0(twp0[n]);
+    if (twp0[n] &&
+        (e = cudaMemcpy(twe0.data(), p->tw_ent, twp0[n] * sizeof(int2), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    // the split CG's entry lists: the two-sided lists without the diagonal
+    // block (its product is added in the row combine: S^_ii x_i)
+    std::vector<int32_t> twp(n + 1, 0);
+    std::vector<int2> twe;
+    twe.reserve(twp0[n]);
+    for (int i = 0; i < n; ++i) {
+        for (int32_t t = twp0[i]; t < twp0[i + 1]; ++t)
+            if (twe0[t].y != i) twe.push_back(twe0[t]);
+        twp[i + 1] = (int32_t)twe.size();
+    }
     const int64_t E = twp[n];
-    std::vector<int2> twe(E);
-    if (E && (e = cudaMemcpy(twe.data(), p->tw_ent, E * sizeof(int2), cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return e;
+    if (twe.empty()) twe.push_back(make_int2(0, 0));  // a valid (unused) upload
     int dev = 0, n_sm = 0, bps = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -1334,6 +1390,39 @@ static cudaError_t split_partition(ba_problem *p) {
             acc += (double)(twp[i + 1] - twp[i]) + ROW_COST;
             while (c < G && acc >= total * c / G) rows[c++] = i + 1;
         }
+        // A CTA's passes are shared round-robin by its warps, so the slowest
+        // warp of a CTA with 16k + 1 passes takes k + 1: cap every CTA at the
+        // fewest whole rounds of passes a contiguous partition allows (the
+        // greedy count decides) and move boundary rows off the CTAs above it.
+        {
+            const int64_t round = 32LL * SPLIT_WARPS;
+            auto fits = [&](int64_t cap) {
+                int cnt = 1;
+                int64_t cur = 0;
+                for (int i = 0; i < n; ++i) {
+                    const int64_t r = twp[i + 1] - twp[i];
+                    if (r > cap) return false;
+                    if (cur + r > cap) {
+                        ++cnt;
+                        cur = 0;
+                    }
+                    cur += r;
+                }
+                return cnt <= G;
+            };
+            int64_t cap = std::max<int64_t>(1, (E + round * G - 1) / (round * G)) * round;
+            while (cap < E && !fits(cap)) cap += round;
+            auto ent = [&](int k) { return (int64_t)twp[rows[k + 1]] - twp[rows[k]]; };
+            for (int sweep = 0; sweep < 4; ++sweep) {
+                bool over = false;
+                for (int k = 0; k + 1 < G; ++k)  // forward: last rows to the next CTA
+                    while (ent(k) > cap && rows[k + 1] > rows[k] + 1) --rows[k + 1];
+                for (int k = G - 1; k > 0; --k)  // backward: first rows to the previous CTA
+                    while (ent(k) > cap && rows[k] < rows[k + 1] - 1) ++rows[k];
+                for (int k = 0; k < G; ++k) over = over || ent(k) > cap;
+                if (!over) break;
+            }
+        }
         // halos
         hptr.assign(G + 1, 0);
         hcol.clear();
@@ -1344,6 +1433,7 @@ static cudaError_t split_partition(ba_problem *p) {
         for (int k = 0; k < G; ++k) {
             cols.clear();
             for (int64_t t = twp[rows[k]]; t < twp[rows[k + 1]]; ++t) cols.push_back(twe[t].y);
+            for (int i = rows[k]; i < rows[k + 1]; ++i) cols.push_back(i);  // own rows (their diagonal products)
             std::sort(cols.begin(), cols.end());
             cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
             obase[k] = (int32_t)(std::lower_bound(cols.begin(), cols.end(), rows[k]) - cols.begin());
@@ -1382,6 +1472,8 @@ static cudaError_t split_partition(ba_problem *p) {
             }
     }
     std::vector<std::pair<void **, std::pair<const void *, size_t>>> up = {
+        {(void **)&p->tws_ptr, {twp.data(), twp.size() * sizeof(int32_t)}},
+        {(void **)&p->tws_ent, {twe.data(), twe.size() * sizeof(int2)}},
         {(void **)&p->cta_rows, {rows.data(), rows.size() * sizeof(int32_t)}},
         {(void **)&p->tw_meta, {meta.data(), meta.size() * sizeof(uint32_t)}},
         {(void **)&p->meta_off, {moff.data(), moff.size() * sizeof(int32_t)}},
@@ -1440,11 +1532,12 @@ cudaError_t launch_pcg_split(ba_problem *p) {
     p->test_wait_limit = 0;
     e = cudaMemsetAsync(p->ar_bar, test_limit > 0 ? 0xFF : 0, AR_SUB * 32 * sizeof(unsigned), p->st);
     if (e == cudaSuccess) {
-        const int *cr = p->cta_rows, *twp = p->tw_ptr, *mo = p->meta_off, *hp = p->halo_ptr, *hc = p->halo_col,
+        const int *cr = p->cta_rows, *twp = p->tws_ptr, *mo = p->meta_off, *hp = p->halo_ptr, *hc = p->halo_col,
                   *ob = p->own_base;
         const uint32_t *meta = p->tw_meta;
         int sf = p->split_slot_floats;
-        const float *Sh = p->Sh, *H = p->Hs;
+        const float *Sh = p->Sh, *H = p->Hs, *Shd = p->Shd;
+        int ident = p->minv_learned ? 0 : 1;
         float **v = (float **)p->sv.pv;
         float *x = v[0], *pp = v[2];
         float *rec0 = p->srec, *rec1 = p->srec + (size_t)SREC * p->n;
@@ -1452,8 +1545,8 @@ cudaError_t launch_pcg_split(ba_problem *p) {
         double *red = p->red;
         unsigned *bar = p->ar_bar;
         long long limit = test_limit > 0 ? test_limit : 4000000000LL;  // ~2 s of SM clock per wait
-        void *args[] = {&cr, &twp, &meta, &mo, &hp, &hc, &ob, &sf, &Sh, &H, &x, &pp, &rec0, &rec1, &sc, &red, &bar,
-                        &limit};
+        void *args[] = {&cr, &twp, &meta, &mo, &hp, &hc, &ob, &sf, &Sh, &H, &Shd, &ident, &x, &pp, &rec0, &rec1, &sc,
+                        &red, &bar, &limit};
         e = cudaLaunchCooperativeKernel((const void *)k_pcg_split, dim3(p->split_grid), dim3(SPLIT_WARPS * 32), args,
                                         p->split_smem, p->st);
     }

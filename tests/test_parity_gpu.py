@@ -256,6 +256,25 @@ def test_paper_tolerance_stops_early(B):
     assert conv and info["pcg_iters"] == res.iters
 
 
+def test_fp32_paper_tolerance_follows_oracle(B):
+    """FP32 split CG in FP64 refinement at the paper's T = 0.1: one sweep, and
+    the PCG stops where the FP64 oracle's block-Jacobi PCG stops (within one
+    iteration: the two stop tests see the same residual in two precisions)."""
+    s = scenes.aerial_small(n_along=12, n_across=8, pts_per_cam=150, seed=57)
+    pb = _oracle(s, tol=0.1)
+    e, Jc, Jp = pb.linearize(s.cams0, s.pts0)
+    for lam in (1e-4, 1e-6):
+        g = _gpu(B, s, precision=B.BA_FP32, pcg_rel_tol=0.1)
+        g.linearize()
+        g.form_rcs(lam)
+        info, conv = g.solve_rcs()
+        _, A, b = pb.rcs(e, Jc, Jp, lam)
+        res = pb.solve(A, b)
+        assert conv and info["refine_steps"] == 1 and info["rcs_rel_resid"] <= 0.1
+        assert abs(info["pcg_iters"] - res.iters) <= 1, (lam, info["pcg_iters"], res.iters)
+        g.close()
+
+
 # ----------------------------------------------------------------------------- LM
 
 def test_lm_trajectory_fp64_ring50(B):
@@ -435,3 +454,10 @@ def test_aerial5k_full_size_sampled_blocks(B, prec, tol):
     info = g.lm_step()
     assert info["accepted"] == 1 and info["cost_trial"] < info["cost_before"]
     assert info["rcs_rel_resid"] <= 0.1
+    # the cost at full size: before the step and at the state it moved to
+    pb = _oracle(s)
+    F0 = pb.cost(s.cams0, s.pts0)
+    assert abs(info["cost_before"] - F0) <= 1e-6 * F0, (info["cost_before"], F0)
+    _, _, F1 = g.lm_state()
+    Fr = pb.cost(g.cameras(), g.points())
+    assert abs(F1 - Fr) <= 1e-6 * Fr, (F1, Fr)
