@@ -298,7 +298,7 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     // planned device bytes (checked against the cap before any allocation)
     const size_t camc_w = p->fp32 ? CAMC32_W * 4 : 12 * 8;
     size_t plan = 2 * (n * 6 * 8 + P * 3 * 8 + n * camc_w + (p->fp32 ? P * 6 * 4 : 0)) +
-                  m * 4 * 2 + (P + 1) * 4 + m * 16 + (p->fp32 ? m * 8 : 0) + m * JW * E + (n + 1) * 4 +
+                  m * 4 * 2 + (P + 1) * 4 + m * 16 + (p->fp32 ? m * 16 : 0) + m * JW * E + (n + 1) * 4 +
                   p->nnzb * 4 + 2 * (n + 1) * 4 + 2 * p->nnzb * 4 + (2 * p->nnzb - n) * 8 + p->nnzb * BW * E + n * 6 * E + n * 36 * E + p->ngroups * sizeof(GroupDesc) +
                   p->nitems * 8 + hs.contrib.size() * 4 + (p->nnzb + 1) * 4 + p->npart * 4 + p->npart * BW * E +
                   P * 9 * E + 8 * n * 6 * E + 3 * n * 6 * 8 + n * 6 * E + P * 3 * E + sizeof(DevScalars) +
@@ -341,6 +341,7 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
     AL(p->trk_ptr, P + 1);
     AL(p->uv64, m * 2);
     if (p->fp32) AL(p->uv32, m * 2);
+    if (p->fp32) AL(p->uv_lo, m * 2);
     ALR(p->J, m * JW * E);
     AL(p->row_ptr, n + 1);
     AL(p->col, p->nnzb);
@@ -398,6 +399,8 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
         std::vector<float> t32(m * 2);
         for (int64_t x = 0; x < m * 2; ++x) t32[x] = (float)tmp[x];
         up_ok(upload(p, p->uv32, t32.data(), m * 2));
+        for (int64_t x = 0; x < m * 2; ++x) t32[x] = (float)(tmp[x] - (double)t32[x]);
+        up_ok(upload(p, p->uv_lo, t32.data(), m * 2));
     }
     up_ok(upload(p, p->row_ptr, hs.row_ptr.data(), n + 1));
     up_ok(upload(p, p->col, hs.col.data(), p->nnzb));

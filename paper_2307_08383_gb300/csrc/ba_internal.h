@@ -140,6 +140,7 @@ struct ba_problem {
     int32_t *obs_cam = nullptr, *obs_pt = nullptr, *trk_ptr = nullptr;
     double *uv64 = nullptr;
     float *uv32 = nullptr;
+    float *uv_lo = nullptr;   // FP32 mode: uv - uv32 (the observations' lo parts for the double-float cost)
     void *J = nullptr;
     int32_t *row_ptr = nullptr, *col = nullptr;
     int32_t *ct_ptr = nullptr, *ct_blk = nullptr, *ct_row = nullptr;

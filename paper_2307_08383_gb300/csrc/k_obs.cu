@@ -110,15 +110,38 @@ __device__ __forceinline__ T huber_rho(T s, int on, T delta) {
 }
 
 // ||e||^2 of observation a (camera i, point given by its hi + lo parts) in
-// double-float arithmetic: X - C, the rotation with R = R_hi + R_lo, the two
-// quotients and the intrinsics each to ~2^-44 relative; e itself is then
-// formed and squared in FP64 against the FP64 observation.  behind: z <= 1e-6.
-__device__ __forceinline__ df32 df_of(double x) {
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
+// double-float arithmetic on the FP32 pipe: X - C, the rotation with
+// R = R_hi + R_lo, the quotients, the intrinsics and e against the
+// observation's hi + lo parts, each to ~2^-44 relative.  behind: z <= 1e-6.
+struct IntrDF {
+    float fxh, fxl, fyh, fyl, cxh, cxl, cyh, cyl;
+};
+__device__ __forceinline__ df32 two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
 }
-__device__ __forceinline__ double sq_resid_df(const float *__restrict__ camc, int i, const float *hl, const Intr &in,
-                                              const double *__restrict__ uv64, int64_t a, bool &behind) {
+// sum_k (ah_k + al_k)(bh_k + bl_k) for k = 0..2: exact leading products and
+// their sums, first-order cross terms
+__device__ __forceinline__ df32 df_dot3(const float *ah, const float *al, const df32 *b) {
+    float p[3], lo = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = ah[k] * b[k].hi;
+        lo += __fmaf_rn(ah[k], b[k].hi, -p[k]);
+        lo = __fmaf_rn(ah[k], b[k].lo, __fmaf_rn(al[k], b[k].hi, lo));
+    }
+    const df32 s1 = two_sum(p[0], p[1]);
+    const df32 s2 = two_sum(s1.hi, p[2]);
+    return df_fast_norm(s2.hi, s2.lo + s1.lo + lo);
+}
+__device__ __forceinline__ df32 df_rcp(df32 b) {
+    const float q1 = __frcp_rn(b.hi);
+    float r = __fmaf_rn(-q1, b.hi, 1.0f);  // exact
+    r = __fmaf_rn(-q1, b.lo, r);
+    return df_fast_norm(q1, r * q1);
+}
+__device__ __forceinline__ df32 sq_resid_df(const float *__restrict__ camc, int i, const float *hl,
+                                            const IntrDF &in, float uh, float ul, float vh, float vl, bool &behind) {
     const float4 *c4 = reinterpret_cast<const float4 *>(camc + CAMC32_W * i);
     const float4 c0 = c4[0], c1 = c4[1], c2 = c4[2], c3 = c4[3], c5 = c4[4], c6 = c4[5], c7 = c4[6];
     const float Rh[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
@@ -126,20 +149,27 @@ __device__ __forceinline__ double sq_resid_df(const float *__restrict__ camc, in
     const float Ch[3] = {c2.y, c2.z, c2.w}, Cl[3] = {c3.x, c3.y, c3.z};
     df32 D[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) D[r] = df_add(df32{hl[r], hl[3 + r]}, df32{-Ch[r], -Cl[r]});
-    df32 X[3];
-#pragma unroll
     for (int r = 0; r < 3; ++r) {
-        df32 acc = df_mul(df32{Rh[3 * r], Rl[3 * r]}, D[0]);
-        acc = df_add(acc, df_mul(df32{Rh[3 * r + 1], Rl[3 * r + 1]}, D[1]));
-        X[r] = df_add(acc, df_mul(df32{Rh[3 * r + 2], Rl[3 * r + 2]}, D[2]));
+        const df32 t = two_sum(hl[r], -Ch[r]);
+        D[r] = df_fast_norm(t.hi, t.lo + (hl[3 + r] - Cl[r]));
     }
-    behind = X[2].hi <= 1e-6f;
-    const df32 u = df_add(df_mul(df_of(in.fx), df_div(X[0], X[2])), df_of(in.cx));
-    const df32 v = df_add(df_mul(df_of(in.fy), df_div(X[1], X[2])), df_of(in.cy));
-    const double e0 = ((double)u.hi - uv64[2 * a]) + (double)u.lo;
-    const double e1 = ((double)v.hi - uv64[2 * a + 1]) + (double)v.lo;
-    return e0 * e0 + e1 * e1;
+    const df32 X0 = df_dot3(Rh, Rl, D), X1 = df_dot3(Rh + 3, Rl + 3, D), X2 = df_dot3(Rh + 6, Rl + 6, D);
+    behind = X2.hi <= 1e-6f;
+    const df32 iz = df_rcp(X2);
+    const df32 u = df_add(df_mul(df32{in.fxh, in.fxl}, df_mul(X0, iz)), df32{in.cxh, in.cxl});
+    const df32 v = df_add(df_mul(df32{in.fyh, in.fyl}, df_mul(X1, iz)), df32{in.cyh, in.cyl});
+    const df32 e0 = df_add(u, df32{-uh, -ul}), e1 = df_add(v, df32{-vh, -vl});
+    // e0^2 + e1^2: exact squares of the leading parts, first-order cross terms
+    const float p0 = e0.hi * e0.hi, p1 = e1.hi * e1.hi;
+    const float l0 = __fmaf_rn(e0.hi, e0.hi, -p0) + 2.f * e0.hi * e0.lo;
+    const float l1 = __fmaf_rn(e1.hi, e1.hi, -p1) + 2.f * e1.hi * e1.lo;
+    const df32 s = two_sum(p0, p1);
+    return df_fast_norm(s.hi, s.lo + l0 + l1);
+}
+// rho(||e||^2) in FP64 from its double-float value (Huber only where it bends)
+__device__ __forceinline__ double rho_df(df32 s, int huber, double delta) {
+    const double sd = (double)s.hi + (double)s.lo;
+    return huber_rho<double>(sd, huber, delta);
 }
 
 // --------------------------------------------------------------------------
@@ -211,15 +241,16 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
                                               const T *__restrict__ uv, const T *__restrict__ camc,
                                               const double *__restrict__ pts, const float *__restrict__ pts_hl,
                                               Intr in, int huber, double delta, DevScalars *sc, int trial,
-                                              double *red, unsigned *ctr, const double *__restrict__ uv64) {
+                                              double *red, unsigned *ctr, const float *__restrict__ uv_lo, IntrDF idf) {
     RunSum<double> f;  // FP64 accumulation (FP64 terms; double-float residuals in FP32 mode)
     int ncheir = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
         const int i = obs_cam[a], k = obs_pt[a];
         if constexpr (sizeof(T) == 4) {
             bool behind;
-            const double s = sq_resid_df(camc, i, pts_hl + 6 * (int64_t)k, in, uv64, a, behind);
-            f.add(huber_rho<double>(s, huber, delta));
+            const df32 s = sq_resid_df(camc, i, pts_hl + 6 * (int64_t)k, idf, uv[2 * a], uv_lo[2 * a],
+                                       uv[2 * a + 1], uv_lo[2 * a + 1], behind);
+            f.add(rho_df(s, huber, delta));
             ncheir += behind ? 1 : 0;
         } else {
             T Xc[3], R[9];
@@ -325,7 +356,7 @@ constexpr int STEP_THREADS = 256;
 constexpr int STEP_OBS_PER_THREAD = (OBS_MAX_LIMIT + STEP_THREADS - 1) / STEP_THREADS;
 
 template <typename T>
-__global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *__restrict__ grp, int ngroups,
+__global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_groups(const GroupDesc *__restrict__ grp, int ngroups,
                                                      const int *__restrict__ trk_ptr, const int *__restrict__ obs_cam,
                                                      const int *__restrict__ obs_pt, const T *__restrict__ uv,
                                                      const T *__restrict__ J, const T *__restrict__ dxc,
@@ -334,7 +365,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *_
                                                      Intr in, int huber, double delta, T *__restrict__ dxp,
                                                      double *__restrict__ pts_trial, float *__restrict__ hl_trial,
                                                      DevScalars *sc, double *red, unsigned *ctr, int obs_max,
-                                                     long long limit, const double *__restrict__ uv64) {
+                                                     long long limit, const float *__restrict__ uv_lo, IntrDF idf) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ GroupDesc sdesc;
@@ -452,8 +483,9 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step_groups(const GroupDesc *_
             const int i = s_cam[al], pl = __ldg(obs_pt + a) - g.pt_begin;
             if constexpr (sizeof(T) == 4) {
                 bool behind;
-                const double s = sq_resid_df(camc_trial, i, s_hl + 6 * pl, in, uv64, a, behind);
-                f.add(huber_rho<double>(s, huber, delta));
+                const df32 s = sq_resid_df(camc_trial, i, s_hl + 6 * pl, idf, uv[2 * a], uv_lo[2 * a],
+                                           uv[2 * a + 1], uv_lo[2 * a + 1], behind);
+                f.add(rho_df(s, huber, delta));
                 ncheir += behind ? 1 : 0;
             } else {
                 T Xc[3];
@@ -664,6 +696,12 @@ static inline int grid_for(int64_t work, int threads, int cap) {
 static constexpr int GRID_CAP = 152 * 8;  // 152 SMs x 8 resident 256-thread CTAs
 
 static Intr intr_of(const ba_problem *p) { return Intr{p->opt.fx, p->opt.fy, p->opt.cx, p->opt.cy}; }
+static IntrDF intrdf_of(const ba_problem *p) {
+    auto hi = [](double x) { return (float)x; };
+    auto lo = [](double x) { return (float)(x - (double)(float)x); };
+    return IntrDF{hi(p->opt.fx), lo(p->opt.fx), hi(p->opt.fy), lo(p->opt.fy),
+                  hi(p->opt.cx), lo(p->opt.cx), hi(p->opt.cy), lo(p->opt.cy)};
+}
 
 // Points between the caller's order and the internal (Morton) one:
 // internal point k is the caller's point perm[k].
@@ -753,11 +791,11 @@ cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial) {
     if (p->fp32)
         k_cost<float><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv32, (const float *)s.camc, s.pts,
                                             s.pts_hl, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
-                                            p->red, p->counters + 0, p->uv64);
+                                            p->red, p->counters + 0, p->uv_lo, intrdf_of(p));
     else
         k_cost<double><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv64, (const double *)s.camc, s.pts,
                                              nullptr, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
-                                             p->red, p->counters + 0, p->uv64);
+                                             p->red, p->counters + 0, p->uv_lo, intrdf_of(p));
     ktimer_end(p, K_COST, ev);
     p->launches += 1;
     return cudaGetLastError();
@@ -800,7 +838,8 @@ static cudaError_t step_groups_T(ba_problem *p, long long limit) {
                                                                                         : (const void *)p->uv64),
         (const T *)p->J, (const T *)p->dxc, (const T *)p->Linv, (const T *)p->lp, p->cur.pts,
         (const T *)p->trial.camc, intr_of(p), hub, p->opt.huber_delta, (T *)p->dxp, p->trial.pts,
-        p->fp32 ? p->trial.pts_hl : nullptr, p->sc, p->red, p->counters + 1, p->obs_max, limit, p->uv64);
+        p->fp32 ? p->trial.pts_hl : nullptr, p->sc, p->red, p->counters + 1, p->obs_max, limit, p->uv_lo,
+        intrdf_of(p));
     return cudaGetLastError();
 }
 
