@@ -68,7 +68,7 @@ typedef struct {
     double pcg_rel_tol;      /* stop when ||b - S x|| / ||b|| <= tol (1e-10) */
     int32_t pcg_max_iters;   /* 0: max(1000, 6n) */
     double inner_rel_tol;    /* FP32 mode: tolerance of each inner FP32 PCG (1e-4); a sweep that
-                                needs less (0.99 * pcg_rel_tol / current rel. residual,
+                                needs less (pcg_rel_tol / current rel. residual,
                                 at most 0.5) asks for that instead */
     int32_t refine_max;      /* FP32 mode: outer refinement steps (20) */
     int32_t preconditioner;  /* BA_PC_BLOCK_JACOBI (only this value is accepted) */

@@ -684,12 +684,12 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
         if (split) CK(p, launch_split_prepare(p, p->minv_learned));
         // FP32 inner PCG + FP64 iterative refinement on r = b - S x.  Each
         // sweep asks its inner solve for inner_rel_tol, or for just the
-        // reduction still missing (0.99 tol / rho, rho = |r|/|b| now) when
-        // that is looser, so a loose tolerance such as the paper's T = 0.1
-        // stops where the FP64 PCG stops (the FP32 recurrence residual and
-        // the true one differ far less than the 1 % margin), and a last sweep
-        // that needs a factor of a few takes a few iterations rather than a
-        // full inner solve.
+        // reduction still missing (tol / rho, rho = |r|/|b| now) when that
+        // is looser, so a loose tolerance such as the paper's T = 0.1 stops
+        // where the FP64 PCG stops (the FP32 recurrence's residual norm, a
+        // double-float sum, and the true one differ by far less than the
+        // steps between iterations), and a last sweep that needs a factor of
+        // a few takes a few iterations rather than a full inner solve.
         // One host synchronisation per sweep: the first sweep always runs (r = b;
         // a zero b stops its PCG at once), and a sweep's PCG, accumulation and
         // residual are queued together and read back once.
@@ -702,7 +702,7 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
             }
             CK(p, launch_refine_rhs(p, p->sv.pv[1]));  // r buffer doubles as the rhs (copied by init)
             const double rho = first ? 1.0 : std::sqrt(p->sc_host->rr64 / p->sc_host->bb64);
-            const double inner = std::min(0.5, std::max(p->opt.inner_rel_tol, 0.99 * tol / rho));
+            const double inner = std::min(0.5, std::max(p->opt.inner_rel_tol, tol / rho));
             if (split) {
                 CK(p, launch_split_init(p, (const float *)p->sv.pv[1], inner, max_iters));
                 CK(p, launch_pcg_split(p));
