@@ -297,7 +297,7 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
 
     // planned device bytes (checked against the cap before any allocation)
     const size_t camc_w = p->fp32 ? CAMC32_W * 4 : 12 * 8;
-    size_t plan = 2 * (n * 6 * 8 + P * 3 * 8 + n * camc_w + (p->fp32 ? P * 6 * 4 : 0)) +
+    size_t plan = 2 * (n * 6 * 8 + P * 3 * 8 + n * camc_w + (p->fp32 ? P * 6 * 4 + m * 2 * 4 : 0)) +
                   m * 4 * 2 + (P + 1) * 4 + m * 16 + (p->fp32 ? m * 16 : 0) + m * JW * E + (n + 1) * 4 +
                   p->nnzb * 4 + 2 * (n + 1) * 4 + 2 * p->nnzb * 4 + (2 * p->nnzb - n) * 8 + p->nnzb * BW * E + n * 6 * E + n * 36 * E + p->ngroups * sizeof(GroupDesc) +
                   p->nitems * 8 + hs.contrib.size() * 4 + (p->nnzb + 1) * 4 + p->npart * 4 + p->npart * BW * E +
@@ -335,6 +335,7 @@ ba_status ba_problem_create(const ba_options *opt, int32_t n_cams, const double 
         AL(sb->pts, P * 3);
         ALR(sb->camc, n * camc_w);
         if (p->fp32) AL(sb->pts_hl, P * 6);
+        if (p->fp32) AL(sb->e, m * 2);
     }
     AL(p->obs_cam, m);
     AL(p->obs_pt, m);
@@ -571,6 +572,7 @@ static ba_status ensure_cost(ba_problem *p) {
     if (s) return s;
     p->F = p->sc_host->cost;
     p->have_F = true;
+    p->last_rel_decrease = INFINITY;  // a fresh state: the next trial cost is evaluated whole
     if (!std::isfinite(p->F)) return fail(BA_ERR_NONFINITE, "non-finite cost");
     return BA_OK;
 }
@@ -820,12 +822,18 @@ ba_status ba_lm_step(ba_problem *p, ba_step_info *info) {
     CK(p, cudaEventRecord(ev[3], p->st));
     CK(p, launch_trial_cameras(p));
     CK(p, cudaEventRecord(ev[4], p->st));
+    // FP32 mode: while accepted steps still change F by 1e-3 of it or more, the
+    // trial cost is evaluated whole (double-float residuals); after that, as
+    // F(x) plus its change formed from the step, accurate relative to the
+    // change itself (the gain ratio compares changes of 1e-7 of F and less)
+    p->step_diff = p->fp32 && p->last_rel_decrease < 1e-3;
     CK(p, launch_step_points(p));  // Eq. 5 + trial point + trial cost and model, one pass
     p->backsub = true;
     CK(p, cudaEventRecord(ev[5], p->st));
     if ((s = sync_scalars(p))) return s;
     if ((s = check_err_flag(p))) return s;
-    const double F1 = p->sc_host->cost_trial, pred = p->sc_host->model;
+    const double F1 = p->step_diff ? p->F + p->sc_host->cost_trial : p->sc_host->cost_trial;
+    const double pred = p->sc_host->model;
     const double rho = pred > 0 ? (p->F - F1) / pred : -INFINITY;
     const bool ok = pred > 0 && std::isfinite(F1) && rho > 1e-3;
     loc.cost_trial = F1;
@@ -837,6 +845,7 @@ ba_status ba_lm_step(ba_problem *p, ba_step_info *info) {
     loc.n_v_fp64 = (int64_t)p->sc_host->n_v64;
     if (ok) {
         std::swap(p->cur, p->trial);
+        p->last_rel_decrease = (p->F - F1) / p->F;
         p->F = F1;
         const double f = 1.0 - std::pow(2.0 * rho - 1.0, 3);
         p->lambda *= std::max(1.0 / 3.0, f);

@@ -107,6 +107,7 @@ struct StateBuf {
     double *pts = nullptr;    // P x 3  (internal point order)
     void *camc = nullptr;     // FP64: n x 12 [R, t]; FP32: n x 32 [R_hi, C_hi, C_lo, 0, R_lo, 0 x 7]
     float *pts_hl = nullptr;  // FP32 mode: P x 6 [X_hi, X_lo]
+    float *e = nullptr;       // FP32 mode: m x 2 residuals of the state (double-float arithmetic, rounded)
 };
 
 }  // namespace ba
@@ -175,6 +176,8 @@ struct ba_problem {
 
     double lambda = 1e-4, nu = 2.0, F = 0.0;
     bool have_F = false, linearized = false, rcs_formed = false, solved = false, backsub = false;
+    bool step_diff = false;              // this step's trial cost is F plus its change (FP32 mode)
+    double last_rel_decrease = INFINITY;  // (F - F') / F of the last accepted step
     bool dead = false;
     double rcs_lambda = 0.0;
     int last_pcg_iters = 0, last_refine = 0;

@@ -141,7 +141,8 @@ __device__ __forceinline__ df32 df_rcp(df32 b) {
     return df_fast_norm(q1, r * q1);
 }
 __device__ __forceinline__ df32 sq_resid_df(const float *__restrict__ camc, int i, const float *hl,
-                                            const IntrDF &in, float uh, float ul, float vh, float vl, bool &behind) {
+                                            const IntrDF &in, float uh, float ul, float vh, float vl, bool &behind,
+                                            float &e0o, float &e1o) {
     const float4 *c4 = reinterpret_cast<const float4 *>(camc + CAMC32_W * i);
     const float4 c0 = c4[0], c1 = c4[1], c2 = c4[2], c3 = c4[3], c5 = c4[4], c6 = c4[5], c7 = c4[6];
     const float Rh[9] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x};
@@ -159,6 +160,8 @@ __device__ __forceinline__ df32 sq_resid_df(const float *__restrict__ camc, int 
     const df32 u = df_add(df_mul(df32{in.fxh, in.fxl}, df_mul(X0, iz)), df32{in.cxh, in.cxl});
     const df32 v = df_add(df_mul(df32{in.fyh, in.fyl}, df_mul(X1, iz)), df32{in.cyh, in.cyl});
     const df32 e0 = df_add(u, df32{-uh, -ul}), e1 = df_add(v, df32{-vh, -vl});
+    e0o = e0.hi;
+    e1o = e1.hi;
     // e0^2 + e1^2: exact squares of the leading parts, first-order cross terms
     const float p0 = e0.hi * e0.hi, p1 = e1.hi * e1.hi;
     const float l0 = __fmaf_rn(e0.hi, e0.hi, -p0) + 2.f * e0.hi * e0.lo;
@@ -166,6 +169,54 @@ __device__ __forceinline__ df32 sq_resid_df(const float *__restrict__ camc, int 
     const df32 s = two_sum(p0, p1);
     return df_fast_norm(s.hi, s.lo + l0 + l1);
 }
+// rho(s') - rho(s) from s and the change ds = s' - s formed exactly (FP32):
+// the change is kept relative to itself where both lie on one branch.
+__device__ __forceinline__ float rho_change(float s, float ds, int huber, float dl) {
+    if (!huber) return ds;
+    const float s1 = s + ds, d2 = dl * dl;
+    if (s <= d2 && s1 <= d2) return ds;
+    if (s > d2 && s1 > d2) return 2.f * dl * ds / (sqrtf(s1) + sqrtf(s));
+    const float r0 = s <= d2 ? s : 2.f * dl * sqrtf(s) - d2;
+    const float r1 = s1 <= d2 ? s1 : 2.f * dl * sqrtf(s1) - d2;
+    return r1 - r0;
+}
+
+// The change de of the residual of observation (camera i, point) under the
+// LM step, formed from the step itself: X_cam' = Exp(dw)(X_cam + R dX) + dt
+// (the camera-frame update), so dX_cam = (Exp(dw) - I) v + R dX + dt with
+// v = X_cam + R dX, and de = f (dx z - x dz) / (z (z + dz)).  FP32 gives de
+// to ~1e-7 of itself, where two FP32 residual evaluations differ by ~1e-4 px
+// of rounding.  behind: z' <= 1e-6.
+__device__ __forceinline__ void resid_change(const float (&Xc)[3], const float (&R)[9], const float *dw6,
+                                             const float *dp, const IntrDF &in, float &du, float &dv,
+                                             bool &behind) {
+    float RdX[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) RdX[r] = R[3 * r] * dp[0] + R[3 * r + 1] * dp[1] + R[3 * r + 2] * dp[2];
+    const float w0 = dw6[0], w1 = dw6[1], w2 = dw6[2];
+    const float v0 = Xc[0] + RdX[0], v1 = Xc[1] + RdX[1], v2 = Xc[2] + RdX[2];
+    const float c0 = w1 * v2 - w2 * v1, c1 = w2 * v0 - w0 * v2, c2 = w0 * v1 - w1 * v0;
+    const float d0 = w1 * c2 - w2 * c1, d1 = w2 * c0 - w0 * c2, d2 = w0 * c1 - w1 * c0;
+    const float th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    float a, b;
+    if (th2 < 1e-8f) {
+        a = 1.f - th2 * (1.f / 6.f);
+        b = 0.5f - th2 * (1.f / 24.f);
+    } else {
+        const float th = sqrtf(th2), sh = sinf(0.5f * th);
+        a = sinf(th) / th;
+        b = 2.f * sh * sh / th2;
+    }
+    const float dX = a * c0 + b * d0 + RdX[0] + dw6[3];
+    const float dY = a * c1 + b * d1 + RdX[1] + dw6[4];
+    const float dZ = a * c2 + b * d2 + RdX[2] + dw6[5];
+    const float z1 = Xc[2] + dZ;
+    behind = z1 <= 1e-6f;
+    const float q = 1.f / (Xc[2] * z1);
+    du = in.fxh * (dX * Xc[2] - Xc[0] * dZ) * q;
+    dv = in.fyh * (dY * Xc[2] - Xc[1] * dZ) * q;
+}
+
 // rho(||e||^2) in FP64 from its double-float value (Huber only where it bends)
 __device__ __forceinline__ double rho_df(df32 s, int huber, double delta) {
     const double sd = (double)s.hi + (double)s.lo;
@@ -241,17 +292,21 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
                                               const T *__restrict__ uv, const T *__restrict__ camc,
                                               const double *__restrict__ pts, const float *__restrict__ pts_hl,
                                               Intr in, int huber, double delta, DevScalars *sc, int trial,
-                                              double *red, unsigned *ctr, const float *__restrict__ uv_lo, IntrDF idf) {
+                                              double *red, unsigned *ctr, const float *__restrict__ uv_lo, IntrDF idf,
+                                              float *__restrict__ e_out) {
     RunSum<double> f;  // FP64 accumulation (FP64 terms; double-float residuals in FP32 mode)
     int ncheir = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
         const int i = obs_cam[a], k = obs_pt[a];
         if constexpr (sizeof(T) == 4) {
             bool behind;
+            float e0, e1;
             const df32 s = sq_resid_df(camc, i, pts_hl + 6 * (int64_t)k, idf, uv[2 * a], uv_lo[2 * a],
-                                       uv[2 * a + 1], uv_lo[2 * a + 1], behind);
+                                       uv[2 * a + 1], uv_lo[2 * a + 1], behind, e0, e1);
             f.add(rho_df(s, huber, delta));
             ncheir += behind ? 1 : 0;
+            e_out[2 * a] = e0;
+            e_out[2 * a + 1] = e1;
         } else {
             T Xc[3], R[9];
             cam_point(camc, pts, pts_hl, i, k, Xc, R);
@@ -365,7 +420,10 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
                                                      Intr in, int huber, double delta, T *__restrict__ dxp,
                                                      double *__restrict__ pts_trial, float *__restrict__ hl_trial,
                                                      DevScalars *sc, double *red, unsigned *ctr, int obs_max,
-                                                     long long limit, const float *__restrict__ uv_lo, IntrDF idf) {
+                                                     long long limit, const float *__restrict__ uv_lo, IntrDF idf,
+                                                     const float *__restrict__ camc_cur,
+                                                     const float *__restrict__ hl_cur, int diff,
+                                                     const float *__restrict__ e_cur, float *__restrict__ e_trial) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ GroupDesc sdesc;
@@ -483,9 +541,24 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
             const int i = s_cam[al], pl = __ldg(obs_pt + a) - g.pt_begin;
             if constexpr (sizeof(T) == 4) {
                 bool behind;
-                const df32 s = sq_resid_df(camc_trial, i, s_hl + 6 * pl, idf, uv[2 * a], uv_lo[2 * a],
-                                           uv[2 * a + 1], uv_lo[2 * a + 1], behind);
-                f.add(rho_df(s, huber, delta));
+                if (diff) {
+                    // the change of rho from the step and the state's residual
+                    float Xc[3], R[9], du, dv;
+                    cam_point(camc_cur, nullptr, hl_cur, i, g.pt_begin + pl, Xc, R);
+                    resid_change(Xc, R, dxc + 6 * i, s_dp + 3 * pl, idf, du, dv, behind);
+                    const float e0 = e_cur[2 * a], e1 = e_cur[2 * a + 1];
+                    const float ds = du * (2.f * e0 + du) + dv * (2.f * e1 + dv);
+                    f.add((double)rho_change(e0 * e0 + e1 * e1, ds, huber, dl));
+                    e_trial[2 * a] = e0 + du;
+                    e_trial[2 * a + 1] = e1 + dv;
+                } else {
+                    float e0, e1;
+                    const df32 s = sq_resid_df(camc_trial, i, s_hl + 6 * pl, idf, uv[2 * a], uv_lo[2 * a],
+                                               uv[2 * a + 1], uv_lo[2 * a + 1], behind, e0, e1);
+                    f.add(rho_df(s, huber, delta));
+                    e_trial[2 * a] = e0;
+                    e_trial[2 * a + 1] = e1;
+                }
                 ncheir += behind ? 1 : 0;
             } else {
                 T Xc[3];
@@ -791,11 +864,11 @@ cudaError_t launch_cost(ba_problem *p, StateBuf &s, bool trial) {
     if (p->fp32)
         k_cost<float><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv32, (const float *)s.camc, s.pts,
                                             s.pts_hl, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
-                                            p->red, p->counters + 0, p->uv_lo, intrdf_of(p));
+                                            p->red, p->counters + 0, p->uv_lo, intrdf_of(p), s.e);
     else
         k_cost<double><<<g, 256, 0, p->st>>>(p->m, p->obs_cam, p->obs_pt, p->uv64, (const double *)s.camc, s.pts,
                                              nullptr, intr_of(p), hub, p->opt.huber_delta, p->sc, trial ? 1 : 0,
-                                             p->red, p->counters + 0, p->uv_lo, intrdf_of(p));
+                                             p->red, p->counters + 0, p->uv_lo, intrdf_of(p), s.e);
     ktimer_end(p, K_COST, ev);
     p->launches += 1;
     return cudaGetLastError();
@@ -839,7 +912,8 @@ static cudaError_t step_groups_T(ba_problem *p, long long limit) {
         (const T *)p->J, (const T *)p->dxc, (const T *)p->Linv, (const T *)p->lp, p->cur.pts,
         (const T *)p->trial.camc, intr_of(p), hub, p->opt.huber_delta, (T *)p->dxp, p->trial.pts,
         p->fp32 ? p->trial.pts_hl : nullptr, p->sc, p->red, p->counters + 1, p->obs_max, limit, p->uv_lo,
-        intrdf_of(p));
+        intrdf_of(p), p->fp32 ? (const float *)p->cur.camc : nullptr, p->fp32 ? p->cur.pts_hl : nullptr,
+        p->step_diff ? 1 : 0, p->cur.e, p->trial.e);
     return cudaGetLastError();
 }
 

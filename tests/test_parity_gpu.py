@@ -319,20 +319,28 @@ def test_lm_fp32_aerial_against_fp64_oracle(B):
 @pytest.mark.parametrize("huber", [False, True])
 def test_fp32_cost_is_the_fp64_cost(B, huber):
     """FP32 mode evaluates F with double-float residuals against the FP64
-    observations: at the initial state and at an accepted trial state it is
-    the oracle's FP64 cost to 1e-12 (FP32 residuals were ~1e-8 off, more than
-    an LM step changes F near convergence)."""
+    observations: at the initial state it is the oracle's FP64 cost to 1e-12
+    (FP32 residuals were ~1e-8 off, more than an LM step changes F near
+    convergence).  A trial cost is either evaluated whole (to 1e-12) or, once
+    steps change F by less than 1e-3 of it, as F plus the change formed from
+    the step (to 1e-6 of the change)."""
     s = scenes.aerial_small(n_along=10, n_across=6, pts_per_cam=100, seed=58, outlier_frac=0.01 if huber else 0.0)
     kw = dict(robust=B.BA_LOSS_HUBER, huber_delta=2.0) if huber else {}
     g = _gpu(B, s, precision=B.BA_FP32, pcg_rel_tol=1e-6, **kw)
     pb = _oracle(s, delta=2.0 if huber else None)
     F0 = pb.cost(s.cams0, s.pts0)
     assert abs(g.lm_state()[2] - F0) <= 1e-12 * F0, (g.lm_state()[2], F0)
-    for _ in range(3):
+    n_small = 0
+    for _ in range(12):
         info = g.lm_step()
         if info["accepted"]:
             Fr = pb.cost(g.cameras(), g.points())
-            assert abs(info["cost_trial"] - Fr) <= 1e-12 * Fr, (info["cost_trial"], Fr)
+            change = abs(info["cost_before"] - Fr)
+            assert abs(info["cost_trial"] - Fr) <= 1e-12 * Fr + 1e-6 * change, (info["cost_trial"], Fr, change)
+            n_small += change < 1e-3 * Fr
+            if n_small >= 2:
+                break
+    assert n_small >= 2
 
 
 def test_lm_fp32_follows_the_oracle_at_the_paper_tolerance(B):
