@@ -217,11 +217,23 @@ __device__ __forceinline__ void resid_change(const float (&Xc)[3], const float (
     dv = in.fyh * (dY * Xc[2] - Xc[1] * dZ) * q;
 }
 
-// rho(||e||^2) in FP64 from its double-float value (Huber only where it bends)
-__device__ __forceinline__ double rho_df(df32 s, int huber, double delta) {
-    const double sd = (double)s.hi + (double)s.lo;
-    return huber_rho<double>(sd, huber, delta);
-}
+// An FP64 sum of rho(||e||^2) over double-float values of ||e||^2: the
+// leading parts are added in FP64, the trailing parts (below the leading
+// part's last bit, so their FP32 sum is exact to ~2^-24 of a quantity already
+// 2^-24 of the total) in FP32 beside it; Huber's bent branch in FP64.
+struct RhoSum {
+    double s = 0.0;
+    float lo = 0.f;
+    __device__ __forceinline__ void add(df32 q, int huber, double delta) {
+        if (huber && q.hi > (float)(delta * delta)) {
+            s += huber_rho<double>((double)q.hi + (double)q.lo, 1, delta);
+        } else {
+            s += (double)q.hi;
+            lo += q.lo;
+        }
+    }
+    __device__ __forceinline__ double get() const { return s + (double)lo; }
+};
 
 // --------------------------------------------------------------------------
 // K1: residuals and Jacobians, one thread per observation
@@ -295,6 +307,7 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
                                               double *red, unsigned *ctr, const float *__restrict__ uv_lo, IntrDF idf,
                                               float *__restrict__ e_out) {
     RunSum<double> f;  // FP64 accumulation (FP64 terms; double-float residuals in FP32 mode)
+    RhoSum fdf;
     int ncheir = 0;
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
         const int i = obs_cam[a], k = obs_pt[a];
@@ -303,7 +316,7 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
             float e0, e1;
             const df32 s = sq_resid_df(camc, i, pts_hl + 6 * (int64_t)k, idf, uv[2 * a], uv_lo[2 * a],
                                        uv[2 * a + 1], uv_lo[2 * a + 1], behind, e0, e1);
-            f.add(rho_df(s, huber, delta));
+            fdf.add(s, huber, delta);
             ncheir += behind ? 1 : 0;
             e_out[2 * a] = e0;
             e_out[2 * a + 1] = e1;
@@ -317,7 +330,7 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
             ncheir += (Xc[2] <= T(1e-6)) ? 1 : 0;
         }
     }
-    double v[2] = {f.get(), (double)ncheir};
+    double v[2] = {f.get() + fdf.get(), (double)ncheir};
     grid_sum<2>(v, red, ctr, [&](double *t) {
         if (trial) {
             sc->cost_trial = 0.5 * t[0];
@@ -458,6 +471,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
         bulk_g2s(smem_raw, J + (int64_t)d.obs_begin * JW, jb, &mbar);
     };
     RunSum<double> f, mdl;  // FP64 accumulation of the gain ratio's sums (terms formed in T)
+    RhoSum fdf;
     int ncheir = 0;
     const T dl = (T)delta;
     uint32_t parity = 0u;
@@ -555,7 +569,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
                     float e0, e1;
                     const df32 s = sq_resid_df(camc_trial, i, s_hl + 6 * pl, idf, uv[2 * a], uv_lo[2 * a],
                                                uv[2 * a + 1], uv_lo[2 * a + 1], behind, e0, e1);
-                    f.add(rho_df(s, huber, delta));
+                    fdf.add(s, huber, delta);
                     e_trial[2 * a] = e0;
                     e_trial[2 * a + 1] = e1;
                 }
@@ -581,7 +595,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
         // the per-point and per-observation areas are rewritten only after the
         // barrier that follows the next group's copy wait
     }
-    double v[3] = {f.get(), mdl.get(), (double)ncheir};
+    double v[3] = {f.get() + fdf.get(), mdl.get(), (double)ncheir};
     grid_sum<3>(v, red, ctr, [&](double *t) {
         sc->cost_trial = 0.5 * t[0];
         sc->model = 0.5 * t[1];
