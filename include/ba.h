@@ -69,7 +69,7 @@ typedef struct {
     int32_t pcg_max_iters;   /* 0: max(1000, 6n) */
     double inner_rel_tol;    /* FP32 mode: tolerance of each inner FP32 PCG (1e-4); a sweep that
                                 needs less (pcg_rel_tol / current rel. residual,
-                                at most 0.5) asks for that instead */
+                                at most 0.9) asks for that instead */
     int32_t refine_max;      /* FP32 mode: outer refinement steps (20) */
     int32_t preconditioner;  /* BA_PC_BLOCK_JACOBI (only this value is accepted) */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = legacy default stream */

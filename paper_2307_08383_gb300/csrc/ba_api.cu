@@ -691,7 +691,10 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
         // where the FP64 PCG stops (the FP32 recurrence's residual norm, a
         // double-float sum, and the true one differ by far less than the
         // steps between iterations), and a last sweep that needs a factor of
-        // a few takes a few iterations rather than a full inner solve.
+        // a few takes a few iterations rather than a full inner solve.  Each
+        // sweep asks for at least a 10 % reduction (at most 0.9): one that
+        // follows a first sweep ending just above T by the recurrence's
+        // residual gap then stops just below T too.
         // One host synchronisation per sweep: the first sweep always runs (r = b;
         // a zero b stops its PCG at once), and a sweep's PCG, accumulation and
         // residual are queued together and read back once.
@@ -704,7 +707,7 @@ static ba_status solve_once_view(ba_problem *p, ba_step_info *info) {
             }
             CK(p, launch_refine_rhs(p, p->sv.pv[1]));  // r buffer doubles as the rhs (copied by init)
             const double rho = first ? 1.0 : std::sqrt(p->sc_host->rr64 / p->sc_host->bb64);
-            const double inner = std::min(0.5, std::max(p->opt.inner_rel_tol, tol / rho));
+            const double inner = std::min(0.9, std::max(p->opt.inner_rel_tol, tol / rho));
             if (split) {
                 CK(p, launch_split_init(p, (const float *)p->sv.pv[1], inner, max_iters));
                 CK(p, launch_pcg_split(p));
