@@ -1,10 +1,14 @@
-"""What the trained block-Jacobi correction gains, measured on a held-out
-system, and the fallback to plain block-Jacobi when a learned M^-1 fails.
+"""The packaged block-Jacobi correction on a held-out system (no
+regression), and the fallback to plain block-Jacobi when a learned M^-1
+fails.
 
 The packaged weights were selected by validation PCG iterations with the
-zero output (plain block-Jacobi) among the candidates, so on held-out
-systems the learned solve must take no more than block-Jacobi's iterations
-(2 % slack for FP32 rounding of M^-1) and reach the same true residual."""
+zero output (plain block-Jacobi) among the candidates, and the zero output
+won: no trained epoch beat block-Jacobi, so the packaged correction gains
+nothing.  What is checked is that attaching it costs no iterations: on a
+held-out system the learned solve takes no more than block-Jacobi's
+iterations (2 % slack for FP32 rounding of M^-1) and reaches the same true
+residual.  The measured gain is printed."""
 import json
 
 import numpy as np
@@ -40,7 +44,7 @@ def _solve(B, rcs, net, **kw):
     return info, conv
 
 
-def test_trained_net_gain_on_a_held_out_system(held_out):
+def test_packaged_net_costs_no_iterations_on_a_held_out_system(held_out):
     B, rcs = held_out
     kw = dict(precision=B.BA_FP64, solve_precision=B.BA_FP32, inner_rel_tol=1e-4, pcg_rel_tol=1e-8,
               pcg_max_iters=50000)
