@@ -731,7 +731,7 @@ __device__ __forceinline__ bool split_passes(SplitPipe &pp, int rb, const int *_
         const int t = eb + 32 * q + lane;
         const bool valid = t < ee;
         const uint32_t b = pp.seq % SPLIT_NBUF;
-        // every lane observes the copy's completion; the verdict is warp-uniform
+        // every lane observes the copy's completion; the outcome is warp-uniform
         if (!__all_sync(0xffffffffu, mbar_wait(pp.mbar + SPLIT_NBUF * wid + b, (pp.seq / SPLIT_NBUF) & 1u, limit))) {
             if (lane == 0) atomicExch(err, (int)BA_ERR_TIMEOUT);
             return false;
