@@ -236,6 +236,11 @@ ba_status ba_get_stats(const ba_problem *p, ba_stats *out);
  * the number of launches and their summed device time since the last reset. */
 ba_status ba_get_kernel_time(ba_problem *p, int32_t k, int64_t *launches, double *total_ms);
 ba_status ba_reset_kernel_times(ba_problem *p);
+/* Sets options.profile of a live problem (0 none, 1 kernel times, 2 also the
+ * phase timers inside the PCG and the RCS formation), so that one problem can
+ * run untimed and then replay steps with its kernels timed; the times
+ * gathered so far are kept.  BA_ERR_INVALID_ARG for a level outside 0..2. */
+ba_status ba_set_profile(ba_problem *p, int32_t level);
 
 /* Test hook for the bounded device waits (not part of the method).  Every
  * grid-wide wait inside the library gives up after a limit of SM clock cycles

@@ -113,6 +113,7 @@ SIGNATURES = [
     ("ba_get_stats", _S, [_P, ctypes.POINTER(ba_stats)]),
     ("ba_get_kernel_time", _S, [_P, ctypes.c_int32, _I64, _D]),
     ("ba_reset_kernel_times", _S, [_P]),
+    ("ba_set_profile", _S, [_P, ctypes.c_int32]),
     ("ba_debug_arm_wait_timeout", _S, [_P, ctypes.c_int64]),
     ("ba_kernel_name", ctypes.c_char_p, [ctypes.c_int32]),
     ("ba_problem_destroy", None, [_P]),
@@ -356,6 +357,10 @@ def ba_reset_kernel_times(h):
     _check(lib().ba_reset_kernel_times(h))
 
 
+def ba_set_profile(h, level):
+    _check(lib().ba_set_profile(h, int(level)))
+
+
 def ba_problem_destroy(h):
     if h:
         lib().ba_problem_destroy(h)
@@ -481,6 +486,10 @@ class Problem:
 
     def reset_kernel_times(self):
         ba_reset_kernel_times(self.h)
+
+    def set_profile(self, level):
+        """0: no kernel timing, 1: kernel times, 2: also the PCG and RCS phase timers."""
+        ba_set_profile(self.h, level)
 
     def arm_wait_timeout(self, limit_cycles):
         """Test hook: the next PCG launch misses one arrival at its first

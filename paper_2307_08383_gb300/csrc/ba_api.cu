@@ -1097,4 +1097,13 @@ ba_status ba_reset_kernel_times(ba_problem *p) {
     return BA_OK;
 }
 
+ba_status ba_set_profile(ba_problem *p, int32_t level) {
+    LIVE(p);
+    if (level < 0 || level > 2) return fail(BA_ERR_INVALID_ARG, "profile level must be 0, 1 or 2");
+    ba_status s = ktimer_flush(p);  // collect the events of launches timed so far
+    if (s) return s;
+    p->opt.profile = level;
+    return BA_OK;
+}
+
 }  // extern "C"
