@@ -76,3 +76,20 @@ def test_arming_is_validated(B):
             g.arm_wait_timeout(bad)
         assert ei.value.status == B.BA_ERR_INVALID_ARG
     g.close()
+
+
+def test_profile_switch(B):
+    """Kernel timers switched on a live problem: none counted while off,
+    the launches of a step counted once on; levels outside 0..2 refused."""
+    s = scenes.ring_scene(n_cams=6, n_pts=60, seed=73)
+    g = B.Problem(s.cams0, s.pts0, s.obs_cam, s.obs_pt, s.obs_uv, profile=0)
+    g.lm_step()
+    assert sum(v[0] for v in g.kernel_times().values()) == 0
+    g.set_profile(1)
+    g.lm_step()
+    assert g.kernel_times()["form_rcs"][0] == 1
+    for bad in (-1, 3):
+        with pytest.raises(B.BAError) as ei:
+            g.set_profile(bad)
+        assert ei.value.status == B.BA_ERR_INVALID_ARG
+    g.close()
