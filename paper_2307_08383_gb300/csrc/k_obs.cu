@@ -309,18 +309,34 @@ __global__ void __launch_bounds__(256) k_cost(int64_t m, const int *__restrict__
     RunSum<double> f;  // FP64 accumulation (FP64 terms; double-float residuals in FP32 mode)
     RhoSum fdf;
     int ncheir = 0;
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if constexpr (sizeof(T) == 4) {
+        // two observations per pass, their double-float chains independent
+        for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < m; a += 2 * stride) {
+            const bool two = a + stride < m;
+            const int64_t b = two ? a + stride : a;
+            const int ia = obs_cam[a], ka = obs_pt[a], ib = obs_cam[b], kb = obs_pt[b];
+            bool behind_a, behind_b;
+            float ea0, ea1, eb0, eb1;
+            const df32 sa = sq_resid_df(camc, ia, pts_hl + 6 * (int64_t)ka, idf, uv[2 * a], uv_lo[2 * a],
+                                        uv[2 * a + 1], uv_lo[2 * a + 1], behind_a, ea0, ea1);
+            const df32 sb = sq_resid_df(camc, ib, pts_hl + 6 * (int64_t)kb, idf, uv[2 * b], uv_lo[2 * b],
+                                        uv[2 * b + 1], uv_lo[2 * b + 1], behind_b, eb0, eb1);
+            fdf.add(sa, huber, delta);
+            ncheir += behind_a ? 1 : 0;
+            e_out[2 * a] = ea0;
+            e_out[2 * a + 1] = ea1;
+            if (two) {
+                fdf.add(sb, huber, delta);
+                ncheir += behind_b ? 1 : 0;
+                e_out[2 * b] = eb0;
+                e_out[2 * b + 1] = eb1;
+            }
+        }
+    }
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sizeof(T) == 8 && a < m; a += stride) {
         const int i = obs_cam[a], k = obs_pt[a];
-        if constexpr (sizeof(T) == 4) {
-            bool behind;
-            float e0, e1;
-            const df32 s = sq_resid_df(camc, i, pts_hl + 6 * (int64_t)k, idf, uv[2 * a], uv_lo[2 * a],
-                                       uv[2 * a + 1], uv_lo[2 * a + 1], behind, e0, e1);
-            fdf.add(s, huber, delta);
-            ncheir += behind ? 1 : 0;
-            e_out[2 * a] = e0;
-            e_out[2 * a + 1] = e1;
-        } else {
+        {
             T Xc[3], R[9];
             cam_point(camc, pts, pts_hl, i, k, Xc, R);
             const T iz = T(1) / Xc[2];
