@@ -557,40 +557,54 @@ __global__ void __launch_bounds__(128) k_split_scale(int n, const int *__restric
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
-    const float *gi = G + 36 * (int64_t)i;
+    // G_i (the warp's row, the same for every lane) and each entry's G_j in
+    // registers, 16-byte loads; the products accumulate in the order of the
+    // plain loops (k ascending), row k of S_ij G_j at a time
+    float gi[36];
+    {
+        const float4 *g4 = reinterpret_cast<const float4 *>(G + 36 * (int64_t)i);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float4 v = __ldg(g4 + q);
+            gi[4 * q] = v.x; gi[4 * q + 1] = v.y; gi[4 * q + 2] = v.z; gi[4 * q + 3] = v.w;
+        }
+    }
     for (int t = __ldg(tw_ptr + i) + lane; t < __ldg(tw_ptr + i + 1); t += 32) {
         const int2 e = __ldg(tw_ent + t);
         const bool tr = e.x < 0;
         const TS *sb = S + (int64_t)(e.x & 0x7fffffff) * BW;
-        const float *gj = G + 36 * (int64_t)e.y;
-        float T1[36];  // S_ij G_j
+        float gj[36];
+        {
+            const float4 *g4 = reinterpret_cast<const float4 *>(G + 36 * (int64_t)e.y);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) {
-            float srow[6];
+            for (int q = 0; q < 9; ++q) {
+                const float4 v = __ldg(g4 + q);
+                gj[4 * q] = v.x; gj[4 * q + 1] = v.y; gj[4 * q + 2] = v.z; gj[4 * q + 3] = v.w;
+            }
+        }
+        float o[36];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) srow[k] = (float)(tr ? sb[6 * k + a] : sb[6 * a + k]);
+        for (int q = 0; q < 36; ++q) o[q] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float srow[6], t1[6];  // row k of S_ij, then of S_ij G_j
+#pragma unroll
+            for (int m = 0; m < 6; ++m) srow[m] = (float)(tr ? sb[6 * m + k] : sb[6 * k + m]);
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 float v = 0.f;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) v = __fmaf_rn(srow[k], __ldg(gj + 6 * k + c), v);
-                T1[6 * a + c] = v;
+                for (int m = 0; m < 6; ++m) v = __fmaf_rn(srow[m], gj[6 * m + c], v);
+                t1[c] = v;
             }
+#pragma unroll
+            for (int a = 0; a < 6; ++a)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) o[6 * a + c] = __fmaf_rn(gi[6 * k + a], t1[c], o[6 * a + c]);
         }
         float4 *o4 = reinterpret_cast<float4 *>(Sh + (int64_t)t * BW);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            float o[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int a = (4 * q + u) / 6, c = (4 * q + u) % 6;
-                float v = 0.f;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) v = __fmaf_rn(__ldg(gi + 6 * k + a), T1[6 * k + c], v);
-                o[u] = v;
-            }
-            o4[q] = make_float4(o[0], o[1], o[2], o[3]);
-        }
+        for (int q = 0; q < 9; ++q) o4[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
     }
 }
 
