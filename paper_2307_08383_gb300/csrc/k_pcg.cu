@@ -225,7 +225,13 @@ __global__ void __launch_bounds__(256) k_spmv_df(int n, const int *__restrict__ 
         for (int t = __ldg(tw_ptr + i) + lane; t < __ldg(tw_ptr + i + 1); t += 32) {
             const int2 e = __ldg(tw_ent + t);
             const bool tr = e.x < 0;
-            const float *sb = S + (int64_t)(e.x & 0x7fffffff) * BW;
+            const float4 *s4 = reinterpret_cast<const float4 *>(S + (int64_t)(e.x & 0x7fffffff) * BW);
+            float sb[36];  // the block, 16-byte loads
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const float4 v = __ldg(s4 + q);
+                sb[4 * q] = v.x; sb[4 * q + 1] = v.y; sb[4 * q + 2] = v.z; sb[4 * q + 3] = v.w;
+            }
             float xh[6], xl[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(256) k_spmv_df(int n, const int *__restrict__ 
             for (int r = 0; r < 6; ++r)
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
-                    const float sv = __ldg(sb + (tr ? 6 * c + r : 6 * r + c));
+                    const float sv = tr ? sb[6 * c + r] : sb[6 * r + c];
                     const float ph = sv * xh[c];
                     const float pl = __fmaf_rn(sv, xh[c], -ph) + sv * xl[c];
                     acc[r] = df_add(acc[r], df32{ph, pl});
