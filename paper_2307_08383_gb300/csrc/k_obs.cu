@@ -473,6 +473,8 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
     T *s_c3 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s_xt) + (sizeof(T) == 8 ? np * 24 : 0));
     T *s_jc = s_c3 + (size_t)obs_max * 3;
     int *s_cam = reinterpret_cast<int *>(s_jc + (size_t)obs_max * 2);
+    int *s_pl = s_cam + obs_max;                                   // each observation's point in the group
+    float *s_hlc = reinterpret_cast<float *>(s_pl + obs_max);     // FP32: each point's current X (hi, lo)
     if (threadIdx.x == 0) {
         mbar_init(&mbar, 1);
         fence_proxy_async();
@@ -514,6 +516,7 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
             const int al = threadIdx.x + k * STEP_THREADS;
             if (al >= g.nobs) break;
             const int i = __ldg(obs_cam + g.obs_begin + al);
+            s_pl[al] = __ldg(obs_pt + g.obs_begin + al) - g.pt_begin;
             const T *dc = dxc + 6 * i;
             T j[JW];
             load_jrow_s(so + al * JW, j);
@@ -557,6 +560,10 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
                 }
                 s_dp[3 * pl + d] = dp[d];
                 if (sizeof(T) == 8) s_xt[3 * pl + d] = x;
+                if (sizeof(T) == 4 && diff) {
+                    s_hlc[6 * pl + d] = hl_cur[6 * kp + d];
+                    s_hlc[6 * pl + 3 + d] = hl_cur[6 * kp + 3 + d];
+                }
                 s_hl[6 * pl + d] = h;
                 s_hl[6 * pl + 3 + d] = l;
             }
@@ -568,13 +575,13 @@ __global__ void __launch_bounds__(STEP_THREADS, sizeof(T) == 4 ? 3 : 1) k_step_g
             const int al = threadIdx.x + k * STEP_THREADS;
             if (al >= g.nobs) break;
             const int64_t a = (int64_t)g.obs_begin + al;
-            const int i = s_cam[al], pl = __ldg(obs_pt + a) - g.pt_begin;
+            const int i = s_cam[al], pl = s_pl[al];
             if constexpr (sizeof(T) == 4) {
                 bool behind;
                 if (diff) {
                     // the change of rho from the step and the state's residual
                     float Xc[3], R[9], du, dv;
-                    cam_point(camc_cur, nullptr, hl_cur, i, g.pt_begin + pl, Xc, R);
+                    cam_point(camc_cur, nullptr, s_hlc, i, pl, Xc, R);
                     resid_change(Xc, R, dxc + 6 * i, s_dp + 3 * pl, idf, du, dv, behind);
                     const float e0 = e_cur[2 * a], e1 = e_cur[2 * a + 1];
                     const float ds = du * (2.f * e0 + du) + dv * (2.f * e1 + dv);
@@ -926,7 +933,8 @@ template <typename T>
 static cudaError_t step_groups_T(ba_problem *p, long long limit) {
     const size_t smem = (size_t)p->obs_max * JW * sizeof(T) +
                         (size_t)p->obs_max / 2 * (3 * sizeof(T) + 6 * sizeof(float) + (sizeof(T) == 8 ? 24 : 0)) +
-                        (size_t)p->obs_max * (5 * sizeof(T) + sizeof(int));
+                        (size_t)p->obs_max * (5 * sizeof(T) + 2 * sizeof(int)) +
+                        (size_t)p->obs_max / 2 * 6 * sizeof(float);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_step_groups<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
