@@ -15,6 +15,11 @@
 // lo parts, against the FP64 observations: near convergence an LM step
 // changes F by less than FP32 residuals resolve (~1e-8 of F at 1M points),
 // and the accept/reject decision must follow the step, not the rounding.
+// Once accepted steps change F by less than 1e-3 of it, the trial cost is F
+// plus its change formed in FP32 from the step itself and the state's
+// residuals, which each state keeps from its last double-float evaluation
+// (updated by accepted steps); the change is then accurate relative to
+// itself.
 #include "device_util.cuh"
 #include "tma_util.cuh"
 
@@ -116,6 +121,7 @@ __device__ __forceinline__ T huber_rho(T s, int on, T delta) {
 struct IntrDF {
     float fxh, fxl, fyh, fyl, cxh, cxl, cyh, cyl;
 };
+// Knuth's TwoSum: s + e = a + b exactly
 __device__ __forceinline__ df32 two_sum(float a, float b) {
     const float s = a + b, bb = s - a;
     return {s, (a - (s - bb)) + (b - bb)};
