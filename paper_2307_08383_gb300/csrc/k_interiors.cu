@@ -203,7 +203,15 @@ __global__ void __launch_bounds__(256) k_vbi_blocks(int64_t nnzb, const int *__r
         const int ai = jc0 ? jc0[i] : 0, aj = jc0 ? jc0[j] : 0;
         const bool diag = i == j;
         T acc[VB_NT], dU[VB_NT], bacc = T(0);
-        for (int t = 0; t < VB_NT; ++t) acc[t] = dU[t] = T(0);
+        // this lane's entries (row, column) of the block, fixed for its pairs
+        int er[VB_NT], ec[VB_NT];
+#pragma unroll
+        for (int t = 0; t < VB_NT; ++t) {
+            acc[t] = dU[t] = T(0);
+            const int E = lane + 32 * t;
+            er[t] = E < nel ? E / cj : 0;
+            ec[t] = E < nel ? E - er[t] * cj : 0;
+        }
         for (int p = pptr[k]; p < pptr[k + 1]; ++p) {  // warp-uniform
             const int2 pr = plist[p];
             const bool same = pr.x == pr.y;
@@ -232,10 +240,10 @@ __global__ void __launch_bounds__(256) k_vbi_blocks(int64_t nnzb, const int *__r
                 }
             }
             __syncwarp();
+#pragma unroll
             for (int t = 0; t < VB_NT; ++t) {
-                const int E = lane + 32 * t;
-                if (E < nel) {
-                    const int r = E / cj, c = E - r * cj;
+                if (lane + 32 * t < nel) {
+                    const int r = er[t], c = ec[t];
                     acc[t] += Jca[r] * Tb[c] + Jca[16 + r] * Tb[16 + c];
                     if (diag && same && r == c) dU[t] += Jca[r] * Jca[r] + Jca[16 + r] * Jca[16 + r];
                 }
