@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_vbi_points(int64_t P, const int *__rest
 // beta.  On a diagonal block a slot paired with itself also gives b_beta's
 // term -J_c,a^T e^_a and the U diagonal that damps the block at the end.
 template <typename T>
-__global__ void __launch_bounds__(256) k_vbi_blocks(int64_t nnzb, const int *__restrict__ brow,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_vbi_blocks(int64_t nnzb, const int *__restrict__ brow,
                                                     const int *__restrict__ col, const int *__restrict__ cdim,
                                                     const int *__restrict__ jc0, const int *__restrict__ off,
                                                     const int64_t *__restrict__ boff,
