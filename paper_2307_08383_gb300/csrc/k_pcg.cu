@@ -1330,13 +1330,15 @@ cudaError_t launch_split_prepare(ba_problem *p, bool from_minv) {
     if (e != cudaSuccess) return e;
     cudaEvent_t ev;
     ktimer_begin(p, K_SPLIT_PREP, &ev);
-    const int nb = (p->n + 127) / 128, ns = (int)(((int64_t)p->n * 32 + 127) / 128);
+    // the factors: a thread per camera in FP64, 32 to a CTA so that the
+    // cameras spread over every SM's FP64 units; S^: a warp per block row
+    const int nb = (p->n + 31) / 32, ns = (int)(((int64_t)p->n * 32 + 127) / 128);
     if (p->fp32) {
-        k_split_factor<float><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const float *)p->S, (const float *)p->Minv,
+        k_split_factor<float><<<nb, 32, 0, p->st>>>(p->n, p->row_ptr, (const float *)p->S, (const float *)p->Minv,
                                                      from_minv ? 1 : 0, p->Gs, p->Hs, p->Shd, p->sc);
         k_split_scale<float><<<ns, 128, 0, p->st>>>(p->n, p->tws_ptr, p->tws_ent, (const float *)p->S, p->Gs, p->Sh);
     } else {
-        k_split_factor<double><<<nb, 128, 0, p->st>>>(p->n, p->row_ptr, (const double *)p->S,
+        k_split_factor<double><<<nb, 32, 0, p->st>>>(p->n, p->row_ptr, (const double *)p->S,
                                                       (const double *)p->Minv, from_minv ? 1 : 0, p->Gs, p->Hs,
                                                       p->Shd, p->sc);
         k_split_scale<double><<<ns, 128, 0, p->st>>>(p->n, p->tws_ptr, p->tws_ent, (const double *)p->S, p->Gs, p->Sh);
